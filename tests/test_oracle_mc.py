@@ -1,0 +1,205 @@
+"""Pins for the oracle's marching cubes (paper Sec. 2.2; Lorensen & Cline).
+
+Checks from outside the oracle: hand-derived single cells, closed oriented
+2-manifolds for all 256 cases and random grids, Euler characteristics of a
+sphere (2), two spheres (4) and a torus (0), exact planes, the enclosed volume
+of a sphere, and normals that point up the gradient."""
+import os
+from collections import Counter, deque
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2408_05462_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _mesh_topology(mesh):
+    """(V, E, F, directed-edge multiset) with vertices identified by edge id."""
+    tri = mesh.edge_id
+    directed = Counter()
+    for a, b, c in tri:
+        for u, v in ((a, b), (b, c), (c, a)):
+            directed[(int(u), int(v))] += 1
+    V = len(np.unique(tri))
+    E = len({(min(u, v), max(u, v)) for (u, v) in directed})
+    return V, E, tri.shape[0], directed
+
+
+def _assert_closed_oriented(mesh):
+    _, _, _, directed = _mesh_topology(mesh)
+    for (u, v), n in directed.items():
+        assert n == 1, f"directed edge {(u, v)} used {n} times"
+        assert directed.get((v, u), 0) == 1, f"edge {(u, v)} has no opposite partner"
+
+
+def _euler(mesh):
+    V, E, F, _ = _mesh_topology(mesh)
+    return V - E + F
+
+
+def _components6(inside):
+    nz, ny, nx = inside.shape
+    seen = np.zeros_like(inside, bool)
+    comps = 0
+    for idx in zip(*np.nonzero(inside)):
+        if seen[idx]:
+            continue
+        comps += 1
+        dq = deque([idx])
+        seen[idx] = True
+        while dq:
+            z, y, x = dq.popleft()
+            for dz, dy, dx in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+                q = (z + dz, y + dy, x + dx)
+                if 0 <= q[0] < nz and 0 <= q[1] < ny and 0 <= q[2] < nx and inside[q] and not seen[q]:
+                    seen[q] = True
+                    dq.append(q)
+    return comps
+
+
+def _read_golden():
+    cases, edges = {}, {}
+    with open(os.path.join(GOLDEN, "mc_single_cell.txt")) as fh:
+        for line in fh:
+            p = line.split()
+            if not p or p[0].startswith("#"):
+                continue
+            if p[0] == "case":
+                cases[int(p[1])] = [int(v) for v in p[3:]]
+            elif p[0] == "edge":
+                edges[int(p[1])] = [float(v) for v in p[2:]]
+    return cases, edges
+
+
+def test_golden_single_cells():
+    cases, edges = _read_golden()
+    for caseb, tri in cases.items():
+        got = oracle.cell_triangles(caseb).ravel().tolist()
+        assert got == tri, (caseb, got, tri)
+        f = np.ones((2, 2, 2), np.float32)
+        for j in range(8):
+            if (caseb >> j) & 1:
+                f[(j >> 2) & 1, (j >> 1) & 1, j & 1] = 0.0
+        m = oracle.mc(f, 0.5)
+        assert m.ntri == len(tri) // 3
+        for t in range(m.ntri):
+            for c in range(3):
+                assert np.allclose(m.pos[t, c], edges[tri[3 * t + c]], atol=0, rtol=0)
+
+
+def test_all_256_cases_closed_and_euler():
+    # each corner pattern embedded in the middle cell of a 4^3 grid whose other
+    # vertices are outside: the surface must close up across the neighbouring
+    # cells (crack-free), be consistently oriented, and be one sphere per
+    # 6-connected component of inside vertices.
+    maxtri = 0
+    for caseb in range(256):
+        f = np.ones((4, 4, 4), np.float32)
+        inside = np.zeros((4, 4, 4), bool)
+        for j in range(8):
+            if (caseb >> j) & 1:
+                z, y, x = 1 + ((j >> 2) & 1), 1 + ((j >> 1) & 1), 1 + (j & 1)
+                f[z, y, x] = -1.0
+                inside[z, y, x] = True
+        m = oracle.mc(f, 0.0)
+        if caseb == 0:
+            assert m.ntri == 0
+            continue
+        _assert_closed_oriented(m)
+        assert _euler(m) == 2 * _components6(inside), caseb
+        maxtri = max(maxtri, oracle.cell_triangles(caseb).shape[0])
+    assert maxtri <= 5
+
+
+def test_random_grids_closed_oriented():
+    g = np.random.Generator(np.random.PCG64(3))
+    for trial in range(40):
+        n = int(g.integers(4, 8))
+        f = g.uniform(-1, 1, size=(n, n, n)).astype(np.float32)
+        f[0, :, :] = f[-1, :, :] = 1.0
+        f[:, 0, :] = f[:, -1, :] = 1.0
+        f[:, :, 0] = f[:, :, -1] = 1.0
+        m = oracle.mc(f, 0.1)
+        _assert_closed_oriented(m)
+        assert _euler(m) % 2 == 0
+
+
+def test_sphere_euler_volume_orientation():
+    n = 32
+    c = (15.3, 16.1, 14.7)
+    r = 10.4
+    f = synth.sphere_distance(n, c)
+    m = oracle.mc(f, r)
+    _assert_closed_oriented(m)
+    assert _euler(m) == 2
+    p = m.pos
+    vol = np.einsum("ti,ti->t", p[:, 0], np.cross(p[:, 1], p[:, 2])).sum() / 6.0
+    assert abs(vol - 4.0 / 3.0 * np.pi * r ** 3) < 0.01 * 4.0 / 3.0 * np.pi * r ** 3
+    nrm = np.cross(p[:, 1] - p[:, 0], p[:, 2] - p[:, 0])
+    cen = p.mean(axis=1) - np.array(c)
+    assert np.all(np.einsum("ti,ti->t", nrm, cen) > 0), "normals must point away from the inside"
+
+
+def test_two_spheres_and_torus():
+    n = 40
+    f = np.minimum(synth.sphere_distance(n, (10.2, 12.1, 11.7)), synth.sphere_distance(n, (28.4, 27.3, 26.9)))
+    m = oracle.mc(f, 7.3)
+    _assert_closed_oriented(m)
+    assert _euler(m) == 4
+    t = synth.torus_field(n, (19.6, 20.2, 19.9), 10.0)
+    m = oracle.mc(t, 3.5 ** 2)
+    _assert_closed_oriented(m)
+    assert _euler(m) == 0
+
+
+def test_plane_exact():
+    nx, ny, nz = 13, 9, 20
+    f = synth.plane_field((nx, ny, nz), (0, 0, 1), 10.375)  # f = z - 10.375, exact in float32
+    m = oracle.mc(f, 0.0)
+    assert m.ntri == 2 * (nx - 1) * (ny - 1)
+    assert np.all(m.pos[:, :, 2] == 10.375)
+    nrm = np.cross(m.pos[:, 1] - m.pos[:, 0], m.pos[:, 2] - m.pos[:, 0])
+    assert np.all(nrm[:, 2] > 0) and np.allclose(nrm[:, :2], 0)
+
+
+def test_tilted_plane_normals_follow_gradient():
+    grad = np.array([1.0, 2.0, 3.0])
+    f = synth.plane_field(12, grad, 17.25)  # no vertex exactly on k
+    m = oracle.mc(f, 0.0)
+    assert m.ntri > 0
+    nrm = np.cross(m.pos[:, 1] - m.pos[:, 0], m.pos[:, 2] - m.pos[:, 0])
+    assert np.all(nrm @ grad > 0)
+    # every vertex lies on the plane
+    assert np.allclose(m.pos @ grad, 17.25, atol=1e-9)
+
+
+def test_vertex_on_crossing_edge_and_order():
+    f = synth.uniform_noise((7, 6, 5), 9)
+    m = oracle.mc(f, 0.2)
+    nz, ny, nx = f.shape
+    flat = f.ravel()
+    assert np.all(np.diff(m.cell) >= 0), "cells ascend"
+    step = {0: 1, 1: nx, 2: nx * ny}
+    for t in range(m.ntri):
+        for c in range(3):
+            eid = int(m.edge_id[t, c])
+            i0, axis = divmod(eid, 3)
+            f0, f1 = flat[i0], flat[i0 + step[axis]]
+            assert (f0 < 0.2) != (f1 < 0.2)
+            x0, y0, z0 = i0 % nx, (i0 // nx) % ny, i0 // (nx * ny)
+            tt = (np.float64(np.float32(0.2)) - f0) / (np.float64(f1) - f0)
+            assert 0 < tt <= 1
+            exp = np.array([x0, y0, z0], float)
+            exp[axis] += tt
+            assert np.allclose(m.pos[t, c], exp, atol=1e-12)
+
+
+def test_value_equal_to_isovalue_is_outside():
+    f = np.ones((2, 2, 2), np.float32)
+    f[0, 0, 0] = 0.5
+    assert oracle.mc(f, 0.5).ntri == 0
+    f[0, 0, 0] = np.nextafter(np.float32(0.5), np.float32(0))
+    assert oracle.mc(f, 0.5).ntri == 1
