@@ -1,0 +1,356 @@
+"""Benchmark of the hot path: chr_compress (quantise, level chain, sign fix,
+Lorenzo, pack) -> chr_reconstruct (decode + exact vertices) -> marching cubes
+for every isovalue, on a seeded 512^3 float32 turbulence field (energy
+spectrum k^-5/3, unit variance), isovalues {-1,-0.5,0.5,1}, relative bounds
+1e-2/1e-3/1e-4, 3 CHR levels, topology fix on.
+
+One step = one pass of the whole path over the field.  `value` is field GB/s
+(4*N bytes of field per step / step time), timed with CUDA events over K
+steps after W warm-up steps, inputs resident in HBM (512 MiB field > L2).
+`e2e` is the same through the public API with the field in pinned host
+memory: host->device copy, the three calls, and the device->host read of the
+triangle counts inside the timed region.
+
+--impl reference times the CPU oracle (tests-only infrastructure) on a
+bounded sub-box of the same field; it is the baseline, not the target.
+Under torchrun every rank runs its own replica on its own field (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ISOVALUES = [-1.0, -0.5, 0.5, 1.0]
+REL_BOUNDS = [1e-2, 1e-3, 1e-4]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="chr", choices=["chr", "reference"])
+    ap.add_argument("--size", type=int, default=512)
+    ap.add_argument("--seed", type=int, default=512)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--sample", type=int, default=128, help="edge of the oracle's sub-box")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def workload_config(n, args, extra=None):
+    cfg = {"workload": f"turbulence {n}^3 float32, k^-5/3, seed {args.seed}; 4 isovalues {ISOVALUES}; "
+                       f"3-level CHR, bounds {REL_BOUNDS} x range; topology fix",
+           "field_shape": [n, n, n], "isovalues": ISOVALUES, "levels": 3, "topo": "fix",
+           "step": "chr_compress + chr_reconstruct(level 2) + isosurface_extract(4 isovalues)",
+           "l2": "inputs larger than L2 (field 512 MiB, compressed stream > 129 MB); no flush"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, enabled, index=0):
+        self.enabled = enabled
+        self.proc = None
+        self.path = None
+        self.index = index
+
+    def __enter__(self):
+        if not self.enabled:
+            return self
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        if not self.proc or not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    rows.append((float(p[1]), float(p[2]), p[5], p[6], p[7], p[8]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(r[0] for r in rows)
+        mx = max(r[1] for r in rows)
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[2:]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def make_field(n, seed):
+    from paper_2408_05462_gb300 import synth
+
+    return synth.turbulence(n, seed=seed)
+
+
+def run_reference(args):
+    """The CPU oracle on a bounded sub-box of the same workload."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2408_05462_gb300 import synth
+
+    oracle.build()
+    f = make_field(args.size, args.seed)
+    r = synth.value_range(f)
+    eb = np.array([b * r for b in REL_BOUNDS], np.float32)
+    s = min(args.sample, args.size)
+    sub = np.ascontiguousarray(f[:s // 2, :s, :s])  # s x s x s/2 vertices
+
+    def step():
+        enc = oracle.encode(sub, eb, ISOVALUES, fix=True)
+        R = oracle.decode(enc, 2)
+        return sum(oracle.mc_count(R, k) for k in ISOVALUES)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    gbs = 4.0 * sub.size / dt / 1e9
+    sample = f"sub-box {s}x{s}x{s // 2} of the {args.size}^3 field per step (oracle encode 3 levels + decode + MC count x4)"
+    print(json.dumps({
+        "impl": "reference", "metric": "field GB/s (decode+fix+marching cubes), % HBM roofline; serve p50/p99 ms",
+        "value": gbs, "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": workload_config(args.size, args, {"sample": sample}),
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def cpu_baseline(f, args):
+    import oracle
+    from paper_2408_05462_gb300 import synth
+
+    oracle.build()
+    r = synth.value_range(f)
+    eb = np.array([b * r for b in REL_BOUNDS], np.float32)
+    s = min(args.sample, f.shape[0])
+    sub = np.ascontiguousarray(f[:s, :s, :s])
+    t0 = time.perf_counter()
+    enc = oracle.encode(sub, eb, ISOVALUES, fix=True)
+    R = oracle.decode(enc, 2)
+    tris = sum(oracle.mc_count(R, k) for k in ISOVALUES)
+    dt = time.perf_counter() - t0
+    return {"value": 4.0 * sub.size / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{s}^3 sub-box of the field: oracle encode (3 levels, fix) + decode + MC for 4 isovalues "
+                      f"({tris} triangles) in {dt:.1f} s, single thread"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2408_05462_gb300 import chr, synth
+
+    n = args.size
+    f_host = make_field(n, args.seed + rank)
+    N = f_host.size
+    r = synth.value_range(f_host)
+    eb = np.array([b * r for b in REL_BOUNDS], np.float32)
+    stream = torch.cuda.current_stream()
+    field = torch.from_numpy(f_host).cuda()
+    recon = torch.empty_like(field)
+
+    # size the triangle buffers from one untimed pass
+    h = chr.chr_compress(field, eb, ISOVALUES)
+    h.reconstruct(2, recon)
+    _, counts, err = chr.isosurface_extract(recon, ISOVALUES, 0)
+    torch.cuda.synchronize()
+    cap = int(counts.max().item() * 1.02) + 1024
+    tris = torch.empty((len(ISOVALUES), cap, 3, 3), dtype=torch.float32, device="cuda")
+    ws = torch.empty(chr.isosurface_workspace_size(field.shape, len(ISOVALUES)), dtype=torch.uint8, device="cuda")
+    st = h.stats()
+    comp_bytes = sum(st["level_bytes"])
+    del h
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        hh = chr.chr_compress(field, eb, ISOVALUES)
+        if ev is not None:
+            ev[1].record(stream)
+        hh.reconstruct(2, recon)
+        if ev is not None:
+            ev[2].record(stream)
+        chr.isosurface_extract(recon, ISOVALUES, cap, tris=tris, counts=counts, err=err, workspace=ws)
+        if ev is not None:
+            ev[3].record(stream)
+        hh.free()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    ntri = [int(c) for c in counts.cpu().tolist()]
+    assert int(err.item()) == 0, "overflow or timeout during warm-up"
+    T = sum(ntri)
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    with Clocks(not args.no_clocks and rank == 0, local) as clk:
+        start.record(stream)
+        for i in range(args.steps):
+            step(evs[i])
+        end.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total_ms = start.elapsed_time(end)
+    t_comp = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
+    t_dec = sum(e[1].elapsed_time(e[2]) for e in evs) / args.steps
+    t_mc = sum(e[2].elapsed_time(e[3]) for e in evs) / args.steps
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    value = world * 4.0 * N / (ms_step * 1e-3) / 1e9
+
+    # end to end through the public API from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        host = torch.from_numpy(f_host).pin_memory()
+        counts_host = torch.empty(len(ISOVALUES), dtype=torch.int64).pin_memory()
+
+        def e2e_step():
+            field.copy_(host, non_blocking=True)
+            step()
+            counts_host.copy_(counts, non_blocking=True)
+
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = s0.elapsed_time(s1) / args.steps
+        e2e = {"value": world * 4.0 * N / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": e2e_ms,
+               "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 8 * len(ISOVALUES)}
+
+    peak, peak_kind = measured_peaks()
+    mc_bytes = 4.0 * N + 36.0 * T
+    dec_bytes = comp_bytes + 4.0 * N
+    stages = {
+        "chr_compress": {"ms": t_comp, "algorithmic_bytes": 4.0 * N + comp_bytes},
+        "chr_reconstruct": {"ms": t_dec, "algorithmic_bytes": dec_bytes},
+        "isosurface_extract": {"ms": t_mc, "algorithmic_bytes": mc_bytes},
+    }
+    for v in stages.values():
+        v["GBps"] = v["algorithmic_bytes"] / (v["ms"] * 1e-3) / 1e9
+        v["frac_of_measured_hbm"] = v["GBps"] / peak
+    dom = max(stages, key=lambda k: stages[k]["ms"])
+    achieved = stages[dom]["GBps"]
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": stages[dom]["algorithmic_bytes"]}
+    out = {
+        "metric": "field GB/s (decode+fix+marching cubes), % HBM roofline; serve p50/p99 ms",
+        "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": workload_config(n, args, {"parallelism": "replicas" if world > 1 else "single"}),
+        "roofline": roofline,
+        "viz_side": {"field_GBps": 4.0 * N / ((t_dec + t_mc) * 1e-3) / 1e9, "ms": t_dec + t_mc,
+                     "tris_per_s": T / ((t_dec + t_mc) * 1e-3)},
+        "stages": stages,
+        "triangles": ntri, "compressed_bytes": comp_bytes, "compression_ratio": 4.0 * N / comp_bytes,
+        "exceptions": st["exceptions"],
+        "gpu_launches": 7 * args.steps,
+        "e2e": e2e,
+    }
+    if rank == 0:
+        clk_s = clk.summary()
+        if clk_s:
+            out["clocks"] = clk_s
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(f_host, args)
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

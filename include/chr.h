@@ -1,0 +1,215 @@
+/*
+ * chr.h — C ABI of libchr.so: topology-preserving compression and marching
+ * cubes on one GB300 GPU (arXiv 2408.05462, Li & Chen, "Accelerating
+ * In-transit Isosurface Generation With Topology Preserving Compression").
+ *
+ * The paper's workflow (Sec. 2): the data source compresses each field into a
+ * Compressed Hierarchical Representation (CHR); the visualization side asks
+ * for an isovalue and an accuracy, reconstructs the field and generates the
+ * isosurface.  Topology preservation (Sec. 2.2) means every marching-cubes
+ * cell keeps its case after compression.
+ *
+ * Conventions for every call:
+ *  - Fields are float32, nx*ny*nz values, x fastest: index x + nx*(y + ny*z).
+ *    Grid coordinates of vertex (x,y,z) are (x,y,z) (unit spacing).
+ *  - Pointers named d_* are device pointers on the current CUDA device; the
+ *    caller owns them and keeps them alive until the work on `stream` ends.
+ *    Host arrays are read before the call returns.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *    enqueued asynchronously unless a call says it synchronises.
+ *  - Every call returns a chr_status and never throws.  Argument errors are
+ *    reported before any work is enqueued, as CHR_ERR_INVALID (or
+ *    CHR_ERR_CORRUPT for bad serialized bytes); chr_last_error() then holds a
+ *    message for the calling thread.
+ *  - Device-side conditions (output overflow, a wait that gave up) are
+ *    reported through a caller-provided device error word: bit
+ *    (1u << CHR_ERR_OVERFLOW) or (1u << CHR_ERR_TIMEOUT) is OR-ed into it.
+ */
+#ifndef CHR_H
+#define CHR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CHR_MAX_LEVELS 8
+#define CHR_MAX_ISO 16
+#define CHR_BRICK 8 /* codec bricks and marching-cubes tiles are 8^3 */
+
+typedef enum chr_status {
+    CHR_OK = 0,
+    CHR_ERR_INVALID = 1,  /* bad argument; nothing was enqueued            */
+    CHR_ERR_OOM = 2,      /* the allocator returned NULL                   */
+    CHR_ERR_CUDA = 3,     /* a CUDA runtime call failed                    */
+    CHR_ERR_OVERFLOW = 4, /* device flag: an output buffer was too small   */
+    CHR_ERR_TIMEOUT = 5,  /* device flag: a bounded wait gave up           */
+    CHR_ERR_CORRUPT = 6   /* serialized bytes failed validation            */
+} chr_status;
+
+typedef struct chr_dims {
+    int64_t nx, ny, nz; /* each >= 2; nx*ny*nz < 2^32 */
+} chr_dims;
+
+/*
+ * Stream-ordered device allocator supplied by the caller.  alloc returns a
+ * device pointer of at least `bytes` bytes (256-byte aligned) usable on
+ * `stream`, or NULL; free releases it after the work already enqueued on
+ * `stream`.  A NULL chr_allocator* selects cudaMallocAsync/cudaFreeAsync.
+ */
+typedef struct chr_allocator {
+    void *(*alloc)(size_t bytes, void *stream, void *ctx);
+    void (*free)(void *ptr, size_t bytes, void *stream, void *ctx);
+    void *ctx;
+} chr_allocator;
+
+/* How topology is preserved (Sec. 2.2). */
+enum {
+    CHR_TOPO_NONE = 0,     /* error bounds only                                  */
+    CHR_TOPO_FIX = 1,      /* every vertex keeps the side of every candidate k:   */
+                           /* vertices whose reconstruction would change side    */
+                           /* are stored exactly (exceptions)                     */
+    CHR_TOPO_TRANSLATE = 2 /* Sec. 2.2 error-bound translation: every level's    */
+                           /* bound becomes min(e_l, the n-th smallest of D)      */
+};
+
+typedef struct chr_params {
+    uint32_t nlevels;          /* 1..CHR_MAX_LEVELS accuracy levels (Sec. 2 "accuracy")      */
+    const float *error_bounds; /* host [nlevels]: absolute bounds, finite, > 0, strictly      */
+                               /* decreasing, < 1e37                                          */
+    const float *isovalues;    /* host [n_iso]: candidate isovalues K (finite)                */
+    uint32_t n_iso;            /* 0..CHR_MAX_ISO                                              */
+    uint32_t topo_mode;        /* CHR_TOPO_*; FIX and TRANSLATE need n_iso >= 1               */
+    float topo_accuracy;       /* TRANSLATE: fraction in (0,1]; 1 = min D, otherwise the      */
+                               /* element of rank floor((1-accuracy)*|D|)                     */
+    uint32_t flags;            /* reserved, must be 0                                         */
+} chr_params;
+
+typedef struct chr_handle chr_handle; /* opaque; owns device buffers */
+
+typedef struct chr_stats_t {
+    chr_dims dims;
+    uint32_t nlevels, n_iso, topo_mode, reserved;
+    uint64_t nbricks;                       /* 8^3 bricks, x fastest                         */
+    float eb[CHR_MAX_LEVELS];               /* bounds in effect per level                    */
+    float eb_translated;                    /* TRANSLATE: the translated bound, else +inf    */
+    float topo_accuracy;
+    uint64_t translate_D_count;             /* TRANSLATE: |D|                                */
+    uint64_t payload_words[CHR_MAX_LEVELS]; /* packed 32-bit words per level                 */
+    uint64_t exceptions[CHR_MAX_LEVELS];    /* exactly stored vertices per level             */
+    uint64_t level_bytes[CHR_MAX_LEVELS];   /* records + payload + exceptions of the level   */
+} chr_stats_t;
+
+/*
+ * chr_compress — build a CHR of d_field (Sec. 2: "compressed into a
+ * Compressed Hierarchical Representation"; Sec. 2.2 topology preservation).
+ *
+ * Level l holds residual codes q with step 2*e_l: level 0 quantises the
+ * field, level l>0 the residual f - R_{l-1}.  R_l = R_{l-1} + q*2e_l in
+ * float32, and every vertex satisfies |f - R_l| < e_l strictly (vertices that
+ * would not are stored exactly).  With CHR_TOPO_FIX, (R_l < k) == (f < k) for
+ * every vertex, level and k in isovalues, so every marching-cubes case of
+ * every candidate isovalue is preserved at every level.  Codes are predicted
+ * per 8^3 brick (3-D Lorenzo or none, whichever packs narrower), zig-zag
+ * coded and bit-packed at the brick's width.
+ *
+ * Synchronises `stream` once (to size the packed stream).  *out receives a
+ * handle whose buffers come from `alloc` (NULL: cudaMallocAsync); release it
+ * with chr_free.  d_field is only read.
+ */
+chr_status chr_compress(const float *d_field, chr_dims dims, const chr_params *params, const chr_allocator *alloc,
+                        void *stream, chr_handle **out);
+
+/*
+ * chr_reconstruct — decode level `level` (0-based, < nlevels) into d_out
+ * (caller-owned, nx*ny*nz floats): the visualization side's reconstruction at
+ * the requested accuracy (Sec. 2).  Levels 0..level are unpacked, their
+ * prediction undone, accumulated in float32 and the stored exact vertices
+ * restored.  Bit-identical to the R_level the encoder checked.  Asynchronous.
+ */
+chr_status chr_reconstruct(const chr_handle *h, uint32_t level, float *d_out, void *stream);
+
+/*
+ * chr_topo_translate — the error-bound translation of Sec. 2.2 on its own:
+ * D holds, for every grid edge (s0,s1) with min < k < max and every k in
+ * isovalues, d0 = k - min and d1 = max - k, each rounded toward -inf in
+ * float32.  *eb_out = element of rank floor((1 - accuracy)*|D|) of D in
+ * ascending order (min D for accuracy 1), +inf when D is empty;
+ * *count_out = |D| (may be NULL).  Exact (radix selection on the float bits).
+ * Synchronises `stream`; scratch comes from `alloc` (NULL: cudaMallocAsync).
+ */
+chr_status chr_topo_translate(const float *d_field, chr_dims dims, const float *isovalues, uint32_t n_iso,
+                              float accuracy, const chr_allocator *alloc, void *stream, float *eb_out,
+                              uint64_t *count_out);
+
+/*
+ * isosurface_workspace_size — bytes of device scratch isosurface_extract
+ * needs for these dims and number of isovalues (a tile counter and one
+ * look-back status word per 8x8x32-cell tile and isovalue).
+ */
+size_t isosurface_workspace_size(chr_dims dims, uint32_t n_iso);
+
+/*
+ * isosurface_extract — marching cubes (Sec. 2.2, Lorensen & Cline) of
+ * d_field for n_iso (1..CHR_MAX_ISO) isovalues in one pass per 4 isovalues.
+ *
+ * A vertex is inside when v < k (NaN is outside).  Each cell's triangles come
+ * from the case table (gen_mc_table.py): faces with two diagonal inside
+ * corners keep them apart, triangles are oriented with normals pointing away
+ * from the inside, and a vertex on edge (v0,v1) (v0 the lower end) sits at
+ * v0 + t*(v1 - v0), t = (k - f0)/(f1 - f0) in float32.
+ *
+ * Output (triangle soup): isovalue j's triangles start at
+ * d_tris + 9*j*cap_tris; triangle t is 3 vertices of (x,y,z) floats.  Order:
+ * 8^3-cell bricks in x-fastest brick order, cells of a brick in x-fastest
+ * order, triangles of a cell in table order.  d_ntris[j] (device uint64)
+ * receives isovalue j's true triangle count even when it exceeds cap_tris;
+ * triangles beyond cap_tris are not written and bit CHR_ERR_OVERFLOW is set in
+ * *d_err.  d_err (device uint32) is cleared by the call; may be NULL.
+ * d_workspace: at least isosurface_workspace_size() bytes of device scratch,
+ * reused by the call (it is cleared on `stream` first).  Asynchronous.
+ */
+chr_status isosurface_extract(const float *d_field, chr_dims dims, const float *isovalues, uint32_t n_iso,
+                              float *d_tris, uint64_t cap_tris, uint64_t *d_ntris, uint32_t *d_err, void *d_workspace,
+                              size_t workspace_bytes, void *stream);
+
+/*
+ * chr_serialize — the CHR as one little-endian byte string, the form that
+ * crosses the network in the paper's in-transit setting (Sec. 3 streams it
+ * over a WAN).  Writes into host_buf when cap >= the size; *need always
+ * receives the size.  Synchronises `stream`.
+ * Layout: "CHR1", u32 version 1, i64 nx,ny,nz, u32 nlevels, n_iso, topo_mode,
+ * flags, f32 topo_accuracy, eb_translated, u64 translate_D_count,
+ * f32 eb[nlevels], f32 isovalues[n_iso], then per level u64 nwords, u64 nexc,
+ * then per level: records (nbricks x {u32 wsum, u32 exc_off, i32 anchor,
+ * u32 w | mode<<8 | nexc<<16}), u32 words[nwords], u16 exc_idx[nexc] padded
+ * to 4 bytes, u32 exc_val[nexc] (value bits).
+ */
+chr_status chr_serialize(const chr_handle *h, void *host_buf, size_t cap, size_t *need, void *stream);
+
+/*
+ * chr_deserialize — validate a byte string from chr_serialize on the host
+ * (CHR_ERR_CORRUPT on any inconsistency: sizes, widths > 32, prefix sums,
+ * exception slots) and upload it into a new handle.  Synchronises `stream`.
+ */
+chr_status chr_deserialize(const void *host_buf, size_t n, const chr_allocator *alloc, void *stream,
+                           chr_handle **out);
+
+/* chr_stats — sizes and bounds of a CHR (host-side, no device work). */
+chr_status chr_stats(const chr_handle *h, chr_stats_t *out);
+
+/* chr_free — release a handle's buffers (stream-ordered on its stream). NULL ok. */
+void chr_free(chr_handle *h);
+
+/* chr_last_error — message for the last failing call on this thread. */
+const char *chr_last_error(void);
+
+/* chr_version — ABI version (1). */
+int chr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHR_H */

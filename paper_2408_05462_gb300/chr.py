@@ -1,0 +1,318 @@
+"""ctypes binding of libchr.so (C ABI in include/chr.h).
+
+Argument marshalling only: every step of compression, reconstruction,
+error-bound translation and marching cubes runs in the library's CUDA
+kernels.  torch provides device memory (through its caching allocator, handed
+to the library as a chr_allocator) and the current CUDA stream.  There is no
+CPU path: if libchr.so is missing or cannot load, every call raises.
+
+Names follow the C ABI: chr_compress, chr_reconstruct, chr_topo_translate,
+isosurface_extract, isosurface_workspace_size, chr_serialize,
+chr_deserialize, chr_stats, chr_free.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from ctypes import POINTER, c_float, c_int, c_int64, c_size_t, c_uint32, c_uint64, c_void_p
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libchr.so")
+
+CHR_MAX_LEVELS = 8
+CHR_MAX_ISO = 16
+TOPO = {"none": 0, "fix": 1, "translate": 2}
+STATUS = {0: "CHR_OK", 1: "CHR_ERR_INVALID", 2: "CHR_ERR_OOM", 3: "CHR_ERR_CUDA", 4: "CHR_ERR_OVERFLOW",
+          5: "CHR_ERR_TIMEOUT", 6: "CHR_ERR_CORRUPT"}
+ERR_OVERFLOW_BIT = 1 << 4
+ERR_TIMEOUT_BIT = 1 << 5
+
+
+class ChrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ChrDims(ctypes.Structure):
+    _fields_ = [("nx", c_int64), ("ny", c_int64), ("nz", c_int64)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, c_void_p, c_size_t, c_void_p, c_void_p)
+
+
+class ChrAllocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", c_void_p)]
+
+
+class ChrParams(ctypes.Structure):
+    _fields_ = [("nlevels", c_uint32), ("error_bounds", POINTER(c_float)), ("isovalues", POINTER(c_float)),
+                ("n_iso", c_uint32), ("topo_mode", c_uint32), ("topo_accuracy", c_float), ("flags", c_uint32)]
+
+
+class ChrStats(ctypes.Structure):
+    _fields_ = [("dims", ChrDims), ("nlevels", c_uint32), ("n_iso", c_uint32), ("topo_mode", c_uint32),
+                ("reserved", c_uint32), ("nbricks", c_uint64), ("eb", c_float * CHR_MAX_LEVELS),
+                ("eb_translated", c_float), ("topo_accuracy", c_float), ("translate_D_count", c_uint64),
+                ("payload_words", c_uint64 * CHR_MAX_LEVELS), ("exceptions", c_uint64 * CHR_MAX_LEVELS),
+                ("level_bytes", c_uint64 * CHR_MAX_LEVELS)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libchr.so; raises if it was not built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libchr.so not built ({LIB_PATH}); run paper_2408_05462_gb300/build.py")
+        L = ctypes.CDLL(LIB_PATH)
+        st = c_int
+        L.chr_version.restype = c_int
+        L.chr_last_error.restype = ctypes.c_char_p
+        L.chr_compress.restype = st
+        L.chr_compress.argtypes = [c_void_p, ChrDims, POINTER(ChrParams), POINTER(ChrAllocator), c_void_p,
+                                   POINTER(c_void_p)]
+        L.chr_reconstruct.restype = st
+        L.chr_reconstruct.argtypes = [c_void_p, c_uint32, c_void_p, c_void_p]
+        L.chr_topo_translate.restype = st
+        L.chr_topo_translate.argtypes = [c_void_p, ChrDims, POINTER(c_float), c_uint32, c_float,
+                                         POINTER(ChrAllocator), c_void_p, POINTER(c_float), POINTER(c_uint64)]
+        L.isosurface_workspace_size.restype = c_size_t
+        L.isosurface_workspace_size.argtypes = [ChrDims, c_uint32]
+        L.isosurface_extract.restype = st
+        L.isosurface_extract.argtypes = [c_void_p, ChrDims, POINTER(c_float), c_uint32, c_void_p, c_uint64, c_void_p,
+                                         c_void_p, c_void_p, c_size_t, c_void_p]
+        L.chr_serialize.restype = st
+        L.chr_serialize.argtypes = [c_void_p, c_void_p, c_size_t, POINTER(c_size_t), c_void_p]
+        L.chr_deserialize.restype = st
+        L.chr_deserialize.argtypes = [c_void_p, c_size_t, POINTER(ChrAllocator), c_void_p, POINTER(c_void_p)]
+        L.chr_stats.restype = st
+        L.chr_stats.argtypes = [c_void_p, POINTER(ChrStats)]
+        L.chr_free.restype = None
+        L.chr_free.argtypes = [c_void_p]
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise ChrError(status, lib().chr_last_error().decode(errors="replace"))
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if isinstance(stream, torch.cuda.Stream) else int(stream)
+
+
+# torch caching allocator behind the chr_allocator vtable
+def _torch_alloc(nbytes, stream, ctx):
+    try:
+        return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+    except Exception:  # reported to the library as NULL -> CHR_ERR_OOM
+        return None
+
+
+def _torch_free(ptr, nbytes, stream, ctx):
+    if ptr:
+        torch.cuda.caching_allocator_delete(ptr)
+
+
+_ALLOC_CB = ALLOC_FN(_torch_alloc)
+_FREE_CB = FREE_FN(_torch_free)
+TORCH_ALLOCATOR = ChrAllocator(_ALLOC_CB, _FREE_CB, None)
+
+
+def _dims(field: torch.Tensor) -> ChrDims:
+    if field.dim() != 3:
+        raise ValueError("field must be a 3-D tensor indexed [z, y, x]")
+    nz, ny, nx = field.shape
+    return ChrDims(nx, ny, nz)
+
+
+def _check_field(field: torch.Tensor):
+    if not (field.is_cuda and field.dtype == torch.float32 and field.is_contiguous()):
+        raise ValueError("field must be a contiguous float32 CUDA tensor")
+
+
+def _floats(vals):
+    vals = [float(v) for v in vals]
+    arr = (c_float * max(len(vals), 1))(*vals)
+    return arr, len(vals)
+
+
+class Chr:
+    """A CHR handle (device buffers owned by the library, memory from torch)."""
+
+    def __init__(self, ptr: int, shape):
+        self._ptr = c_void_p(ptr)
+        self.shape = tuple(shape)
+
+    @property
+    def ptr(self):
+        return self._ptr
+
+    def stats(self) -> dict:
+        return chr_stats(self)
+
+    def reconstruct(self, level: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        return chr_reconstruct(self, level, out, stream)
+
+    def serialize(self, stream=None) -> bytes:
+        return chr_serialize(self, stream)
+
+    def free(self):
+        if self._ptr is not None and self._ptr.value:
+            lib().chr_free(self._ptr)
+        self._ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def chr_compress(field: torch.Tensor, error_bounds, isovalues=(), topo: str = "fix", accuracy: float = 1.0,
+                 stream=None) -> Chr:
+    """Compress a [nz, ny, nx] float32 CUDA field into a CHR (chr.h: chr_compress)."""
+    _check_field(field)
+    eb, ne = _floats(error_bounds)
+    iso, ni = _floats(isovalues)
+    prm = ChrParams(ne, eb, iso, ni, TOPO[topo], float(accuracy), 0)
+    out = c_void_p()
+    _check(lib().chr_compress(field.data_ptr(), _dims(field), ctypes.byref(prm), ctypes.byref(TORCH_ALLOCATOR),
+                              _stream(stream), ctypes.byref(out)))
+    return Chr(out.value, field.shape)
+
+
+def chr_reconstruct(h: Chr, level: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Decode level `level` of a CHR into a float32 tensor (chr.h: chr_reconstruct)."""
+    if out is None:
+        out = torch.empty(h.shape, dtype=torch.float32, device="cuda")
+    _check_field(out)
+    if tuple(out.shape) != h.shape:
+        raise ValueError("out has the wrong shape")
+    _check(lib().chr_reconstruct(h.ptr, int(level), out.data_ptr(), _stream(stream)))
+    return out
+
+
+def chr_topo_translate(field: torch.Tensor, isovalues, accuracy: float = 1.0, stream=None):
+    """(eb, |D|): the Sec. 2.2 translated error bound (chr.h: chr_topo_translate)."""
+    _check_field(field)
+    iso, ni = _floats(isovalues)
+    eb = c_float()
+    cnt = c_uint64()
+    _check(lib().chr_topo_translate(field.data_ptr(), _dims(field), iso, ni, float(accuracy),
+                                    ctypes.byref(TORCH_ALLOCATOR), _stream(stream), ctypes.byref(eb),
+                                    ctypes.byref(cnt)))
+    return float(eb.value), int(cnt.value)
+
+
+def isosurface_workspace_size(shape, n_iso: int) -> int:
+    nz, ny, nx = shape
+    return int(lib().isosurface_workspace_size(ChrDims(nx, ny, nz), int(n_iso)))
+
+
+def isosurface_extract(field: torch.Tensor, isovalues, cap: int, tris: torch.Tensor | None = None,
+                       counts: torch.Tensor | None = None, err: torch.Tensor | None = None,
+                       workspace: torch.Tensor | None = None, stream=None):
+    """Marching cubes of `field` for each isovalue (chr.h: isosurface_extract).
+
+    Returns (tris [n_iso, cap, 3, 3] float32, counts [n_iso] int64 true counts,
+    err [1] int32 device error word).  Asynchronous: read counts/err after the
+    stream finishes; counts[j] > cap means isovalue j overflowed."""
+    _check_field(field)
+    iso, ni = _floats(isovalues)
+    if tris is None:
+        tris = torch.empty((ni, max(int(cap), 0), 3, 3), dtype=torch.float32, device="cuda")
+    if counts is None:
+        counts = torch.empty(ni, dtype=torch.int64, device="cuda")
+    if err is None:
+        err = torch.empty(1, dtype=torch.int32, device="cuda")
+    need = isosurface_workspace_size(field.shape, ni)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device="cuda")
+    if tris.numel() < ni * int(cap) * 9:
+        raise ValueError("tris too small for n_iso * cap triangles")
+    _check(lib().isosurface_extract(field.data_ptr(), _dims(field), iso, ni, tris.data_ptr() if cap > 0 else None,
+                                    int(cap), counts.data_ptr(), err.data_ptr(), workspace.data_ptr(),
+                                    workspace.numel(), _stream(stream)))
+    return tris, counts, err
+
+
+def chr_serialize(h: Chr, stream=None) -> bytes:
+    need = c_size_t()
+    _check(lib().chr_serialize(h.ptr, None, 0, ctypes.byref(need), _stream(stream)))
+    buf = ctypes.create_string_buffer(need.value)
+    _check(lib().chr_serialize(h.ptr, buf, need.value, ctypes.byref(need), _stream(stream)))
+    return buf.raw
+
+
+def chr_deserialize(data: bytes, stream=None) -> Chr:
+    out = c_void_p()
+    _check(lib().chr_deserialize(data, len(data), ctypes.byref(TORCH_ALLOCATOR), _stream(stream), ctypes.byref(out)))
+    h = Chr(out.value, (1, 1, 1))
+    st = chr_stats(h)
+    h.shape = (st["dims"][2], st["dims"][1], st["dims"][0])
+    return h
+
+
+def chr_stats(h: Chr) -> dict:
+    s = ChrStats()
+    _check(lib().chr_stats(h.ptr, ctypes.byref(s)))
+    L = s.nlevels
+    return {
+        "dims": (s.dims.nx, s.dims.ny, s.dims.nz), "nlevels": L, "n_iso": s.n_iso, "topo_mode": s.topo_mode,
+        "nbricks": s.nbricks, "eb": [s.eb[i] for i in range(L)], "eb_translated": s.eb_translated,
+        "topo_accuracy": s.topo_accuracy, "translate_D_count": s.translate_D_count,
+        "payload_words": [s.payload_words[i] for i in range(L)], "exceptions": [s.exceptions[i] for i in range(L)],
+        "level_bytes": [s.level_bytes[i] for i in range(L)],
+    }
+
+
+def chr_free(h: Chr):
+    h.free()
+
+
+def parse_serialized(data: bytes) -> dict:
+    """Split a chr_serialize byte string into numpy arrays (format in chr.h)."""
+    import numpy as np
+
+    off = 0
+
+    def take(dtype, n):
+        nonlocal off
+        a = np.frombuffer(data, dtype=dtype, count=n, offset=off)
+        off += a.nbytes
+        return a
+
+    assert data[:4] == b"CHR1"
+    off = 4
+    version = int(take(np.uint32, 1)[0])
+    nx, ny, nz = (int(v) for v in take(np.int64, 3))
+    nlevels, n_iso, topo, flags = (int(v) for v in take(np.uint32, 4))
+    acc, ebt = (float(v) for v in take(np.float32, 2))
+    dcount = int(take(np.uint64, 1)[0])
+    eb = take(np.float32, nlevels).copy()
+    iso = take(np.float32, n_iso).copy()
+    sizes = take(np.uint64, 2 * nlevels).reshape(nlevels, 2)
+    nb = math.ceil(nx / 8) * math.ceil(ny / 8) * math.ceil(nz / 8)
+    levels = []
+    for l in range(nlevels):
+        nw, ne = int(sizes[l, 0]), int(sizes[l, 1])
+        recs = take(np.uint32, 4 * nb).reshape(nb, 4).copy()
+        words = take(np.uint32, nw).copy()
+        idx = take(np.uint16, ne).copy()
+        off += ((2 * ne + 3) & ~3) - 2 * ne
+        val = take(np.uint32, ne).copy()
+        levels.append({"recs": recs, "words": words, "exc_idx": idx, "exc_val": val})
+    return {"version": version, "dims": (nx, ny, nz), "nlevels": nlevels, "n_iso": n_iso, "topo_mode": topo,
+            "flags": flags, "topo_accuracy": acc, "eb_translated": ebt, "translate_D_count": dcount, "eb": eb,
+            "isovalues": iso, "levels": levels}

@@ -1,0 +1,633 @@
+// C ABI of libchr (include/chr.h): argument validation, CHR handles,
+// serialization, and the launch sequences of the kernels in codec.cu, mc.cu
+// and translate.cu.
+#include <math.h>
+#include <string.h>
+
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace chr {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+namespace {
+
+struct Alloc {
+    chr_allocator a{};
+    bool dflt = true;
+    cudaStream_t s = nullptr;
+
+    Alloc(const chr_allocator *al, cudaStream_t st) : s(st)
+    {
+        if (al) {
+            a = *al;
+            dflt = false;
+        }
+    }
+    void *get(size_t n)
+    {
+        if (n == 0) n = 16;
+        n = (n + 255) & ~size_t(255);
+        void *p = nullptr;
+        if (dflt) {
+            if (cudaMallocAsync(&p, n, s) != cudaSuccess) {
+                cudaGetLastError();
+                return nullptr;
+            }
+        } else {
+            p = a.alloc(n, s, a.ctx);
+        }
+        return p;
+    }
+    void put(void *p, size_t n)
+    {
+        if (!p) return;
+        if (n == 0) n = 16;
+        n = (n + 255) & ~size_t(255);
+        if (dflt)
+            cudaFreeAsync(p, s);
+        else
+            a.free(p, n, s, a.ctx);
+    }
+};
+
+chr_status fail(chr_status st, const std::string &msg)
+{
+    set_error(msg);
+    return st;
+}
+
+chr_status cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(CHR_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CHR_CUDA(call, where)                         \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+bool dims_ok(chr_dims d, std::string &why)
+{
+    if (d.nx < 2 || d.ny < 2 || d.nz < 2) {
+        why = "dims must be >= 2 along every axis";
+        return false;
+    }
+    if (d.nx > (1ll << 31) || d.ny > (1ll << 31) || d.nz > (1ll << 31) ||
+        (double)d.nx * (double)d.ny * (double)d.nz >= 4294967295.0) {
+        why = "nx*ny*nz must be < 2^32";
+        return false;
+    }
+    return true;
+}
+
+void free_handle_buffers(chr_handle *h)
+{
+    Alloc al(h->default_alloc ? nullptr : &h->alloc, h->stream);
+    for (uint32_t l = 0; l < CHR_MAX_LEVELS; l++) {
+        al.put(h->d_recs[l], h->sz_recs);
+        al.put(h->d_words[l], h->sz_words[l]);
+        al.put(h->d_exc_idx[l], h->sz_exc_idx[l]);
+        al.put(h->d_exc_val[l], h->sz_exc_val[l]);
+        h->d_recs[l] = nullptr;
+        h->d_words[l] = nullptr;
+        h->d_exc_idx[l] = nullptr;
+        h->d_exc_val[l] = nullptr;
+    }
+}
+
+chr_handle *new_handle(chr_dims dims, const chr_allocator *alloc, cudaStream_t s)
+{
+    chr_handle *h = new chr_handle();
+    memset(h, 0, sizeof(*h));
+    h->dims = dims;
+    h->g = make_grid(dims);
+    h->default_alloc = (alloc == nullptr);
+    if (alloc) h->alloc = *alloc;
+    h->stream = s;
+    h->eb_translated = INFINITY;
+    return h;
+}
+
+void fill_codec_params(const chr_handle *h, CodecParams &p)
+{
+    memset(&p, 0, sizeof(p));
+    p.nx = h->g.nx;
+    p.ny = h->g.ny;
+    p.nz = h->g.nz;
+    p.nbx = (int32_t)h->g.nbx;
+    p.nby = (int32_t)h->g.nby;
+    p.nbz = (int32_t)h->g.nbz;
+    p.ngx = (int32_t)((h->g.nbx + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    p.nlevels = (int32_t)h->nlevels;
+    for (uint32_t l = 0; l < h->nlevels; l++) {
+        p.e[l] = h->eb[l];
+        p.two_e[l] = h->two_e[l];
+        p.inv2e[l] = h->inv2e[l];
+        p.recs[l] = h->d_recs[l];
+        p.words[l] = h->d_words[l];
+        p.exc_idx[l] = h->d_exc_idx[l];
+        p.exc_val[l] = h->d_exc_val[l];
+    }
+    p.nK = (int32_t)h->n_iso;
+    for (uint32_t j = 0; j < h->n_iso; j++) p.K[j] = h->iso[j];
+    p.fix = (h->topo_mode == CHR_TOPO_FIX) ? 1 : 0;
+}
+
+void set_constants(chr_handle *h)
+{
+    for (uint32_t l = 0; l < h->nlevels; l++) {
+        volatile float e = h->eb[l];
+        volatile float two = 2.0f * e;
+        h->two_e[l] = two;
+        h->inv2e[l] = 1.0f / two;
+    }
+}
+
+// The radix selection of chr_topo_translate; synchronises the stream.
+chr_status translate_impl(const float *d_field, const Grid &g, const float *K, uint32_t nK, float accuracy, Alloc &al,
+                          float *eb_out, uint64_t *count_out)
+{
+    const size_t sb = translate_scratch_bytes();
+    char *scr = (char *)al.get(sb);
+    if (!scr) return fail(CHR_ERR_OOM, "chr_topo_translate: allocator returned NULL");
+    TranslateScratch sc;
+    sc.hist = reinterpret_cast<unsigned long long *>(scr);
+    sc.count = reinterpret_cast<unsigned long long *>(scr + 256 * 8);
+    sc.minbits = reinterpret_cast<unsigned int *>(scr + 256 * 8 + 8);
+    chr_status st = CHR_OK;
+    std::vector<unsigned long long> hist(256);
+    unsigned long long count = 0;
+    unsigned int minbits = 0xffffffffu;
+    float eb = INFINITY;
+    do {
+        cudaError_t e;
+        const bool min_only = (accuracy >= 1.0f);
+        if ((e = cudaMemsetAsync(scr, 0, 256 * 8 + 8, al.s)) != cudaSuccess ||
+            (e = cudaMemsetAsync(sc.minbits, 0xff, 4, al.s)) != cudaSuccess ||
+            (e = launch_translate_pass(d_field, g, K, (int)nK, 0, 0u, min_only, sc, al.s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(&count, sc.count, 8, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(&minbits, sc.minbits, 4, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(hist.data(), sc.hist, 256 * 8, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(al.s)) != cudaSuccess) {
+            st = cuda_fail(e, "chr_topo_translate");
+            break;
+        }
+        if (count == 0) break;
+        if (min_only) {
+            memcpy(&eb, &minbits, 4);
+            break;
+        }
+        double r = floor((1.0 - (double)accuracy) * (double)count);
+        unsigned long long rank = (r < 0) ? 0ull : (unsigned long long)r;
+        if (rank > count - 1) rank = count - 1;
+        uint32_t prefix = 0;
+        for (int pass = 0; pass < 4; pass++) {
+            if (pass > 0) {
+                if ((e = cudaMemsetAsync(sc.hist, 0, 256 * 8, al.s)) != cudaSuccess ||
+                    (e = launch_translate_pass(d_field, g, K, (int)nK, pass, prefix, false, sc, al.s)) != cudaSuccess ||
+                    (e = cudaMemcpyAsync(hist.data(), sc.hist, 256 * 8, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess ||
+                    (e = cudaStreamSynchronize(al.s)) != cudaSuccess) {
+                    st = cuda_fail(e, "chr_topo_translate");
+                    break;
+                }
+            }
+            unsigned long long cum = 0;
+            int bucket = 255;
+            for (int b = 0; b < 256; b++) {
+                if (rank < cum + hist[b]) {
+                    bucket = b;
+                    break;
+                }
+                cum += hist[b];
+            }
+            rank -= cum;
+            prefix = (prefix << 8) | (uint32_t)bucket;
+        }
+        if (st != CHR_OK) break;
+        memcpy(&eb, &prefix, 4);
+    } while (0);
+    al.put(scr, sb);
+    if (st == CHR_OK) {
+        *eb_out = eb;
+        if (count_out) *count_out = count;
+    }
+    return st;
+}
+
+// ---- serialization helpers -------------------------------------------------
+
+struct Writer {
+    std::vector<char> *buf;
+    template <class T>
+    void put(const T &v)
+    {
+        const char *p = reinterpret_cast<const char *>(&v);
+        buf->insert(buf->end(), p, p + sizeof(T));
+    }
+};
+
+size_t header_bytes(uint32_t nlevels, uint32_t n_iso)
+{
+    return 4 + 4 + 24 + 16 + 8 + 8 + 4 * (size_t)nlevels + 4 * (size_t)n_iso + 16 * (size_t)nlevels;
+}
+
+size_t level_bytes(const chr_handle *h, uint32_t l)
+{
+    size_t idx = ((size_t)h->nexc[l] * 2 + 3) & ~size_t(3);
+    return (size_t)h->g.nbricks * 16 + (size_t)h->nwords[l] * 4 + idx + (size_t)h->nexc[l] * 4;
+}
+
+}  // namespace
+}  // namespace chr
+
+using namespace chr;
+
+extern "C" {
+
+int chr_version(void) { return 1; }
+
+const char *chr_last_error(void) { return g_last_error.c_str(); }
+
+chr_status chr_compress(const float *d_field, chr_dims dims, const chr_params *prm, const chr_allocator *alloc,
+                        void *stream, chr_handle **out)
+{
+    std::string why;
+    if (!out) return fail(CHR_ERR_INVALID, "chr_compress: out is NULL");
+    *out = nullptr;
+    if (!d_field || !prm) return fail(CHR_ERR_INVALID, "chr_compress: NULL field or params");
+    if (!dims_ok(dims, why)) return fail(CHR_ERR_INVALID, "chr_compress: " + why);
+    if (prm->nlevels < 1 || prm->nlevels > CHR_MAX_LEVELS || !prm->error_bounds)
+        return fail(CHR_ERR_INVALID, "chr_compress: nlevels must be 1..8 with error_bounds");
+    for (uint32_t l = 0; l < prm->nlevels; l++) {
+        const float e = prm->error_bounds[l];
+        if (!(e > 0.0f) || !(e < 1e37f)) return fail(CHR_ERR_INVALID, "chr_compress: error bounds must be finite, > 0, < 1e37");
+        if (l > 0 && !(e < prm->error_bounds[l - 1]))
+            return fail(CHR_ERR_INVALID, "chr_compress: error bounds must decrease strictly");
+    }
+    if (prm->n_iso > CHR_MAX_ISO || (prm->n_iso > 0 && !prm->isovalues))
+        return fail(CHR_ERR_INVALID, "chr_compress: n_iso must be <= 16 with isovalues");
+    for (uint32_t j = 0; j < prm->n_iso; j++)
+        if (!isfinite(prm->isovalues[j])) return fail(CHR_ERR_INVALID, "chr_compress: isovalues must be finite");
+    if (prm->topo_mode > CHR_TOPO_TRANSLATE) return fail(CHR_ERR_INVALID, "chr_compress: bad topo_mode");
+    if (prm->topo_mode != CHR_TOPO_NONE && prm->n_iso == 0)
+        return fail(CHR_ERR_INVALID, "chr_compress: topology preservation needs isovalues");
+    if (prm->topo_mode == CHR_TOPO_TRANSLATE && !(prm->topo_accuracy > 0.0f && prm->topo_accuracy <= 1.0f))
+        return fail(CHR_ERR_INVALID, "chr_compress: topo_accuracy must be in (0, 1]");
+    if (prm->flags != 0) return fail(CHR_ERR_INVALID, "chr_compress: flags must be 0");
+
+    cudaStream_t s = (cudaStream_t)stream;
+    chr_handle *h = new_handle(dims, alloc, s);
+    h->nlevels = prm->nlevels;
+    h->n_iso = prm->n_iso;
+    h->topo_mode = prm->topo_mode;
+    h->topo_accuracy = (prm->topo_mode == CHR_TOPO_TRANSLATE) ? prm->topo_accuracy : 1.0f;
+    for (uint32_t j = 0; j < prm->n_iso; j++) h->iso[j] = prm->isovalues[j];
+    for (uint32_t l = 0; l < prm->nlevels; l++) h->eb[l] = prm->error_bounds[l];
+    Alloc al(alloc, s);
+    chr_status st = CHR_OK;
+
+    if (h->topo_mode == CHR_TOPO_TRANSLATE) {
+        float ebt = INFINITY;
+        uint64_t cnt = 0;
+        st = translate_impl(d_field, h->g, h->iso, h->n_iso, h->topo_accuracy, al, &ebt, &cnt);
+        if (st != CHR_OK) {
+            delete h;
+            return st;
+        }
+        h->eb_translated = ebt;
+        h->D_count = cnt;
+        for (uint32_t l = 0; l < h->nlevels; l++)
+            if (ebt < h->eb[l]) h->eb[l] = ebt;
+    }
+    set_constants(h);
+
+    const Grid &g = h->g;
+    h->sz_recs = (size_t)g.nbricks * sizeof(uint4);
+    for (uint32_t l = 0; l < h->nlevels; l++) {
+        h->d_recs[l] = (uint4 *)al.get(h->sz_recs);
+        if (!h->d_recs[l]) {
+            free_handle_buffers(h);
+            delete h;
+            return fail(CHR_ERR_OOM, "chr_compress: allocator returned NULL");
+        }
+    }
+    CodecParams p;
+    fill_codec_params(h, p);
+    p.f = d_field;
+    cudaError_t e = launch_encode(p, false, s);
+    const size_t scr_bytes = scan_scratch_bytes(g.nbricks, (int)h->nlevels) + 16 * CHR_MAX_LEVELS;
+    char *scr = nullptr;
+    uint64_t totals[2 * CHR_MAX_LEVELS] = {0};
+    if (e == cudaSuccess) {
+        scr = (char *)al.get(scr_bytes);
+        if (!scr) st = fail(CHR_ERR_OOM, "chr_compress: allocator returned NULL");
+    }
+    if (e == cudaSuccess && st == CHR_OK) {
+        uint64_t *d_tot = reinterpret_cast<uint64_t *>(scr + scan_scratch_bytes(g.nbricks, (int)h->nlevels));
+        e = launch_scan_records(h->d_recs, (int)h->nlevels, g.nbricks, scr, d_tot, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(totals, d_tot, 16 * h->nlevels, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (e == cudaSuccess && st == CHR_OK) {
+        for (uint32_t l = 0; l < h->nlevels && st == CHR_OK; l++) {
+            h->nwords[l] = 16 * totals[2 * l];
+            h->nexc[l] = totals[2 * l + 1];
+            h->sz_words[l] = h->nwords[l] * 4 + 64;
+            h->sz_exc_idx[l] = h->nexc[l] * 2 + 64;
+            h->sz_exc_val[l] = h->nexc[l] * 4 + 64;
+            h->d_words[l] = (uint32_t *)al.get(h->sz_words[l]);
+            h->d_exc_idx[l] = (uint16_t *)al.get(h->sz_exc_idx[l]);
+            h->d_exc_val[l] = (uint32_t *)al.get(h->sz_exc_val[l]);
+            if (!h->d_words[l] || !h->d_exc_idx[l] || !h->d_exc_val[l])
+                st = fail(CHR_ERR_OOM, "chr_compress: allocator returned NULL");
+        }
+    }
+    if (e == cudaSuccess && st == CHR_OK) {
+        fill_codec_params(h, p);
+        p.f = d_field;
+        e = launch_encode(p, true, s);
+    }
+    al.put(scr, scr_bytes);
+    if (e != cudaSuccess) st = cuda_fail(e, "chr_compress");
+    if (st != CHR_OK) {
+        free_handle_buffers(h);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return CHR_OK;
+}
+
+chr_status chr_reconstruct(const chr_handle *h, uint32_t level, float *d_out, void *stream)
+{
+    if (!h || !d_out) return fail(CHR_ERR_INVALID, "chr_reconstruct: NULL handle or output");
+    if (level >= h->nlevels) return fail(CHR_ERR_INVALID, "chr_reconstruct: level out of range");
+    CodecParams p;
+    fill_codec_params(h, p);
+    p.out = d_out;
+    p.nlevels = (int32_t)level + 1;
+    cudaError_t e = launch_decode(p, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "chr_reconstruct");
+    return CHR_OK;
+}
+
+chr_status chr_topo_translate(const float *d_field, chr_dims dims, const float *isovalues, uint32_t n_iso,
+                              float accuracy, const chr_allocator *alloc, void *stream, float *eb_out,
+                              uint64_t *count_out)
+{
+    std::string why;
+    if (!d_field || !eb_out) return fail(CHR_ERR_INVALID, "chr_topo_translate: NULL field or output");
+    if (!dims_ok(dims, why)) return fail(CHR_ERR_INVALID, "chr_topo_translate: " + why);
+    if (n_iso < 1 || n_iso > CHR_MAX_ISO || !isovalues)
+        return fail(CHR_ERR_INVALID, "chr_topo_translate: n_iso must be 1..16 with isovalues");
+    for (uint32_t j = 0; j < n_iso; j++)
+        if (!isfinite(isovalues[j])) return fail(CHR_ERR_INVALID, "chr_topo_translate: isovalues must be finite");
+    if (!(accuracy > 0.0f && accuracy <= 1.0f)) return fail(CHR_ERR_INVALID, "chr_topo_translate: accuracy must be in (0, 1]");
+    Alloc al(alloc, (cudaStream_t)stream);
+    return translate_impl(d_field, make_grid(dims), isovalues, n_iso, accuracy, al, eb_out, count_out);
+}
+
+size_t isosurface_workspace_size(chr_dims dims, uint32_t n_iso)
+{
+    std::string why;
+    if (!dims_ok(dims, why)) return 0;
+    return mc_workspace_bytes(make_grid(dims), (int)n_iso);
+}
+
+chr_status isosurface_extract(const float *d_field, chr_dims dims, const float *isovalues, uint32_t n_iso,
+                              float *d_tris, uint64_t cap_tris, uint64_t *d_ntris, uint32_t *d_err, void *d_workspace,
+                              size_t workspace_bytes, void *stream)
+{
+    std::string why;
+    if (!d_field || !d_ntris || !isovalues) return fail(CHR_ERR_INVALID, "isosurface_extract: NULL field, counts or isovalues");
+    if (!dims_ok(dims, why)) return fail(CHR_ERR_INVALID, "isosurface_extract: " + why);
+    if (n_iso < 1 || n_iso > CHR_MAX_ISO) return fail(CHR_ERR_INVALID, "isosurface_extract: n_iso must be 1..16");
+    for (uint32_t j = 0; j < n_iso; j++)
+        if (!isfinite(isovalues[j])) return fail(CHR_ERR_INVALID, "isosurface_extract: isovalues must be finite");
+    if (cap_tris > 0 && !d_tris) return fail(CHR_ERR_INVALID, "isosurface_extract: NULL triangle buffer");
+    if (cap_tris > (1ull << 58)) return fail(CHR_ERR_INVALID, "isosurface_extract: cap_tris too large");
+    const Grid g = make_grid(dims);
+    if (!d_workspace || workspace_bytes < mc_workspace_bytes(g, (int)n_iso))
+        return fail(CHR_ERR_INVALID, "isosurface_extract: workspace smaller than isosurface_workspace_size()");
+    cudaStream_t s = (cudaStream_t)stream;
+    CHR_CUDA(cudaMemsetAsync(d_ntris, 0, sizeof(uint64_t) * n_iso, s), "isosurface_extract");
+    if (d_err) CHR_CUDA(cudaMemsetAsync(d_err, 0, sizeof(uint32_t), s), "isosurface_extract");
+    CHR_CUDA(launch_mc(d_field, g, isovalues, (int)n_iso, d_tris, cap_tris, d_ntris, d_err, d_workspace, s),
+             "isosurface_extract");
+    return CHR_OK;
+}
+
+chr_status chr_stats(const chr_handle *h, chr_stats_t *out)
+{
+    if (!h || !out) return fail(CHR_ERR_INVALID, "chr_stats: NULL argument");
+    memset(out, 0, sizeof(*out));
+    out->dims = h->dims;
+    out->nlevels = h->nlevels;
+    out->n_iso = h->n_iso;
+    out->topo_mode = h->topo_mode;
+    out->nbricks = (uint64_t)h->g.nbricks;
+    for (uint32_t l = 0; l < h->nlevels; l++) {
+        out->eb[l] = h->eb[l];
+        out->payload_words[l] = h->nwords[l];
+        out->exceptions[l] = h->nexc[l];
+        out->level_bytes[l] = level_bytes(h, l);
+    }
+    out->eb_translated = h->eb_translated;
+    out->topo_accuracy = h->topo_accuracy;
+    out->translate_D_count = h->D_count;
+    return CHR_OK;
+}
+
+chr_status chr_serialize(const chr_handle *h, void *host_buf, size_t cap, size_t *need, void *stream)
+{
+    if (!h || !need) return fail(CHR_ERR_INVALID, "chr_serialize: NULL handle or size");
+    size_t total = header_bytes(h->nlevels, h->n_iso);
+    for (uint32_t l = 0; l < h->nlevels; l++) total += level_bytes(h, l);
+    *need = total;
+    if (!host_buf || cap < total) return CHR_OK;
+    std::vector<char> hdr;
+    Writer w{&hdr};
+    hdr.insert(hdr.end(), {'C', 'H', 'R', '1'});
+    w.put<uint32_t>(1);
+    w.put<int64_t>(h->dims.nx);
+    w.put<int64_t>(h->dims.ny);
+    w.put<int64_t>(h->dims.nz);
+    w.put<uint32_t>(h->nlevels);
+    w.put<uint32_t>(h->n_iso);
+    w.put<uint32_t>(h->topo_mode);
+    w.put<uint32_t>(h->flags);
+    w.put<float>(h->topo_accuracy);
+    w.put<float>(h->eb_translated);
+    w.put<uint64_t>(h->D_count);
+    for (uint32_t l = 0; l < h->nlevels; l++) w.put<float>(h->eb[l]);
+    for (uint32_t j = 0; j < h->n_iso; j++) w.put<float>(h->iso[j]);
+    for (uint32_t l = 0; l < h->nlevels; l++) {
+        w.put<uint64_t>(h->nwords[l]);
+        w.put<uint64_t>(h->nexc[l]);
+    }
+    char *dst = (char *)host_buf;
+    memcpy(dst, hdr.data(), hdr.size());
+    size_t off = hdr.size();
+    cudaStream_t s = (cudaStream_t)stream;
+    for (uint32_t l = 0; l < h->nlevels; l++) {
+        const size_t nr = (size_t)h->g.nbricks * 16, nw = (size_t)h->nwords[l] * 4, ne = (size_t)h->nexc[l];
+        CHR_CUDA(cudaMemcpyAsync(dst + off, h->d_recs[l], nr, cudaMemcpyDeviceToHost, s), "chr_serialize");
+        off += nr;
+        if (nw) CHR_CUDA(cudaMemcpyAsync(dst + off, h->d_words[l], nw, cudaMemcpyDeviceToHost, s), "chr_serialize");
+        off += nw;
+        if (ne) CHR_CUDA(cudaMemcpyAsync(dst + off, h->d_exc_idx[l], ne * 2, cudaMemcpyDeviceToHost, s), "chr_serialize");
+        const size_t idx = (ne * 2 + 3) & ~size_t(3);
+        if (idx > ne * 2) memset(dst + off + ne * 2, 0, idx - ne * 2);
+        off += idx;
+        if (ne) CHR_CUDA(cudaMemcpyAsync(dst + off, h->d_exc_val[l], ne * 4, cudaMemcpyDeviceToHost, s), "chr_serialize");
+        off += ne * 4;
+    }
+    CHR_CUDA(cudaStreamSynchronize(s), "chr_serialize");
+    return CHR_OK;
+}
+
+chr_status chr_deserialize(const void *host_buf, size_t n, const chr_allocator *alloc, void *stream, chr_handle **out)
+{
+    if (!out) return fail(CHR_ERR_INVALID, "chr_deserialize: out is NULL");
+    *out = nullptr;
+    if (!host_buf) return fail(CHR_ERR_INVALID, "chr_deserialize: NULL buffer");
+    const char *src = (const char *)host_buf;
+    size_t off = 0;
+    auto take = [&](void *dst, size_t k) -> bool {
+        if (off + k > n) return false;
+        memcpy(dst, src + off, k);
+        off += k;
+        return true;
+    };
+    char magic[4];
+    uint32_t version = 0, nlevels = 0, n_iso = 0, topo = 0, flags = 0;
+    chr_dims dims;
+    float acc = 1.0f, ebt = INFINITY;
+    uint64_t dcount = 0;
+    if (!take(magic, 4) || memcmp(magic, "CHR1", 4) != 0) return fail(CHR_ERR_CORRUPT, "chr_deserialize: bad magic");
+    if (!take(&version, 4) || version != 1) return fail(CHR_ERR_CORRUPT, "chr_deserialize: unsupported version");
+    if (!take(&dims.nx, 8) || !take(&dims.ny, 8) || !take(&dims.nz, 8) || !take(&nlevels, 4) || !take(&n_iso, 4) ||
+        !take(&topo, 4) || !take(&flags, 4) || !take(&acc, 4) || !take(&ebt, 4) || !take(&dcount, 8))
+        return fail(CHR_ERR_CORRUPT, "chr_deserialize: truncated header");
+    std::string why;
+    if (!dims_ok(dims, why)) return fail(CHR_ERR_CORRUPT, "chr_deserialize: " + why);
+    if (nlevels < 1 || nlevels > CHR_MAX_LEVELS || n_iso > CHR_MAX_ISO || topo > CHR_TOPO_TRANSLATE || flags != 0)
+        return fail(CHR_ERR_CORRUPT, "chr_deserialize: bad level/isovalue/mode fields");
+    cudaStream_t s = (cudaStream_t)stream;
+    chr_handle *h = new_handle(dims, alloc, s);
+    h->nlevels = nlevels;
+    h->n_iso = n_iso;
+    h->topo_mode = topo;
+    h->topo_accuracy = acc;
+    h->eb_translated = ebt;
+    h->D_count = dcount;
+    bool ok = true;
+    for (uint32_t l = 0; l < nlevels && ok; l++) ok = take(&h->eb[l], 4) && h->eb[l] >= 0.0f && h->eb[l] < 1e37f;
+    for (uint32_t j = 0; j < n_iso && ok; j++) ok = take(&h->iso[j], 4);
+    for (uint32_t l = 0; l < nlevels && ok; l++) ok = take(&h->nwords[l], 8) && take(&h->nexc[l], 8);
+    if (!ok) {
+        delete h;
+        return fail(CHR_ERR_CORRUPT, "chr_deserialize: truncated or invalid header arrays");
+    }
+    set_constants(h);
+    const Grid &g = h->g;
+    // validate every level on the host before anything is uploaded
+    std::vector<size_t> level_off(nlevels);
+    for (uint32_t l = 0; l < nlevels; l++) {
+        level_off[l] = off;
+        const size_t nr = (size_t)g.nbricks * 16;
+        if (h->nexc[l] > (uint64_t)g.N || h->nwords[l] > (uint64_t)g.nbricks * 512 || off + level_bytes(h, l) > n) {
+            delete h;
+            return fail(CHR_ERR_CORRUPT, "chr_deserialize: level sizes inconsistent with the buffer");
+        }
+        const uint32_t *rec = reinterpret_cast<const uint32_t *>(src + off);
+        const uint16_t *eidx = reinterpret_cast<const uint16_t *>(src + off + nr + h->nwords[l] * 4);
+        uint64_t wsum = 0, esum = 0;
+        for (int64_t b = 0; b < g.nbricks && ok; b++) {
+            uint32_t r[4];
+            memcpy(r, rec + 4 * b, 16);
+            const uint32_t w = r[3] & 0xffu, mode = (r[3] >> 8) & 0xffu, ne = r[3] >> 16;
+            if (w > 32 || mode > 1 || ne > 512 || r[0] != wsum || r[1] != esum) {
+                ok = false;
+                break;
+            }
+            const int64_t bx = b % g.nbx, by = (b / g.nbx) % g.nby, bz = b / (g.nbx * g.nby);
+            int prev = -1;
+            for (uint32_t j = 0; j < ne; j++) {
+                if (esum + j >= h->nexc[l]) {
+                    ok = false;
+                    break;
+                }
+                uint16_t sl;
+                memcpy(&sl, eidx + esum + j, 2);
+                const int64_t x = bx * 8 + (sl & 7), y = by * 8 + ((sl >> 3) & 7), z = bz * 8 + (sl >> 6);
+                if (sl >= 512 || (int)sl <= prev || x >= g.nx || y >= g.ny || z >= g.nz) {
+                    ok = false;
+                    break;
+                }
+                prev = sl;
+            }
+            wsum += w;
+            esum += ne;
+        }
+        if (!ok || 16 * wsum != h->nwords[l] || esum != h->nexc[l]) {
+            delete h;
+            return fail(CHR_ERR_CORRUPT, "chr_deserialize: records inconsistent (widths, prefix sums or exception slots)");
+        }
+        off += level_bytes(h, l);
+    }
+    Alloc al(alloc, s);
+    h->sz_recs = (size_t)g.nbricks * sizeof(uint4);
+    chr_status st = CHR_OK;
+    for (uint32_t l = 0; l < nlevels && st == CHR_OK; l++) {
+        h->sz_words[l] = h->nwords[l] * 4 + 64;
+        h->sz_exc_idx[l] = h->nexc[l] * 2 + 64;
+        h->sz_exc_val[l] = h->nexc[l] * 4 + 64;
+        h->d_recs[l] = (uint4 *)al.get(h->sz_recs);
+        h->d_words[l] = (uint32_t *)al.get(h->sz_words[l]);
+        h->d_exc_idx[l] = (uint16_t *)al.get(h->sz_exc_idx[l]);
+        h->d_exc_val[l] = (uint32_t *)al.get(h->sz_exc_val[l]);
+        if (!h->d_recs[l] || !h->d_words[l] || !h->d_exc_idx[l] || !h->d_exc_val[l]) {
+            st = fail(CHR_ERR_OOM, "chr_deserialize: allocator returned NULL");
+            break;
+        }
+        size_t o = level_off[l];
+        const size_t nr = (size_t)g.nbricks * 16, nw = (size_t)h->nwords[l] * 4, ne = (size_t)h->nexc[l];
+        cudaError_t e = cudaMemcpyAsync(h->d_recs[l], src + o, nr, cudaMemcpyHostToDevice, s);
+        o += nr;
+        if (e == cudaSuccess && nw) e = cudaMemcpyAsync(h->d_words[l], src + o, nw, cudaMemcpyHostToDevice, s);
+        o += nw;
+        if (e == cudaSuccess && ne) e = cudaMemcpyAsync(h->d_exc_idx[l], src + o, ne * 2, cudaMemcpyHostToDevice, s);
+        o += (ne * 2 + 3) & ~size_t(3);
+        if (e == cudaSuccess && ne) e = cudaMemcpyAsync(h->d_exc_val[l], src + o, ne * 4, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) st = cuda_fail(e, "chr_deserialize");
+    }
+    if (st == CHR_OK) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_fail(e, "chr_deserialize");
+    }
+    if (st != CHR_OK) {
+        free_handle_buffers(h);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return CHR_OK;
+}
+
+void chr_free(chr_handle *h)
+{
+    if (!h) return;
+    free_handle_buffers(h);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,481 @@
+// CHR codec kernels: encode (quantise + level chain + sign fix + Lorenzo +
+// pack), the record scans, and decode (unpack + inverse Lorenzo + level chain
+// + exact vertices).  Paper Sec. 2 (CHR, accuracy levels) and Sec. 2.2
+// (topology preservation); the format is this library's (see chr.h).
+//
+// Work decomposition: one warp owns one 8^3 brick (512 vertices), each lane
+// two x-rows of 8 vertices: row r0 = lane (y = lane&7, z = lane>>3) and
+// row r1 = lane + 32 (z + 4).  A block of 8 warps takes 8 bricks that follow
+// each other along x, so the rows a block touches are 256-byte runs.
+#include "common.cuh"
+#include "internal.h"
+
+namespace chr {
+
+namespace {
+
+struct BrickCoord {
+    int32_t bx, by, bz;
+    int64_t b;  // linear brick index
+};
+
+__device__ __forceinline__ bool brick_of_warp(const CodecParams &p, BrickCoord &c)
+{
+    int warp = threadIdx.x >> 5;
+    int64_t g = blockIdx.x;
+    int32_t gx = (int32_t)(g % p.ngx);
+    int64_t rest = g / p.ngx;
+    c.by = (int32_t)(rest % p.nby);
+    c.bz = (int32_t)(rest / p.nby);
+    c.bx = gx * kWarpsPerBlock + warp;
+    c.b = c.bx + (int64_t)p.nbx * (c.by + (int64_t)p.nby * c.bz);
+    return c.bx < p.nbx;
+}
+
+// Loads the lane's two rows of the field; out-of-grid values read as 0 and are
+// flagged off in *valid (bit s*8 + x).
+__device__ __forceinline__ void load_rows(const CodecParams &p, const BrickCoord &c, int lane, float (&v)[2][8],
+                                          uint32_t &valid)
+{
+    const int64_t x0 = (int64_t)c.bx * 8;
+    const int ex = (int)((p.nx - x0) < 8 ? (p.nx - x0) : 8);
+    const bool vec = (ex == 8) && ((p.nx & 3) == 0);
+    valid = 0;
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+        const int64_t y = (int64_t)c.by * 8 + (lane & 7);
+        const int64_t z = (int64_t)c.bz * 8 + (lane >> 3) + 4 * s;
+        const bool rowok = (y < p.ny) && (z < p.nz);
+#pragma unroll
+        for (int x = 0; x < 8; x++) v[s][x] = 0.0f;
+        if (!rowok) continue;
+        const float *row = p.f + x0 + p.nx * (y + p.ny * z);
+        if (vec) {
+            float4 a = ld_stream_f4(reinterpret_cast<const float4 *>(row));
+            float4 b = ld_stream_f4(reinterpret_cast<const float4 *>(row + 4));
+            v[s][0] = a.x; v[s][1] = a.y; v[s][2] = a.z; v[s][3] = a.w;
+            v[s][4] = b.x; v[s][5] = b.y; v[s][6] = b.z; v[s][7] = b.w;
+            valid |= 0xffu << (8 * s);
+        } else {
+#pragma unroll
+            for (int x = 0; x < 8; x++)
+                if (x < ex) {
+                    v[s][x] = __ldg(row + x);
+                    valid |= 1u << (8 * s + x);
+                }
+        }
+    }
+}
+
+template <bool PACK>
+__global__ void __launch_bounds__(256) k_encode(const __grid_constant__ CodecParams p)
+{
+    __shared__ __align__(16) uint32_t s_zz[kWarpsPerBlock][512];
+    BrickCoord c;
+    if (!brick_of_warp(p, c)) return;  // the whole warp leaves; no block barrier below
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ly = lane & 7;
+
+    float f[2][8];
+    uint32_t valid;
+    load_rows(p, c, lane, f, valid);
+
+    float R[2][8];
+#pragma unroll
+    for (int s = 0; s < 2; s++)
+#pragma unroll
+        for (int x = 0; x < 8; x++) R[s][x] = 0.0f;
+
+    for (int l = 0; l < p.nlevels; l++) {
+        int32_t q[2][8];
+        uint32_t excm = 0;
+#pragma unroll
+        for (int s = 0; s < 2; s++)
+#pragma unroll
+            for (int x = 0; x < 8; x++) {
+                q[s][x] = 0;
+                if ((valid >> (8 * s + x)) & 1u) {
+                    float Rn;
+                    int32_t qq;
+                    bool e = level_step(f[s][x], R[s][x], l == 0, p.e[l], p.two_e[l], p.inv2e[l], p.K, p.nK,
+                                        p.fix != 0, qq, Rn);
+                    q[s][x] = qq;
+                    R[s][x] = Rn;
+                    if (e) excm |= 1u << (8 * s + x);
+                }
+            }
+
+        // Lorenzo residual = first differences along x, then y, then z, with
+        // zero outside the brick.  Padding slots and slot 0 (the anchor) pack 0.
+        uint32_t zl[2][8], zn[2][8];
+        uint32_t maxl = 0, maxn = 0;
+        {
+            int32_t d[2][8];
+#pragma unroll
+            for (int s = 0; s < 2; s++) {
+#pragma unroll
+                for (int x = 7; x > 0; x--) d[s][x] = (int32_t)((uint32_t)q[s][x] - (uint32_t)q[s][x - 1]);
+                d[s][0] = q[s][0];
+            }
+#pragma unroll
+            for (int s = 0; s < 2; s++)
+#pragma unroll
+                for (int x = 0; x < 8; x++) {
+                    int32_t up = __shfl_up_sync(CHR_FULL_MASK, d[s][x], 1, 8);
+                    if (ly > 0) d[s][x] = (int32_t)((uint32_t)d[s][x] - (uint32_t)up);
+                }
+#pragma unroll
+            for (int x = 0; x < 8; x++) {
+                const int src = (lane + 24) & 31;  // lane - 8, or lane + 24 for the first z of set 1
+                int32_t a = __shfl_sync(CHR_FULL_MASK, d[0][x], src);
+                int32_t b = __shfl_sync(CHR_FULL_MASK, d[1][x], src);
+                if (lane >= 8) d[0][x] = (int32_t)((uint32_t)d[0][x] - (uint32_t)a);
+                d[1][x] = (int32_t)((uint32_t)d[1][x] - (uint32_t)(lane >= 8 ? b : a));
+            }
+#pragma unroll
+            for (int s = 0; s < 2; s++)
+#pragma unroll
+                for (int x = 0; x < 8; x++) {
+                    const bool live = ((valid >> (8 * s + x)) & 1u) && !(s == 0 && lane == 0 && x == 0);
+                    zl[s][x] = live ? zigzag(d[s][x]) : 0u;
+                    zn[s][x] = live ? zigzag(q[s][x]) : 0u;
+                    maxl = max(maxl, zl[s][x]);
+                    maxn = max(maxn, zn[s][x]);
+                }
+        }
+        maxl = __reduce_max_sync(CHR_FULL_MASK, maxl);
+        maxn = __reduce_max_sync(CHR_FULL_MASK, maxn);
+        const int wl = bitlen(maxl), wn = bitlen(maxn);
+        const int mode = (wl < wn) ? 1 : 0;
+        const int w = mode ? wl : wn;
+        const uint32_t cnt0 = __popc(excm & 0xffu), cnt1 = __popc(excm >> 8);
+        const uint32_t nexc = __reduce_add_sync(CHR_FULL_MASK, cnt0 + cnt1);
+        const int32_t anchor = __shfl_sync(CHR_FULL_MASK, q[0][0], 0);
+
+        if (!PACK) {
+            if (lane == 0)
+                p.recs[l][c.b] = make_uint4(0u, 0u, (uint32_t)anchor,
+                                            (uint32_t)w | ((uint32_t)mode << 8) | (nexc << 16));
+            continue;
+        }
+
+        const uint4 rec = p.recs[l][c.b];  // wsum and exc_off filled by the scan
+        if (w > 0) {
+            uint32_t *buf = s_zz[warp];
+#pragma unroll
+            for (int s = 0; s < 2; s++) {
+                const int slot = 8 * (lane + 32 * s);
+                uint32_t z[8];
+#pragma unroll
+                for (int x = 0; x < 8; x++) z[x] = mode ? zl[s][x] : zn[s][x];
+                const uint4 lo = make_uint4(z[0], z[1], z[2], z[3]);
+                const uint4 hi = make_uint4(z[4], z[5], z[6], z[7]);
+                *reinterpret_cast<uint4 *>(buf + slot) = lo;
+                *reinterpret_cast<uint4 *>(buf + slot + 4) = hi;
+            }
+            __syncwarp();
+            uint32_t *dst = p.words[l] + 16ull * rec.x;
+            const int nw = 16 * w;
+            for (int j = lane; j < nw; j += 32) {
+                const int bit0 = 32 * j;
+                const int s0 = bit0 / w;
+                const int s1 = min(511, (bit0 + 31) / w);
+                uint32_t word = 0;
+                for (int s = s0; s <= s1; s++) {
+                    const int pos = s * w - bit0;
+                    const uint32_t v = buf[s];
+                    word |= (pos >= 0) ? (v << pos) : (v >> (-pos));
+                }
+                dst[j] = word;
+            }
+            __syncwarp();
+        }
+        if (nexc > 0) {
+            const uint32_t inc0 = warp_incl_scan_u32(cnt0, lane);
+            const uint32_t tot0 = __shfl_sync(CHR_FULL_MASK, inc0, 31);
+            const uint32_t inc1 = warp_incl_scan_u32(cnt1, lane);
+#pragma unroll
+            for (int s = 0; s < 2; s++) {
+                uint32_t pos = rec.y + (s == 0 ? inc0 - cnt0 : tot0 + inc1 - cnt1);
+#pragma unroll
+                for (int x = 0; x < 8; x++) {
+                    if ((excm >> (8 * s + x)) & 1u) {
+                        p.exc_idx[l][pos] = (uint16_t)(8 * (lane + 32 * s) + x);
+                        p.exc_val[l][pos] = __float_as_uint(f[s][x]);
+                        pos++;
+                    }
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_decode(const __grid_constant__ CodecParams p)
+{
+    __shared__ __align__(16) uint32_t s_buf[kWarpsPerBlock][520];
+    BrickCoord c;
+    if (!brick_of_warp(p, c)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ly = lane & 7;
+    uint32_t *buf = s_buf[warp];
+
+    float R[2][8];
+    for (int l = 0; l < p.nlevels; l++) {
+        const uint4 rec = __ldg(p.recs[l] + c.b);
+        const int w = min((int)(rec.w & 0xffu), 32), mode = (int)((rec.w >> 8) & 0xffu);
+        const int nexc = (int)(rec.w >> 16);
+        uint32_t q[2][8];  // unsigned: prefix sums wrap like the encoder's int32
+        if (w > 0) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(p.words[l] + 16ull * rec.x);
+            for (int j = lane; j < 4 * w; j += 32) reinterpret_cast<uint4 *>(buf)[j] = ld_stream_u4(src + j);
+            __syncwarp();
+            const uint32_t mask = width_mask(w);
+#pragma unroll
+            for (int s = 0; s < 2; s++)
+#pragma unroll
+                for (int x = 0; x < 8; x++) {
+                    const int slot = 8 * (lane + 32 * s) + x;
+                    const int pos = slot * w;
+                    const int wd = pos >> 5;
+                    const uint32_t z = __funnelshift_r(buf[wd], buf[wd + 1], pos & 31) & mask;
+                    q[s][x] = (uint32_t)unzigzag(z);
+                }
+            __syncwarp();
+        } else {
+#pragma unroll
+            for (int s = 0; s < 2; s++)
+#pragma unroll
+                for (int x = 0; x < 8; x++) q[s][x] = 0u;
+        }
+        if (lane == 0) q[0][0] = rec.z;  // anchor
+
+        if (mode == 1) {  // inverse Lorenzo: inclusive prefix sums along x, y, z
+#pragma unroll
+            for (int s = 0; s < 2; s++)
+#pragma unroll
+                for (int x = 1; x < 8; x++) q[s][x] += q[s][x - 1];
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1)
+#pragma unroll
+                for (int s = 0; s < 2; s++)
+#pragma unroll
+                    for (int x = 0; x < 8; x++) {
+                        uint32_t t = __shfl_up_sync(CHR_FULL_MASK, q[s][x], o, 8);
+                        if (ly >= o) q[s][x] += t;
+                    }
+#pragma unroll
+            for (int o = 8; o < 32; o <<= 1)
+#pragma unroll
+                for (int s = 0; s < 2; s++)
+#pragma unroll
+                    for (int x = 0; x < 8; x++) {
+                        uint32_t t = __shfl_up_sync(CHR_FULL_MASK, q[s][x], o);
+                        if (lane >= o) q[s][x] += t;
+                    }
+#pragma unroll
+            for (int x = 0; x < 8; x++) q[1][x] += __shfl_sync(CHR_FULL_MASK, q[0][x], 24 + ly);
+        }
+
+        const float two_e = p.two_e[l];
+#pragma unroll
+        for (int s = 0; s < 2; s++)
+#pragma unroll
+            for (int x = 0; x < 8; x++) {
+                const float P = __fmul_rn(__int2float_rn((int32_t)q[s][x]), two_e);
+                R[s][x] = (l == 0) ? P : __fadd_rn(R[s][x], P);
+            }
+
+        if (nexc > 0) {  // vertices stored exactly at this level
+            float *fb = reinterpret_cast<float *>(buf);
+#pragma unroll
+            for (int s = 0; s < 2; s++) {
+                const int slot = 8 * (lane + 32 * s);
+                *reinterpret_cast<float4 *>(fb + slot) = make_float4(R[s][0], R[s][1], R[s][2], R[s][3]);
+                *reinterpret_cast<float4 *>(fb + slot + 4) = make_float4(R[s][4], R[s][5], R[s][6], R[s][7]);
+            }
+            __syncwarp();
+            const uint16_t *ei = p.exc_idx[l] + rec.y;
+            const uint32_t *ev = p.exc_val[l] + rec.y;
+            for (int j = lane; j < nexc; j += 32) fb[__ldg(ei + j) & 511] = __uint_as_float(__ldg(ev + j));
+            __syncwarp();
+#pragma unroll
+            for (int s = 0; s < 2; s++) {
+                const int slot = 8 * (lane + 32 * s);
+                float4 a = *reinterpret_cast<const float4 *>(fb + slot);
+                float4 b = *reinterpret_cast<const float4 *>(fb + slot + 4);
+                R[s][0] = a.x; R[s][1] = a.y; R[s][2] = a.z; R[s][3] = a.w;
+                R[s][4] = b.x; R[s][5] = b.y; R[s][6] = b.z; R[s][7] = b.w;
+            }
+            __syncwarp();
+        }
+    }
+
+    // store the lane's two rows
+    const int64_t x0 = (int64_t)c.bx * 8;
+    const int ex = (int)((p.nx - x0) < 8 ? (p.nx - x0) : 8);
+    const bool vec = (ex == 8) && ((p.nx & 3) == 0);
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+        const int64_t y = (int64_t)c.by * 8 + ly;
+        const int64_t z = (int64_t)c.bz * 8 + (lane >> 3) + 4 * s;
+        if (y >= p.ny || z >= p.nz) continue;
+        float *row = p.out + x0 + p.nx * (y + p.ny * z);
+        if (vec) {
+            __stcs(reinterpret_cast<float4 *>(row), make_float4(R[s][0], R[s][1], R[s][2], R[s][3]));
+            __stcs(reinterpret_cast<float4 *>(row + 4), make_float4(R[s][4], R[s][5], R[s][6], R[s][7]));
+        } else {
+#pragma unroll
+            for (int x = 0; x < 8; x++)
+                if (x < ex) row[x] = R[s][x];
+        }
+    }
+}
+
+// ---- record scans: wsum / exc_off = exclusive prefix over bricks ----------
+
+constexpr int kScanThreads = 256;
+constexpr int kScanPerThread = 8;
+constexpr int kScanChunk = kScanThreads * kScanPerThread;  // bricks per block
+
+struct ScanArgs {
+    uint4 *recs[CHR_MAX_LEVELS];
+    int64_t nbricks;
+    int64_t nchunks;
+    uint2 *chunk;  // [nlevels][nchunks] (sum w, sum nexc) -> exclusive offsets
+    uint64_t *totals;
+};
+
+__device__ __forceinline__ uint2 rec_counts(const uint4 &r) { return make_uint2(r.w & 0xffu, r.w >> 16); }
+
+// block-wide exclusive scan of (w, nexc) pairs packed in 64 bits
+__device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t *s_warp, uint64_t &total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t inc = warp_incl_scan_u64(v, lane);
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t t = (lane < kScanThreads / 32) ? s_warp[lane] : 0;
+        uint64_t ti = warp_incl_scan_u64(t, lane);
+        if (lane < kScanThreads / 32) s_warp[lane] = ti - t;
+        if (lane == kScanThreads / 32 - 1) s_warp[kScanThreads / 32] = ti;
+    }
+    __syncthreads();
+    total = s_warp[kScanThreads / 32];
+    uint64_t r = s_warp[warp] + inc - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const __grid_constant__ ScanArgs a)
+{
+    __shared__ uint64_t s_warp[kScanThreads / 32 + 1];
+    const int l = blockIdx.y;
+    const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanPerThread;
+    uint64_t v = 0;
+    for (int i = 0; i < kScanPerThread; i++) {
+        int64_t b = base + i;
+        if (b < a.nbricks) {
+            uint2 c = rec_counts(a.recs[l][b]);
+            v += (uint64_t)c.x | ((uint64_t)c.y << 32);
+        }
+    }
+    uint64_t total;
+    block_excl_scan(v, s_warp, total);
+    if (threadIdx.x == 0) a.chunk[(int64_t)l * a.nchunks + blockIdx.x] = make_uint2((uint32_t)total, (uint32_t)(total >> 32));
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_chunks(const __grid_constant__ ScanArgs a)
+{
+    __shared__ uint64_t s_warp[kScanThreads / 32 + 1];
+    const int l = blockIdx.x;
+    uint2 *ch = a.chunk + (int64_t)l * a.nchunks;
+    uint64_t carry_w = 0, carry_e = 0;
+    for (int64_t c0 = 0; c0 < a.nchunks; c0 += kScanThreads) {
+        int64_t c = c0 + threadIdx.x;
+        uint2 v = (c < a.nchunks) ? ch[c] : make_uint2(0, 0);
+        uint64_t packed = (uint64_t)v.x | ((uint64_t)v.y << 32);
+        uint64_t total;
+        uint64_t ex = block_excl_scan(packed, s_warp, total);
+        if (c < a.nchunks) ch[c] = make_uint2((uint32_t)(carry_w + (ex & 0xffffffffull)), (uint32_t)(carry_e + (ex >> 32)));
+        carry_w += total & 0xffffffffull;
+        carry_e += total >> 32;
+    }
+    if (threadIdx.x == 0) {
+        a.totals[2 * l] = carry_w;
+        a.totals[2 * l + 1] = carry_e;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const __grid_constant__ ScanArgs a)
+{
+    __shared__ uint64_t s_warp[kScanThreads / 32 + 1];
+    const int l = blockIdx.y;
+    const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanPerThread;
+    uint4 r[kScanPerThread];
+    uint64_t v = 0;
+    for (int i = 0; i < kScanPerThread; i++) {
+        int64_t b = base + i;
+        r[i] = (b < a.nbricks) ? a.recs[l][b] : make_uint4(0, 0, 0, 0);
+        uint2 c = rec_counts(r[i]);
+        v += (uint64_t)c.x | ((uint64_t)c.y << 32);
+    }
+    uint64_t total;
+    uint64_t ex = block_excl_scan(v, s_warp, total);
+    const uint2 off = a.chunk[(int64_t)l * a.nchunks + blockIdx.x];
+    uint32_t ws = off.x + (uint32_t)(ex & 0xffffffffull), es = off.y + (uint32_t)(ex >> 32);
+    for (int i = 0; i < kScanPerThread; i++) {
+        int64_t b = base + i;
+        if (b < a.nbricks) {
+            r[i].x = ws;
+            r[i].y = es;
+            a.recs[l][b] = r[i];
+            uint2 c = rec_counts(r[i]);
+            ws += c.x;
+            es += c.y;
+        }
+    }
+}
+
+}  // namespace
+
+static dim3 codec_grid(const CodecParams &p) { return dim3((unsigned)((int64_t)p.ngx * p.nby * p.nbz)); }
+
+cudaError_t launch_encode(const CodecParams &p, bool pack, cudaStream_t s)
+{
+    if (pack)
+        k_encode<true><<<codec_grid(p), 256, 0, s>>>(p);
+    else
+        k_encode<false><<<codec_grid(p), 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decode(const CodecParams &p, cudaStream_t s)
+{
+    k_decode<<<codec_grid(p), 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+size_t scan_scratch_bytes(int64_t nbricks, int nlevels)
+{
+    int64_t nchunks = (nbricks + kScanChunk - 1) / kScanChunk;
+    return (size_t)nchunks * nlevels * sizeof(uint2) + 256;
+}
+
+cudaError_t launch_scan_records(uint4 *const *recs, int nlevels, int64_t nbricks, void *scratch, uint64_t *totals,
+                                cudaStream_t s)
+{
+    ScanArgs a;
+    for (int l = 0; l < CHR_MAX_LEVELS; l++) a.recs[l] = (l < nlevels) ? recs[l] : nullptr;
+    a.nbricks = nbricks;
+    a.nchunks = (nbricks + kScanChunk - 1) / kScanChunk;
+    a.chunk = reinterpret_cast<uint2 *>(scratch);
+    a.totals = totals;
+    dim3 g((unsigned)a.nchunks, (unsigned)nlevels);
+    k_scan_reduce<<<g, kScanThreads, 0, s>>>(a);
+    k_scan_chunks<<<nlevels, kScanThreads, 0, s>>>(a);
+    k_scan_apply<<<g, kScanThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace chr

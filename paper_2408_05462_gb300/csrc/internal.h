@@ -1,0 +1,97 @@
+// Host-side declarations shared by the libchr translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "chr.h"
+
+namespace chr {
+
+constexpr int kWarpsPerBlock = 8;  // codec: one warp per 8^3 brick, 8 bricks along x per block
+constexpr int kMcBricksX = 4;      // marching cubes: a tile is 4 cell bricks along x (32x8x8 cells)
+constexpr int kMcIsoPerPass = 4;   // isovalues classified per read of the field
+
+struct Grid {
+    int64_t nx, ny, nz, N;
+    int64_t nbx, nby, nbz, nbricks;  // 8^3 vertex bricks
+};
+
+inline Grid make_grid(chr_dims d)
+{
+    Grid g;
+    g.nx = d.nx;
+    g.ny = d.ny;
+    g.nz = d.nz;
+    g.N = d.nx * d.ny * d.nz;
+    g.nbx = (d.nx + 7) / 8;
+    g.nby = (d.ny + 7) / 8;
+    g.nbz = (d.nz + 7) / 8;
+    g.nbricks = g.nbx * g.nby * g.nbz;
+    return g;
+}
+
+// Codec launch parameters (passed by value to the kernels).
+struct CodecParams {
+    const float *f;  // encode: input field
+    float *out;      // decode: output field
+    int64_t nx, ny, nz;
+    int32_t nbx, nby, nbz, ngx;  // ngx = ceil(nbx / 8) brick groups along x
+    int32_t nlevels;             // encode: levels to build; decode: levels to apply (target + 1)
+    int32_t nK;
+    int32_t fix;
+    float e[CHR_MAX_LEVELS], two_e[CHR_MAX_LEVELS], inv2e[CHR_MAX_LEVELS];
+    float K[CHR_MAX_ISO];
+    uint4 *recs[CHR_MAX_LEVELS];
+    uint32_t *words[CHR_MAX_LEVELS];
+    uint16_t *exc_idx[CHR_MAX_LEVELS];
+    uint32_t *exc_val[CHR_MAX_LEVELS];
+};
+
+cudaError_t launch_encode(const CodecParams &p, bool pack, cudaStream_t s);
+cudaError_t launch_decode(const CodecParams &p, cudaStream_t s);
+// Exclusive scans of the widths and exception counts of each level's records;
+// totals[2*l] = sum of w, totals[2*l+1] = exceptions.  scratch needs
+// scan_scratch_bytes(nbricks, nlevels).
+size_t scan_scratch_bytes(int64_t nbricks, int nlevels);
+cudaError_t launch_scan_records(uint4 *const *recs, int nlevels, int64_t nbricks, void *scratch, uint64_t *totals,
+                                cudaStream_t s);
+
+// Marching cubes over a plain field.
+size_t mc_workspace_bytes(const Grid &g, int n_iso);
+cudaError_t launch_mc(const float *field, const Grid &g, const float *iso, int n_iso, float *tris, uint64_t cap,
+                      uint64_t *ntris, uint32_t *err, void *workspace, cudaStream_t s);
+
+// Error-bound translation (radix selection over D).
+struct TranslateScratch {
+    unsigned long long *hist;  // 256 counters
+    unsigned long long *count; // |D|
+    unsigned int *minbits;     // min D as float bits
+};
+size_t translate_scratch_bytes();
+cudaError_t launch_translate_pass(const float *field, const Grid &g, const float *K, int nK, int pass,
+                                  uint32_t prefix, bool min_only, TranslateScratch sc, cudaStream_t s);
+
+void set_error(const std::string &msg);
+
+}  // namespace chr
+
+struct chr_handle {
+    chr::Grid g;
+    chr_dims dims;
+    uint32_t nlevels, n_iso, topo_mode, flags;
+    float topo_accuracy, eb_translated;
+    uint64_t D_count;
+    float eb[CHR_MAX_LEVELS], two_e[CHR_MAX_LEVELS], inv2e[CHR_MAX_LEVELS];
+    float iso[CHR_MAX_ISO];
+    uint64_t nwords[CHR_MAX_LEVELS], nexc[CHR_MAX_LEVELS];
+    uint4 *d_recs[CHR_MAX_LEVELS];
+    uint32_t *d_words[CHR_MAX_LEVELS];
+    uint16_t *d_exc_idx[CHR_MAX_LEVELS];
+    uint32_t *d_exc_val[CHR_MAX_LEVELS];
+    size_t sz_recs, sz_words[CHR_MAX_LEVELS], sz_exc_idx[CHR_MAX_LEVELS], sz_exc_val[CHR_MAX_LEVELS];
+    chr_allocator alloc;
+    bool default_alloc;
+    cudaStream_t stream;
+};

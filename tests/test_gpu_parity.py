@@ -1,0 +1,199 @@
+"""GPU parity: libchr (through its C ABI) against the CPU oracle on the same
+seeded inputs.  Integer results (records, packed words, exceptions, triangle
+counts, case-determined triangle order) must match bit for bit; decoded
+fields bit for bit; vertex positions within 1e-5 of a cell edge plus one
+float32 ulp of the coordinate (tests/helpers.py)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import compare_mesh
+from paper_2408_05462_gb300 import build as chr_build
+from paper_2408_05462_gb300 import chr, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    chr_build.build()
+    chr.lib()
+
+
+def _dev(f):
+    return torch.from_numpy(np.ascontiguousarray(f)).cuda()
+
+
+def _extract(f, isovalues, cap=None):
+    fd = _dev(f)
+    if cap is None:
+        cap = max(64, 5 * f.size // 2)
+    tris, counts, err = chr.isosurface_extract(fd, isovalues, cap)
+    torch.cuda.synchronize()
+    return tris.cpu().numpy(), counts.cpu().numpy(), int(err.item())
+
+
+def _fields_mc():
+    blobs = synth.gaussian_blobs(64, seed=64)
+    turb = synth.turbulence((37, 50, 65), seed=3)
+    noise = synth.uniform_noise((17, 9, 23), 5)
+    return [
+        ("blobs64", blobs, [0.5 * float(blobs.max())]),
+        ("turb_odd_4iso", turb, [-1.0, -0.5, 0.5, 1.0]),
+        ("turb_odd_6iso", turb, [-1.5, -0.25, 0.0, 0.3, 0.9, 2.0]),
+        ("noise", noise, [0.0, 0.5]),
+    ]
+
+
+@pytest.mark.parametrize("name,f,isos", _fields_mc(), ids=lambda v: v if isinstance(v, str) else "")
+def test_mc_matches_oracle(name, f, isos):
+    nz, ny, nx = f.shape
+    tris, counts, err = _extract(f, isos)
+    assert err == 0
+    for j, k in enumerate(isos):
+        mesh = oracle.mc(f, k)
+        assert int(counts[j]) == mesh.ntri, (name, k)
+        compare_mesh(tris[j, :mesh.ntri], mesh, (nx, ny, nz), f"{name} k={k}")
+
+
+@pytest.mark.parametrize("case", ["constant", "all_equal_k", "checker", "plane", "tiny"])
+def test_mc_degenerate_fields(case):
+    if case == "constant":
+        f = np.full((9, 10, 11), 3.0, np.float32)
+        k = 1.0
+    elif case == "all_equal_k":
+        f = np.full((9, 10, 11), 0.5, np.float32)
+        k = 0.5
+    elif case == "checker":
+        z, y, x = np.meshgrid(np.arange(12), np.arange(13), np.arange(14), indexing="ij")
+        f = np.where((x + y + z) % 2 == 0, -1.0, 1.0).astype(np.float32)
+        k = 0.0
+    elif case == "plane":
+        f = synth.plane_field((40, 33, 20), (0, 0, 1), 10.375)
+        k = 0.0
+    else:
+        f = synth.uniform_noise((2, 2, 2), 1)
+        k = 0.0
+    nz, ny, nx = f.shape
+    tris, counts, err = _extract(f, [k])
+    mesh = oracle.mc(f, k)
+    assert err == 0 and int(counts[0]) == mesh.ntri
+    compare_mesh(tris[0, :mesh.ntri], mesh, (nx, ny, nz), case)
+
+
+def test_mc_overflow_reports_true_count_and_stays_in_bounds():
+    f = synth.turbulence(32, seed=8)
+    mesh = oracle.mc(f, 0.0)
+    cap = mesh.ntri // 3
+    fd = _dev(f)
+    guard = 1 << 12
+    buf = torch.full((cap * 9 + guard,), 7.0, dtype=torch.float32, device="cuda")
+    tris = buf[:cap * 9].view(1, cap, 3, 3)
+    tris, counts, err = chr.isosurface_extract(fd, [0.0], cap, tris=tris)
+    torch.cuda.synchronize()
+    assert int(counts[0]) == mesh.ntri
+    assert int(err.item()) & chr.ERR_OVERFLOW_BIT
+    assert torch.all(buf[cap * 9:] == 7.0)
+    # the triangles that fit are the first `cap` of the full output
+    full, counts2, err2 = _extract(f, [0.0])
+    assert np.array_equal(tris.cpu().numpy()[0], full[0, :cap])
+
+
+def _compare_codec(h, enc, f, label):
+    parsed = chr.parse_serialized(chr.chr_serialize(h))
+    assert parsed["nlevels"] == enc.nlevels
+    for l in range(enc.nlevels):
+        lv = parsed["levels"][l]
+        assert np.array_equal(lv["recs"], enc.recs[l]), f"{label}: records differ at level {l}"
+        assert np.array_equal(lv["words"], enc.words[l]), f"{label}: packed words differ at level {l}"
+        assert np.array_equal(lv["exc_idx"], enc.exc_idx[l]), f"{label}: exception slots differ at level {l}"
+        assert np.array_equal(lv["exc_val"], enc.exc_val[l]), f"{label}: exception values differ at level {l}"
+        dec = h.reconstruct(l).cpu().numpy()
+        assert np.array_equal(dec.view(np.uint32), enc.R[l].view(np.uint32)), f"{label}: level {l} decode differs"
+
+
+def _codec_cases():
+    blobs = synth.gaussian_blobs(64, seed=64)
+    rb = synth.value_range(blobs)
+    turb = synth.turbulence((37, 50, 65), seed=3)
+    rt = synth.value_range(turb)
+    adv = synth.uniform_noise((20, 19, 18), 2, -4, 4)
+    adv.ravel()[::97] = np.nan
+    adv.ravel()[5::101] = np.inf
+    adv.ravel()[7::103] = -1e30
+    adv.ravel()[11::89] = 0.5           # exactly on an isovalue
+    adv.ravel()[13::83] = -0.0
+    ints = np.random.Generator(np.random.PCG64(9)).integers(-(1 << 20), 1 << 20, size=(16, 24, 40)).astype(np.float32)
+    return [
+        ("blobs64", blobs, [1e-2 * rb, 1e-3 * rb], [0.5 * float(blobs.max())], "fix"),
+        ("turb_odd", turb, [1e-2 * rt, 1e-3 * rt, 1e-4 * rt], [-1.0, -0.5, 0.5, 1.0], "fix"),
+        ("turb_nofix", turb, [1e-2 * rt, 1e-3 * rt], [], "none"),
+        ("adversarial", adv, [0.25, 0.01, 1e-4], [0.5, -1.0], "fix"),
+        ("integers", ints, [0.5], [], "none"),
+    ]
+
+
+@pytest.mark.parametrize("name,f,eb,isos,topo", _codec_cases(), ids=lambda v: v if isinstance(v, str) else "")
+def test_codec_matches_oracle(name, f, eb, isos, topo):
+    eb = np.array(eb, np.float32)
+    enc = oracle.encode(f, eb, isos, fix=(topo == "fix"))
+    h = chr.chr_compress(_dev(f), eb, isos, topo=topo)
+    _compare_codec(h, enc, f, name)
+    st = h.stats()
+    assert st["exceptions"] == [int(e.size) for e in enc.exc_idx]
+
+
+def test_serialize_roundtrip_and_decode():
+    f = synth.turbulence(40, seed=12)
+    r = synth.value_range(f)
+    h = chr.chr_compress(_dev(f), [1e-2 * r, 1e-3 * r], [0.0, 1.0])
+    blob = chr.chr_serialize(h)
+    h2 = chr.chr_deserialize(blob)
+    assert chr.chr_serialize(h2) == blob
+    for l in range(2):
+        a = h.reconstruct(l).cpu().numpy()
+        b = h2.reconstruct(l).cpu().numpy()
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+@pytest.mark.parametrize("acc", [1.0, 0.99, 0.95, 0.8])
+def test_translate_matches_oracle(acc):
+    f = synth.turbulence((33, 40, 29), seed=int(round(acc * 100)))
+    K = [-0.5, 0.25, 1.0]
+    eb_o, n_o = oracle.translate_eb(f, K, acc)
+    eb_g, n_g = chr.chr_topo_translate(_dev(f), K, acc)
+    assert n_g == n_o
+    assert np.float32(eb_g).view(np.uint32) == np.float32(eb_o).view(np.uint32)
+
+
+def test_compress_translate_mode_matches_oracle():
+    f = synth.turbulence(36, seed=77)
+    K = [-0.5, 0.5]
+    eb_user = np.array([0.05, 0.005], np.float32)
+    h = chr.chr_compress(_dev(f), eb_user, K, topo="translate", accuracy=0.95)
+    eb_t, _ = oracle.translate_eb(f, K, 0.95)
+    eff = np.minimum(eb_user, np.float32(eb_t)).astype(np.float32)
+    st = h.stats()
+    assert np.array_equal(np.array(st["eb"], np.float32), eff)
+    enc = oracle.encode(f, eff, [], fix=False)
+    _compare_codec(h, enc, f, "translate")
+
+
+def test_sign_preservation_on_gpu_output():
+    # topology preservation (Sec. 2.2): every case byte of every candidate
+    # isovalue is unchanged at every level, so meshes have identical counts
+    f = synth.turbulence(48, seed=31)
+    r = synth.value_range(f)
+    K = [-1.0, -0.5, 0.5, 1.0]
+    h = chr.chr_compress(_dev(f), [1e-2 * r, 1e-3 * r, 1e-4 * r], K)
+    _, counts_f, _ = _extract(f, K)
+    for l in range(3):
+        R = h.reconstruct(l)
+        for k in K:
+            assert torch.equal(R < k, _dev(f) < k)
+        err = (R.double() - _dev(f).double()).abs().max().item()
+        assert err < float(np.float32([1e-2 * r, 1e-3 * r, 1e-4 * r][l]))
+        _, counts_r, _ = _extract(R.cpu().numpy(), K)
+        assert np.array_equal(counts_r, counts_f)
