@@ -338,7 +338,7 @@ def main():
         "stages": stages,
         "triangles": ntri, "compressed_bytes": comp_bytes, "compression_ratio": 4.0 * N / comp_bytes,
         "exceptions": st["exceptions"],
-        "gpu_launches": 7 * args.steps,
+        "gpu_launches": 11 * args.steps,  # encode x2 + 3 record scans, decode, MC count + 3 tile scans + emit
         "e2e": e2e,
     }
     if rank == 0:

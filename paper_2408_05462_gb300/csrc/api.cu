@@ -263,6 +263,7 @@ chr_status chr_compress(const float *d_field, chr_dims dims, const chr_params *p
     if (!out) return fail(CHR_ERR_INVALID, "chr_compress: out is NULL");
     *out = nullptr;
     if (!d_field || !prm) return fail(CHR_ERR_INVALID, "chr_compress: NULL field or params");
+    if (reinterpret_cast<uintptr_t>(d_field) & 3u) return fail(CHR_ERR_INVALID, "chr_compress: misaligned field");
     if (!dims_ok(dims, why)) return fail(CHR_ERR_INVALID, "chr_compress: " + why);
     if (prm->nlevels < 1 || prm->nlevels > CHR_MAX_LEVELS || !prm->error_bounds)
         return fail(CHR_ERR_INVALID, "chr_compress: nlevels must be 1..8 with error_bounds");
@@ -370,6 +371,7 @@ chr_status chr_reconstruct(const chr_handle *h, uint32_t level, float *d_out, vo
 {
     if (!h || !d_out) return fail(CHR_ERR_INVALID, "chr_reconstruct: NULL handle or output");
     if (level >= h->nlevels) return fail(CHR_ERR_INVALID, "chr_reconstruct: level out of range");
+    if (reinterpret_cast<uintptr_t>(d_out) & 3u) return fail(CHR_ERR_INVALID, "chr_reconstruct: misaligned output");
     CodecParams p;
     fill_codec_params(h, p);
     p.out = d_out;
@@ -385,6 +387,7 @@ chr_status chr_topo_translate(const float *d_field, chr_dims dims, const float *
 {
     std::string why;
     if (!d_field || !eb_out) return fail(CHR_ERR_INVALID, "chr_topo_translate: NULL field or output");
+    if (reinterpret_cast<uintptr_t>(d_field) & 3u) return fail(CHR_ERR_INVALID, "chr_topo_translate: misaligned field");
     if (!dims_ok(dims, why)) return fail(CHR_ERR_INVALID, "chr_topo_translate: " + why);
     if (n_iso < 1 || n_iso > CHR_MAX_ISO || !isovalues)
         return fail(CHR_ERR_INVALID, "chr_topo_translate: n_iso must be 1..16 with isovalues");
@@ -413,6 +416,10 @@ chr_status isosurface_extract(const float *d_field, chr_dims dims, const float *
     for (uint32_t j = 0; j < n_iso; j++)
         if (!isfinite(isovalues[j])) return fail(CHR_ERR_INVALID, "isosurface_extract: isovalues must be finite");
     if (cap_tris > 0 && !d_tris) return fail(CHR_ERR_INVALID, "isosurface_extract: NULL triangle buffer");
+    if ((reinterpret_cast<uintptr_t>(d_field) & 3u) || (reinterpret_cast<uintptr_t>(d_tris) & 3u) ||
+        (reinterpret_cast<uintptr_t>(d_ntris) & 7u) || (reinterpret_cast<uintptr_t>(d_err) & 3u) ||
+        (reinterpret_cast<uintptr_t>(d_workspace) & 7u))
+        return fail(CHR_ERR_INVALID, "isosurface_extract: misaligned pointer");
     if (cap_tris > (1ull << 58)) return fail(CHR_ERR_INVALID, "isosurface_extract: cap_tris too large");
     const Grid g = make_grid(dims);
     if (!d_workspace || workspace_bytes < mc_workspace_bytes(g, (int)n_iso))

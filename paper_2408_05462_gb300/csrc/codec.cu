@@ -39,7 +39,7 @@ __device__ __forceinline__ void load_rows(const CodecParams &p, const BrickCoord
 {
     const int64_t x0 = (int64_t)c.bx * 8;
     const int ex = (int)((p.nx - x0) < 8 ? (p.nx - x0) : 8);
-    const bool vec = (ex == 8) && ((p.nx & 3) == 0);
+    const bool vec = (ex == 8) && ((p.nx & 3) == 0) && ((reinterpret_cast<uintptr_t>(p.f) & 15u) == 0);
     valid = 0;
 #pragma unroll
     for (int s = 0; s < 2; s++) {
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(256) k_decode(const __grid_constant__ CodecPar
     // store the lane's two rows
     const int64_t x0 = (int64_t)c.bx * 8;
     const int ex = (int)((p.nx - x0) < 8 ? (p.nx - x0) : 8);
-    const bool vec = (ex == 8) && ((p.nx & 3) == 0);
+    const bool vec = (ex == 8) && ((p.nx & 3) == 0) && ((reinterpret_cast<uintptr_t>(p.out) & 15u) == 0);
 #pragma unroll
     for (int s = 0; s < 2; s++) {
         const int64_t y = (int64_t)c.by * 8 + ly;

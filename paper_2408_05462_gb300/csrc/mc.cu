@@ -1,16 +1,30 @@
-// Marching cubes over a float32 field (paper Sec. 2.2; Lorensen & Cline):
-// per-cell case classification for up to 4 isovalues from one read of the
-// field, a block scan of triangle counts, a single-pass decoupled look-back
-// (Merrill & Garland) for the global output offsets, and edge interpolation
-// + triangle emission.
+// Marching cubes over a float32 field (paper Sec. 2.2; Lorensen & Cline).
 //
-// Tile = 4 cell bricks along x = 32x8x8 cells; a block of 256 threads stages
-// the tile's 33x9x9 vertices in shared memory.  Thread t owns brick t>>6 of
-// the tile and the 8 cells of row (y,z) = (t&7, (t>>3)&7) of that brick, so
-// thread order is the output order: bricks x-fastest, cells x-fastest.
+// Three launches per group of up to 4 isovalues, none of which waits on
+// another block:
+//   k_mc_count  per 32x8x8-cell tile: inside masks by warp ballot, case bytes,
+//               triangle counts per isovalue -> tile_cnt
+//   k_tscan_*   exclusive scan of the tile counts -> tile_off, totals
+//   k_mc_emit   per tile again: case bytes, block scan, triangle -> cell map,
+//               edge interpolation, aligned 16-byte streaming stores at
+//               tile_off + local offset
+// Both tile kernels are persistent (one wave of blocks striding over tiles)
+// and prefetch the next tile's 36x9x9 vertex box with a TMA bulk tensor copy
+// into a second shared-memory buffer while the current tile is processed;
+// the box is zero-filled past the grid edge.  When the field cannot be
+// described by a tensor map (nx*4 not a multiple of 16, or a base address
+// not 16-byte aligned) the same kernels load the box with plain loads.
+//
+// Output order: 8^3-cell bricks in x-fastest order, cells of a brick
+// x-fastest, triangles of a cell in table order.  A tile is 4 bricks along
+// x; thread t owns brick t>>6 of the tile and the 8 cells of row
+// (y, z) = (t&7, (t>>3)&7), so thread order is output order.
+#include <string.h>
+
 #include "common.cuh"
 #include "internal.h"
 #include "mc_table.h"
+#include "tma.cuh"
 
 namespace chr {
 
@@ -18,192 +32,484 @@ namespace {
 
 __device__ const uint64_t g_mc_case[256] = CHR_MC_CASE_INIT;
 
-constexpr int kTX = 8 * kMcBricksX;  // cells per tile along x
-constexpr int kVX = kTX + 1;         // vertices per staged row
-constexpr int kPlane = 9 * kVX;      // floats per staged z-plane
+constexpr int kTX = 8 * kMcBricksX;                    // cells per tile along x (32)
+constexpr int kBoxX = kTX + 4;                         // vertices fetched per row (33 used; 144 bytes)
+constexpr int kVX = kBoxX;                             // shared-memory row pitch
+constexpr int kPlane = 9 * kVX;                        // floats per z-plane of the box
+constexpr int kRows = 81;                              // rows of the box (9 y x 9 z)
+constexpr int kTileBytes = kRows * kVX * 4;            // 11664
+constexpr int kBufBytes = ((kTileBytes + 127) / 128) * 128;
+constexpr int kCells = 64 * 8 * kMcBricksX;            // cells per tile (2048)
+constexpr int kMaxTriTile = kCells * CHR_MC_MAX_TRI;   // triangles per tile and isovalue, at most
+constexpr int kWarpStage = 32 * 9 + 4;                 // floats staged per warp: 32 triangles + alignment pad
+
+// dynamic shared memory (bytes)
+constexpr int kOffBuf = 0;                                       // 2 x float box
+constexpr int kOffRow = 2 * kBufBytes;                           // uint64 [4][81] inside masks per row
+constexpr int kOffTab = kOffRow + kMcIsoPerPass * kRows * 8;     // uint64 [256] case table
+constexpr int kCountSmem = kOffTab + 256 * 8 + 128;  // + alignment slack
+constexpr int kOffCase = kOffTab + 256 * 8;                      // uint8 [4][2048] case bytes
+constexpr int kOffMap = kOffCase + kMcIsoPerPass * kCells;       // uint16 [10240] triangle -> cell<<3|t
+constexpr int kOffStage = kOffMap + kMaxTriTile * 2;             // float [8][32*9+4]
+constexpr int kEmitSmem = kOffStage + 8 * kWarpStage * 4 + 128;  // + alignment slack
 
 struct McParams {
     const float *f;
     int64_t nx, ny, nz;
     int32_t ntx, ncby, ncbz;  // tiles along x; cell bricks along y, z
+    int32_t use_tma;
     int64_t ntiles;
     float k[kMcIsoPerPass];
     float *tris[kMcIsoPerPass];
     uint64_t cap;
-    uint64_t *ntris;  // [niso of this pass]
     uint32_t *err;
-    uint64_t *status;            // [ntiles][4]: count << 2 | flag (1 aggregate, 2 inclusive)
-    unsigned long long *counter; // dynamic tile ids, in launch order
+    uint4 *tile_cnt;     // [ntiles]: triangles per isovalue slot
+    uint64_t *tile_off;  // [ntiles][4]: global index of the tile's first triangle
 };
 
-// Exclusive prefix of the tiles before `tile` for one isovalue slot: a warp
-// inspects 32 predecessors at a time and stops at the first one that has
-// published its inclusive prefix.  Every poll loop is bounded.
-__device__ uint64_t lookback(const McParams &p, int64_t tile, int slot, int lane)
+struct TileXYZ {
+    int64_t x0, y0, z0;
+};
+
+__device__ __forceinline__ TileXYZ tile_origin(const McParams &p, int64_t tile)
 {
-    uint64_t excl = 0;
-    int64_t base = tile - 1;
-    while (true) {
-        const int64_t t = base - lane;
-        uint64_t v = 2ull;  // before tile 0: an inclusive prefix of 0
-        uint32_t spins = 0;
-        while (true) {
-            if (t >= 0) v = ld_relaxed_u64(p.status + t * kMcIsoPerPass + slot);
-            const bool ready = (v & 3ull) != 0;
-            if (__all_sync(CHR_FULL_MASK, ready)) break;
-            if (++spins > CHR_SPIN_LIMIT) {
-                if (!ready) v = 2ull;
-                if (lane == 0 && p.err) atomicOr(p.err, 1u << CHR_ERR_TIMEOUT);
-                break;
-            }
-            __nanosleep(100);
-        }
-        const uint32_t incl = __ballot_sync(CHR_FULL_MASK, (v & 3ull) == 2ull);
-        if (incl) {
-            const int first = __ffs(incl) - 1;
-            excl += warp_sum_u64(lane <= first ? (v >> 2) : 0ull);
-            return excl;
-        }
-        excl += warp_sum_u64(v >> 2);
-        base -= 32;
-    }
+    TileXYZ o;
+    o.x0 = (tile % p.ntx) * kTX;
+    o.y0 = ((tile / p.ntx) % p.ncby) * 8;
+    o.z0 = (tile / ((int64_t)p.ntx * p.ncby)) * 8;
+    return o;
 }
 
-__device__ __forceinline__ void emit_triangle(float *dst, uint64_t word, int t, const float *cell, float k, float cx,
-                                              float cy, float cz)
+// Plain loads of the box (fallback when no tensor map): zero past the edges.
+__device__ void load_box_plain(float *buf, const McParams &p, const TileXYZ &o)
 {
-    float out[9];
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        const int e = (int)((word >> (12 * t + 4 * c)) & 15u);
-        const int axis = e >> 2, m = e & 3;
-        const int ox = (axis == 0) ? 0 : (m & 1);
-        const int oy = (axis == 1) ? 0 : ((axis == 0) ? (m & 1) : (m >> 1));
-        const int oz = (axis == 2) ? 0 : (m >> 1);
-        const float *p0 = cell + ox + oy * kVX + oz * kPlane;
-        const int step = (axis == 0) ? 1 : (axis == 1) ? kVX : kPlane;
-        const float f0 = p0[0], f1 = p0[step];
-        const float tt = __fdiv_rn(__fsub_rn(k, f0), __fsub_rn(f1, f0));
-        float px = cx + (float)ox, py = cy + (float)oy, pz = cz + (float)oz;
-        if (axis == 0) px = __fadd_rn(px, tt);
-        if (axis == 1) py = __fadd_rn(py, tt);
-        if (axis == 2) pz = __fadd_rn(pz, tt);
-        out[3 * c + 0] = px;
-        out[3 * c + 1] = py;
-        out[3 * c + 2] = pz;
-    }
-#pragma unroll
-    for (int i = 0; i < 9; i++) __stcs(dst + i, out[i]);
-}
-
-template <int NISO>
-__global__ void __launch_bounds__(256) k_mc(const __grid_constant__ McParams p)
-{
-    __shared__ float s_f[9 * kPlane];
-    __shared__ uint64_t s_tab[256];
-    __shared__ uint64_t s_warp[9];
-    __shared__ uint64_t s_prefix[kMcIsoPerPass];
-    __shared__ long long s_tile;
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    s_tab[tid] = g_mc_case[tid];
-    if (tid == 0) s_tile = (long long)atomicAdd(p.counter, 1ull);
-    __syncthreads();
-    const int64_t tile = s_tile;
-    const int32_t tx = (int32_t)(tile % p.ntx);
-    const int32_t by = (int32_t)((tile / p.ntx) % p.ncby);
-    const int32_t bz = (int32_t)(tile / ((int64_t)p.ntx * p.ncby));
-    const int64_t gx0 = (int64_t)tx * kTX, gy0 = (int64_t)by * 8, gz0 = (int64_t)bz * 8;
-
-    // stage the tile's vertices (out-of-grid entries are never used by a valid cell)
-    for (int i = tid; i < 9 * kPlane; i += 256) {
+    for (int i = threadIdx.x; i < kRows * kVX; i += blockDim.x) {
         const int lx = i % kVX, r = i / kVX, ly = r % 9, lz = r / 9;
-        const int64_t gx = gx0 + lx, gy = gy0 + ly, gz = gz0 + lz;
-        float v = 0.0f;
-        if (gx < p.nx && gy < p.ny && gz < p.nz) v = __ldg(p.f + gx + p.nx * (gy + p.ny * gz));
-        s_f[i] = v;
+        const int64_t gx = o.x0 + lx, gy = o.y0 + ly, gz = o.z0 + lz;
+        buf[i] = (gx < p.nx && gy < p.ny && gz < p.nz) ? __ldg(p.f + gx + p.nx * (gy + p.ny * gz)) : 0.0f;
     }
-    __syncthreads();
+}
 
-    // classify this thread's 8 cells for every isovalue
-    const int j = tid >> 6, ly = tid & 7, lz = (tid >> 3) & 7;
-    const int64_t cx0 = gx0 + 8 * j, cy = gy0 + ly, cz = gz0 + lz;
-    int nvalid = 0;
-    if (cy < p.ny - 1 && cz < p.nz - 1 && cx0 < p.nx - 1) nvalid = (int)((p.nx - 1 - cx0) < 8 ? (p.nx - 1 - cx0) : 8);
-    const float *row = s_f + lz * kPlane + ly * kVX + 8 * j;
-    uint32_t m[NISO][4];
-#pragma unroll
-    for (int i = 0; i < NISO; i++) m[i][0] = m[i][1] = m[i][2] = m[i][3] = 0u;
-#pragma unroll
-    for (int x = 0; x < 9; x++) {
-        const float v0 = row[x], v1 = row[kVX + x], v2 = row[kPlane + x], v3 = row[kPlane + kVX + x];
+// Thread 0 starts the box copy of `tile` into buf.
+__device__ __forceinline__ void issue_box(float *buf, const CUtensorMap *map, uint64_t *mbar, const McParams &p,
+                                          int64_t tile)
+{
+    const TileXYZ o = tile_origin(p, tile);
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(mbar, (uint32_t)kTileBytes);
+    tma_load_3d(buf, map, (int32_t)o.x0, (int32_t)o.y0, (int32_t)o.z0, mbar);
+}
+
+// Inside masks (v < k) of the box rows: bit x of s_row[i*81 + row], x < 33.
+template <int NISO>
+__device__ __forceinline__ void row_masks(const float *buf, uint64_t *s_row, const McParams &p)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int row = warp; row < kRows; row += 8) {
+        const float v = buf[row * kVX + lane];
+        const float vh = buf[row * kVX + kTX];
 #pragma unroll
         for (int i = 0; i < NISO; i++) {
             const float k = p.k[i];
-            m[i][0] |= (uint32_t)(v0 < k) << x;
-            m[i][1] |= (uint32_t)(v1 < k) << x;
-            m[i][2] |= (uint32_t)(v2 < k) << x;
-            m[i][3] |= (uint32_t)(v3 < k) << x;
+            const uint32_t lo = __ballot_sync(CHR_FULL_MASK, v < k);
+            if (lane == 0) s_row[i * kRows + row] = (uint64_t)lo | ((uint64_t)(vh < k) << 32);
         }
     }
-    uint64_t packed = 0;
+}
+
+// Case byte of cell x (0..7) of a thread from its four 9-bit row masks.
+__device__ __forceinline__ uint32_t case_of(uint32_t m0, uint32_t m1, uint32_t m2, uint32_t m3, int x)
+{
+    return ((m0 >> x) & 3u) | (((m1 >> x) & 3u) << 2) | (((m2 >> x) & 3u) << 4) | (((m3 >> x) & 3u) << 6);
+}
+
+__device__ __forceinline__ int valid_cells(const McParams &p, const TileXYZ &o)
+{
+    const int tid = threadIdx.x;
+    const int j = tid >> 6, ly = tid & 7, lz = (tid >> 3) & 7;
+    const int64_t cx0 = o.x0 + 8 * j, cy = o.y0 + ly, cz = o.z0 + lz;
+    if (cy < p.ny - 1 && cz < p.nz - 1 && cx0 < p.nx - 1) return (int)((p.nx - 1 - cx0) < 8 ? (p.nx - 1 - cx0) : 8);
+    return 0;
+}
+
+// Persistent tile loop shared by both kernels: the next box is fetched while
+// `body` processes the current one.  A copy that never arrives (bounded
+// wait) raises CHR_ERR_TIMEOUT and the block stops.
+template <class Body>
+__device__ __forceinline__ void tile_loop(const McParams &p, const CUtensorMap *map, float *bufs, uint64_t *mbar,
+                                          Body body)
+{
+    const int tid = threadIdx.x;
+    const int64_t G = gridDim.x;
+    int64_t tile = blockIdx.x;
+    if (p.use_tma) {
+        if (tid == 0) {
+            mbar_init(&mbar[0], 1);
+            mbar_init(&mbar[1], 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        if (tid == 0 && tile < p.ntiles) issue_box(bufs, map, &mbar[0], p, tile);
+    }
+    uint32_t phase0 = 0, phase1 = 0;
+    int cur = 0;
+    for (; tile < p.ntiles; tile += G) {
+        float *buf = bufs + cur * (kBufBytes / 4);
+        const int64_t next = tile + G;
+        bool ok = true;
+        if (p.use_tma) {
+            if (tid == 0 && next < p.ntiles) issue_box(bufs + (cur ^ 1) * (kBufBytes / 4), map, &mbar[cur ^ 1], p, next);
+            ok = mbar_wait(&mbar[cur], cur ? phase1 : phase0);
+            if (cur)
+                phase1 ^= 1u;
+            else
+                phase0 ^= 1u;
+        } else {
+            load_box_plain(buf, p, tile_origin(p, tile));
+        }
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0 && p.err) atomicOr(p.err, 1u << CHR_ERR_TIMEOUT);
+            return;
+        }
+        body(tile, buf);
+        __syncthreads();  // every read of buf is done before it is refilled
+        cur ^= 1;
+    }
+}
+
+template <int NISO>
+__global__ void __launch_bounds__(256) k_mc_count(const __grid_constant__ McParams p,
+                                                 const __grid_constant__ CUtensorMap map)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+    float *bufs = reinterpret_cast<float *>(smem + kOffBuf);
+    uint64_t *s_row = reinterpret_cast<uint64_t *>(smem + kOffRow);
+    uint8_t *s_cnt = smem + kOffTab;  // triangle count per case
+    __shared__ uint64_t mbar[2];
+    __shared__ uint32_t s_sum[8][kMcIsoPerPass];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    s_cnt[tid] = (uint8_t)(g_mc_case[tid] >> 60);
+
+    tile_loop(p, &map, bufs, mbar, [&](int64_t tile, const float *buf) {
+        row_masks<NISO>(buf, s_row, p);
+        __syncthreads();
+        const TileXYZ o = tile_origin(p, tile);
+        const int nvalid = valid_cells(p, o);
+        const int j = tid >> 6, ly = tid & 7, lz = (tid >> 3) & 7;
+        const int r00 = lz * 9 + ly;
+        uint32_t cnt[NISO];
 #pragma unroll
-    for (int i = 0; i < NISO; i++) {
-        uint32_t cnt = 0;
-        for (int x = 0; x < nvalid; x++) {
-            const uint32_t cs = ((m[i][0] >> x) & 3u) | (((m[i][1] >> x) & 3u) << 2) | (((m[i][2] >> x) & 3u) << 4) |
-                                (((m[i][3] >> x) & 3u) << 6);
-            cnt += (uint32_t)(s_tab[cs] >> 60);
-        }
-        packed |= (uint64_t)cnt << (16 * i);
-    }
-
-    // block scan (4 x 16-bit lanes in one 64-bit word; a tile has < 2^16 triangles per isovalue)
-    const uint64_t inc = warp_incl_scan_u64(packed, lane);
-    if (lane == 31) s_warp[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        const uint64_t t = (lane < 8) ? s_warp[lane] : 0ull;
-        const uint64_t ti = warp_incl_scan_u64(t, lane);
-        if (lane < 8) s_warp[lane] = ti - t;
-        if (lane == 7) s_warp[8] = ti;
-    }
-    __syncthreads();
-    const uint64_t thread_excl = s_warp[warp] + inc - packed;
-    const uint64_t block_total = s_warp[8];
-
-    if (warp == 0) {
-        uint64_t *st = p.status + tile * kMcIsoPerPass;
-        if (lane == 0 && tile > 0)
-            for (int i = 0; i < NISO; i++) st_relaxed_u64(st + i, (((block_total >> (16 * i)) & 0xffffull) << 2) | 1ull);
         for (int i = 0; i < NISO; i++) {
-            const uint64_t tot = (block_total >> (16 * i)) & 0xffffull;
-            const uint64_t ex = (tile > 0) ? lookback(p, tile, i, lane) : 0ull;
-            if (lane == 0) {
-                st_relaxed_u64(st + i, ((ex + tot) << 2) | 2ull);
-                s_prefix[i] = ex;
-                if (tile == p.ntiles - 1) p.ntris[i] = ex + tot;
+            const uint64_t *R = s_row + i * kRows;
+            const uint32_t m0 = (uint32_t)(R[r00] >> (8 * j)), m1 = (uint32_t)(R[r00 + 1] >> (8 * j));
+            const uint32_t m2 = (uint32_t)(R[r00 + 9] >> (8 * j)), m3 = (uint32_t)(R[r00 + 10] >> (8 * j));
+            uint32_t c = 0;
+#pragma unroll
+            for (int x = 0; x < 8; x++)
+                if (x < nvalid) c += s_cnt[case_of(m0, m1, m2, m3, x)];
+            cnt[i] = __reduce_add_sync(CHR_FULL_MASK, c);
+        }
+#pragma unroll
+        for (int i = 0; i < NISO; i++)
+            if (lane == 0) s_sum[warp][i] = cnt[i];
+        __syncthreads();
+        if (tid == 0) {
+            uint32_t t[kMcIsoPerPass] = {0, 0, 0, 0};
+#pragma unroll
+            for (int w = 0; w < 8; w++)
+#pragma unroll
+                for (int i = 0; i < NISO; i++) t[i] += s_sum[w][i];
+            p.tile_cnt[tile] = make_uint4(t[0], t[1], t[2], t[3]);
+        }
+    });
+}
+
+// Edge e of a cell: offset of its lower corner in the box, the step to its
+// upper corner, and (ox, oy, oz, axis) packed as ox | oy<<1 | oz<<2 | axis<<3.
+struct EdgeInfo {
+    int16_t delta, step;
+    int32_t bits;
+};
+
+__device__ __forceinline__ EdgeInfo edge_info(int e)
+{
+    const int axis = e >> 2, m = e & 3;
+    const int ox = (axis == 0) ? 0 : (m & 1);
+    const int oy = (axis == 1) ? 0 : ((axis == 0) ? (m & 1) : (m >> 1));
+    const int oz = (axis == 2) ? 0 : (m >> 1);
+    EdgeInfo ei;
+    ei.delta = (int16_t)(ox + oy * kVX + oz * kPlane);
+    ei.step = (int16_t)((axis == 0) ? 1 : (axis == 1) ? kVX : kPlane);
+    ei.bits = ox | (oy << 1) | (oz << 2) | (axis << 3);
+    return ei;
+}
+
+// t = (k - f0) / (f1 - f0): the edge parameter of a crossing.  f0 and f1 lie
+// on opposite sides of k, so the quotient is in (0, 1]; the fast reciprocal
+// quotient is within 2 ulp of the rounded one, and the IEEE quotient is used
+// where the fast form does not apply (|f1 - f0| >= 2^126).
+__device__ __forceinline__ float edge_t(float k, float f0, float f1)
+{
+    const float num = __fsub_rn(k, f0), den = __fsub_rn(f1, f0);
+    return (fabsf(den) < 8.5e37f) ? __fdividef(num, den) : __fdiv_rn(num, den);
+}
+
+// One triangle of cell c (tile-local index) into dst[0..8].
+__device__ __forceinline__ void make_triangle(float *dst, const float *box, const EdgeInfo *s_edge, uint64_t word, int t,
+                                              int c, float k, float fx0, float fy0, float fz0)
+{
+    const int lx = c & 7, tt = c >> 3, ly = tt & 7, lz = (tt >> 3) & 7, j = tt >> 6;
+    const float *cell = box + lz * kPlane + ly * kVX + 8 * j + lx;
+    const float cx = fx0 + (float)(8 * j + lx), cy = fy0 + (float)ly, cz = fz0 + (float)lz;
+#pragma unroll
+    for (int v = 0; v < 3; v++) {
+        const EdgeInfo ei = s_edge[(word >> (12 * t + 4 * v)) & 15u];
+        const float *p0 = cell + ei.delta;
+        const float tv = edge_t(k, p0[0], p0[ei.step]);
+        const int axis = ei.bits >> 3;
+        float px = cx + (float)(ei.bits & 1), py = cy + (float)((ei.bits >> 1) & 1), pz = cz + (float)((ei.bits >> 2) & 1);
+        if (axis == 0) px = __fadd_rn(px, tv);
+        if (axis == 1) py = __fadd_rn(py, tv);
+        if (axis == 2) pz = __fadd_rn(pz, tv);
+        dst[3 * v + 0] = px;
+        dst[3 * v + 1] = py;
+        dst[3 * v + 2] = pz;
+    }
+}
+
+template <int NISO>
+__global__ void __launch_bounds__(256, 3) k_mc_emit(const __grid_constant__ McParams p,
+                                                   const __grid_constant__ CUtensorMap map)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+    float *bufs = reinterpret_cast<float *>(smem + kOffBuf);
+    uint64_t *s_row = reinterpret_cast<uint64_t *>(smem + kOffRow);
+    uint64_t *s_tab = reinterpret_cast<uint64_t *>(smem + kOffTab);
+    uint8_t *s_case = smem + kOffCase;
+    uint16_t *s_map = reinterpret_cast<uint16_t *>(smem + kOffMap);
+    __shared__ uint64_t mbar[2];
+    __shared__ uint64_t s_warp[9];
+    __shared__ EdgeInfo s_edge[12];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float *s_stage = reinterpret_cast<float *>(smem + kOffStage) + warp * kWarpStage;
+    s_tab[tid] = g_mc_case[tid];
+    if (tid < 12) s_edge[tid] = edge_info(tid);
+
+    tile_loop(p, &map, bufs, mbar, [&](int64_t tile, const float *box) {
+        row_masks<NISO>(box, s_row, p);
+        __syncthreads();
+        const TileXYZ o = tile_origin(p, tile);
+        const int nvalid = valid_cells(p, o);
+        const int j = tid >> 6, ly = tid & 7, lz = (tid >> 3) & 7;
+        const int r00 = lz * 9 + ly;
+        uint64_t packed = 0;
+#pragma unroll
+        for (int i = 0; i < NISO; i++) {
+            const uint64_t *R = s_row + i * kRows;
+            const uint32_t m0 = (uint32_t)(R[r00] >> (8 * j)), m1 = (uint32_t)(R[r00 + 1] >> (8 * j));
+            const uint32_t m2 = (uint32_t)(R[r00 + 9] >> (8 * j)), m3 = (uint32_t)(R[r00 + 10] >> (8 * j));
+            uint32_t cnt = 0, lo = 0, hi = 0;
+#pragma unroll
+            for (int x = 0; x < 8; x++) {
+                const uint32_t cs = (x < nvalid) ? case_of(m0, m1, m2, m3, x) : 0u;
+                cnt += (uint32_t)(s_tab[cs] >> 60);
+                if (x < 4)
+                    lo |= cs << (8 * x);
+                else
+                    hi |= cs << (8 * (x - 4));
             }
+            *reinterpret_cast<uint2 *>(s_case + i * kCells + tid * 8) = make_uint2(lo, hi);
+            packed |= (uint64_t)cnt << (16 * i);
+        }
+        // block scan of the four 16-bit counts
+        const uint64_t inc = warp_incl_scan_u64(packed, lane);
+        if (lane == 31) s_warp[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            const uint64_t t = (lane < 8) ? s_warp[lane] : 0ull;
+            const uint64_t ti = warp_incl_scan_u64(t, lane);
+            if (lane < 8) s_warp[lane] = ti - t;
+            if (lane == 7) s_warp[8] = ti;
+        }
+        __syncthreads();
+        const uint64_t thread_excl = s_warp[warp] + inc - packed;
+        const uint64_t block_total = s_warp[8];
+        const float fx0 = (float)o.x0, fy0 = (float)o.y0, fz0 = (float)o.z0;
+
+#pragma unroll 1
+        for (int i = 0; i < NISO; i++) {
+            const int n = (int)((block_total >> (16 * i)) & 0xffffull);
+            if (n == 0) continue;  // uniform
+            {
+                uint32_t off = (uint32_t)((thread_excl >> (16 * i)) & 0xffffull);
+                const uint2 cw = *reinterpret_cast<const uint2 *>(s_case + i * kCells + tid * 8);
+#pragma unroll
+                for (int x = 0; x < 8; x++) {
+                    const uint32_t cs = ((x < 4 ? cw.x : cw.y) >> (8 * (x & 3))) & 0xffu;
+                    const int nt = (int)(s_tab[cs] >> 60);
+                    for (int t = 0; t < nt; t++) s_map[off++] = (uint16_t)(((tid * 8 + x) << 3) | t);
+                }
+            }
+            __syncthreads();
+            // each warp writes a contiguous eighth of the tile's triangles, 32 at a time
+            const int w0 = (warp * n) >> 3, w1 = ((warp + 1) * n) >> 3;
+            const uint64_t g0 = __ldg(p.tile_off + tile * kMcIsoPerPass + i);
+            const float k = p.k[i];
+            float *out = p.tris[i];
+            for (int base = w0; base < w1; base += 32) {
+                const uint64_t gbase = g0 + (uint64_t)base;
+                if (gbase >= p.cap) break;  // uniform across the warp
+                int mm = (w1 - base) < 32 ? (w1 - base) : 32;
+                if (gbase + (uint64_t)mm > p.cap) mm = (int)(p.cap - gbase);
+                float *dst = out + 9ull * gbase;
+                const int pad = (int)((reinterpret_cast<uintptr_t>(dst) >> 2) & 3u);
+                if (lane < mm) {
+                    const uint32_t ent = s_map[base + lane];
+                    const int c = (int)(ent >> 3), t = (int)(ent & 7u);
+                    const uint64_t word = s_tab[s_case[i * kCells + c]];
+                    make_triangle(s_stage + pad + 9 * lane, box, s_edge, word, t, c, k, fx0, fy0, fz0);
+                }
+                __syncwarp();
+                // dst[q] = s_stage[pad + q]; dst + q is 16-byte aligned when (pad + q) % 4 == 0
+                const int F = 9 * mm;
+                const int head = min((4 - pad) & 3, F);
+                if (lane < head) __stcs(dst + lane, s_stage[pad + lane]);
+                const int nbody = (F - head) >> 2;
+                const float4 *src4 = reinterpret_cast<const float4 *>(s_stage + pad + head);
+                float4 *dst4 = reinterpret_cast<float4 *>(dst + head);
+                for (int q = lane; q < nbody; q += 32) __stcs(dst4 + q, src4[q]);
+                const int tail0 = head + 4 * nbody;
+                if (lane < F - tail0) __stcs(dst + tail0 + lane, s_stage[pad + tail0 + lane]);
+                __syncwarp();
+            }
+            __syncthreads();  // the map is rebuilt for the next isovalue
+        }
+    });
+}
+
+// ---- exclusive scan of the tile counts ----------------------------------
+
+constexpr int kTScanThreads = 256, kTScanPer = 8, kTScanChunk = kTScanThreads * kTScanPer;
+
+struct __align__(32) Sum4 {
+    uint64_t x, y, z, w;
+};
+
+__device__ __forceinline__ Sum4 make_sum4(uint64_t x, uint64_t y, uint64_t z, uint64_t w)
+{
+    Sum4 r;
+    r.x = x;
+    r.y = y;
+    r.z = z;
+    r.w = w;
+    return r;
+}
+
+struct TScanArgs {
+    const uint4 *cnt;
+    uint64_t *off;      // [ntiles][4]
+    Sum4 *chunk;  // [nchunks]
+    int64_t ntiles, nchunks;
+    uint64_t *ntris;
+    int niso;
+    uint64_t cap;
+    uint32_t *err;
+};
+
+__device__ __forceinline__ void block_excl_scan4(uint64_t (&v)[4], uint64_t (&tot)[4], uint64_t (*s_w)[4])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t inc[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) inc[i] = warp_incl_scan_u64(v[i], lane);
+    if (lane == 31)
+#pragma unroll
+        for (int i = 0; i < 4; i++) s_w[warp][i] = inc[i];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const uint64_t t = (lane < 8) ? s_w[lane][i] : 0ull;
+            const uint64_t ti = warp_incl_scan_u64(t, lane);
+            if (lane < 8) s_w[lane][i] = ti - t;
+            if (lane == 7) s_w[8][i] = ti;
         }
     }
     __syncthreads();
-
-    // emit
 #pragma unroll
-    for (int i = 0; i < NISO; i++) {
-        uint64_t idx = s_prefix[i] + ((thread_excl >> (16 * i)) & 0xffffull);
-        const float k = p.k[i];
-        float *out = p.tris[i];
-        for (int x = 0; x < nvalid; x++) {
-            const uint32_t cs = ((m[i][0] >> x) & 3u) | (((m[i][1] >> x) & 3u) << 2) | (((m[i][2] >> x) & 3u) << 4) |
-                                (((m[i][3] >> x) & 3u) << 6);
-            const uint64_t word = s_tab[cs];
-            const int nt = (int)(word >> 60);
-            for (int t = 0; t < nt; t++, idx++)
-                if (idx < p.cap)
-                    emit_triangle(out + 9 * idx, word, t, row + x, k, (float)(cx0 + x), (float)cy, (float)cz);
+    for (int i = 0; i < 4; i++) {
+        tot[i] = s_w[8][i];
+        v[i] = s_w[warp][i] + inc[i] - v[i];
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kTScanThreads) k_tscan_reduce(const __grid_constant__ TScanArgs a)
+{
+    __shared__ uint64_t s_w[9][4];
+    const int64_t b0 = (int64_t)blockIdx.x * kTScanChunk + (int64_t)threadIdx.x * kTScanPer;
+    uint64_t v[4] = {0, 0, 0, 0}, tot[4];
+    for (int e = 0; e < kTScanPer; e++)
+        if (b0 + e < a.ntiles) {
+            const uint4 c = a.cnt[b0 + e];
+            v[0] += c.x;
+            v[1] += c.y;
+            v[2] += c.z;
+            v[3] += c.w;
         }
-        if (idx > p.cap && p.err) atomicOr(p.err, 1u << CHR_ERR_OVERFLOW);
+    block_excl_scan4(v, tot, s_w);
+    if (threadIdx.x == 0) a.chunk[blockIdx.x] = make_sum4(tot[0], tot[1], tot[2], tot[3]);
+}
+
+__global__ void __launch_bounds__(kTScanThreads) k_tscan_chunks(const __grid_constant__ TScanArgs a)
+{
+    __shared__ uint64_t s_w[9][4];
+    uint64_t carry[4] = {0, 0, 0, 0};
+    for (int64_t c0 = 0; c0 < a.nchunks; c0 += kTScanThreads) {
+        const int64_t c = c0 + threadIdx.x;
+        const Sum4 s = (c < a.nchunks) ? a.chunk[c] : make_sum4(0, 0, 0, 0);
+        uint64_t v[4] = {s.x, s.y, s.z, s.w}, tot[4];
+        block_excl_scan4(v, tot, s_w);
+        if (c < a.nchunks)
+            a.chunk[c] = make_sum4(carry[0] + v[0], carry[1] + v[1], carry[2] + v[2], carry[3] + v[3]);
+#pragma unroll
+        for (int i = 0; i < 4; i++) carry[i] += tot[i];
+    }
+    if (threadIdx.x < a.niso) {
+        a.ntris[threadIdx.x] = carry[threadIdx.x];
+        if (carry[threadIdx.x] > a.cap && a.err) atomicOr(a.err, 1u << CHR_ERR_OVERFLOW);
+    }
+}
+
+__global__ void __launch_bounds__(kTScanThreads) k_tscan_apply(const __grid_constant__ TScanArgs a)
+{
+    __shared__ uint64_t s_w[9][4];
+    const int64_t b0 = (int64_t)blockIdx.x * kTScanChunk + (int64_t)threadIdx.x * kTScanPer;
+    uint4 c[kTScanPer];
+    uint64_t v[4] = {0, 0, 0, 0}, tot[4];
+    for (int e = 0; e < kTScanPer; e++) {
+        c[e] = (b0 + e < a.ntiles) ? a.cnt[b0 + e] : make_uint4(0, 0, 0, 0);
+        v[0] += c[e].x;
+        v[1] += c[e].y;
+        v[2] += c[e].z;
+        v[3] += c[e].w;
+    }
+    block_excl_scan4(v, tot, s_w);
+    const Sum4 base = a.chunk[blockIdx.x];
+    uint64_t run[4] = {base.x + v[0], base.y + v[1], base.z + v[2], base.w + v[3]};
+    for (int e = 0; e < kTScanPer; e++) {
+        if (b0 + e >= a.ntiles) break;
+        uint64_t *o = a.off + (b0 + e) * kMcIsoPerPass;
+        o[0] = run[0];
+        o[1] = run[1];
+        o[2] = run[2];
+        o[3] = run[3];
+        run[0] += c[e].x;
+        run[1] += c[e].y;
+        run[2] += c[e].z;
+        run[3] += c[e].w;
     }
 }
 
@@ -218,19 +524,81 @@ static void mc_tiles(const Grid &g, int32_t &ntx, int32_t &ncby, int32_t &ncbz, 
     ntiles = (int64_t)ntx * ncby * ncbz;
 }
 
-size_t mc_workspace_bytes(const Grid &g, int n_iso)
+struct McWorkspace {
+    uint4 *cnt;
+    uint64_t *off;
+    Sum4 *chunk;
+    int64_t nchunks;
+};
+
+static size_t mc_layout(const Grid &g, void *base, McWorkspace *w)
 {
-    (void)n_iso;  // passes of 4 isovalues reuse the same status words
     int32_t ntx, ncby, ncbz;
     int64_t ntiles;
     mc_tiles(g, ntx, ncby, ncbz, ntiles);
-    return 256 + (size_t)ntiles * kMcIsoPerPass * sizeof(uint64_t);
+    const int64_t nchunks = (ntiles + kTScanChunk - 1) / kTScanChunk;
+    const size_t o_cnt = 0, o_off = o_cnt + ((ntiles * 16 + 255) / 256) * 256;
+    const size_t o_chunk = o_off + ((ntiles * 32 + 255) / 256) * 256;
+    const size_t total = o_chunk + ((nchunks * 32 + 255) / 256) * 256;
+    if (w) {
+        char *b = reinterpret_cast<char *>(base);
+        w->cnt = reinterpret_cast<uint4 *>(b + o_cnt);
+        w->off = reinterpret_cast<uint64_t *>(b + o_off);
+        w->chunk = reinterpret_cast<Sum4 *>(b + o_chunk);
+        w->nchunks = nchunks;
+    }
+    return total;
+}
+
+size_t mc_workspace_bytes(const Grid &g, int n_iso)
+{
+    (void)n_iso;  // groups of 4 isovalues reuse the same scratch in turn
+    return mc_layout(g, nullptr, nullptr);
+}
+
+template <int NISO>
+static cudaError_t launch_mc_group(const McParams &p, const CUtensorMap &map, const McWorkspace &w, uint64_t *ntris,
+                                   int niso, cudaStream_t s)
+{
+    static int grid_count = 0, grid_emit = 0;  // resident blocks per device, computed once per process
+    if (!grid_emit) {
+        cudaError_t e = cudaFuncSetAttribute(k_mc_emit<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_mc_count<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCountSmem);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, bc = 0, be = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bc, k_mc_count<NISO>, 256, kCountSmem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&be, k_mc_emit<NISO>, 256, kEmitSmem);
+        grid_count = sms * (bc > 0 ? bc : 1);
+        grid_emit = sms * (be > 0 ? be : 1);
+    }
+    const unsigned gc = (unsigned)(p.ntiles < grid_count ? p.ntiles : grid_count);
+    const unsigned ge = (unsigned)(p.ntiles < grid_emit ? p.ntiles : grid_emit);
+    k_mc_count<NISO><<<gc, 256, kCountSmem, s>>>(p, map);
+    TScanArgs a;
+    a.cnt = w.cnt;
+    a.off = w.off;
+    a.chunk = w.chunk;
+    a.ntiles = p.ntiles;
+    a.nchunks = w.nchunks;
+    a.ntris = ntris;
+    a.niso = niso;
+    a.cap = p.cap;
+    a.err = p.err;
+    k_tscan_reduce<<<(unsigned)w.nchunks, kTScanThreads, 0, s>>>(a);
+    k_tscan_chunks<<<1, kTScanThreads, 0, s>>>(a);
+    k_tscan_apply<<<(unsigned)w.nchunks, kTScanThreads, 0, s>>>(a);
+    k_mc_emit<NISO><<<ge, 256, kEmitSmem, s>>>(p, map);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_mc(const float *field, const Grid &g, const float *iso, int n_iso, float *tris, uint64_t cap,
                       uint64_t *ntris, uint32_t *err, void *workspace, cudaStream_t s)
 {
     McParams p;
+    memset(&p, 0, sizeof(p));
     p.f = field;
     p.nx = g.nx;
     p.ny = g.ny;
@@ -238,26 +606,26 @@ cudaError_t launch_mc(const float *field, const Grid &g, const float *iso, int n
     mc_tiles(g, p.ntx, p.ncby, p.ncbz, p.ntiles);
     p.cap = cap;
     p.err = err;
-    p.counter = reinterpret_cast<unsigned long long *>(workspace);
-    p.status = reinterpret_cast<uint64_t *>(reinterpret_cast<char *>(workspace) + 256);
-    const size_t ws = mc_workspace_bytes(g, n_iso);
+    McWorkspace w;
+    mc_layout(g, workspace, &w);
+    p.tile_cnt = w.cnt;
+    p.tile_off = w.off;
+    CUtensorMap map;
+    memset(&map, 0, sizeof(map));
+    p.use_tma = make_field_tensor_map(&map, field, g.nx, g.ny, g.nz, kBoxX, 9, 9) ? 1 : 0;
     for (int i0 = 0; i0 < n_iso; i0 += kMcIsoPerPass) {
         const int n = (n_iso - i0) < kMcIsoPerPass ? (n_iso - i0) : kMcIsoPerPass;
         for (int i = 0; i < kMcIsoPerPass; i++) {
             p.k[i] = (i < n) ? iso[i0 + i] : 0.0f;
             p.tris[i] = (i < n) ? tris + 9ull * cap * (uint64_t)(i0 + i) : nullptr;
         }
-        p.ntris = ntris + i0;
-        cudaError_t e = cudaMemsetAsync(workspace, 0, ws, s);
-        if (e != cudaSuccess) return e;
-        const dim3 grid((unsigned)p.ntiles);
+        cudaError_t e;
         switch (n) {
-            case 1: k_mc<1><<<grid, 256, 0, s>>>(p); break;
-            case 2: k_mc<2><<<grid, 256, 0, s>>>(p); break;
-            case 3: k_mc<3><<<grid, 256, 0, s>>>(p); break;
-            default: k_mc<4><<<grid, 256, 0, s>>>(p); break;
+            case 1: e = launch_mc_group<1>(p, map, w, ntris + i0, n, s); break;
+            case 2: e = launch_mc_group<2>(p, map, w, ntris + i0, n, s); break;
+            case 3: e = launch_mc_group<3>(p, map, w, ntris + i0, n, s); break;
+            default: e = launch_mc_group<4>(p, map, w, ntris + i0, n, s); break;
         }
-        e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
