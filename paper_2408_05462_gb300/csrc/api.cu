@@ -323,17 +323,26 @@ chr_status chr_compress(const float *d_field, chr_dims dims, const chr_params *p
     CodecParams p;
     fill_codec_params(h, p);
     p.f = d_field;
-    cudaError_t e = launch_encode(p, false, s);
-    const size_t scr_bytes = scan_scratch_bytes(g.nbricks, (int)h->nlevels) + 16 * CHR_MAX_LEVELS;
-    char *scr = nullptr;
+    // scratch: the per-brick slots of every level, then the record-scan buffers
+    const size_t slot_bytes = encode_slot_bytes(g.nbricks);
+    const size_t scan_bytes = scan_scratch_bytes(g.nbricks, (int)h->nlevels);
+    const size_t scr_bytes = slot_bytes * h->nlevels + scan_bytes + 16 * CHR_MAX_LEVELS;
+    char *scr = (char *)al.get(scr_bytes);
+    cudaError_t e = cudaSuccess;
     uint64_t totals[2 * CHR_MAX_LEVELS] = {0};
-    if (e == cudaSuccess) {
-        scr = (char *)al.get(scr_bytes);
-        if (!scr) st = fail(CHR_ERR_OOM, "chr_compress: allocator returned NULL");
-    }
-    if (e == cudaSuccess && st == CHR_OK) {
-        uint64_t *d_tot = reinterpret_cast<uint64_t *>(scr + scan_scratch_bytes(g.nbricks, (int)h->nlevels));
-        e = launch_scan_records(h->d_recs, (int)h->nlevels, g.nbricks, scr, d_tot, s);
+    if (!scr) st = fail(CHR_ERR_OOM, "chr_compress: allocator returned NULL");
+    if (st == CHR_OK) {
+        const size_t nb512 = (size_t)g.nbricks * 512;
+        for (uint32_t l = 0; l < h->nlevels; l++) {
+            char *b = scr + slot_bytes * l;
+            p.slot_words[l] = reinterpret_cast<uint32_t *>(b);
+            p.slot_val[l] = reinterpret_cast<uint32_t *>(b + nb512 * 4);
+            p.slot_idx[l] = reinterpret_cast<uint16_t *>(b + nb512 * 8);
+        }
+        char *scan_scr = scr + slot_bytes * h->nlevels;
+        uint64_t *d_tot = reinterpret_cast<uint64_t *>(scan_scr + scan_bytes);
+        e = launch_encode(p, s);
+        if (e == cudaSuccess) e = launch_scan_records(h->d_recs, (int)h->nlevels, g.nbricks, scan_scr, d_tot, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(totals, d_tot, 16 * h->nlevels, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     }
@@ -352,9 +361,12 @@ chr_status chr_compress(const float *d_field, chr_dims dims, const chr_params *p
         }
     }
     if (e == cudaSuccess && st == CHR_OK) {
-        fill_codec_params(h, p);
-        p.f = d_field;
-        e = launch_encode(p, true, s);
+        for (uint32_t l = 0; l < h->nlevels; l++) {
+            p.words[l] = h->d_words[l];
+            p.exc_idx[l] = h->d_exc_idx[l];
+            p.exc_val[l] = h->d_exc_val[l];
+        }
+        e = launch_compact(p, s);
     }
     al.put(scr, scr_bytes);
     if (e != cudaSuccess) st = cuda_fail(e, "chr_compress");

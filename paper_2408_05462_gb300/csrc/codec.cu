@@ -67,18 +67,62 @@ __device__ __forceinline__ void load_rows(const CodecParams &p, const BrickCoord
     }
 }
 
-template <bool PACK>
-__global__ void __launch_bounds__(256) k_encode(const __grid_constant__ CodecParams p)
+// Number of candidate isovalues strictly above v (K sorted ascending).  Two
+// values lie on the same side of every k exactly when these counts agree,
+// because {j : v < K[j]} is always a suffix of the sorted K.
+__device__ __forceinline__ int count_above(float v, const float *K, int nK)
 {
-    __shared__ __align__(16) uint32_t s_zz[kWarpsPerBlock][512];
-    BrickCoord c;
-    if (!brick_of_warp(p, c)) return;  // the whole warp leaves; no block barrier below
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ly = lane & 7;
+    int c = 0;
+    for (int j = 0; j < nK; j++) c += (v < K[j]) ? 1 : 0;
+    return c;
+}
 
+// One level of the residual chain for one vertex (paper Sec. 2 accuracy
+// levels; Sec. 2.2 sign preservation).  Every float operation is one IEEE
+// binary32 operation rounded to nearest-even.  Returns true for a vertex
+// stored exactly (bound or sign check failed, or not quantisable).
+__device__ __forceinline__ bool encode_step(float f, float Rprev, bool first, float e, float two_e, float inv2e,
+                                            const float *K, int nK, bool fix, int cf, int32_t &q, float &R)
+{
+    const float r = first ? f : __fsub_rn(f, Rprev);
+    const float x = __fmul_rn(r, inv2e);
+    q = 0;
+    R = f;
+    if (!(fabsf(x) <= CHR_QMAX)) return true;
+    const int32_t qi = __float2int_rn(x);  // round half to even
+    const float P = __fmul_rn(__int2float_rn(qi), two_e);
+    const float Rn = first ? P : __fadd_rn(Rprev, P);
+    if (!(fabsf(__fsub_rn(f, Rn)) < e)) return true;
+    if (fix && count_above(Rn, K, nK) != cf) return true;
+    q = qi;
+    R = Rn;
+    return false;
+}
+
+// One warp encodes one brick through every level.  The level's packed words
+// go to the brick's fixed slot of 512 words and its exceptions to the
+// brick's slot of 512 entries in scratch; the record gets the anchor, width,
+// mode and exception count (its prefix sums are filled by the record scan,
+// after which k_compact moves the slots into the dense stream).
+template <bool FULL>
+__device__ __forceinline__ void encode_brick(const CodecParams &p, const BrickCoord &c, uint32_t *zbuf)
+{
+    const int lane = threadIdx.x & 31;
+    const int ly = lane & 7;
     float f[2][8];
     uint32_t valid;
     load_rows(p, c, lane, f, valid);
+    if (FULL) valid = 0xffffu;
+
+    // count_above(f) of the 16 values, one byte each
+    uint32_t cfp[4] = {0u, 0u, 0u, 0u};
+    const bool fix = p.fix != 0;
+    if (fix) {
+#pragma unroll
+        for (int s = 0; s < 2; s++)
+#pragma unroll
+            for (int x = 0; x < 8; x++) cfp[(8 * s + x) >> 2] |= (uint32_t)count_above(f[s][x], p.K, p.nK) << (8 * (x & 3));
+    }
 
     float R[2][8];
 #pragma unroll
@@ -89,92 +133,86 @@ __global__ void __launch_bounds__(256) k_encode(const __grid_constant__ CodecPar
     for (int l = 0; l < p.nlevels; l++) {
         int32_t q[2][8];
         uint32_t excm = 0;
+        const float e = p.e[l], two_e = p.two_e[l], inv2e = p.inv2e[l];
 #pragma unroll
         for (int s = 0; s < 2; s++)
 #pragma unroll
             for (int x = 0; x < 8; x++) {
                 q[s][x] = 0;
-                if ((valid >> (8 * s + x)) & 1u) {
+                if (FULL || ((valid >> (8 * s + x)) & 1u)) {
                     float Rn;
                     int32_t qq;
-                    bool e = level_step(f[s][x], R[s][x], l == 0, p.e[l], p.two_e[l], p.inv2e[l], p.K, p.nK,
-                                        p.fix != 0, qq, Rn);
+                    const bool ex = encode_step(f[s][x], R[s][x], l == 0, e, two_e, inv2e, p.K, p.nK, fix, (int)((cfp[(8 * s + x) >> 2] >> (8 * (x & 3))) & 0xffu),
+                                                qq, Rn);
                     q[s][x] = qq;
                     R[s][x] = Rn;
-                    if (e) excm |= 1u << (8 * s + x);
+                    if (ex) excm |= 1u << (8 * s + x);
                 }
             }
 
         // Lorenzo residual = first differences along x, then y, then z, with
         // zero outside the brick.  Padding slots and slot 0 (the anchor) pack 0.
-        uint32_t zl[2][8], zn[2][8];
+        int32_t d[2][8];
         uint32_t maxl = 0, maxn = 0;
-        {
-            int32_t d[2][8];
 #pragma unroll
-            for (int s = 0; s < 2; s++) {
+        for (int s = 0; s < 2; s++) {
 #pragma unroll
-                for (int x = 7; x > 0; x--) d[s][x] = (int32_t)((uint32_t)q[s][x] - (uint32_t)q[s][x - 1]);
-                d[s][0] = q[s][0];
-            }
+            for (int x = 7; x > 0; x--) d[s][x] = (int32_t)((uint32_t)q[s][x] - (uint32_t)q[s][x - 1]);
+            d[s][0] = q[s][0];
+        }
 #pragma unroll
-            for (int s = 0; s < 2; s++)
-#pragma unroll
-                for (int x = 0; x < 8; x++) {
-                    int32_t up = __shfl_up_sync(CHR_FULL_MASK, d[s][x], 1, 8);
-                    if (ly > 0) d[s][x] = (int32_t)((uint32_t)d[s][x] - (uint32_t)up);
-                }
+        for (int s = 0; s < 2; s++)
 #pragma unroll
             for (int x = 0; x < 8; x++) {
-                const int src = (lane + 24) & 31;  // lane - 8, or lane + 24 for the first z of set 1
-                int32_t a = __shfl_sync(CHR_FULL_MASK, d[0][x], src);
-                int32_t b = __shfl_sync(CHR_FULL_MASK, d[1][x], src);
-                if (lane >= 8) d[0][x] = (int32_t)((uint32_t)d[0][x] - (uint32_t)a);
-                d[1][x] = (int32_t)((uint32_t)d[1][x] - (uint32_t)(lane >= 8 ? b : a));
+                const int32_t up = __shfl_up_sync(CHR_FULL_MASK, d[s][x], 1, 8);
+                if (ly > 0) d[s][x] = (int32_t)((uint32_t)d[s][x] - (uint32_t)up);
             }
 #pragma unroll
-            for (int s = 0; s < 2; s++)
-#pragma unroll
-                for (int x = 0; x < 8; x++) {
-                    const bool live = ((valid >> (8 * s + x)) & 1u) && !(s == 0 && lane == 0 && x == 0);
-                    zl[s][x] = live ? zigzag(d[s][x]) : 0u;
-                    zn[s][x] = live ? zigzag(q[s][x]) : 0u;
-                    maxl = max(maxl, zl[s][x]);
-                    maxn = max(maxn, zn[s][x]);
-                }
+        for (int x = 0; x < 8; x++) {
+            const int src = (lane + 24) & 31;  // lane - 8, or lane + 24 for the first z of set 1
+            const int32_t a = __shfl_sync(CHR_FULL_MASK, d[0][x], src);
+            const int32_t b = __shfl_sync(CHR_FULL_MASK, d[1][x], src);
+            if (lane >= 8) d[0][x] = (int32_t)((uint32_t)d[0][x] - (uint32_t)a);
+            d[1][x] = (int32_t)((uint32_t)d[1][x] - (uint32_t)(lane >= 8 ? b : a));
         }
+#pragma unroll
+        for (int s = 0; s < 2; s++)
+#pragma unroll
+            for (int x = 0; x < 8; x++) {
+                const bool live = (FULL || ((valid >> (8 * s + x)) & 1u)) && !(s == 0 && lane == 0 && x == 0);
+                if (!live) d[s][x] = 0;  // d is only read for packing from here on
+                maxl = max(maxl, zigzag(d[s][x]));
+                maxn = max(maxn, live ? zigzag(q[s][x]) : 0u);
+            }
         maxl = __reduce_max_sync(CHR_FULL_MASK, maxl);
         maxn = __reduce_max_sync(CHR_FULL_MASK, maxn);
         const int wl = bitlen(maxl), wn = bitlen(maxn);
         const int mode = (wl < wn) ? 1 : 0;
         const int w = mode ? wl : wn;
         const uint32_t cnt0 = __popc(excm & 0xffu), cnt1 = __popc(excm >> 8);
-        const uint32_t nexc = __reduce_add_sync(CHR_FULL_MASK, cnt0 + cnt1);
+        const uint32_t inc0 = warp_incl_scan_u32(cnt0, lane);
+        const uint32_t tot0 = __shfl_sync(CHR_FULL_MASK, inc0, 31);
+        const uint32_t inc1 = warp_incl_scan_u32(cnt1, lane);
+        const uint32_t nexc = tot0 + __shfl_sync(CHR_FULL_MASK, inc1, 31);
         const int32_t anchor = __shfl_sync(CHR_FULL_MASK, q[0][0], 0);
+        if (lane == 0)
+            p.recs[l][c.b] = make_uint4(0u, 0u, (uint32_t)anchor, (uint32_t)w | ((uint32_t)mode << 8) | (nexc << 16));
 
-        if (!PACK) {
-            if (lane == 0)
-                p.recs[l][c.b] = make_uint4(0u, 0u, (uint32_t)anchor,
-                                            (uint32_t)w | ((uint32_t)mode << 8) | (nexc << 16));
-            continue;
-        }
-
-        const uint4 rec = p.recs[l][c.b];  // wsum and exc_off filled by the scan
         if (w > 0) {
-            uint32_t *buf = s_zz[warp];
 #pragma unroll
             for (int s = 0; s < 2; s++) {
                 const int slot = 8 * (lane + 32 * s);
                 uint32_t z[8];
 #pragma unroll
-                for (int x = 0; x < 8; x++) z[x] = mode ? zl[s][x] : zn[s][x];
-                const uint4 lo = make_uint4(z[0], z[1], z[2], z[3]);
-                const uint4 hi = make_uint4(z[4], z[5], z[6], z[7]);
-                *reinterpret_cast<uint4 *>(buf + slot) = lo;
-                *reinterpret_cast<uint4 *>(buf + slot + 4) = hi;
+                for (int x = 0; x < 8; x++) {
+                    const bool live = (FULL || ((valid >> (8 * s + x)) & 1u)) && !(s == 0 && lane == 0 && x == 0);
+                    z[x] = mode ? zigzag(d[s][x]) : (live ? zigzag(q[s][x]) : 0u);
+                }
+                *reinterpret_cast<uint4 *>(zbuf + slot) = make_uint4(z[0], z[1], z[2], z[3]);
+                *reinterpret_cast<uint4 *>(zbuf + slot + 4) = make_uint4(z[4], z[5], z[6], z[7]);
             }
             __syncwarp();
-            uint32_t *dst = p.words[l] + 16ull * rec.x;
+            uint32_t *dst = p.slot_words[l] + 512ull * c.b;
             const int nw = 16 * w;
             for (int j = lane; j < nw; j += 32) {
                 const int bit0 = 32 * j;
@@ -183,7 +221,7 @@ __global__ void __launch_bounds__(256) k_encode(const __grid_constant__ CodecPar
                 uint32_t word = 0;
                 for (int s = s0; s <= s1; s++) {
                     const int pos = s * w - bit0;
-                    const uint32_t v = buf[s];
+                    const uint32_t v = zbuf[s];
                     word |= (pos >= 0) ? (v << pos) : (v >> (-pos));
                 }
                 dst[j] = word;
@@ -191,17 +229,14 @@ __global__ void __launch_bounds__(256) k_encode(const __grid_constant__ CodecPar
             __syncwarp();
         }
         if (nexc > 0) {
-            const uint32_t inc0 = warp_incl_scan_u32(cnt0, lane);
-            const uint32_t tot0 = __shfl_sync(CHR_FULL_MASK, inc0, 31);
-            const uint32_t inc1 = warp_incl_scan_u32(cnt1, lane);
 #pragma unroll
             for (int s = 0; s < 2; s++) {
-                uint32_t pos = rec.y + (s == 0 ? inc0 - cnt0 : tot0 + inc1 - cnt1);
+                uint32_t pos = (s == 0) ? inc0 - cnt0 : tot0 + inc1 - cnt1;
 #pragma unroll
                 for (int x = 0; x < 8; x++) {
                     if ((excm >> (8 * s + x)) & 1u) {
-                        p.exc_idx[l][pos] = (uint16_t)(8 * (lane + 32 * s) + x);
-                        p.exc_val[l][pos] = __float_as_uint(f[s][x]);
+                        p.slot_idx[l][512ull * c.b + pos] = (uint16_t)(8 * (lane + 32 * s) + x);
+                        p.slot_val[l][512ull * c.b + pos] = __float_as_uint(f[s][x]);
                         pos++;
                     }
                 }
@@ -210,104 +245,202 @@ __global__ void __launch_bounds__(256) k_encode(const __grid_constant__ CodecPar
     }
 }
 
+__global__ void __launch_bounds__(256, 2) k_encode(const __grid_constant__ CodecParams p)
+{
+    __shared__ __align__(16) uint32_t s_zz[kWarpsPerBlock][512];
+    BrickCoord c;
+    if (!brick_of_warp(p, c)) return;  // the whole warp leaves; no block barrier below
+    const bool full = ((int64_t)c.bx * 8 + 8 <= p.nx) && ((int64_t)c.by * 8 + 8 <= p.ny) && ((int64_t)c.bz * 8 + 8 <= p.nz);
+    uint32_t *zbuf = s_zz[threadIdx.x >> 5];
+    if (full)
+        encode_brick<true>(p, c, zbuf);
+    else
+        encode_brick<false>(p, c, zbuf);
+}
+
+// Moves every brick's slot contents to its place in the dense stream (one
+// warp per brick and level): 16*w words to words + 16*wsum, and the
+// exceptions to exc_off.
+__global__ void __launch_bounds__(256) k_compact(const __grid_constant__ CodecParams p)
+{
+    BrickCoord c;
+    if (!brick_of_warp(p, c)) return;
+    const int lane = threadIdx.x & 31;
+    const int l = blockIdx.y;
+    const uint4 rec = p.recs[l][c.b];
+    const int w = min((int)(rec.w & 0xffu), 32), nexc = (int)(rec.w >> 16);
+    const uint4 *src = reinterpret_cast<const uint4 *>(p.slot_words[l] + 512ull * c.b);
+    uint4 *dst = reinterpret_cast<uint4 *>(p.words[l] + 16ull * rec.x);
+    for (int j = lane; j < 4 * w; j += 32) __stcs(dst + j, ld_stream_u4(src + j));
+    for (int j = lane; j < nexc; j += 32) {
+        p.exc_idx[l][rec.y + j] = p.slot_idx[l][512ull * c.b + j];
+        p.exc_val[l][rec.y + j] = p.slot_val[l][512ull * c.b + j];
+    }
+}
+
+constexpr int kDecGroup = 3;       // levels whose loads are in flight together
+constexpr int kLevelWords = 516;   // shared words per level and warp: 512 payload + read-ahead slack
+constexpr int kExcPrefetch = 2;    // exception entries per lane and level loaded ahead (64 per brick)
+constexpr int kDecodeSmem = kWarpsPerBlock * kDecGroup * kLevelWords * 4;
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+                 "l"(gmem_src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Decode one brick per warp.  For each group of up to three levels every
+// load is issued before any is consumed: the records (one lane per level),
+// the packed words (cp.async straight into shared memory) and the first 64
+// exception entries of each level (registers), so a brick costs about two
+// memory round trips instead of three per level.
 __global__ void __launch_bounds__(256) k_decode(const __grid_constant__ CodecParams p)
 {
-    __shared__ __align__(16) uint32_t s_buf[kWarpsPerBlock][520];
+    extern __shared__ __align__(16) uint32_t s_dyn[];
     BrickCoord c;
     if (!brick_of_warp(p, c)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ly = lane & 7;
-    uint32_t *buf = s_buf[warp];
 
     float R[2][8];
-    for (int l = 0; l < p.nlevels; l++) {
-        const uint4 rec = __ldg(p.recs[l] + c.b);
-        const int w = min((int)(rec.w & 0xffu), 32), mode = (int)((rec.w >> 8) & 0xffu);
-        const int nexc = (int)(rec.w >> 16);
-        uint32_t q[2][8];  // unsigned: prefix sums wrap like the encoder's int32
-        if (w > 0) {
-            const uint4 *src = reinterpret_cast<const uint4 *>(p.words[l] + 16ull * rec.x);
-            for (int j = lane; j < 4 * w; j += 32) reinterpret_cast<uint4 *>(buf)[j] = ld_stream_u4(src + j);
-            __syncwarp();
-            const uint32_t mask = width_mask(w);
+#pragma unroll
+    for (int s = 0; s < 2; s++)
+#pragma unroll
+        for (int x = 0; x < 8; x++) R[s][x] = 0.0f;
+
+    for (int g0 = 0; g0 < p.nlevels; g0 += kDecGroup) {
+        const int ng = min(kDecGroup, p.nlevels - g0);
+        // records: lane l holds level g0 + l
+        uint4 myrec = make_uint4(0, 0, 0, 0);
+        if (lane < ng) myrec = __ldg(p.recs[g0 + lane] + c.b);
+        uint4 rec[kDecGroup];
+        uint16_t eidx[kDecGroup][kExcPrefetch];
+        uint32_t eval[kDecGroup][kExcPrefetch];
+#pragma unroll
+        for (int u = 0; u < kDecGroup; u++) {
+            rec[u].x = __shfl_sync(CHR_FULL_MASK, myrec.x, u);
+            rec[u].y = __shfl_sync(CHR_FULL_MASK, myrec.y, u);
+            rec[u].z = __shfl_sync(CHR_FULL_MASK, myrec.z, u);
+            rec[u].w = __shfl_sync(CHR_FULL_MASK, myrec.w, u);
+        }
+        // issue payload copies and exception loads of the whole group
+#pragma unroll
+        for (int u = 0; u < kDecGroup; u++) {
+            if (u >= ng) break;
+            const int l = g0 + u;
+            const int w = min((int)(rec[u].w & 0xffu), 32);
+            const int nexc = (int)(rec[u].w >> 16);
+            const uint4 *src = reinterpret_cast<const uint4 *>(p.words[l] + 16ull * rec[u].x);
+            uint32_t *dst = (s_dyn + warp * (kDecGroup * kLevelWords)) + u * kLevelWords;
+            for (int j = lane; j < 4 * w; j += 32) cp_async16(dst + 4 * j, src + j);
+#pragma unroll
+            for (int e = 0; e < kExcPrefetch; e++) {
+                const int jj = lane + 32 * e;
+                eidx[u][e] = 0xffffu;
+                eval[u][e] = 0u;
+                if (jj < nexc) {
+                    eidx[u][e] = __ldg(p.exc_idx[l] + rec[u].y + jj);
+                    eval[u][e] = __ldg(p.exc_val[l] + rec[u].y + jj);
+                }
+            }
+        }
+        cp_async_wait_all();
+        __syncwarp();
+
+#pragma unroll
+        for (int u = 0; u < kDecGroup; u++) {
+            if (u >= ng) break;
+            const int l = g0 + u;
+            const int w = min((int)(rec[u].w & 0xffu), 32), mode = (int)((rec[u].w >> 8) & 0xffu);
+            const int nexc = (int)(rec[u].w >> 16);
+            const uint32_t *buf = (s_dyn + warp * (kDecGroup * kLevelWords)) + u * kLevelWords;
+            uint32_t q[2][8];  // unsigned: prefix sums wrap like the encoder's int32
+            if (w > 0) {
+                const uint32_t mask = width_mask(w);
+#pragma unroll
+                for (int s = 0; s < 2; s++)
+#pragma unroll
+                    for (int x = 0; x < 8; x++) {
+                        const int slot = 8 * (lane + 32 * s) + x;
+                        const int pos = slot * w;
+                        const int wd = pos >> 5;
+                        const uint32_t z = __funnelshift_r(buf[wd], buf[wd + 1], pos & 31) & mask;
+                        q[s][x] = (uint32_t)unzigzag(z);
+                    }
+            } else {
+#pragma unroll
+                for (int s = 0; s < 2; s++)
+#pragma unroll
+                    for (int x = 0; x < 8; x++) q[s][x] = 0u;
+            }
+            if (lane == 0) q[0][0] = rec[u].z;  // anchor
+
+            if (mode == 1) {  // inverse Lorenzo: inclusive prefix sums along x, y, z
+#pragma unroll
+                for (int s = 0; s < 2; s++)
+#pragma unroll
+                    for (int x = 1; x < 8; x++) q[s][x] += q[s][x - 1];
+#pragma unroll
+                for (int o = 1; o < 8; o <<= 1)
+#pragma unroll
+                    for (int s = 0; s < 2; s++)
+#pragma unroll
+                        for (int x = 0; x < 8; x++) {
+                            uint32_t t = __shfl_up_sync(CHR_FULL_MASK, q[s][x], o, 8);
+                            if (ly >= o) q[s][x] += t;
+                        }
+#pragma unroll
+                for (int o = 8; o < 32; o <<= 1)
+#pragma unroll
+                    for (int s = 0; s < 2; s++)
+#pragma unroll
+                        for (int x = 0; x < 8; x++) {
+                            uint32_t t = __shfl_up_sync(CHR_FULL_MASK, q[s][x], o);
+                            if (lane >= o) q[s][x] += t;
+                        }
+#pragma unroll
+                for (int x = 0; x < 8; x++) q[1][x] += __shfl_sync(CHR_FULL_MASK, q[0][x], 24 + ly);
+            }
+
+            const float two_e = p.two_e[l];
 #pragma unroll
             for (int s = 0; s < 2; s++)
 #pragma unroll
                 for (int x = 0; x < 8; x++) {
-                    const int slot = 8 * (lane + 32 * s) + x;
-                    const int pos = slot * w;
-                    const int wd = pos >> 5;
-                    const uint32_t z = __funnelshift_r(buf[wd], buf[wd + 1], pos & 31) & mask;
-                    q[s][x] = (uint32_t)unzigzag(z);
+                    const float P = __fmul_rn(__int2float_rn((int32_t)q[s][x]), two_e);
+                    R[s][x] = (l == 0) ? P : __fadd_rn(R[s][x], P);
                 }
-            __syncwarp();
-        } else {
-#pragma unroll
-            for (int s = 0; s < 2; s++)
-#pragma unroll
-                for (int x = 0; x < 8; x++) q[s][x] = 0u;
-        }
-        if (lane == 0) q[0][0] = rec.z;  // anchor
 
-        if (mode == 1) {  // inverse Lorenzo: inclusive prefix sums along x, y, z
+            if (nexc > 0) {  // vertices stored exactly at this level
+                __syncwarp();
+                float *fb = reinterpret_cast<float *>((s_dyn + warp * (kDecGroup * kLevelWords)) + u * kLevelWords);  // payload no longer needed
 #pragma unroll
-            for (int s = 0; s < 2; s++)
+                for (int s = 0; s < 2; s++) {
+                    const int slot = 8 * (lane + 32 * s);
+                    *reinterpret_cast<float4 *>(fb + slot) = make_float4(R[s][0], R[s][1], R[s][2], R[s][3]);
+                    *reinterpret_cast<float4 *>(fb + slot + 4) = make_float4(R[s][4], R[s][5], R[s][6], R[s][7]);
+                }
+                __syncwarp();
 #pragma unroll
-                for (int x = 1; x < 8; x++) q[s][x] += q[s][x - 1];
+                for (int e = 0; e < kExcPrefetch; e++)
+                    if (lane + 32 * e < nexc) fb[eidx[u][e] & 511] = __uint_as_float(eval[u][e]);
+                for (int j = lane + 32 * kExcPrefetch; j < nexc; j += 32)
+                    fb[__ldg(p.exc_idx[l] + rec[u].y + j) & 511] = __uint_as_float(__ldg(p.exc_val[l] + rec[u].y + j));
+                __syncwarp();
 #pragma unroll
-            for (int o = 1; o < 8; o <<= 1)
-#pragma unroll
-                for (int s = 0; s < 2; s++)
-#pragma unroll
-                    for (int x = 0; x < 8; x++) {
-                        uint32_t t = __shfl_up_sync(CHR_FULL_MASK, q[s][x], o, 8);
-                        if (ly >= o) q[s][x] += t;
-                    }
-#pragma unroll
-            for (int o = 8; o < 32; o <<= 1)
-#pragma unroll
-                for (int s = 0; s < 2; s++)
-#pragma unroll
-                    for (int x = 0; x < 8; x++) {
-                        uint32_t t = __shfl_up_sync(CHR_FULL_MASK, q[s][x], o);
-                        if (lane >= o) q[s][x] += t;
-                    }
-#pragma unroll
-            for (int x = 0; x < 8; x++) q[1][x] += __shfl_sync(CHR_FULL_MASK, q[0][x], 24 + ly);
+                for (int s = 0; s < 2; s++) {
+                    const int slot = 8 * (lane + 32 * s);
+                    const float4 a = *reinterpret_cast<const float4 *>(fb + slot);
+                    const float4 b = *reinterpret_cast<const float4 *>(fb + slot + 4);
+                    R[s][0] = a.x; R[s][1] = a.y; R[s][2] = a.z; R[s][3] = a.w;
+                    R[s][4] = b.x; R[s][5] = b.y; R[s][6] = b.z; R[s][7] = b.w;
+                }
+            }
         }
-
-        const float two_e = p.two_e[l];
-#pragma unroll
-        for (int s = 0; s < 2; s++)
-#pragma unroll
-            for (int x = 0; x < 8; x++) {
-                const float P = __fmul_rn(__int2float_rn((int32_t)q[s][x]), two_e);
-                R[s][x] = (l == 0) ? P : __fadd_rn(R[s][x], P);
-            }
-
-        if (nexc > 0) {  // vertices stored exactly at this level
-            float *fb = reinterpret_cast<float *>(buf);
-#pragma unroll
-            for (int s = 0; s < 2; s++) {
-                const int slot = 8 * (lane + 32 * s);
-                *reinterpret_cast<float4 *>(fb + slot) = make_float4(R[s][0], R[s][1], R[s][2], R[s][3]);
-                *reinterpret_cast<float4 *>(fb + slot + 4) = make_float4(R[s][4], R[s][5], R[s][6], R[s][7]);
-            }
-            __syncwarp();
-            const uint16_t *ei = p.exc_idx[l] + rec.y;
-            const uint32_t *ev = p.exc_val[l] + rec.y;
-            for (int j = lane; j < nexc; j += 32) fb[__ldg(ei + j) & 511] = __uint_as_float(__ldg(ev + j));
-            __syncwarp();
-#pragma unroll
-            for (int s = 0; s < 2; s++) {
-                const int slot = 8 * (lane + 32 * s);
-                float4 a = *reinterpret_cast<const float4 *>(fb + slot);
-                float4 b = *reinterpret_cast<const float4 *>(fb + slot + 4);
-                R[s][0] = a.x; R[s][1] = a.y; R[s][2] = a.z; R[s][3] = a.w;
-                R[s][4] = b.x; R[s][5] = b.y; R[s][6] = b.z; R[s][7] = b.w;
-            }
-            __syncwarp();
-        }
+        __syncwarp();  // shared buffers are refilled by the next group
     }
 
     // store the lane's two rows
@@ -441,18 +574,28 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const __grid_consta
 
 static dim3 codec_grid(const CodecParams &p) { return dim3((unsigned)((int64_t)p.ngx * p.nby * p.nbz)); }
 
-cudaError_t launch_encode(const CodecParams &p, bool pack, cudaStream_t s)
+cudaError_t launch_encode(const CodecParams &p, cudaStream_t s)
 {
-    if (pack)
-        k_encode<true><<<codec_grid(p), 256, 0, s>>>(p);
-    else
-        k_encode<false><<<codec_grid(p), 256, 0, s>>>(p);
+    k_encode<<<codec_grid(p), 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const CodecParams &p, cudaStream_t s)
+{
+    const dim3 g = codec_grid(p);
+    k_compact<<<dim3(g.x, (unsigned)p.nlevels), 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_decode(const CodecParams &p, cudaStream_t s)
 {
-    k_decode<<<codec_grid(p), 256, 0, s>>>(p);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, kDecodeSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_decode<<<codec_grid(p), 256, kDecodeSmem, s>>>(p);
     return cudaGetLastError();
 }
 

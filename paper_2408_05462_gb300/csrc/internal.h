@@ -47,9 +47,17 @@ struct CodecParams {
     uint32_t *words[CHR_MAX_LEVELS];
     uint16_t *exc_idx[CHR_MAX_LEVELS];
     uint32_t *exc_val[CHR_MAX_LEVELS];
+    // encode scratch: fixed per-brick slots (512 words, 512 exception entries)
+    uint32_t *slot_words[CHR_MAX_LEVELS];
+    uint16_t *slot_idx[CHR_MAX_LEVELS];
+    uint32_t *slot_val[CHR_MAX_LEVELS];
 };
 
-cudaError_t launch_encode(const CodecParams &p, bool pack, cudaStream_t s);
+// Encode scratch per level: 512 words + 512 exception entries per brick.
+inline size_t encode_slot_bytes(int64_t nbricks) { return (size_t)nbricks * 512 * (4 + 2 + 4); }
+
+cudaError_t launch_encode(const CodecParams &p, cudaStream_t s);
+cudaError_t launch_compact(const CodecParams &p, cudaStream_t s);
 cudaError_t launch_decode(const CodecParams &p, cudaStream_t s);
 // Exclusive scans of the widths and exception counts of each level's records;
 // totals[2*l] = sum of w, totals[2*l+1] = exceptions.  scratch needs

@@ -40,17 +40,18 @@ constexpr int kRows = 81;                              // rows of the box (9 y x
 constexpr int kTileBytes = kRows * kVX * 4;            // 11664
 constexpr int kBufBytes = ((kTileBytes + 127) / 128) * 128;
 constexpr int kCells = 64 * 8 * kMcBricksX;            // cells per tile (2048)
-constexpr int kMaxTriTile = kCells * CHR_MC_MAX_TRI;   // triangles per tile and isovalue, at most
 constexpr int kWarpStage = 32 * 9 + 4;                 // floats staged per warp: 32 triangles + alignment pad
 
 // dynamic shared memory (bytes)
 constexpr int kOffBuf = 0;                                       // 2 x float box
 constexpr int kOffRow = 2 * kBufBytes;                           // uint64 [4][81] inside masks per row
-constexpr int kOffTab = kOffRow + kMcIsoPerPass * kRows * 8;     // uint64 [256] case table
-constexpr int kCountSmem = kOffTab + 256 * 8 + 128;  // + alignment slack
-constexpr int kOffCase = kOffTab + 256 * 8;                      // uint8 [4][2048] case bytes
-constexpr int kOffMap = kOffCase + kMcIsoPerPass * kCells;       // uint16 [10240] triangle -> cell<<3|t
-constexpr int kOffStage = kOffMap + kMaxTriTile * 2;             // float [8][32*9+4]
+constexpr int kOffCnt = kOffRow + kMcIsoPerPass * kRows * 8;     // uint8 [256] triangles per case
+constexpr int kCountSmem = kOffCnt + 256 + 128;                  // + alignment slack
+constexpr int kOffTri = kOffCnt + 256;                           // uint32 [256][5] edges of each triangle
+constexpr int kOffEdge = kOffTri + 256 * CHR_MC_MAX_TRI * 4;     // EdgeVec [12]
+constexpr int kOffCase = kOffEdge + 12 * 32;                     // uint8 [4][2048] case bytes
+constexpr int kOffPre = kOffCase + kMcIsoPerPass * kCells;       // uint16 [8][256] per-cell prefix counts
+constexpr int kOffStage = kOffPre + kCells * 2;                  // float [8][32*9+4]
 constexpr int kEmitSmem = kOffStage + 8 * kWarpStage * 4 + 128;  // + alignment slack
 
 struct McParams {
@@ -71,12 +72,15 @@ struct TileXYZ {
     int64_t x0, y0, z0;
 };
 
+// Tile indices fit 32 bits (a grid has < 2^32 vertices, a tile 2048 cells).
 __device__ __forceinline__ TileXYZ tile_origin(const McParams &p, int64_t tile)
 {
+    const uint32_t t = (uint32_t)tile, ntx = (uint32_t)p.ntx, nby = (uint32_t)p.ncby;
+    const uint32_t q = t / ntx, z = q / nby;
     TileXYZ o;
-    o.x0 = (tile % p.ntx) * kTX;
-    o.y0 = ((tile / p.ntx) % p.ncby) * 8;
-    o.z0 = (tile / ((int64_t)p.ntx * p.ncby)) * 8;
+    o.x0 = (int64_t)(t - q * ntx) * kTX;
+    o.y0 = (int64_t)(q - z * nby) * 8;
+    o.z0 = (int64_t)z * 8;
     return o;
 }
 
@@ -117,10 +121,34 @@ __device__ __forceinline__ void row_masks(const float *buf, uint64_t *s_row, con
     }
 }
 
-// Case byte of cell x (0..7) of a thread from its four 9-bit row masks.
-__device__ __forceinline__ uint32_t case_of(uint32_t m0, uint32_t m1, uint32_t m2, uint32_t m3, int x)
+// Byte x of the result = bit x of v (v < 16): the four shifted copies of v
+// made by the multiply do not overlap, so masking keeps one bit per byte.
+__device__ __forceinline__ uint32_t spread4(uint32_t v) { return (v * 0x00204081u) & 0x01010101u; }
+
+// Bytes x = 0..3 (lo) and 4..7 (hi) hold b(x) | b(x+1) << 1 of a 9-bit row mask.
+__device__ __forceinline__ void pair_bytes(uint32_t m, uint32_t &lo, uint32_t &hi)
 {
-    return ((m0 >> x) & 3u) | (((m1 >> x) & 3u) << 2) | (((m2 >> x) & 3u) << 4) | (((m3 >> x) & 3u) << 6);
+    lo = spread4(m & 15u) | (spread4((m >> 1) & 15u) << 1);
+    hi = spread4((m >> 4) & 15u) | (spread4((m >> 5) & 15u) << 1);
+}
+
+// Case bytes of this thread's 8 cells from the inside masks of its four rows
+// (y, z), (y+1, z), (y, z+1), (y+1, z+1): corner j = ox + 2*oy + 4*oz is bit j.
+// Cells past `nvalid` get case 0.
+__device__ __forceinline__ void cases8(const uint64_t *R, int r00, int j, int nvalid, uint32_t &lo, uint32_t &hi)
+{
+    uint32_t l0, h0, l1, h1, l2, h2, l3, h3;
+    pair_bytes((uint32_t)(R[r00] >> (8 * j)) & 511u, l0, h0);
+    pair_bytes((uint32_t)(R[r00 + 1] >> (8 * j)) & 511u, l1, h1);
+    pair_bytes((uint32_t)(R[r00 + 9] >> (8 * j)) & 511u, l2, h2);
+    pair_bytes((uint32_t)(R[r00 + 10] >> (8 * j)) & 511u, l3, h3);
+    lo = l0 | (l1 << 2) | (l2 << 4) | (l3 << 6);
+    hi = h0 | (h1 << 2) | (h2 << 4) | (h3 << 6);
+    if (nvalid < 8) {
+        const uint64_t keep = (nvalid <= 0) ? 0ull : ((1ull << (8 * nvalid)) - 1ull);
+        lo &= (uint32_t)keep;
+        hi &= (uint32_t)(keep >> 32);
+    }
 }
 
 __device__ __forceinline__ int valid_cells(const McParams &p, const TileXYZ &o)
@@ -185,7 +213,7 @@ __global__ void __launch_bounds__(256) k_mc_count(const __grid_constant__ McPara
     unsigned char *smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     float *bufs = reinterpret_cast<float *>(smem + kOffBuf);
     uint64_t *s_row = reinterpret_cast<uint64_t *>(smem + kOffRow);
-    uint8_t *s_cnt = smem + kOffTab;  // triangle count per case
+    uint8_t *s_cnt = smem + kOffCnt;  // triangle count per case
     __shared__ uint64_t mbar[2];
     __shared__ uint32_t s_sum[8][kMcIsoPerPass];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -198,21 +226,16 @@ __global__ void __launch_bounds__(256) k_mc_count(const __grid_constant__ McPara
         const int nvalid = valid_cells(p, o);
         const int j = tid >> 6, ly = tid & 7, lz = (tid >> 3) & 7;
         const int r00 = lz * 9 + ly;
-        uint32_t cnt[NISO];
 #pragma unroll
         for (int i = 0; i < NISO; i++) {
-            const uint64_t *R = s_row + i * kRows;
-            const uint32_t m0 = (uint32_t)(R[r00] >> (8 * j)), m1 = (uint32_t)(R[r00 + 1] >> (8 * j));
-            const uint32_t m2 = (uint32_t)(R[r00 + 9] >> (8 * j)), m3 = (uint32_t)(R[r00 + 10] >> (8 * j));
+            uint32_t lo, hi;
+            cases8(s_row + i * kRows, r00, j, nvalid, lo, hi);
             uint32_t c = 0;
 #pragma unroll
-            for (int x = 0; x < 8; x++)
-                if (x < nvalid) c += s_cnt[case_of(m0, m1, m2, m3, x)];
-            cnt[i] = __reduce_add_sync(CHR_FULL_MASK, c);
+            for (int x = 0; x < 4; x++) c += s_cnt[(lo >> (8 * x)) & 0xffu] + s_cnt[(hi >> (8 * x)) & 0xffu];
+            c = __reduce_add_sync(CHR_FULL_MASK, c);
+            if (lane == 0) s_sum[warp][i] = c;
         }
-#pragma unroll
-        for (int i = 0; i < NISO; i++)
-            if (lane == 0) s_sum[warp][i] = cnt[i];
         __syncthreads();
         if (tid == 0) {
             uint32_t t[kMcIsoPerPass] = {0, 0, 0, 0};
@@ -225,24 +248,33 @@ __global__ void __launch_bounds__(256) k_mc_count(const __grid_constant__ McPara
     });
 }
 
-// Edge e of a cell: offset of its lower corner in the box, the step to its
-// upper corner, and (ox, oy, oz, axis) packed as ox | oy<<1 | oz<<2 | axis<<3.
-struct EdgeInfo {
-    int16_t delta, step;
-    int32_t bits;
+// Edge e of a cell: the float offsets (ox, oy, oz) of its lower corner, the
+// corner's offset in the box, the unit vector along the edge, and the box
+// step to the upper corner.  A crossing at parameter t then sits at
+// fma(t, dir, cell + off), i.e. (cell + off) + t along the edge axis.
+struct __align__(16) EdgeVec {
+    float ox, oy, oz;
+    int delta;
+    float dx, dy, dz;
+    int step;
 };
 
-__device__ __forceinline__ EdgeInfo edge_info(int e)
+__device__ __forceinline__ EdgeVec edge_vec(int e)
 {
     const int axis = e >> 2, m = e & 3;
     const int ox = (axis == 0) ? 0 : (m & 1);
     const int oy = (axis == 1) ? 0 : ((axis == 0) ? (m & 1) : (m >> 1));
     const int oz = (axis == 2) ? 0 : (m >> 1);
-    EdgeInfo ei;
-    ei.delta = (int16_t)(ox + oy * kVX + oz * kPlane);
-    ei.step = (int16_t)((axis == 0) ? 1 : (axis == 1) ? kVX : kPlane);
-    ei.bits = ox | (oy << 1) | (oz << 2) | (axis << 3);
-    return ei;
+    EdgeVec v;
+    v.ox = (float)ox;
+    v.oy = (float)oy;
+    v.oz = (float)oz;
+    v.delta = ox + oy * kVX + oz * kPlane;
+    v.dx = (axis == 0) ? 1.0f : 0.0f;
+    v.dy = (axis == 1) ? 1.0f : 0.0f;
+    v.dz = (axis == 2) ? 1.0f : 0.0f;
+    v.step = (axis == 0) ? 1 : (axis == 1) ? kVX : kPlane;
+    return v;
 }
 
 // t = (k - f0) / (f1 - f0): the edge parameter of a crossing.  f0 and f1 lie
@@ -255,47 +287,52 @@ __device__ __forceinline__ float edge_t(float k, float f0, float f1)
     return (fabsf(den) < 8.5e37f) ? __fdividef(num, den) : __fdiv_rn(num, den);
 }
 
-// One triangle of cell c (tile-local index) into dst[0..8].
-__device__ __forceinline__ void make_triangle(float *dst, const float *box, const EdgeInfo *s_edge, uint64_t word, int t,
-                                              int c, float k, float fx0, float fy0, float fz0)
+// Triangle `tri` (three edge numbers, one per byte) of cell c (tile-local
+// index) into dst[0..8].
+__device__ __forceinline__ void make_triangle(float *dst, const float *box, const EdgeVec *s_edge, uint32_t tri, int c,
+                                              float k, float fx0, float fy0, float fz0)
 {
     const int lx = c & 7, tt = c >> 3, ly = tt & 7, lz = (tt >> 3) & 7, j = tt >> 6;
     const float *cell = box + lz * kPlane + ly * kVX + 8 * j + lx;
     const float cx = fx0 + (float)(8 * j + lx), cy = fy0 + (float)ly, cz = fz0 + (float)lz;
 #pragma unroll
     for (int v = 0; v < 3; v++) {
-        const EdgeInfo ei = s_edge[(word >> (12 * t + 4 * v)) & 15u];
-        const float *p0 = cell + ei.delta;
-        const float tv = edge_t(k, p0[0], p0[ei.step]);
-        const int axis = ei.bits >> 3;
-        float px = cx + (float)(ei.bits & 1), py = cy + (float)((ei.bits >> 1) & 1), pz = cz + (float)((ei.bits >> 2) & 1);
-        if (axis == 0) px = __fadd_rn(px, tv);
-        if (axis == 1) py = __fadd_rn(py, tv);
-        if (axis == 2) pz = __fadd_rn(pz, tv);
-        dst[3 * v + 0] = px;
-        dst[3 * v + 1] = py;
-        dst[3 * v + 2] = pz;
+        const EdgeVec E = s_edge[(tri >> (8 * v)) & 0xffu];
+        const float *p0 = cell + E.delta;
+        const float tv = edge_t(k, p0[0], p0[E.step]);
+        dst[3 * v + 0] = __fmaf_rn(tv, E.dx, cx + E.ox);
+        dst[3 * v + 1] = __fmaf_rn(tv, E.dy, cy + E.oy);
+        dst[3 * v + 2] = __fmaf_rn(tv, E.dz, cz + E.oz);
     }
 }
 
 template <int NISO>
-__global__ void __launch_bounds__(256, 3) k_mc_emit(const __grid_constant__ McParams p,
+__global__ void __launch_bounds__(256, 4) k_mc_emit(const __grid_constant__ McParams p,
                                                    const __grid_constant__ CUtensorMap map)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     float *bufs = reinterpret_cast<float *>(smem + kOffBuf);
     uint64_t *s_row = reinterpret_cast<uint64_t *>(smem + kOffRow);
-    uint64_t *s_tab = reinterpret_cast<uint64_t *>(smem + kOffTab);
+    uint8_t *s_cnt = smem + kOffCnt;
+    uint32_t *s_tri = reinterpret_cast<uint32_t *>(smem + kOffTri);
+    EdgeVec *s_edge = reinterpret_cast<EdgeVec *>(smem + kOffEdge);
     uint8_t *s_case = smem + kOffCase;
-    uint16_t *s_map = reinterpret_cast<uint16_t *>(smem + kOffMap);
     __shared__ uint64_t mbar[2];
     __shared__ uint64_t s_warp[9];
-    __shared__ EdgeInfo s_edge[12];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint16_t *s_pre = reinterpret_cast<uint16_t *>(smem + kOffPre) + warp * 256;  // this warp's 256 cells
     float *s_stage = reinterpret_cast<float *>(smem + kOffStage) + warp * kWarpStage;
-    s_tab[tid] = g_mc_case[tid];
-    if (tid < 12) s_edge[tid] = edge_info(tid);
+    s_cnt[tid] = (uint8_t)(g_mc_case[tid] >> 60);
+    for (int i = tid; i < 256 * CHR_MC_MAX_TRI; i += 256) {
+        const uint64_t word = g_mc_case[i / CHR_MC_MAX_TRI];
+        const int t = i % CHR_MC_MAX_TRI;
+        uint32_t tri = 0;
+        if (t < (int)(word >> 60))
+            for (int v = 0; v < 3; v++) tri |= (uint32_t)((word >> (12 * t + 4 * v)) & 15u) << (8 * v);
+        s_tri[i] = tri;
+    }
+    if (tid < 12) s_edge[tid] = edge_vec(tid);
 
     tile_loop(p, &map, bufs, mbar, [&](int64_t tile, const float *box) {
         row_masks<NISO>(box, s_row, p);
@@ -307,69 +344,70 @@ __global__ void __launch_bounds__(256, 3) k_mc_emit(const __grid_constant__ McPa
         uint64_t packed = 0;
 #pragma unroll
         for (int i = 0; i < NISO; i++) {
-            const uint64_t *R = s_row + i * kRows;
-            const uint32_t m0 = (uint32_t)(R[r00] >> (8 * j)), m1 = (uint32_t)(R[r00 + 1] >> (8 * j));
-            const uint32_t m2 = (uint32_t)(R[r00 + 9] >> (8 * j)), m3 = (uint32_t)(R[r00 + 10] >> (8 * j));
-            uint32_t cnt = 0, lo = 0, hi = 0;
+            uint32_t lo, hi;
+            cases8(s_row + i * kRows, r00, j, nvalid, lo, hi);
+            uint32_t cnt = 0;
 #pragma unroll
-            for (int x = 0; x < 8; x++) {
-                const uint32_t cs = (x < nvalid) ? case_of(m0, m1, m2, m3, x) : 0u;
-                cnt += (uint32_t)(s_tab[cs] >> 60);
-                if (x < 4)
-                    lo |= cs << (8 * x);
-                else
-                    hi |= cs << (8 * (x - 4));
-            }
+            for (int x = 0; x < 4; x++) cnt += s_cnt[(lo >> (8 * x)) & 0xffu] + s_cnt[(hi >> (8 * x)) & 0xffu];
             *reinterpret_cast<uint2 *>(s_case + i * kCells + tid * 8) = make_uint2(lo, hi);
             packed |= (uint64_t)cnt << (16 * i);
         }
-        // block scan of the four 16-bit counts
+        // warp scan, then the block's warp offsets (four 16-bit counts per word)
         const uint64_t inc = warp_incl_scan_u64(packed, lane);
+        const uint64_t lane_excl = inc - packed;
         if (lane == 31) s_warp[warp] = inc;
         __syncthreads();
         if (warp == 0) {
             const uint64_t t = (lane < 8) ? s_warp[lane] : 0ull;
             const uint64_t ti = warp_incl_scan_u64(t, lane);
             if (lane < 8) s_warp[lane] = ti - t;
-            if (lane == 7) s_warp[8] = ti;
         }
         __syncthreads();
-        const uint64_t thread_excl = s_warp[warp] + inc - packed;
-        const uint64_t block_total = s_warp[8];
+        const uint64_t warp_excl = s_warp[warp];
+        const uint64_t warp_tot = __shfl_sync(CHR_FULL_MASK, inc, 31);
         const float fx0 = (float)o.x0, fy0 = (float)o.y0, fz0 = (float)o.z0;
+        const uint8_t *wcase = s_case + warp * 256;  // + i * kCells: this warp's cells
 
+        // every warp writes the triangles of its own 256 cells, 32 at a time
 #pragma unroll 1
         for (int i = 0; i < NISO; i++) {
-            const int n = (int)((block_total >> (16 * i)) & 0xffffull);
-            if (n == 0) continue;  // uniform
-            {
-                uint32_t off = (uint32_t)((thread_excl >> (16 * i)) & 0xffffull);
-                const uint2 cw = *reinterpret_cast<const uint2 *>(s_case + i * kCells + tid * 8);
+            const int W = (int)((warp_tot >> (16 * i)) & 0xffffull);
+            if (W == 0) continue;  // uniform across the warp
+            {   // per-cell exclusive prefix of the warp's triangles, 8 cells per lane in one 16-byte store
+                const uint2 cw = *reinterpret_cast<const uint2 *>(wcase + i * kCells + lane * 8);
+                uint32_t run = (uint32_t)((lane_excl >> (16 * i)) & 0xffffull);
+                uint32_t pk[4];
 #pragma unroll
-                for (int x = 0; x < 8; x++) {
-                    const uint32_t cs = ((x < 4 ? cw.x : cw.y) >> (8 * (x & 3))) & 0xffu;
-                    const int nt = (int)(s_tab[cs] >> 60);
-                    for (int t = 0; t < nt; t++) s_map[off++] = (uint16_t)(((tid * 8 + x) << 3) | t);
+                for (int x = 0; x < 8; x += 2) {
+                    const uint32_t c0 = ((x < 4 ? cw.x : cw.y) >> (8 * (x & 3))) & 0xffu;
+                    const uint32_t c1 = ((x < 4 ? cw.x : cw.y) >> (8 * ((x + 1) & 3))) & 0xffu;
+                    const uint32_t a = run;
+                    run += s_cnt[c0];
+                    pk[x >> 1] = a | (run << 16);
+                    run += s_cnt[c1];
                 }
+                *reinterpret_cast<uint4 *>(s_pre + lane * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
             }
-            __syncthreads();
-            // each warp writes a contiguous eighth of the tile's triangles, 32 at a time
-            const int w0 = (warp * n) >> 3, w1 = ((warp + 1) * n) >> 3;
-            const uint64_t g0 = __ldg(p.tile_off + tile * kMcIsoPerPass + i);
+            __syncwarp();
+            const uint64_t g0 = __ldg(p.tile_off + tile * kMcIsoPerPass + i) + ((warp_excl >> (16 * i)) & 0xffffull);
             const float k = p.k[i];
-            float *out = p.tris[i];
-            for (int base = w0; base < w1; base += 32) {
-                const uint64_t gbase = g0 + (uint64_t)base;
-                if (gbase >= p.cap) break;  // uniform across the warp
-                int mm = (w1 - base) < 32 ? (w1 - base) : 32;
-                if (gbase + (uint64_t)mm > p.cap) mm = (int)(p.cap - gbase);
-                float *dst = out + 9ull * gbase;
+            // triangles of this warp that fit below cap (the rest are counted, not written)
+            const int lim = (g0 >= p.cap) ? 0 : (int)((p.cap - g0) < (uint64_t)W ? (p.cap - g0) : (uint64_t)W);
+            float *wout = p.tris[i] + 9ull * g0;
+            for (int base = 0; base < lim; base += 32) {
+                const int mm = (lim - base) < 32 ? (lim - base) : 32;
+                float *dst = wout + 9 * base;
                 const int pad = (int)((reinterpret_cast<uintptr_t>(dst) >> 2) & 3u);
                 if (lane < mm) {
-                    const uint32_t ent = s_map[base + lane];
-                    const int c = (int)(ent >> 3), t = (int)(ent & 7u);
-                    const uint64_t word = s_tab[s_case[i * kCells + c]];
-                    make_triangle(s_stage + pad + 9 * lane, box, s_edge, word, t, c, k, fx0, fy0, fz0);
+                    // the last of the warp's cells whose prefix is <= m owns triangle m
+                    const int m = base + lane;
+                    int c = 0;
+#pragma unroll
+                    for (int step = 128; step > 0; step >>= 1)
+                        if ((int)s_pre[c + step] <= m) c += step;
+                    const int t = m - (int)s_pre[c];
+                    const uint32_t tri = s_tri[wcase[i * kCells + c] * CHR_MC_MAX_TRI + t];
+                    make_triangle(s_stage + pad + 9 * lane, box, s_edge, tri, warp * 256 + c, k, fx0, fy0, fz0);
                 }
                 __syncwarp();
                 // dst[q] = s_stage[pad + q]; dst + q is 16-byte aligned when (pad + q) % 4 == 0
@@ -384,7 +422,6 @@ __global__ void __launch_bounds__(256, 3) k_mc_emit(const __grid_constant__ McPa
                 if (lane < F - tail0) __stcs(dst + tail0 + lane, s_stage[pad + tail0 + lane]);
                 __syncwarp();
             }
-            __syncthreads();  // the map is rebuilt for the next isovalue
         }
     });
 }
