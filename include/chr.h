@@ -176,6 +176,30 @@ chr_status isosurface_extract(const float *d_field, chr_dims dims, const float *
                               size_t workspace_bytes, void *stream);
 
 /*
+ * isosurface_extract_noalloc — isosurface_extract for callers that may not
+ * allocate device memory: code inside an application or framework that owns
+ * all GPU memory through its own pool, plugins and callbacks that must not
+ * allocate, and latency-bound loops that cannot afford an allocation (which
+ * may synchronise the device).  The paper has no counterpart; this is a
+ * deployment convenience of this library.
+ *
+ * Same arguments, outputs and results as isosurface_extract, without the
+ * workspace: the scratch is one fixed 4 MiB array in the library's device
+ * image, present on every GPU that loads the library until the process
+ * exits.  Grids needing more scratch than that (more than about 87,000 tiles
+ * of 32x8x8 cells, i.e. roughly 178 million cells; a 512^3 grid fits) are
+ * rejected with CHR_ERR_INVALID before any work is enqueued.
+ * The first call on each device looks up the array's device address with
+ * that device current; make that first call before any stream capture.
+ * All calls share the one array, so calls whose work overlaps on a GPU race
+ * on it and must be serialised by the caller.  No call clears it: every
+ * scratch value is written before it is read.  Asynchronous.
+ */
+chr_status isosurface_extract_noalloc(const float *d_field, chr_dims dims, const float *isovalues, uint32_t n_iso,
+                                      float *d_tris, uint64_t cap_tris, uint64_t *d_ntris, uint32_t *d_err,
+                                      void *stream);
+
+/*
  * chr_serialize — the CHR as one little-endian byte string, the form that
  * crosses the network in the paper's in-transit setting (Sec. 3 streams it
  * over a WAN).  Writes into host_buf when cap >= the size; *need always

@@ -7,8 +7,8 @@ to the library as a chr_allocator) and the current CUDA stream.  There is no
 CPU path: if libchr.so is missing or cannot load, every call raises.
 
 Names follow the C ABI: chr_compress, chr_reconstruct, chr_topo_translate,
-isosurface_extract, isosurface_workspace_size, chr_serialize,
-chr_deserialize, chr_stats, chr_free.
+isosurface_extract, isosurface_workspace_size, isosurface_extract_noalloc,
+chr_serialize, chr_deserialize, chr_stats, chr_free.
 """
 from __future__ import annotations
 
@@ -88,6 +88,9 @@ def lib():
         L.isosurface_extract.restype = st
         L.isosurface_extract.argtypes = [c_void_p, ChrDims, POINTER(c_float), c_uint32, c_void_p, c_uint64, c_void_p,
                                          c_void_p, c_void_p, c_size_t, c_void_p]
+        L.isosurface_extract_noalloc.restype = st
+        L.isosurface_extract_noalloc.argtypes = [c_void_p, ChrDims, POINTER(c_float), c_uint32, c_void_p, c_uint64,
+                                                 c_void_p, c_void_p, c_void_p]
         L.chr_serialize.restype = st
         L.chr_serialize.argtypes = [c_void_p, c_void_p, c_size_t, POINTER(c_size_t), c_void_p]
         L.chr_deserialize.restype = st
@@ -244,6 +247,28 @@ def isosurface_extract(field: torch.Tensor, isovalues, cap: int, tris: torch.Ten
     _check(lib().isosurface_extract(field.data_ptr(), _dims(field), iso, ni, tris.data_ptr() if cap > 0 else None,
                                     int(cap), counts.data_ptr(), err.data_ptr(), workspace.data_ptr(),
                                     workspace.numel(), _stream(stream)))
+    return tris, counts, err
+
+
+def isosurface_extract_noalloc(field: torch.Tensor, isovalues, cap: int, tris: torch.Tensor | None = None,
+                               counts: torch.Tensor | None = None, err: torch.Tensor | None = None, stream=None):
+    """isosurface_extract without a workspace: the library's fixed device
+    scratch is used, so the call itself allocates nothing (chr.h:
+    isosurface_extract_noalloc).  Output tensors passed in are used as they
+    are; tensors left as None are created here, for convenience."""
+    _check_field(field)
+    iso, ni = _floats(isovalues)
+    if tris is None:
+        tris = torch.empty((ni, max(int(cap), 0), 3, 3), dtype=torch.float32, device="cuda")
+    if counts is None:
+        counts = torch.empty(ni, dtype=torch.int64, device="cuda")
+    if err is None:
+        err = torch.empty(1, dtype=torch.int32, device="cuda")
+    if tris.numel() < ni * int(cap) * 9:
+        raise ValueError("tris too small for n_iso * cap triangles")
+    _check(lib().isosurface_extract_noalloc(field.data_ptr(), _dims(field), iso, ni,
+                                            tris.data_ptr() if cap > 0 else None, int(cap), counts.data_ptr(),
+                                            err.data_ptr(), _stream(stream)))
     return tris, counts, err
 
 
