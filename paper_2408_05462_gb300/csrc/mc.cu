@@ -50,7 +50,7 @@ constexpr int kCountSmem = kOffCnt + 256 + 128;                  // + alignment 
 constexpr int kOffTri = kOffCnt + 256;                           // uint32 [256][5] edges of each triangle
 constexpr int kOffEdge = kOffTri + 256 * CHR_MC_MAX_TRI * 4;     // EdgeVec [12]
 constexpr int kOffCase = kOffEdge + 12 * 32;                     // uint8 [4][2048] case bytes
-constexpr int kOffPre = kOffCase + kMcIsoPerPass * kCells;       // uint16 [8][256] per-cell prefix counts
+constexpr int kOffPre = kOffCase + kMcIsoPerPass * kCells;       // uint16 [2048] per-cell prefix counts
 constexpr int kOffStage = kOffPre + kCells * 2;                  // float [8][32*9+4]
 constexpr int kEmitSmem = kOffStage + 8 * kWarpStage * 4 + 128;  // + alignment slack
 
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(256, 4) k_mc_emit(const __grid_constant__ McPa
     __shared__ uint64_t mbar[2];
     __shared__ uint64_t s_warp[9];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    uint16_t *s_pre = reinterpret_cast<uint16_t *>(smem + kOffPre) + warp * 256;  // this warp's 256 cells
+    uint16_t *s_pre = reinterpret_cast<uint16_t *>(smem + kOffPre);  // per-cell triangle prefix of the tile
     float *s_stage = reinterpret_cast<float *>(smem + kOffStage) + warp * kWarpStage;
     s_cnt[tid] = (uint8_t)(g_mc_case[tid] >> 60);
     for (int i = tid; i < 256 * CHR_MC_MAX_TRI; i += 256) {
@@ -352,30 +352,28 @@ __global__ void __launch_bounds__(256, 4) k_mc_emit(const __grid_constant__ McPa
             *reinterpret_cast<uint2 *>(s_case + i * kCells + tid * 8) = make_uint2(lo, hi);
             packed |= (uint64_t)cnt << (16 * i);
         }
-        // warp scan, then the block's warp offsets (four 16-bit counts per word)
+        // block scan of the four 16-bit counts
         const uint64_t inc = warp_incl_scan_u64(packed, lane);
-        const uint64_t lane_excl = inc - packed;
         if (lane == 31) s_warp[warp] = inc;
         __syncthreads();
         if (warp == 0) {
             const uint64_t t = (lane < 8) ? s_warp[lane] : 0ull;
             const uint64_t ti = warp_incl_scan_u64(t, lane);
             if (lane < 8) s_warp[lane] = ti - t;
+            if (lane == 7) s_warp[8] = ti;
         }
         __syncthreads();
-        const uint64_t warp_excl = s_warp[warp];
-        const uint64_t warp_tot = __shfl_sync(CHR_FULL_MASK, inc, 31);
+        const uint64_t thread_excl = s_warp[warp] + inc - packed;
+        const uint64_t block_total = s_warp[8];
         const float fx0 = (float)o.x0, fy0 = (float)o.y0, fz0 = (float)o.z0;
-        const uint8_t *wcase = s_case + warp * 256;  // + i * kCells: this warp's cells
 
-        // every warp writes the triangles of its own 256 cells, 32 at a time
 #pragma unroll 1
         for (int i = 0; i < NISO; i++) {
-            const int W = (int)((warp_tot >> (16 * i)) & 0xffffull);
-            if (W == 0) continue;  // uniform across the warp
-            {   // per-cell exclusive prefix of the warp's triangles, 8 cells per lane in one 16-byte store
-                const uint2 cw = *reinterpret_cast<const uint2 *>(wcase + i * kCells + lane * 8);
-                uint32_t run = (uint32_t)((lane_excl >> (16 * i)) & 0xffffull);
+            const int n = (int)((block_total >> (16 * i)) & 0xffffull);
+            if (n == 0) continue;  // uniform across the block
+            {   // per-cell exclusive prefix of the tile's triangles, 8 cells per thread in one 16-byte store
+                const uint2 cw = *reinterpret_cast<const uint2 *>(s_case + i * kCells + tid * 8);
+                uint32_t run = (uint32_t)((thread_excl >> (16 * i)) & 0xffffull);
                 uint32_t pk[4];
 #pragma unroll
                 for (int x = 0; x < 8; x += 2) {
@@ -386,28 +384,30 @@ __global__ void __launch_bounds__(256, 4) k_mc_emit(const __grid_constant__ McPa
                     pk[x >> 1] = a | (run << 16);
                     run += s_cnt[c1];
                 }
-                *reinterpret_cast<uint4 *>(s_pre + lane * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                *reinterpret_cast<uint4 *>(s_pre + tid * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
             }
-            __syncwarp();
-            const uint64_t g0 = __ldg(p.tile_off + tile * kMcIsoPerPass + i) + ((warp_excl >> (16 * i)) & 0xffffull);
+            __syncthreads();
+            const uint64_t g0 = __ldg(p.tile_off + tile * kMcIsoPerPass + i);
             const float k = p.k[i];
-            // triangles of this warp that fit below cap (the rest are counted, not written)
-            const int lim = (g0 >= p.cap) ? 0 : (int)((p.cap - g0) < (uint64_t)W ? (p.cap - g0) : (uint64_t)W);
-            float *wout = p.tris[i] + 9ull * g0;
-            for (int base = 0; base < lim; base += 32) {
+            // triangles of this tile that fit below cap (the rest are counted, not written)
+            const int lim = (g0 >= p.cap) ? 0 : (int)((p.cap - g0) < (uint64_t)n ? (p.cap - g0) : (uint64_t)n);
+            float *tout = p.tris[i] + 9ull * g0;
+            const uint8_t *icase = s_case + i * kCells;
+            // 32-triangle chunks dealt round-robin to the warps
+            for (int base = warp * 32; base < lim; base += 8 * 32) {
                 const int mm = (lim - base) < 32 ? (lim - base) : 32;
-                float *dst = wout + 9 * base;
+                float *dst = tout + 9 * base;
                 const int pad = (int)((reinterpret_cast<uintptr_t>(dst) >> 2) & 3u);
                 if (lane < mm) {
-                    // the last of the warp's cells whose prefix is <= m owns triangle m
+                    // the last cell whose prefix is <= m owns triangle m
                     const int m = base + lane;
                     int c = 0;
 #pragma unroll
-                    for (int step = 128; step > 0; step >>= 1)
+                    for (int step = 1024; step > 0; step >>= 1)
                         if ((int)s_pre[c + step] <= m) c += step;
                     const int t = m - (int)s_pre[c];
-                    const uint32_t tri = s_tri[wcase[i * kCells + c] * CHR_MC_MAX_TRI + t];
-                    make_triangle(s_stage + pad + 9 * lane, box, s_edge, tri, warp * 256 + c, k, fx0, fy0, fz0);
+                    const uint32_t tri = s_tri[icase[c] * CHR_MC_MAX_TRI + t];
+                    make_triangle(s_stage + pad + 9 * lane, box, s_edge, tri, c, k, fx0, fy0, fz0);
                 }
                 __syncwarp();
                 // dst[q] = s_stage[pad + q]; dst + q is 16-byte aligned when (pad + q) % 4 == 0
@@ -422,6 +422,7 @@ __global__ void __launch_bounds__(256, 4) k_mc_emit(const __grid_constant__ McPa
                 if (lane < F - tail0) __stcs(dst + tail0 + lane, s_stage[pad + tail0 + lane]);
                 __syncwarp();
             }
+            __syncthreads();  // the prefix array is rewritten for the next isovalue
         }
     });
 }
