@@ -32,41 +32,6 @@ __device__ __forceinline__ bool brick_of_warp(const CodecParams &p, BrickCoord &
     return c.bx < p.nbx;
 }
 
-// Loads the lane's two rows of the field; out-of-grid values read as 0 and are
-// flagged off in *valid (bit s*8 + x).
-__device__ __forceinline__ void load_rows(const CodecParams &p, const BrickCoord &c, int lane, float (&v)[2][8],
-                                          uint32_t &valid)
-{
-    const int64_t x0 = (int64_t)c.bx * 8;
-    const int ex = (int)((p.nx - x0) < 8 ? (p.nx - x0) : 8);
-    const bool vec = (ex == 8) && ((p.nx & 3) == 0) && ((reinterpret_cast<uintptr_t>(p.f) & 15u) == 0);
-    valid = 0;
-#pragma unroll
-    for (int s = 0; s < 2; s++) {
-        const int64_t y = (int64_t)c.by * 8 + (lane & 7);
-        const int64_t z = (int64_t)c.bz * 8 + (lane >> 3) + 4 * s;
-        const bool rowok = (y < p.ny) && (z < p.nz);
-#pragma unroll
-        for (int x = 0; x < 8; x++) v[s][x] = 0.0f;
-        if (!rowok) continue;
-        const float *row = p.f + x0 + p.nx * (y + p.ny * z);
-        if (vec) {
-            float4 a = ld_stream_f4(reinterpret_cast<const float4 *>(row));
-            float4 b = ld_stream_f4(reinterpret_cast<const float4 *>(row + 4));
-            v[s][0] = a.x; v[s][1] = a.y; v[s][2] = a.z; v[s][3] = a.w;
-            v[s][4] = b.x; v[s][5] = b.y; v[s][6] = b.z; v[s][7] = b.w;
-            valid |= 0xffu << (8 * s);
-        } else {
-#pragma unroll
-            for (int x = 0; x < 8; x++)
-                if (x < ex) {
-                    v[s][x] = __ldg(row + x);
-                    valid |= 1u << (8 * s + x);
-                }
-        }
-    }
-}
-
 // Number of candidate isovalues strictly above v (K sorted ascending).  Two
 // values lie on the same side of every k exactly when these counts agree,
 // because {j : v < K[j]} is always a suffix of the sorted K.
@@ -99,163 +64,190 @@ __device__ __forceinline__ bool encode_step(float f, float Rprev, bool first, fl
     return false;
 }
 
-// One warp encodes one brick through every level.  The level's packed words
-// go to the brick's fixed slot of 512 words and its exceptions to the
-// brick's slot of 512 entries in scratch; the record gets the anchor, width,
-// mode and exception count (its prefix sums are filled by the record scan,
-// after which k_compact moves the slots into the dense stream).
-template <bool FULL>
-__device__ __forceinline__ void encode_brick(const CodecParams &p, const BrickCoord &c, uint32_t *zbuf)
-{
-    const int lane = threadIdx.x & 31;
-    const int ly = lane & 7;
-    float f[2][8];
-    uint32_t valid;
-    load_rows(p, c, lane, f, valid);
-    if (FULL) valid = 0xffffu;
+// One 8^3 brick per 64 threads (two warps), one x-row of 8 vertices per
+// thread: row r = ly + 8*lz, so a warp holds z = 0..3 or z = 4..7 of its
+// brick.  A block of 256 threads encodes 4 bricks that follow each other
+// along x.  Every thread of the block runs the same level loop (threads of a
+// brick past the grid only idle), because the bricks' two warps meet at
+// block barriers to exchange the z = 3 row, their maxima and their
+// exception counts.
+constexpr int kEncBricks = 4;  // bricks per block
 
-    // count_above(f) of the 16 values, one byte each
-    uint32_t cfp[4] = {0u, 0u, 0u, 0u};
+template <bool FULL>
+__global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ CodecParams p)
+{
+    __shared__ __align__(16) uint32_t s_zz[kEncBricks][512];
+    __shared__ __align__(16) int32_t s_zrow[kEncBricks][8][8];  // z = 3 rows after the x and y differences
+    __shared__ uint32_t s_red[kEncBricks][2][4];                // per warp: max L, max plain, exceptions, -
+
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int j = tid >> 6, r = tid & 63, wb = r >> 5;
+    const int ly = r & 7, lz = r >> 3;
+    const int ngx = (p.nbx + kEncBricks - 1) / kEncBricks;
+    const int64_t g = blockIdx.x;
+    BrickCoord c;
+    c.bx = (int32_t)(g % ngx) * kEncBricks + j;
+    const int64_t rest = g / ngx;
+    c.by = (int32_t)(rest % p.nby);
+    c.bz = (int32_t)(rest / p.nby);
+    c.b = c.bx + (int64_t)p.nbx * (c.by + (int64_t)p.nby * c.bz);
+    bool mine = c.bx < p.nbx;
+    if (mine) {
+        const bool full = ((int64_t)c.bx * 8 + 8 <= p.nx) && ((int64_t)c.by * 8 + 8 <= p.ny) && ((int64_t)c.bz * 8 + 8 <= p.nz);
+        mine = (full == FULL);
+    }
+    if (!__syncthreads_or(mine)) return;  // uniform: no brick of this block is ours
+
+    // load this thread's row
+    const int64_t x0 = (int64_t)c.bx * 8, y = (int64_t)c.by * 8 + ly, z = (int64_t)c.bz * 8 + lz;
+    float f[8];
+    uint32_t valid = 0;
+#pragma unroll
+    for (int x = 0; x < 8; x++) f[x] = 0.0f;
+    if (mine && y < p.ny && z < p.nz) {
+        const float *row = p.f + x0 + p.nx * (y + p.ny * z);
+        const int ex = (int)((p.nx - x0) < 8 ? (p.nx - x0) : 8);
+        if (FULL && (p.nx & 3) == 0 && (reinterpret_cast<uintptr_t>(p.f) & 15u) == 0) {
+            const float4 a = ld_stream_f4(reinterpret_cast<const float4 *>(row));
+            const float4 b = ld_stream_f4(reinterpret_cast<const float4 *>(row + 4));
+            f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w;
+            f[4] = b.x; f[5] = b.y; f[6] = b.z; f[7] = b.w;
+            valid = 0xffu;
+        } else {
+#pragma unroll
+            for (int x = 0; x < 8; x++)
+                if (x < ex) {
+                    f[x] = __ldg(row + x);
+                    valid |= 1u << x;
+                }
+        }
+    }
+    if (FULL && mine) valid = 0xffu;
+
     const bool fix = p.fix != 0;
+    uint32_t cfp[2] = {0u, 0u};  // count_above(f), one byte per vertex
     if (fix) {
 #pragma unroll
-        for (int s = 0; s < 2; s++)
-#pragma unroll
-            for (int x = 0; x < 8; x++) cfp[(8 * s + x) >> 2] |= (uint32_t)count_above(f[s][x], p.K, p.nK) << (8 * (x & 3));
+        for (int x = 0; x < 8; x++) cfp[x >> 2] |= (uint32_t)count_above(f[x], p.K, p.nK) << (8 * (x & 3));
     }
-
-    float R[2][8];
+    float R[8];
 #pragma unroll
-    for (int s = 0; s < 2; s++)
-#pragma unroll
-        for (int x = 0; x < 8; x++) R[s][x] = 0.0f;
+    for (int x = 0; x < 8; x++) R[x] = 0.0f;
 
     for (int l = 0; l < p.nlevels; l++) {
-        int32_t q[2][8];
+        int32_t q[8];
         uint32_t excm = 0;
         const float e = p.e[l], two_e = p.two_e[l], inv2e = p.inv2e[l];
 #pragma unroll
-        for (int s = 0; s < 2; s++)
-#pragma unroll
-            for (int x = 0; x < 8; x++) {
-                q[s][x] = 0;
-                if (FULL || ((valid >> (8 * s + x)) & 1u)) {
-                    float Rn;
-                    int32_t qq;
-                    const bool ex = encode_step(f[s][x], R[s][x], l == 0, e, two_e, inv2e, p.K, p.nK, fix, (int)((cfp[(8 * s + x) >> 2] >> (8 * (x & 3))) & 0xffu),
-                                                qq, Rn);
-                    q[s][x] = qq;
-                    R[s][x] = Rn;
-                    if (ex) excm |= 1u << (8 * s + x);
-                }
+        for (int x = 0; x < 8; x++) {
+            q[x] = 0;
+            if ((valid >> x) & 1u) {
+                float Rn;
+                int32_t qq;
+                const bool ex = encode_step(f[x], R[x], l == 0, e, two_e, inv2e, p.K, p.nK, fix,
+                                            (int)((cfp[x >> 2] >> (8 * (x & 3))) & 0xffu), qq, Rn);
+                q[x] = qq;
+                R[x] = Rn;
+                if (ex) excm |= 1u << x;
             }
-
-        // Lorenzo residual = first differences along x, then y, then z, with
-        // zero outside the brick.  Padding slots and slot 0 (the anchor) pack 0.
-        int32_t d[2][8];
-        uint32_t maxl = 0, maxn = 0;
-#pragma unroll
-        for (int s = 0; s < 2; s++) {
-#pragma unroll
-            for (int x = 7; x > 0; x--) d[s][x] = (int32_t)((uint32_t)q[s][x] - (uint32_t)q[s][x - 1]);
-            d[s][0] = q[s][0];
         }
+
+        // Lorenzo residual: first differences along x, y (lanes 1 apart) and z
+        // (lanes 8 apart; the z = 4 rows take the z = 3 rows from shared memory)
+        int32_t d[8];
 #pragma unroll
-        for (int s = 0; s < 2; s++)
-#pragma unroll
-            for (int x = 0; x < 8; x++) {
-                const int32_t up = __shfl_up_sync(CHR_FULL_MASK, d[s][x], 1, 8);
-                if (ly > 0) d[s][x] = (int32_t)((uint32_t)d[s][x] - (uint32_t)up);
-            }
+        for (int x = 7; x > 0; x--) d[x] = (int32_t)((uint32_t)q[x] - (uint32_t)q[x - 1]);
+        d[0] = q[0];
 #pragma unroll
         for (int x = 0; x < 8; x++) {
-            const int src = (lane + 24) & 31;  // lane - 8, or lane + 24 for the first z of set 1
-            const int32_t a = __shfl_sync(CHR_FULL_MASK, d[0][x], src);
-            const int32_t b = __shfl_sync(CHR_FULL_MASK, d[1][x], src);
-            if (lane >= 8) d[0][x] = (int32_t)((uint32_t)d[0][x] - (uint32_t)a);
-            d[1][x] = (int32_t)((uint32_t)d[1][x] - (uint32_t)(lane >= 8 ? b : a));
+            const int32_t up = __shfl_up_sync(CHR_FULL_MASK, d[x], 1, 8);
+            if (ly > 0) d[x] = (int32_t)((uint32_t)d[x] - (uint32_t)up);
         }
+        if (lz == 3)
 #pragma unroll
-        for (int s = 0; s < 2; s++)
+            for (int x = 0; x < 8; x++) s_zrow[j][ly][x] = d[x];
+        int32_t below[8];
 #pragma unroll
-            for (int x = 0; x < 8; x++) {
-                const bool live = (FULL || ((valid >> (8 * s + x)) & 1u)) && !(s == 0 && lane == 0 && x == 0);
-                if (!live) d[s][x] = 0;  // d is only read for packing from here on
-                maxl = max(maxl, zigzag(d[s][x]));
-                maxn = max(maxn, live ? zigzag(q[s][x]) : 0u);
-            }
+        for (int x = 0; x < 8; x++) below[x] = __shfl_up_sync(CHR_FULL_MASK, d[x], 8);
+        __syncthreads();
+        if (lz == 4)
+#pragma unroll
+            for (int x = 0; x < 8; x++) below[x] = s_zrow[j][ly][x];
+        if (lz > 0)
+#pragma unroll
+            for (int x = 0; x < 8; x++) d[x] = (int32_t)((uint32_t)d[x] - (uint32_t)below[x]);
+
+        uint32_t maxl = 0, maxn = 0;
+#pragma unroll
+        for (int x = 0; x < 8; x++) {
+            const bool live = ((valid >> x) & 1u) && !(r == 0 && x == 0);
+            if (!live) d[x] = 0;  // d is only read for packing from here on
+            maxl = max(maxl, zigzag(d[x]));
+            maxn = max(maxn, live ? zigzag(q[x]) : 0u);
+        }
+        const uint32_t cnt = __popc(excm);
+        const uint32_t inc = warp_incl_scan_u32(cnt, lane);
         maxl = __reduce_max_sync(CHR_FULL_MASK, maxl);
         maxn = __reduce_max_sync(CHR_FULL_MASK, maxn);
+        if (lane == 31) {
+            s_red[j][wb][0] = maxl;
+            s_red[j][wb][1] = maxn;
+            s_red[j][wb][2] = inc;
+        }
+        __syncthreads();
+        maxl = max(s_red[j][0][0], s_red[j][1][0]);
+        maxn = max(s_red[j][0][1], s_red[j][1][1]);
+        const uint32_t tot0 = s_red[j][0][2];
+        const uint32_t nexc = tot0 + s_red[j][1][2];
+        const uint32_t exc_rank = inc - cnt + (wb ? tot0 : 0u);
         const int wl = bitlen(maxl), wn = bitlen(maxn);
         const int mode = (wl < wn) ? 1 : 0;
         const int w = mode ? wl : wn;
-        const uint32_t cnt0 = __popc(excm & 0xffu), cnt1 = __popc(excm >> 8);
-        const uint32_t inc0 = warp_incl_scan_u32(cnt0, lane);
-        const uint32_t tot0 = __shfl_sync(CHR_FULL_MASK, inc0, 31);
-        const uint32_t inc1 = warp_incl_scan_u32(cnt1, lane);
-        const uint32_t nexc = tot0 + __shfl_sync(CHR_FULL_MASK, inc1, 31);
-        const int32_t anchor = __shfl_sync(CHR_FULL_MASK, q[0][0], 0);
-        if (lane == 0)
-            p.recs[l][c.b] = make_uint4(0u, 0u, (uint32_t)anchor, (uint32_t)w | ((uint32_t)mode << 8) | (nexc << 16));
+        if (mine && r == 0)
+            p.recs[l][c.b] = make_uint4(0u, 0u, (uint32_t)q[0], (uint32_t)w | ((uint32_t)mode << 8) | (nexc << 16));
 
-        if (w > 0) {
+        // pack: every row's zig-zag codes into shared memory, then 16*w words
+        uint32_t *zb = s_zz[j];
+        {
+            uint32_t zz[8];
 #pragma unroll
-            for (int s = 0; s < 2; s++) {
-                const int slot = 8 * (lane + 32 * s);
-                uint32_t z[8];
-#pragma unroll
-                for (int x = 0; x < 8; x++) {
-                    const bool live = (FULL || ((valid >> (8 * s + x)) & 1u)) && !(s == 0 && lane == 0 && x == 0);
-                    z[x] = mode ? zigzag(d[s][x]) : (live ? zigzag(q[s][x]) : 0u);
-                }
-                *reinterpret_cast<uint4 *>(zbuf + slot) = make_uint4(z[0], z[1], z[2], z[3]);
-                *reinterpret_cast<uint4 *>(zbuf + slot + 4) = make_uint4(z[4], z[5], z[6], z[7]);
+            for (int x = 0; x < 8; x++) {
+                const bool live = ((valid >> x) & 1u) && !(r == 0 && x == 0);
+                zz[x] = mode ? zigzag(d[x]) : (live ? zigzag(q[x]) : 0u);
             }
-            __syncwarp();
+            *reinterpret_cast<uint4 *>(zb + 8 * r) = make_uint4(zz[0], zz[1], zz[2], zz[3]);
+            *reinterpret_cast<uint4 *>(zb + 8 * r + 4) = make_uint4(zz[4], zz[5], zz[6], zz[7]);
+        }
+        __syncthreads();
+        if (mine && w > 0) {
             uint32_t *dst = p.slot_words[l] + 512ull * c.b;
             const int nw = 16 * w;
-            for (int j = lane; j < nw; j += 32) {
-                const int bit0 = 32 * j;
+            for (int jw = r; jw < nw; jw += 64) {
+                const int bit0 = 32 * jw;
                 const int s0 = bit0 / w;
                 const int s1 = min(511, (bit0 + 31) / w);
                 uint32_t word = 0;
                 for (int s = s0; s <= s1; s++) {
                     const int pos = s * w - bit0;
-                    const uint32_t v = zbuf[s];
+                    const uint32_t v = zb[s];
                     word |= (pos >= 0) ? (v << pos) : (v >> (-pos));
                 }
-                dst[j] = word;
+                dst[jw] = word;
             }
-            __syncwarp();
         }
-        if (nexc > 0) {
+        if (mine && cnt) {
+            uint32_t pos = exc_rank;
 #pragma unroll
-            for (int s = 0; s < 2; s++) {
-                uint32_t pos = (s == 0) ? inc0 - cnt0 : tot0 + inc1 - cnt1;
-#pragma unroll
-                for (int x = 0; x < 8; x++) {
-                    if ((excm >> (8 * s + x)) & 1u) {
-                        p.slot_idx[l][512ull * c.b + pos] = (uint16_t)(8 * (lane + 32 * s) + x);
-                        p.slot_val[l][512ull * c.b + pos] = __float_as_uint(f[s][x]);
-                        pos++;
-                    }
+            for (int x = 0; x < 8; x++) {
+                if ((excm >> x) & 1u) {
+                    p.slot_idx[l][512ull * c.b + pos] = (uint16_t)(8 * r + x);
+                    p.slot_val[l][512ull * c.b + pos] = __float_as_uint(f[x]);
+                    pos++;
                 }
             }
         }
+        __syncthreads();  // s_zz, s_zrow and s_red are reused by the next level
     }
-}
-
-__global__ void __launch_bounds__(256, 2) k_encode(const __grid_constant__ CodecParams p)
-{
-    __shared__ __align__(16) uint32_t s_zz[kWarpsPerBlock][512];
-    BrickCoord c;
-    if (!brick_of_warp(p, c)) return;  // the whole warp leaves; no block barrier below
-    const bool full = ((int64_t)c.bx * 8 + 8 <= p.nx) && ((int64_t)c.by * 8 + 8 <= p.ny) && ((int64_t)c.bz * 8 + 8 <= p.nz);
-    uint32_t *zbuf = s_zz[threadIdx.x >> 5];
-    if (full)
-        encode_brick<true>(p, c, zbuf);
-    else
-        encode_brick<false>(p, c, zbuf);
 }
 
 // Moves every brick's slot contents to its place in the dense stream (one
@@ -576,7 +568,9 @@ static dim3 codec_grid(const CodecParams &p) { return dim3((unsigned)((int64_t)p
 
 cudaError_t launch_encode(const CodecParams &p, cudaStream_t s)
 {
-    k_encode<<<codec_grid(p), 256, 0, s>>>(p);
+    const dim3 g((unsigned)((int64_t)((p.nbx + kEncBricks - 1) / kEncBricks) * p.nby * p.nbz));
+    k_encode<true><<<g, 256, 0, s>>>(p);
+    if ((p.nx & 7) || (p.ny & 7) || (p.nz & 7)) k_encode<false><<<g, 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 
