@@ -24,10 +24,10 @@ struct TrParams {
 
 __global__ void __launch_bounds__(256) k_translate(const __grid_constant__ TrParams p)
 {
-    __shared__ unsigned int s_hist[256];
+    __shared__ unsigned int s_hist[8 * 256];  // one histogram per warp: fewer collisions
     __shared__ unsigned long long s_cnt;
     __shared__ unsigned int s_min;
-    s_hist[threadIdx.x] = 0u;
+    for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) s_hist[i] = 0u;
     if (threadIdx.x == 0) {
         s_cnt = 0ull;
         s_min = 0xffffffffu;
@@ -36,33 +36,39 @@ __global__ void __launch_bounds__(256) k_translate(const __grid_constant__ TrPar
 
     unsigned long long cnt = 0;
     unsigned int mn = 0xffffffffu;
+    unsigned int *wh = s_hist + 256 * (threadIdx.x >> 5);  // this warp's histogram
     const int shift = 24 - 8 * p.pass;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.N; i += stride) {
-        const int64_t x = i % p.nx, y = (i / p.nx) % p.ny, z = i / (p.nx * p.ny);
-        const float s = __ldg(p.f + i);
-        const bool has[3] = {x + 1 < p.nx, y + 1 < p.ny, z + 1 < p.nz};
-        const int64_t off[3] = {1, p.nx, p.nx * p.ny};
+    // rows (y, z) are spread over the grid, x over the threads of a block
+    const int64_t nrows = p.ny * p.nz;
+    for (int64_t row = blockIdx.x; row < nrows; row += gridDim.x) {
+        const uint32_t y = (uint32_t)row % (uint32_t)p.ny;  // rows < 2^32
+        const bool has_y = (int64_t)y + 1 < p.ny, has_z = row + p.ny < nrows;
+        const float *src = p.f + row * p.nx;
+        for (int32_t x = threadIdx.x; x < p.nx; x += blockDim.x) {
+            const float s = __ldg(src + x);
+            const bool has[3] = {x + 1 < p.nx, has_y, has_z};
+            const int64_t off[3] = {1, p.nx, p.nx * p.ny};
 #pragma unroll
-        for (int a = 0; a < 3; a++) {
-            if (!has[a]) continue;
-            float lo = s, hi = __ldg(p.f + i + off[a]);
-            if (hi < lo) {
-                const float t = lo;
-                lo = hi;
-                hi = t;
-            }
-            for (int j = 0; j < p.nK; j++) {
-                const float k = p.K[j];
-                if (!(lo < k && k < hi)) continue;
-                const uint32_t d[2] = {__float_as_uint(__fsub_rd(k, lo)), __float_as_uint(__fsub_rd(hi, k))};
+            for (int a = 0; a < 3; a++) {
+                if (!has[a]) continue;
+                float lo = s, hi = __ldg(src + x + off[a]);
+                if (hi < lo) {
+                    const float t = lo;
+                    lo = hi;
+                    hi = t;
+                }
+                for (int j = 0; j < p.nK; j++) {
+                    const float k = p.K[j];
+                    if (!(lo < k && k < hi)) continue;
+                    const uint32_t d[2] = {__float_as_uint(__fsub_rd(k, lo)), __float_as_uint(__fsub_rd(hi, k))};
 #pragma unroll
-                for (int u = 0; u < 2; u++) {
-                    cnt++;
-                    if (p.min_only) {
-                        mn = min(mn, d[u]);
-                    } else if (p.pass == 0 || (d[u] >> (shift + 8)) == p.prefix) {
-                        atomicAdd(&s_hist[(d[u] >> shift) & 255u], 1u);
+                    for (int u = 0; u < 2; u++) {
+                        cnt++;
+                        if (p.min_only) {
+                            mn = min(mn, d[u]);
+                        } else if (p.pass == 0 || (d[u] >> (shift + 8)) == p.prefix) {
+                            atomicAdd(&wh[(d[u] >> shift) & 255u], 1u);
+                        }
                     }
                 }
             }
@@ -82,7 +88,11 @@ __global__ void __launch_bounds__(256) k_translate(const __grid_constant__ TrPar
         if (s_cnt && p.pass == 0) atomicAdd(p.sc.count, s_cnt);
         if (p.min_only) atomicMin(p.sc.minbits, s_min);
     }
-    if (!p.min_only && s_hist[threadIdx.x]) atomicAdd(p.sc.hist + threadIdx.x, (unsigned long long)s_hist[threadIdx.x]);
+    if (!p.min_only) {
+        unsigned long long h = 0;
+        for (int w = 0; w < 8; w++) h += s_hist[256 * w + threadIdx.x];
+        if (h) atomicAdd(p.sc.hist + threadIdx.x, h);
+    }
 }
 
 }  // namespace
@@ -107,7 +117,7 @@ cudaError_t launch_translate_pass(const float *field, const Grid &g, const float
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int64_t blocks = (g.N + 255) / 256;
+    int64_t blocks = g.ny * g.nz;
     const int64_t cap = (int64_t)sms * 8;
     if (blocks > cap) blocks = cap;
     k_translate<<<(unsigned)blocks, 256, 0, s>>>(p);
