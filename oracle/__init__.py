@@ -64,6 +64,10 @@ def _load():
         lib.orc_mc.argtypes = [P, i64, i64, i64, ctypes.c_float, P, P, P, i64]
         lib.orc_translate_D.restype = i64
         lib.orc_translate_D.argtypes = [P, i64, i64, i64, P, ctypes.c_int, P, i64]
+        lib.orc_mc_backward.restype = i64
+        lib.orc_mc_backward.argtypes = [P, i64, i64, i64, ctypes.c_float, P, P]
+        lib.orc_dist_loss.restype = ctypes.c_double
+        lib.orc_dist_loss.argtypes = [P, i64, i64, i64, ctypes.c_float, P, i64, P]
         lib.orc_translate_eb.restype = ctypes.c_float
         lib.orc_translate_eb.argtypes = [P, i64, i64, i64, P, ctypes.c_int, ctypes.c_float, P]
         _lib = lib
@@ -229,3 +233,28 @@ def translate_eb(f: np.ndarray, isovalues, accuracy: float = 1.0):
     cnt = np.zeros(1, np.int64)
     eb = lib.orc_translate_eb(_ptr(f), nx, ny, nz, _ptr(K), K.size, ctypes.c_float(accuracy), _ptr(cnt))
     return float(np.float32(eb)), int(cnt[0])
+
+
+def mc_backward(f: np.ndarray, k: float, grad_pos: np.ndarray) -> np.ndarray:
+    """dL/df of L through the oracle's vertex positions (grad_pos: (T, 3, 3),
+    in mc()'s order); float64."""
+    lib = _load()
+    f = _field(f)
+    nz, ny, nx = f.shape
+    g = np.ascontiguousarray(grad_pos, dtype=np.float64)
+    out = np.zeros(f.size, np.float64)
+    T = lib.orc_mc_backward(_ptr(f), nx, ny, nz, ctypes.c_float(k), _ptr(g), _ptr(out))
+    if T < 0 or T * 9 != g.size:
+        raise ValueError("grad_pos does not match the mesh")
+    return out.reshape(nz, ny, nx)
+
+
+def dist_loss(f_orig: np.ndarray, k: float, pts: np.ndarray, with_grad: bool = True):
+    """(mean |F(p)-k|/|grad F(p)| over the points, d/dp) in float64."""
+    lib = _load()
+    f = _field(f_orig)
+    nz, ny, nx = f.shape
+    P = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
+    g = np.zeros_like(P) if with_grad else None
+    L = lib.orc_dist_loss(_ptr(f), nx, ny, nz, ctypes.c_float(k), _ptr(P), P.shape[0], _ptr(g) if with_grad else None)
+    return float(L), (g.reshape(np.shape(pts)) if with_grad else None)

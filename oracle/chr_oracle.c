@@ -590,3 +590,129 @@ float orc_translate_eb(const float *f, int64_t nx, int64_t ny, int64_t nz, const
     free(D);
     return eb;
 }
+
+/* ------------------------------------------------------------------ */
+/* Adjoints (reading of the paper: attributing isosurface error to the */
+/* grid points, Sec. 2.2 error translation run backwards)              */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Adjoint of orc_mc's vertex positions with respect to the field.  A vertex
+ * on edge (i0, i1) along `axis` sits at p_axis = x0 + t, t = (k-f0)/(f1-f0),
+ * so dp_axis/df0 = (t-1)/(f1-f0) and dp_axis/df1 = -t/(f1-f0); the other two
+ * coordinates do not depend on the field.  grad_pos[T*9] holds dL/dp in the
+ * order orc_mc emits; grad_field[N] receives dL/df (overwritten).
+ * Returns the number of triangles, or -1.
+ */
+int64_t orc_mc_backward(const float *f, int64_t nx, int64_t ny, int64_t nz, float k, const double *grad_pos,
+                        double *grad_field)
+{
+    int64_t N = nx * ny * nz, T = 0;
+    for (int64_t i = 0; i < N; i++) grad_field[i] = 0.0;
+    if (nx < 2 || ny < 2 || nz < 2) return 0;
+    for (int64_t z = 0; z + 1 < nz; z++)
+        for (int64_t y = 0; y + 1 < ny; y++)
+            for (int64_t x = 0; x + 1 < nx; x++) {
+                int caseb = 0;
+                for (int j = 0; j < 8; j++) {
+                    int64_t v = (x + corner_off(j, 0)) + nx * ((y + corner_off(j, 1)) + ny * (z + corner_off(j, 2)));
+                    if (f[v] < k) caseb |= 1 << j;
+                }
+                if (caseb == 0 || caseb == 255) continue;
+                int8_t edges[36];
+                int nt = orc_cell_triangles(caseb, edges);
+                if (nt < 0) return -1;
+                for (int t = 0; t < nt; t++, T++) {
+                    for (int c = 0; c < 3; c++) {
+                        int e = edges[3 * t + c];
+                        int axis = e >> 2, m = e & 3;
+                        int o[3] = {0, 0, 0};
+                        int others[2], n = 0;
+                        for (int a = 0; a < 3; a++)
+                            if (a != axis) others[n++] = a;
+                        o[others[0]] = m & 1;
+                        o[others[1]] = (m >> 1) & 1;
+                        int64_t i0 = (x + o[0]) + nx * ((y + o[1]) + ny * (z + o[2]));
+                        int64_t step = (axis == 0) ? 1 : (axis == 1) ? nx : nx * ny;
+                        double f0 = f[i0], f1 = f[i0 + step];
+                        double tt = ((double)k - f0) / (f1 - f0);
+                        double g = grad_pos[T * 9 + c * 3 + axis];
+                        grad_field[i0] += g * (tt - 1.0) / (f1 - f0);
+                        grad_field[i0 + step] += g * (-tt) / (f1 - f0);
+                    }
+                }
+            }
+    return T;
+}
+
+/*
+ * Mean first-order distance of points to the isosurface of an original
+ * field: for each point p, |F(p) - k| / |grad F(p)|, F the trilinear
+ * interpolant of f in the cell with lower corner clamp(floor(p), 0, n-2)
+ * (grid units); points where grad F vanishes count as distance 0.  Returns
+ * the mean over the npts points; grad_pts (may be NULL) receives
+ * d(mean)/dp = (1/npts) [ s G/|G| - |F-k| H G / |G|^3 ], s = sign(F-k),
+ * G = grad F, H = the Hessian of F (trilinear: only mixed second
+ * derivatives are non-zero).
+ */
+double orc_dist_loss(const float *f, int64_t nx, int64_t ny, int64_t nz, float k, const double *pts, int64_t npts,
+                     double *grad_pts)
+{
+    double sum = 0.0;
+    const int64_t n[3] = {nx, ny, nz};
+    for (int64_t v = 0; v < npts; v++) {
+        const double *p = pts + 3 * v;
+        int64_t c[3];
+        double u[3];
+        for (int a = 0; a < 3; a++) {
+            double fl = floor(p[a]);
+            if (fl < 0) fl = 0;
+            if (fl > (double)(n[a] - 2)) fl = (double)(n[a] - 2);
+            c[a] = (int64_t)fl;
+            u[a] = p[a] - fl;
+        }
+        double val[2][2][2]; /* [dz][dy][dx] */
+        for (int dz = 0; dz < 2; dz++)
+            for (int dy = 0; dy < 2; dy++)
+                for (int dx = 0; dx < 2; dx++)
+                    val[dz][dy][dx] = f[(c[0] + dx) + nx * ((c[1] + dy) + ny * (c[2] + dz))];
+        double w[3][2];
+        for (int a = 0; a < 3; a++) {
+            w[a][0] = 1.0 - u[a];
+            w[a][1] = u[a];
+        }
+        double F = 0, G[3] = {0, 0, 0}, H[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int dz = 0; dz < 2; dz++)
+            for (int dy = 0; dy < 2; dy++)
+                for (int dx = 0; dx < 2; dx++) {
+                    double fv = val[dz][dy][dx];
+                    double sx = dx ? 1.0 : -1.0, sy = dy ? 1.0 : -1.0, sz = dz ? 1.0 : -1.0;
+                    F += w[0][dx] * w[1][dy] * w[2][dz] * fv;
+                    G[0] += sx * w[1][dy] * w[2][dz] * fv;
+                    G[1] += w[0][dx] * sy * w[2][dz] * fv;
+                    G[2] += w[0][dx] * w[1][dy] * sz * fv;
+                    H[0][1] += sx * sy * w[2][dz] * fv;
+                    H[0][2] += sx * w[1][dy] * sz * fv;
+                    H[1][2] += w[0][dx] * sy * sz * fv;
+                }
+        H[1][0] = H[0][1];
+        H[2][0] = H[0][2];
+        H[2][1] = H[1][2];
+        double gn = sqrt(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
+        double r = F - (double)k;
+        if (gn == 0.0) {
+            if (grad_pts)
+                for (int a = 0; a < 3; a++) grad_pts[3 * v + a] = 0.0;
+            continue;
+        }
+        sum += fabs(r) / gn;
+        if (grad_pts) {
+            double s = (r > 0) ? 1.0 : (r < 0) ? -1.0 : 0.0;
+            for (int a = 0; a < 3; a++) {
+                double hg = H[a][0] * G[0] + H[a][1] * G[1] + H[a][2] * G[2];
+                grad_pts[3 * v + a] = (s * G[a] / gn - fabs(r) * hg / (gn * gn * gn)) / (double)npts;
+            }
+        }
+    }
+    return npts ? sum / (double)npts : 0.0;
+}
