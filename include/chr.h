@@ -176,6 +176,41 @@ chr_status isosurface_extract(const float *d_field, chr_dims dims, const float *
                               size_t workspace_bytes, void *stream);
 
 /*
+ * isosurface_backward — adjoint of isosurface_extract's vertex positions with
+ * respect to the field (this library's reading of attributing isosurface
+ * error to grid points; the paper's translation of Sec. 2.2 runs from
+ * isosurface error to field error).  A vertex on edge (i0,i1) sits at
+ * p_axis = x0 + t, t = (k - f0)/(f1 - f0), so dp_axis/df0 = (t-1)/(f1-f0) and
+ * dp_axis/df1 = -t/(f1-f0).  d_grad_tris holds dL/dp in isosurface_extract's
+ * layout (isovalue j at d_grad_tris + 9*j*cap_tris, same order); triangles
+ * past cap_tris are ignored.  d_grad_field (nx*ny*nz floats) receives
+ * dL/dfield, summed over every vertex and isovalue.  The sums are exact
+ * integer sums of fixed-point terms scaled from the largest term, so the
+ * result does not depend on scheduling; non-finite terms are skipped.
+ * d_workspace: at least isosurface_backward_workspace_size() bytes.
+ * Asynchronous.
+ */
+size_t isosurface_backward_workspace_size(chr_dims dims, uint32_t n_iso);
+chr_status isosurface_backward(const float *d_field, chr_dims dims, const float *isovalues, uint32_t n_iso,
+                               const float *d_grad_tris, uint64_t cap_tris, float *d_grad_field, void *d_workspace,
+                               size_t workspace_bytes, void *stream);
+
+/*
+ * isosurface_distance_loss — mean first-order distance of npts points
+ * (x,y,z floats, e.g. a triangle soup) to the isovalue surface of an original
+ * field: |F(p) - k| / |grad F(p)|, F the trilinear interpolant in the cell
+ * with lower corner clamp(floor(p), 0, n-2); points where grad F vanishes
+ * count as 0.  *d_loss (device double) receives the mean, d_grad_points (may
+ * be NULL) its gradient with respect to every point coordinate.  Computed in
+ * double, reduced in a fixed order.  d_workspace: at least
+ * isosurface_distance_loss_workspace_size(npts) bytes.  Asynchronous.
+ */
+size_t isosurface_distance_loss_workspace_size(uint64_t npts);
+chr_status isosurface_distance_loss(const float *d_orig_field, chr_dims dims, float isovalue, const float *d_points,
+                                    uint64_t npts, double *d_loss, float *d_grad_points, void *d_workspace,
+                                    size_t workspace_bytes, void *stream);
+
+/*
  * isosurface_extract_noalloc — isosurface_extract for callers that may not
  * allocate device memory: code inside an application or framework that owns
  * all GPU memory through its own pool, plugins and callbacks that must not

@@ -8,7 +8,8 @@ CPU path: if libchr.so is missing or cannot load, every call raises.
 
 Names follow the C ABI: chr_compress, chr_reconstruct, chr_topo_translate,
 isosurface_extract, isosurface_workspace_size, isosurface_extract_noalloc,
-chr_serialize, chr_deserialize, chr_stats, chr_free.
+isosurface_backward, isosurface_distance_loss, chr_serialize, chr_deserialize,
+chr_stats, chr_free.
 """
 from __future__ import annotations
 
@@ -91,6 +92,16 @@ def lib():
         L.isosurface_extract_noalloc.restype = st
         L.isosurface_extract_noalloc.argtypes = [c_void_p, ChrDims, POINTER(c_float), c_uint32, c_void_p, c_uint64,
                                                  c_void_p, c_void_p, c_void_p]
+        L.isosurface_backward_workspace_size.restype = c_size_t
+        L.isosurface_backward_workspace_size.argtypes = [ChrDims, c_uint32]
+        L.isosurface_backward.restype = st
+        L.isosurface_backward.argtypes = [c_void_p, ChrDims, POINTER(c_float), c_uint32, c_void_p, c_uint64, c_void_p,
+                                          c_void_p, c_size_t, c_void_p]
+        L.isosurface_distance_loss_workspace_size.restype = c_size_t
+        L.isosurface_distance_loss_workspace_size.argtypes = [c_uint64]
+        L.isosurface_distance_loss.restype = st
+        L.isosurface_distance_loss.argtypes = [c_void_p, ChrDims, c_float, c_void_p, c_uint64, c_void_p, c_void_p,
+                                               c_void_p, c_size_t, c_void_p]
         L.chr_serialize.restype = st
         L.chr_serialize.argtypes = [c_void_p, c_void_p, c_size_t, POINTER(c_size_t), c_void_p]
         L.chr_deserialize.restype = st
@@ -270,6 +281,44 @@ def isosurface_extract_noalloc(field: torch.Tensor, isovalues, cap: int, tris: t
                                             tris.data_ptr() if cap > 0 else None, int(cap), counts.data_ptr(),
                                             err.data_ptr(), _stream(stream)))
     return tris, counts, err
+
+
+def isosurface_backward(field: torch.Tensor, isovalues, grad_tris: torch.Tensor, cap: int,
+                        grad_field: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """dL/dfield from dL/dtris in isosurface_extract's layout [n_iso, cap, 3, 3]
+    (chr.h: isosurface_backward).  Deterministic."""
+    _check_field(field)
+    iso, ni = _floats(isovalues)
+    if not (grad_tris.is_cuda and grad_tris.dtype == torch.float32 and grad_tris.is_contiguous()):
+        raise ValueError("grad_tris must be a contiguous float32 CUDA tensor")
+    if grad_tris.numel() < ni * int(cap) * 9:
+        raise ValueError("grad_tris smaller than n_iso * cap triangles")
+    if grad_field is None:
+        grad_field = torch.empty_like(field)
+    ws = torch.empty(int(lib().isosurface_backward_workspace_size(_dims(field), ni)), dtype=torch.uint8, device="cuda")
+    _check(lib().isosurface_backward(field.data_ptr(), _dims(field), iso, ni, grad_tris.data_ptr() if cap > 0 else None,
+                                     int(cap), grad_field.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)))
+    return grad_field
+
+
+def isosurface_distance_loss(orig_field: torch.Tensor, isovalue: float, points: torch.Tensor, with_grad: bool = True,
+                             stream=None):
+    """(mean distance of the points to orig_field's isovalue surface as a
+    float64 device scalar, its gradient [npts, 3] or None) (chr.h:
+    isosurface_distance_loss)."""
+    _check_field(orig_field)
+    pts = points.reshape(-1, 3)
+    if not (pts.is_cuda and pts.dtype == torch.float32 and pts.is_contiguous()):
+        raise ValueError("points must be a contiguous float32 CUDA tensor")
+    n = pts.shape[0]
+    loss = torch.empty((), dtype=torch.float64, device="cuda")
+    grad = torch.empty_like(pts) if with_grad else None
+    ws = torch.empty(int(lib().isosurface_distance_loss_workspace_size(n)), dtype=torch.uint8, device="cuda")
+    _check(lib().isosurface_distance_loss(orig_field.data_ptr(), _dims(orig_field), float(isovalue),
+                                          pts.data_ptr() if n else None, n, loss.data_ptr(),
+                                          grad.data_ptr() if with_grad else None, ws.data_ptr(), ws.numel(),
+                                          _stream(stream)))
+    return loss, grad
 
 
 def chr_serialize(h: Chr, stream=None) -> bytes:

@@ -444,6 +444,60 @@ chr_status isosurface_extract(const float *d_field, chr_dims dims, const float *
     return CHR_OK;
 }
 
+size_t isosurface_backward_workspace_size(chr_dims dims, uint32_t n_iso)
+{
+    std::string why;
+    if (!dims_ok(dims, why)) return 0;
+    return mc_adjoint_workspace_bytes(make_grid(dims), (int)n_iso);
+}
+
+chr_status isosurface_backward(const float *d_field, chr_dims dims, const float *isovalues, uint32_t n_iso,
+                               const float *d_grad_tris, uint64_t cap_tris, float *d_grad_field, void *d_workspace,
+                               size_t workspace_bytes, void *stream)
+{
+    std::string why;
+    if (!d_field || !isovalues || !d_grad_field) return fail(CHR_ERR_INVALID, "isosurface_backward: NULL argument");
+    if (!dims_ok(dims, why)) return fail(CHR_ERR_INVALID, "isosurface_backward: " + why);
+    if (n_iso < 1 || n_iso > CHR_MAX_ISO) return fail(CHR_ERR_INVALID, "isosurface_backward: n_iso must be 1..16");
+    for (uint32_t j = 0; j < n_iso; j++)
+        if (!isfinite(isovalues[j])) return fail(CHR_ERR_INVALID, "isosurface_backward: isovalues must be finite");
+    if (cap_tris > 0 && !d_grad_tris) return fail(CHR_ERR_INVALID, "isosurface_backward: NULL gradient buffer");
+    if (cap_tris > (1ull << 58)) return fail(CHR_ERR_INVALID, "isosurface_backward: cap_tris too large");
+    if ((reinterpret_cast<uintptr_t>(d_field) & 3u) || (reinterpret_cast<uintptr_t>(d_grad_tris) & 3u) ||
+        (reinterpret_cast<uintptr_t>(d_grad_field) & 3u) || (reinterpret_cast<uintptr_t>(d_workspace) & 7u))
+        return fail(CHR_ERR_INVALID, "isosurface_backward: misaligned pointer");
+    const Grid g = make_grid(dims);
+    if (!d_workspace || workspace_bytes < mc_adjoint_workspace_bytes(g, (int)n_iso))
+        return fail(CHR_ERR_INVALID, "isosurface_backward: workspace smaller than isosurface_backward_workspace_size()");
+    CHR_CUDA(launch_mc_adjoint(d_field, g, isovalues, (int)n_iso, d_grad_tris, cap_tris, d_grad_field, d_workspace,
+                               (cudaStream_t)stream),
+             "isosurface_backward");
+    return CHR_OK;
+}
+
+size_t isosurface_distance_loss_workspace_size(uint64_t npts) { return dist_loss_workspace_bytes(npts); }
+
+chr_status isosurface_distance_loss(const float *d_orig_field, chr_dims dims, float isovalue, const float *d_points,
+                                    uint64_t npts, double *d_loss, float *d_grad_points, void *d_workspace,
+                                    size_t workspace_bytes, void *stream)
+{
+    std::string why;
+    if (!d_orig_field || !d_loss || (npts > 0 && !d_points))
+        return fail(CHR_ERR_INVALID, "isosurface_distance_loss: NULL argument");
+    if (!dims_ok(dims, why)) return fail(CHR_ERR_INVALID, "isosurface_distance_loss: " + why);
+    if (!isfinite(isovalue)) return fail(CHR_ERR_INVALID, "isosurface_distance_loss: isovalue must be finite");
+    if ((reinterpret_cast<uintptr_t>(d_orig_field) & 3u) || (reinterpret_cast<uintptr_t>(d_points) & 3u) ||
+        (reinterpret_cast<uintptr_t>(d_grad_points) & 3u) || (reinterpret_cast<uintptr_t>(d_loss) & 7u) ||
+        (reinterpret_cast<uintptr_t>(d_workspace) & 7u))
+        return fail(CHR_ERR_INVALID, "isosurface_distance_loss: misaligned pointer");
+    if (!d_workspace || workspace_bytes < dist_loss_workspace_bytes(npts))
+        return fail(CHR_ERR_INVALID, "isosurface_distance_loss: workspace too small");
+    CHR_CUDA(launch_dist_loss(d_orig_field, make_grid(dims), isovalue, d_points, npts, d_loss, d_grad_points,
+                              d_workspace, (cudaStream_t)stream),
+             "isosurface_distance_loss");
+    return CHR_OK;
+}
+
 chr_status chr_stats(const chr_handle *h, chr_stats_t *out)
 {
     if (!h || !out) return fail(CHR_ERR_INVALID, "chr_stats: NULL argument");

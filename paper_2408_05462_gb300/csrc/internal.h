@@ -71,6 +71,16 @@ size_t mc_workspace_bytes(const Grid &g, int n_iso);
 cudaError_t launch_mc(const float *field, const Grid &g, const float *iso, int n_iso, float *tris, uint64_t cap,
                       uint64_t *ntris, uint32_t *err, void *workspace, cudaStream_t s);
 
+// Adjoint of the vertex positions: dL/dfield from dL/dtris (forward layout).
+size_t mc_adjoint_workspace_bytes(const Grid &g, int n_iso);
+cudaError_t launch_mc_adjoint(const float *field, const Grid &g, const float *iso, int n_iso, const float *grad_tris,
+                              uint64_t cap, float *grad_field, void *workspace, cudaStream_t s);
+
+// Mean distance of points to an original field's isosurface, and its gradient.
+size_t dist_loss_workspace_bytes(uint64_t npts);
+cudaError_t launch_dist_loss(const float *orig, const Grid &g, float k, const float *pts, uint64_t npts, double *loss,
+                             float *grad_pts, void *workspace, cudaStream_t s);
+
 // Error-bound translation (radix selection over D).
 struct TranslateScratch {
     unsigned long long *hist;  // 256 counters

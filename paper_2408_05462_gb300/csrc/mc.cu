@@ -427,6 +427,189 @@ __global__ void __launch_bounds__(256, 4) k_mc_emit(const __grid_constant__ McPa
     });
 }
 
+// ---- adjoint of the vertex positions ----------------------------------------
+//
+// A vertex on edge (i0, i1) along `axis` sits at p_axis = x0 + t with
+// t = (k - f0)/(f1 - f0): dp_axis/df0 = (t - 1)/(f1 - f0) and
+// dp_axis/df1 = -t/(f1 - f0); the other coordinates do not depend on the
+// field.  The adjoint walks the triangles in exactly the emit order (same
+// tiles, scan and search), reads dL/dp where the forward pass wrote p, and
+// adds each contribution to both edge ends.  Sums are made deterministic by
+// fixed-point int64 atomics: pass 0 finds the largest |contribution|, pass 1
+// adds round(c * S) with S = 2^(52 - exponent of that maximum), so every
+// term is an exact integer and integer addition does not depend on order.
+// Non-finite contributions are skipped.
+
+struct AdjParams {
+    const float *grad[kMcIsoPerPass];  // dL/dtris per isovalue slot (the forward layout)
+    unsigned long long *acc;           // [N] fixed-point sums
+    unsigned int *maxbits;             // max |contribution| as float bits
+    int32_t pass;
+};
+
+__device__ __forceinline__ double adj_scale(unsigned int maxbits)
+{
+    const float m = __uint_as_float(maxbits);
+    if (!(m > 0.0f) || !isfinite(m)) return 1.0;
+    return ldexp(1.0, 52 - ilogbf(m));
+}
+
+template <int NISO>
+__global__ void __launch_bounds__(256, 4) k_mc_adjoint(const __grid_constant__ McParams p,
+                                                      const __grid_constant__ AdjParams a,
+                                                      const __grid_constant__ CUtensorMap map)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+    float *bufs = reinterpret_cast<float *>(smem + kOffBuf);
+    uint64_t *s_row = reinterpret_cast<uint64_t *>(smem + kOffRow);
+    uint8_t *s_cnt = smem + kOffCnt;
+    uint32_t *s_tri = reinterpret_cast<uint32_t *>(smem + kOffTri);
+    EdgeVec *s_edge = reinterpret_cast<EdgeVec *>(smem + kOffEdge);
+    uint8_t *s_case = smem + kOffCase;
+    __shared__ uint64_t mbar[2];
+    __shared__ uint64_t s_warp[9];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint16_t *s_pre = reinterpret_cast<uint16_t *>(smem + kOffPre);
+    float *s_stage = reinterpret_cast<float *>(smem + kOffStage) + warp * kWarpStage;
+    s_cnt[tid] = (uint8_t)(g_mc_case[tid] >> 60);
+    for (int i = tid; i < 256 * CHR_MC_MAX_TRI; i += 256) {
+        const uint64_t word = g_mc_case[i / CHR_MC_MAX_TRI];
+        const int t = i % CHR_MC_MAX_TRI;
+        uint32_t tri = 0;
+        if (t < (int)(word >> 60))
+            for (int v = 0; v < 3; v++) tri |= (uint32_t)((word >> (12 * t + 4 * v)) & 15u) << (8 * v);
+        s_tri[i] = tri;
+    }
+    if (tid < 12) s_edge[tid] = edge_vec(tid);
+    const double S = (a.pass == 1) ? adj_scale(*a.maxbits) : 1.0;
+    float lane_max = 0.0f;
+
+    tile_loop(p, &map, bufs, mbar, [&](int64_t tile, const float *box) {
+        row_masks<NISO>(box, s_row, p);
+        __syncthreads();
+        const TileXYZ o = tile_origin(p, tile);
+        const int nvalid = valid_cells(p, o);
+        const int j = tid >> 6, ly = tid & 7, lz = (tid >> 3) & 7;
+        const int r00 = lz * 9 + ly;
+        uint64_t packed = 0;
+#pragma unroll
+        for (int i = 0; i < NISO; i++) {
+            uint32_t lo, hi;
+            cases8(s_row + i * kRows, r00, j, nvalid, lo, hi);
+            uint32_t cnt = 0;
+#pragma unroll
+            for (int x = 0; x < 4; x++) cnt += s_cnt[(lo >> (8 * x)) & 0xffu] + s_cnt[(hi >> (8 * x)) & 0xffu];
+            *reinterpret_cast<uint2 *>(s_case + i * kCells + tid * 8) = make_uint2(lo, hi);
+            packed |= (uint64_t)cnt << (16 * i);
+        }
+        const uint64_t inc = warp_incl_scan_u64(packed, lane);
+        if (lane == 31) s_warp[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            const uint64_t t = (lane < 8) ? s_warp[lane] : 0ull;
+            const uint64_t ti = warp_incl_scan_u64(t, lane);
+            if (lane < 8) s_warp[lane] = ti - t;
+            if (lane == 7) s_warp[8] = ti;
+        }
+        __syncthreads();
+        const uint64_t thread_excl = s_warp[warp] + inc - packed;
+        const uint64_t block_total = s_warp[8];
+
+#pragma unroll 1
+        for (int i = 0; i < NISO; i++) {
+            const int n = (int)((block_total >> (16 * i)) & 0xffffull);
+            if (n == 0) continue;
+            {
+                const uint2 cw = *reinterpret_cast<const uint2 *>(s_case + i * kCells + tid * 8);
+                uint32_t run = (uint32_t)((thread_excl >> (16 * i)) & 0xffffull);
+                uint32_t pk[4];
+#pragma unroll
+                for (int x = 0; x < 8; x += 2) {
+                    const uint32_t c0 = ((x < 4 ? cw.x : cw.y) >> (8 * (x & 3))) & 0xffu;
+                    const uint32_t c1 = ((x < 4 ? cw.x : cw.y) >> (8 * ((x + 1) & 3))) & 0xffu;
+                    const uint32_t a0 = run;
+                    run += s_cnt[c0];
+                    pk[x >> 1] = a0 | (run << 16);
+                    run += s_cnt[c1];
+                }
+                *reinterpret_cast<uint4 *>(s_pre + tid * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
+            __syncthreads();
+            const uint64_t g0 = __ldg(p.tile_off + tile * kMcIsoPerPass + i);
+            const float k = p.k[i];
+            const int lim = (g0 >= p.cap) ? 0 : (int)((p.cap - g0) < (uint64_t)n ? (p.cap - g0) : (uint64_t)n);
+            const float *gin = a.grad[i] + 9ull * g0;
+            const uint8_t *icase = s_case + i * kCells;
+            for (int base = warp * 32; base < lim; base += 8 * 32) {
+                const int mm = (lim - base) < 32 ? (lim - base) : 32;
+                const float *src = gin + 9 * base;
+                const int pad = (int)((reinterpret_cast<uintptr_t>(src) >> 2) & 3u);
+                // s_stage[pad + q] = src[q]: the same alignment split as the forward stores
+                const int F = 9 * mm;
+                const int head = min((4 - pad) & 3, F);
+                if (lane < head) s_stage[pad + lane] = __ldg(src + lane);
+                const int nbody = (F - head) >> 2;
+                const float4 *src4 = reinterpret_cast<const float4 *>(src + head);
+                float4 *dst4 = reinterpret_cast<float4 *>(s_stage + pad + head);
+                for (int q = lane; q < nbody; q += 32) dst4[q] = ld_stream_f4(src4 + q);
+                const int tail0 = head + 4 * nbody;
+                if (lane < F - tail0) s_stage[pad + tail0 + lane] = __ldg(src + tail0 + lane);
+                __syncwarp();
+                if (lane < mm) {
+                    const int m = base + lane;
+                    int c = 0;
+#pragma unroll
+                    for (int step = 1024; step > 0; step >>= 1)
+                        if ((int)s_pre[c + step] <= m) c += step;
+                    const int t = m - (int)s_pre[c];
+                    const uint32_t tri = s_tri[icase[c] * CHR_MC_MAX_TRI + t];
+                    const int lx = c & 7, tt = c >> 3, cly = tt & 7, clz = (tt >> 3) & 7, cj = tt >> 6;
+                    const float *cell = box + clz * kPlane + cly * kVX + 8 * cj + lx;
+                    const int64_t gx = o.x0 + 8 * cj + lx, gy = o.y0 + cly, gz = o.z0 + clz;
+                    const float *g9 = s_stage + pad + 9 * lane;
+#pragma unroll
+                    for (int v = 0; v < 3; v++) {
+                        const EdgeVec E = s_edge[(tri >> (8 * v)) & 0xffu];
+                        const float *p0 = cell + E.delta;
+                        const float f0 = p0[0], f1 = p0[E.step];
+                        const float tv = edge_t(k, f0, f1);
+                        const int axis = (E.dx != 0.0f) ? 0 : (E.dy != 0.0f) ? 1 : 2;
+                        const float gax = g9[3 * v + axis];
+                        const float inv = 1.0f / __fsub_rn(f1, f0);
+                        const float c0 = gax * (tv - 1.0f) * inv, c1 = -gax * tv * inv;
+                        if (a.pass == 0) {
+                            if (isfinite(c0)) lane_max = fmaxf(lane_max, fabsf(c0));
+                            if (isfinite(c1)) lane_max = fmaxf(lane_max, fabsf(c1));
+                        } else {
+                            const int64_t i0 = (gx + (int64_t)E.ox) + p.nx * ((gy + (int64_t)E.oy) + p.ny * (gz + (int64_t)E.oz));
+                            const int64_t i1 = i0 + ((axis == 0) ? 1 : (axis == 1) ? p.nx : p.nx * p.ny);
+                            if (isfinite(c0))
+                                atomicAdd(a.acc + i0, (unsigned long long)(long long)llrint((double)c0 * S));
+                            if (isfinite(c1))
+                                atomicAdd(a.acc + i1, (unsigned long long)(long long)llrint((double)c1 * S));
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            __syncthreads();
+        }
+    });
+    if (a.pass == 0) {
+        const unsigned int mb = __reduce_max_sync(CHR_FULL_MASK, __float_as_uint(lane_max));
+        if (lane == 0 && mb) atomicMax(a.maxbits, mb);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_adj_finalize(const unsigned long long *acc, const unsigned int *maxbits,
+                                                      float *grad, int64_t N)
+{
+    const double S = adj_scale(*maxbits);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        grad[i] = (float)((double)(long long)acc[i] / S);
+}
+
 // ---- exclusive scan of the tile counts ----------------------------------
 
 constexpr int kTScanThreads = 256, kTScanPer = 8, kTScanChunk = kTScanThreads * kTScanPer;
@@ -595,12 +778,13 @@ size_t mc_workspace_bytes(const Grid &g, int n_iso)
 }
 
 template <int NISO>
-static cudaError_t launch_mc_group(const McParams &p, const CUtensorMap &map, const McWorkspace &w, uint64_t *ntris,
-                                   int niso, cudaStream_t s)
+static cudaError_t mc_prepare(int &grid_count, int &grid_emit)
 {
-    static int grid_count = 0, grid_emit = 0;  // resident blocks per device, computed once per process
-    if (!grid_emit) {
+    static int gc = 0, ge = 0;  // resident blocks per device, computed once per process
+    if (!ge) {
         cudaError_t e = cudaFuncSetAttribute(k_mc_emit<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_mc_adjoint<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(k_mc_count<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCountSmem);
         if (e != cudaSuccess) return e;
@@ -609,11 +793,23 @@ static cudaError_t launch_mc_group(const McParams &p, const CUtensorMap &map, co
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bc, k_mc_count<NISO>, 256, kCountSmem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&be, k_mc_emit<NISO>, 256, kEmitSmem);
-        grid_count = sms * (bc > 0 ? bc : 1);
-        grid_emit = sms * (be > 0 ? be : 1);
+        gc = sms * (bc > 0 ? bc : 1);
+        ge = sms * (be > 0 ? be : 1);
     }
+    grid_count = gc;
+    grid_emit = ge;
+    return cudaSuccess;
+}
+
+// Tile counts and their exclusive scan (tile_off, totals into ntris).
+template <int NISO>
+static cudaError_t launch_count_scan(const McParams &p, const CUtensorMap &map, const McWorkspace &w, uint64_t *ntris,
+                                     int niso, cudaStream_t s)
+{
+    int grid_count, grid_emit;
+    cudaError_t e = mc_prepare<NISO>(grid_count, grid_emit);
+    if (e != cudaSuccess) return e;
     const unsigned gc = (unsigned)(p.ntiles < grid_count ? p.ntiles : grid_count);
-    const unsigned ge = (unsigned)(p.ntiles < grid_emit ? p.ntiles : grid_emit);
     k_mc_count<NISO><<<gc, 256, kCountSmem, s>>>(p, map);
     TScanArgs a;
     a.cnt = w.cnt;
@@ -628,7 +824,35 @@ static cudaError_t launch_mc_group(const McParams &p, const CUtensorMap &map, co
     k_tscan_reduce<<<(unsigned)w.nchunks, kTScanThreads, 0, s>>>(a);
     k_tscan_chunks<<<1, kTScanThreads, 0, s>>>(a);
     k_tscan_apply<<<(unsigned)w.nchunks, kTScanThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NISO>
+static cudaError_t launch_mc_group(const McParams &p, const CUtensorMap &map, const McWorkspace &w, uint64_t *ntris,
+                                   int niso, cudaStream_t s)
+{
+    cudaError_t e = launch_count_scan<NISO>(p, map, w, ntris, niso, s);
+    if (e != cudaSuccess) return e;
+    int grid_count, grid_emit;
+    mc_prepare<NISO>(grid_count, grid_emit);
+    const unsigned ge = (unsigned)(p.ntiles < grid_emit ? p.ntiles : grid_emit);
     k_mc_emit<NISO><<<ge, 256, kEmitSmem, s>>>(p, map);
+    return cudaGetLastError();
+}
+
+template <int NISO>
+static cudaError_t launch_adjoint_group(const McParams &p, const AdjParams &a, const CUtensorMap &map,
+                                        const McWorkspace &w, uint64_t *ntris, int niso, bool recount, cudaStream_t s)
+{
+    if (recount) {
+        cudaError_t e = launch_count_scan<NISO>(p, map, w, ntris, niso, s);
+        if (e != cudaSuccess) return e;
+    }
+    int grid_count, grid_emit;
+    cudaError_t e = mc_prepare<NISO>(grid_count, grid_emit);
+    if (e != cudaSuccess) return e;
+    const unsigned ge = (unsigned)(p.ntiles < grid_emit ? p.ntiles : grid_emit);
+    k_mc_adjoint<NISO><<<ge, 256, kEmitSmem, s>>>(p, a, map);
     return cudaGetLastError();
 }
 
@@ -667,6 +891,66 @@ cudaError_t launch_mc(const float *field, const Grid &g, const float *iso, int n
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+size_t mc_adjoint_workspace_bytes(const Grid &g, int n_iso)
+{
+    const size_t base = ((mc_workspace_bytes(g, n_iso) + 255) / 256) * 256;
+    return base + (size_t)g.N * 8 + 256;
+}
+
+cudaError_t launch_mc_adjoint(const float *field, const Grid &g, const float *iso, int n_iso, const float *grad_tris,
+                              uint64_t cap, float *grad_field, void *workspace, cudaStream_t s)
+{
+    McParams p;
+    memset(&p, 0, sizeof(p));
+    p.f = field;
+    p.nx = g.nx;
+    p.ny = g.ny;
+    p.nz = g.nz;
+    mc_tiles(g, p.ntx, p.ncby, p.ncbz, p.ntiles);
+    p.cap = cap;
+    p.err = nullptr;
+    McWorkspace w;
+    mc_layout(g, workspace, &w);
+    p.tile_cnt = w.cnt;
+    p.tile_off = w.off;
+    const size_t base = ((mc_workspace_bytes(g, n_iso) + 255) / 256) * 256;
+    AdjParams a;
+    memset(&a, 0, sizeof(a));
+    a.acc = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(workspace) + base);
+    a.maxbits = reinterpret_cast<unsigned int *>(reinterpret_cast<char *>(workspace) + base + (size_t)g.N * 8);
+    cudaError_t e = cudaMemsetAsync(a.acc, 0, (size_t)g.N * 8 + 256, s);
+    if (e != cudaSuccess) return e;
+    CUtensorMap map;
+    memset(&map, 0, sizeof(map));
+    p.use_tma = make_field_tensor_map(&map, field, g.nx, g.ny, g.nz, kBoxX, 9, 9) ? 1 : 0;
+    // the tile counts are recomputed per group unless one group covers every isovalue
+    uint64_t *scratch_counts = reinterpret_cast<uint64_t *>(reinterpret_cast<char *>(workspace) + base + (size_t)g.N * 8 + 64);
+    const bool single = n_iso <= kMcIsoPerPass;
+    for (int pass = 0; pass < 2; pass++) {
+        a.pass = pass;
+        for (int i0 = 0; i0 < n_iso; i0 += kMcIsoPerPass) {
+            const int n = (n_iso - i0) < kMcIsoPerPass ? (n_iso - i0) : kMcIsoPerPass;
+            for (int i = 0; i < kMcIsoPerPass; i++) {
+                p.k[i] = (i < n) ? iso[i0 + i] : 0.0f;
+                a.grad[i] = (i < n) ? grad_tris + 9ull * cap * (uint64_t)(i0 + i) : nullptr;
+            }
+            const bool recount = !single || pass == 0;
+            switch (n) {
+                case 1: e = launch_adjoint_group<1>(p, a, map, w, scratch_counts, n, recount, s); break;
+                case 2: e = launch_adjoint_group<2>(p, a, map, w, scratch_counts, n, recount, s); break;
+                case 3: e = launch_adjoint_group<3>(p, a, map, w, scratch_counts, n, recount, s); break;
+                default: e = launch_adjoint_group<4>(p, a, map, w, scratch_counts, n, recount, s); break;
+            }
+            if (e != cudaSuccess) return e;
+        }
+    }
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_adj_finalize<<<(unsigned)(sms * 8), 256, 0, s>>>(a.acc, a.maxbits, grad_field, g.N);
+    return cudaGetLastError();
 }
 
 }  // namespace chr
