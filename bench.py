@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--sample", type=int, default=352, help="edge of the oracle's sub-box")
+    ap.add_argument("--no-serve", action="store_true", help="skip the request-loop measurement")
+    ap.add_argument("--serve-size", type=int, default=1024, help="grid side of the served timesteps")
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing")
     return ap.parse_args()
 
 
@@ -225,6 +229,82 @@ def cpu_baseline(f, args):
                       f"({tris} triangles) in {dt:.1f} s, single thread"}
 
 
+def adjoint_timing(n=256, seed=256256, reps=10):
+    """The differentiation workload (256^3 k^-5/3 turbulence, k = 0, error
+    bound 1e-3): isosurface_backward of the vertex positions and the
+    distance loss to the original surface, each timed alone with CUDA events
+    after warm-up."""
+    import torch
+
+    from paper_2408_05462_gb300 import chr, synth
+
+    f0 = torch.from_numpy(synth.turbulence(n, seed=seed)).cuda()
+    h = chr.chr_compress(f0, [1e-3], [0.0])
+    R = h.reconstruct(0)
+    cap = 12 * n ** 3 // 10
+    tris, counts, _ = chr.isosurface_extract(R, [0.0], cap)
+    torch.cuda.synchronize()
+    T = int(counts[0])
+    g = torch.Generator(device="cuda")
+    g.manual_seed(7)
+    G = torch.randn(tris.shape, generator=g, device="cuda")
+    pts = tris[0, :T].reshape(-1, 3).contiguous()
+    out = {"workload": "turbulence k^-5/3 %d^3, k=0, eb=1e-3" % n, "triangles": T}
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    gf = torch.empty_like(R)
+    ms = timed(lambda: chr.isosurface_backward(R, [0.0], G, cap, grad_field=gf))
+    # two walks over the field and the incoming gradients, the fixed-point
+    # accumulator written and read, the gradient field written
+    nb = 2 * (4.0 * n ** 3 + 36.0 * T) + 16.0 * n ** 3 + 4.0 * n ** 3
+    out["isosurface_backward"] = {"ms": ms, "algorithmic_bytes": nb, "GBps": nb / (ms * 1e-3) / 1e9}
+    ms = timed(lambda: chr.isosurface_distance_loss(f0, 0.0, pts))
+    nb = 2 * 12.0 * 3 * T
+    out["isosurface_distance_loss"] = {"ms": ms, "points": 3 * T, "points_per_s": 3 * T / (ms * 1e-3)}
+    del f0, R, tris, G, pts, gf
+    h.free()
+    return out
+
+
+def serve_measurement(args):
+    """The request loop over resident CHRs of two advected turbulence
+    timesteps (4 accuracy levels each): capacity with all requests queued,
+    the same requests one at a time on one stream (the plain path), and
+    Poisson arrivals at 0.25, 0.5 and 0.8 of capacity with p50/p99."""
+    import torch
+
+    from paper_2408_05462_gb300 import serve, synth
+
+    n = args.serve_size
+    srv = serve.Server(budget_bytes=96 << 30, slots=4, max_resident=2)
+    f = synth.turbulence_cuda(n, seed=1024)
+    srv.ingest(0, f)
+    f = torch.roll(f, shifts=(1, 2, 3), dims=(0, 1, 2))  # advected by (3, 2, 1) voxels in (x, y, z)
+    srv.ingest(1, f)
+    del f
+    torch.cuda.empty_cache()
+    out = serve.measure(srv, (n, n, n), [0, 1], args.serve_requests)
+    out.update({"workload": "turbulence k^-5/3 %d^3 (GPU generator, seed 1024), 2 timesteps advected by (3,2,1), "
+                            "levels 1e-2..1e-5 x range, requests: k~U[-1,1], level~U{0..3}, sides~U{64..512}, "
+                            "seed 5" % n,
+                "resident_gib": srv.resident_bytes / 2 ** 30,
+                "latency": "arrival to triangles and count ready (device event), results left on the device"})
+    for ts in list(srv.steps.values()):
+        ts.handle.free()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -354,6 +434,9 @@ def main():
         translate[f"accuracy_{acc}"] = {"ms": t_ms, "eb": eb_t, "D": nD, "passes": passes,
                                         "field_GBps": passes * 4.0 * N / (t_ms * 1e-3) / 1e9}
 
+    adjoint = None if args.no_adjoint or world > 1 else adjoint_timing()
+    serving = None if args.no_serve or world > 1 else serve_measurement(args)
+
     peak, peak_kind = measured_peaks()
     mc_bytes = 4.0 * N + 36.0 * T
     dec_bytes = comp_bytes + 4.0 * N
@@ -393,6 +476,10 @@ def main():
         "gpu_launches": 11 * args.steps,  # encode, 3 record scans, compact, decode, MC count, 3 tile scans, emit
         "e2e": e2e,
     }
+    if adjoint is not None:
+        out["adjoint"] = adjoint
+    if serving is not None:
+        out["serve"] = serving
     if rank == 0:
         clk_s = clk.summary()
         if clk_s:

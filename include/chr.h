@@ -132,6 +132,31 @@ chr_status chr_compress(const float *d_field, chr_dims dims, const chr_params *p
 chr_status chr_reconstruct(const chr_handle *h, uint32_t level, float *d_out, void *stream);
 
 /*
+ * chr_reconstruct_box — chr_reconstruct restricted to the vertices
+ * [x0, x0+box.nx) x [y0, y0+box.ny) x [z0, z0+box.nz) of the grid (each
+ * box side >= 1 and inside the grid): only the 8^3 bricks that meet the box
+ * are decoded, and d_out (caller-owned, box.nx*box.ny*box.nz floats, x
+ * fastest) receives exactly the matching values of the full reconstruction.
+ * The visualization side's request for a subvolume at a given accuracy
+ * (Sec. 2).  Asynchronous.
+ */
+chr_status chr_reconstruct_box(const chr_handle *h, uint32_t level, int64_t x0, int64_t y0, int64_t z0, chr_dims box,
+                               float *d_out, void *stream);
+
+/*
+ * chr_brick_range — per-brick value range of level `level`: d_range
+ * (caller-owned, 2 floats per 8^3 brick, brick (bx, by, bz) at index
+ * bx + nbx*(by + nby*bz), nbx = ceil(nx/8) and so on) receives the (min, max)
+ * of the reconstructed values at the brick's grid vertices, NaN counted as
+ * +inf.  An index of the CHR (Sec. 2: the visualization side picks the
+ * blocks a request needs): a cell whose 8 corners lie in bricks whose
+ * combined range does not straddle k (min < k <= max) has no triangles.
+ * Decodes the level without writing the field.  d_range must be 8-byte
+ * aligned.  Asynchronous.
+ */
+chr_status chr_brick_range(const chr_handle *h, uint32_t level, float *d_range, void *stream);
+
+/*
  * chr_topo_translate — the error-bound translation of Sec. 2.2 on its own:
  * D holds, for every grid edge (s0,s1) with min < k < max and every k in
  * isovalues, d0 = k - min and d1 = max - k, each rounded toward -inf in

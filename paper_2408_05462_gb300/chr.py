@@ -6,7 +6,8 @@ kernels.  torch provides device memory (through its caching allocator, handed
 to the library as a chr_allocator) and the current CUDA stream.  There is no
 CPU path: if libchr.so is missing or cannot load, every call raises.
 
-Names follow the C ABI: chr_compress, chr_reconstruct, chr_topo_translate,
+Names follow the C ABI: chr_compress, chr_reconstruct, chr_reconstruct_box, chr_brick_range,
+chr_topo_translate,
 isosurface_extract, isosurface_workspace_size, isosurface_extract_noalloc,
 isosurface_backward, isosurface_distance_loss, chr_serialize, chr_deserialize,
 chr_stats, chr_free.
@@ -81,6 +82,10 @@ def lib():
                                    POINTER(c_void_p)]
         L.chr_reconstruct.restype = st
         L.chr_reconstruct.argtypes = [c_void_p, c_uint32, c_void_p, c_void_p]
+        L.chr_reconstruct_box.restype = st
+        L.chr_reconstruct_box.argtypes = [c_void_p, c_uint32, c_int64, c_int64, c_int64, ChrDims, c_void_p, c_void_p]
+        L.chr_brick_range.restype = st
+        L.chr_brick_range.argtypes = [c_void_p, c_uint32, c_void_p, c_void_p]
         L.chr_topo_translate.restype = st
         L.chr_topo_translate.argtypes = [c_void_p, ChrDims, POINTER(c_float), c_uint32, c_float,
                                          POINTER(ChrAllocator), c_void_p, POINTER(c_float), POINTER(c_uint64)]
@@ -181,6 +186,12 @@ class Chr:
     def serialize(self, stream=None) -> bytes:
         return chr_serialize(self, stream)
 
+    def reconstruct_box(self, level: int, origin, size, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        return chr_reconstruct_box(self, level, origin, size, out, stream)
+
+    def brick_range(self, level: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        return chr_brick_range(self, level, out, stream)
+
     def free(self):
         if self._ptr is not None and self._ptr.value:
             lib().chr_free(self._ptr)
@@ -214,6 +225,34 @@ def chr_reconstruct(h: Chr, level: int, out: torch.Tensor | None = None, stream=
     if tuple(out.shape) != h.shape:
         raise ValueError("out has the wrong shape")
     _check(lib().chr_reconstruct(h.ptr, int(level), out.data_ptr(), _stream(stream)))
+    return out
+
+
+def chr_reconstruct_box(h: Chr, level: int, origin, size, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Decode the vertices origin .. origin+size (x, y, z) of level `level`
+    into a [size_z, size_y, size_x] tensor (chr.h: chr_reconstruct_box)."""
+    x0, y0, z0 = (int(v) for v in origin)
+    bx, by, bz = (int(v) for v in size)
+    if out is None:
+        out = torch.empty((bz, by, bx), dtype=torch.float32, device="cuda")
+    _check_field(out)
+    if tuple(out.shape) != (bz, by, bx):
+        raise ValueError("out has the wrong shape")
+    _check(lib().chr_reconstruct_box(h.ptr, int(level), x0, y0, z0, ChrDims(bx, by, bz), out.data_ptr(),
+                                     _stream(stream)))
+    return out
+
+
+def chr_brick_range(h: Chr, level: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Per-brick (min, max) of level `level`, shape [nbz, nby, nbx, 2]
+    (chr.h: chr_brick_range)."""
+    nz, ny, nx = h.shape
+    shape = ((nz + 7) // 8, (ny + 7) // 8, (nx + 7) // 8, 2)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, device="cuda")
+    if tuple(out.shape) != shape or out.dtype != torch.float32 or not out.is_contiguous() or not out.is_cuda:
+        raise ValueError("out must be a contiguous float32 CUDA tensor of shape %s" % (shape,))
+    _check(lib().chr_brick_range(h.ptr, int(level), out.data_ptr(), _stream(stream)))
     return out
 
 

@@ -141,6 +141,18 @@ void fill_codec_params(const chr_handle *h, CodecParams &p)
     p.fix = (h->topo_mode == CHR_TOPO_FIX) ? 1 : 0;
 }
 
+void set_box(CodecParams &p, const Grid &g, int64_t x0, int64_t y0, int64_t z0, int64_t bx, int64_t by, int64_t bz)
+{
+    const int64_t org[3] = {x0, y0, z0}, dim[3] = {bx, by, bz};
+    for (int a = 0; a < 3; a++) {
+        p.box_org[a] = org[a];
+        p.box_dim[a] = dim[a];
+        p.box_brick0[a] = (int32_t)(org[a] / 8);
+        p.box_bricks[a] = (int32_t)((org[a] + dim[a] - 1) / 8 - org[a] / 8 + 1);
+    }
+    (void)g;
+}
+
 void set_constants(chr_handle *h)
 {
     for (uint32_t l = 0; l < h->nlevels; l++) {
@@ -388,8 +400,44 @@ chr_status chr_reconstruct(const chr_handle *h, uint32_t level, float *d_out, vo
     fill_codec_params(h, p);
     p.out = d_out;
     p.nlevels = (int32_t)level + 1;
+    set_box(p, h->g, 0, 0, 0, h->g.nx, h->g.ny, h->g.nz);
     cudaError_t e = launch_decode(p, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "chr_reconstruct");
+    return CHR_OK;
+}
+
+chr_status chr_brick_range(const chr_handle *h, uint32_t level, float *d_range, void *stream)
+{
+    if (!h || !d_range) return fail(CHR_ERR_INVALID, "chr_brick_range: NULL handle or output");
+    if (level >= h->nlevels) return fail(CHR_ERR_INVALID, "chr_brick_range: level out of range");
+    if (reinterpret_cast<uintptr_t>(d_range) & 7u) return fail(CHR_ERR_INVALID, "chr_brick_range: misaligned output");
+    CodecParams p;
+    fill_codec_params(h, p);
+    p.out = nullptr;
+    p.range = reinterpret_cast<float2 *>(d_range);
+    p.nlevels = (int32_t)level + 1;
+    set_box(p, h->g, 0, 0, 0, h->g.nx, h->g.ny, h->g.nz);
+    cudaError_t e = launch_decode(p, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "chr_brick_range");
+    return CHR_OK;
+}
+
+chr_status chr_reconstruct_box(const chr_handle *h, uint32_t level, int64_t x0, int64_t y0, int64_t z0, chr_dims box,
+                               float *d_out, void *stream)
+{
+    if (!h || !d_out) return fail(CHR_ERR_INVALID, "chr_reconstruct_box: NULL handle or output");
+    if (level >= h->nlevels) return fail(CHR_ERR_INVALID, "chr_reconstruct_box: level out of range");
+    if (reinterpret_cast<uintptr_t>(d_out) & 3u) return fail(CHR_ERR_INVALID, "chr_reconstruct_box: misaligned output");
+    if (box.nx < 1 || box.ny < 1 || box.nz < 1 || x0 < 0 || y0 < 0 || z0 < 0 || x0 + box.nx > h->g.nx ||
+        y0 + box.ny > h->g.ny || z0 + box.nz > h->g.nz)
+        return fail(CHR_ERR_INVALID, "chr_reconstruct_box: box outside the grid");
+    CodecParams p;
+    fill_codec_params(h, p);
+    p.out = d_out;
+    p.nlevels = (int32_t)level + 1;
+    set_box(p, h->g, x0, y0, z0, box.nx, box.ny, box.nz);
+    cudaError_t e = launch_decode(p, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "chr_reconstruct_box");
     return CHR_OK;
 }
 

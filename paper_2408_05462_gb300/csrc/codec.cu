@@ -293,7 +293,19 @@ __global__ void __launch_bounds__(256) k_decode(const __grid_constant__ CodecPar
 {
     extern __shared__ __align__(16) uint32_t s_dyn[];
     BrickCoord c;
-    if (!brick_of_warp(p, c)) return;
+    {   // bricks of the output box: groups of 8 along x inside the box's brick range
+        const int warp = threadIdx.x >> 5;
+        const int ngx = (p.box_bricks[0] + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        const int64_t g = blockIdx.x;
+        const int32_t gx = (int32_t)(g % ngx);
+        const int64_t rest = g / ngx;
+        const int32_t lbx = gx * kWarpsPerBlock + warp;
+        if (lbx >= p.box_bricks[0]) return;
+        c.bx = p.box_brick0[0] + lbx;
+        c.by = p.box_brick0[1] + (int32_t)(rest % p.box_bricks[1]);
+        c.bz = p.box_brick0[2] + (int32_t)(rest / p.box_bricks[1]);
+        c.b = c.bx + (int64_t)p.nbx * (c.by + (int64_t)p.nby * c.bz);
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ly = lane & 7;
 
@@ -435,23 +447,54 @@ __global__ void __launch_bounds__(256) k_decode(const __grid_constant__ CodecPar
         __syncwarp();  // shared buffers are refilled by the next group
     }
 
-    // store the lane's two rows
     const int64_t x0 = (int64_t)c.bx * 8;
-    const int ex = (int)((p.nx - x0) < 8 ? (p.nx - x0) : 8);
-    const bool vec = (ex == 8) && ((p.nx & 3) == 0) && ((reinterpret_cast<uintptr_t>(p.out) & 15u) == 0);
+    if (p.range) {
+        // the brick's value range over its grid vertices; NaN is never below
+        // an isovalue, so it counts as +inf
+        const int exg = (int)((p.nx - x0) < 8 ? (p.nx - x0) : 8);
+        float mn = __int_as_float(0x7f800000), mx = -mn;
+#pragma unroll
+        for (int s = 0; s < 2; s++) {
+            const int64_t y = (int64_t)c.by * 8 + ly, z = (int64_t)c.bz * 8 + (lane >> 3) + 4 * s;
+            if (y >= p.ny || z >= p.nz) continue;
+#pragma unroll
+            for (int x = 0; x < 8; x++) {
+                const float v = isnan(R[s][x]) ? __int_as_float(0x7f800000) : R[s][x];
+                if (x < exg) {
+                    mn = fminf(mn, v);
+                    mx = fmaxf(mx, v);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mn = fminf(mn, __shfl_xor_sync(CHR_FULL_MASK, mn, o));
+            mx = fmaxf(mx, __shfl_xor_sync(CHR_FULL_MASK, mx, o));
+        }
+        if (lane == 0) p.range[c.b] = make_float2(mn, mx);
+    }
+    if (!p.out) return;
+    // store the lane's two rows (the part inside the output box)
+    const int64_t bx0 = x0 - p.box_org[0];
+    int xlo = (int)(bx0 < 0 ? -bx0 : 0);
+    int xhi = (int)((p.nx - x0) < 8 ? (p.nx - x0) : 8);
+    if (bx0 + xhi > p.box_dim[0]) xhi = (int)(p.box_dim[0] - bx0);
+    const bool vec = (xlo == 0) && (xhi == 8) && ((p.box_dim[0] & 3) == 0) && ((bx0 & 3) == 0) &&
+                     ((reinterpret_cast<uintptr_t>(p.out) & 15u) == 0);
 #pragma unroll
     for (int s = 0; s < 2; s++) {
-        const int64_t y = (int64_t)c.by * 8 + ly;
-        const int64_t z = (int64_t)c.bz * 8 + (lane >> 3) + 4 * s;
-        if (y >= p.ny || z >= p.nz) continue;
-        float *row = p.out + x0 + p.nx * (y + p.ny * z);
+        const int64_t y = (int64_t)c.by * 8 + ly - p.box_org[1];
+        const int64_t z = (int64_t)c.bz * 8 + (lane >> 3) + 4 * s - p.box_org[2];
+        if (y < 0 || z < 0 || y >= p.box_dim[1] || z >= p.box_dim[2]) continue;
+        if (y + p.box_org[1] >= p.ny || z + p.box_org[2] >= p.nz) continue;
+        float *row = p.out + bx0 + p.box_dim[0] * (y + p.box_dim[1] * z);
         if (vec) {
             __stcs(reinterpret_cast<float4 *>(row), make_float4(R[s][0], R[s][1], R[s][2], R[s][3]));
             __stcs(reinterpret_cast<float4 *>(row + 4), make_float4(R[s][4], R[s][5], R[s][6], R[s][7]));
         } else {
 #pragma unroll
             for (int x = 0; x < 8; x++)
-                if (x < ex) row[x] = R[s][x];
+                if (x >= xlo && x < xhi) row[x] = R[s][x];
         }
     }
 }
@@ -583,13 +626,15 @@ cudaError_t launch_compact(const CodecParams &p, cudaStream_t s)
 
 cudaError_t launch_decode(const CodecParams &p, cudaStream_t s)
 {
+    const dim3 grid((unsigned)((int64_t)((p.box_bricks[0] + kWarpsPerBlock - 1) / kWarpsPerBlock) * p.box_bricks[1] *
+                               p.box_bricks[2]));
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, kDecodeSmem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_decode<<<codec_grid(p), 256, kDecodeSmem, s>>>(p);
+    k_decode<<<grid, 256, kDecodeSmem, s>>>(p);
     return cudaGetLastError();
 }
 

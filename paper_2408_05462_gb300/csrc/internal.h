@@ -47,6 +47,12 @@ struct CodecParams {
     uint32_t *words[CHR_MAX_LEVELS];
     uint16_t *exc_idx[CHR_MAX_LEVELS];
     uint32_t *exc_val[CHR_MAX_LEVELS];
+    // decode output box: vertices [box_org, box_org + box_dim) of the grid,
+    // written x-fastest with the box's own strides; bricks box_brick0 ..
+    // box_brick0 + box_bricks cover it (the whole grid for chr_reconstruct)
+    int64_t box_org[3], box_dim[3];
+    int32_t box_brick0[3], box_bricks[3];
+    float2 *range;  // optional per-brick (min, max) of the decoded values
     // encode scratch: fixed per-brick slots (512 words, 512 exception entries)
     uint32_t *slot_words[CHR_MAX_LEVELS];
     uint16_t *slot_idx[CHR_MAX_LEVELS];

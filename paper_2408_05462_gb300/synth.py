@@ -78,6 +78,36 @@ def turbulence(n, seed: int = 512, slope: float = -5.0 / 3.0) -> np.ndarray:
     return np.ascontiguousarray(f, dtype=np.float32)
 
 
+def turbulence_cuda(n, seed: int = 1024, slope: float = -5.0 / 3.0):
+    """The spectral field of `turbulence`, generated on the GPU in float32
+    with torch's seeded CUDA generator (for grids too large for the host FFT;
+    the random draws, hence the values, differ from `turbulence`).  Returns a
+    [nz, ny, nx] float32 CUDA tensor with zero mean and unit variance."""
+    import torch
+
+    nx, ny, nz = (n, n, n) if np.isscalar(n) else n
+    dev = torch.device("cuda")
+    g = torch.Generator(device=dev)
+    g.manual_seed(int(seed))
+    kz = torch.fft.fftfreq(nz, 1.0 / nz, device=dev)
+    ky = torch.fft.fftfreq(ny, 1.0 / ny, device=dev)
+    kx = torch.fft.rfftfreq(nx, 1.0 / nx, device=dev)
+    k2 = kz[:, None, None] ** 2 + ky[None, :, None] ** 2 + kx[None, None, :] ** 2
+    k2[0, 0, 0] = 1.0
+    amp = k2.pow_((slope - 2.0) / 4.0)
+    del k2
+    amp[0, 0, 0] = 0.0
+    shape = (nz, ny, nx // 2 + 1)
+    spec = torch.complex(torch.randn(shape, generator=g, device=dev), torch.randn(shape, generator=g, device=dev))
+    spec *= amp
+    del amp
+    f = torch.fft.irfftn(spec, s=(nz, ny, nx))
+    del spec
+    f -= f.mean(dtype=torch.float64).float()
+    f /= f.double().std().float()
+    return f.contiguous()
+
+
 def sphere_distance(n, center, radius_unused=None) -> np.ndarray:
     """|p - c| in grid units (a sphere of radius r is its level set r)."""
     nx, ny, nz = (n, n, n) if np.isscalar(n) else n
