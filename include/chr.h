@@ -281,6 +281,72 @@ chr_status chr_serialize(const chr_handle *h, void *host_buf, size_t cap, size_t
 chr_status chr_deserialize(const void *host_buf, size_t n, const chr_allocator *alloc, void *stream,
                            chr_handle **out);
 
+/*
+ * ---- batches: many CHRs of uneven size in one launch sequence ----------
+ *
+ * The paper merges active blocks into rectangular boxes of uneven size and
+ * compresses each (Sec. 2); a batch decodes level `level` of every item's
+ * CHR and runs marching cubes on it at the item's own isovalue, as one
+ * captured sequence of launches: one decode over the concatenated brick
+ * list, one tile-count pass, one scan and one emit pass over the
+ * concatenated tile list.  Item i's triangles equal, bit for bit, those of
+ * chr_reconstruct + isosurface_extract of that item alone, and lie in the
+ * batch's triangle buffer from box_start[i] to box_start[i+1]
+ * (box_start[n] = total; total > cap sets CHR_ERR_OVERFLOW in the error
+ * word and only the first cap triangles are written).
+ */
+typedef struct chr_batch chr_batch; /* opaque; owns device buffers and a CUDA graph */
+
+typedef struct chr_batch_item {
+    const chr_handle *h; /* must outlive the batch */
+    uint32_t level;      /* accuracy level to decode */
+    float isovalue;
+} chr_batch_item;
+
+typedef struct chr_batch_config {
+    int32_t count_blocks_per_sm; /* resident blocks per SM of the tile-count pass (0: the most that fit) */
+    int32_t emit_blocks_per_sm;  /* the same for the emit pass */
+    int32_t use_graph;           /* 1: capture the sequence once and replay it */
+} chr_batch_config;
+
+/*
+ * chr_batch_create — plan a batch of n items (n >= 1).  Outputs are
+ * caller-owned device buffers, written by every run: d_tris (cap_tris
+ * triangles of 9 floats, 4-byte aligned; may be NULL when cap_tris = 0),
+ * d_box_start (n+1 uint64) and d_err (one uint32 error word, reset by each
+ * run).  The library allocates the pitched field buffer (rows padded to 16
+ * bytes), the per-item parameters and tensor maps and the scan scratch from
+ * `alloc` (NULL: cudaMallocAsync) on `stream`, which it synchronises once.
+ * The configuration is the one the autotuner last chose for a batch with the
+ * same size-class signature, else the defaults.
+ */
+chr_status chr_batch_create(const chr_batch_item *items, uint32_t n, float *d_tris, uint64_t cap_tris,
+                            uint64_t *d_box_start, uint32_t *d_err, const chr_allocator *alloc, void *stream,
+                            chr_batch **out);
+
+/* chr_batch_run — decode + marching cubes of every item, asynchronous on stream. */
+chr_status chr_batch_run(chr_batch *b, void *stream);
+
+/*
+ * chr_batch_autotune — time every candidate configuration (tile-kernel grid
+ * sizes) on this batch, reps runs each, keep the fastest and remember it for
+ * the batch's size-class signature.  Synchronises stream.  The outputs then
+ * hold the last candidate's (identical) results.
+ */
+chr_status chr_batch_autotune(chr_batch *b, uint32_t reps, void *stream, chr_batch_config *chosen);
+chr_status chr_batch_get_config(const chr_batch *b, chr_batch_config *cfg);
+/* chr_batch_set_config — zero fields pick the largest grid; over-large values are clamped. */
+chr_status chr_batch_set_config(chr_batch *b, const chr_batch_config *cfg);
+
+/* chr_batch_field — item i's decoded field (library-owned): value (x, y, z) at d_field[x + sx*y + sy*z]. */
+chr_status chr_batch_field(const chr_batch *b, uint32_t i, float **d_field, int64_t *sx, int64_t *sy);
+
+/* chr_batch_field_copy — item i's decoded field into d_out (nx*ny*nz floats, x fastest), asynchronous. */
+chr_status chr_batch_field_copy(const chr_batch *b, uint32_t i, float *d_out, void *stream);
+
+/* chr_batch_free — release the batch (after its work has finished). NULL ok. */
+void chr_batch_free(chr_batch *b);
+
 /* chr_stats — sizes and bounds of a CHR (host-side, no device work). */
 chr_status chr_stats(const chr_handle *h, chr_stats_t *out);
 

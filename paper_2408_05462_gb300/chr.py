@@ -10,7 +10,7 @@ Names follow the C ABI: chr_compress, chr_reconstruct, chr_reconstruct_box, chr_
 chr_topo_translate,
 isosurface_extract, isosurface_workspace_size, isosurface_extract_noalloc,
 isosurface_backward, isosurface_distance_loss, chr_serialize, chr_deserialize,
-chr_stats, chr_free.
+chr_stats, chr_free, and the chr_batch_* calls (class Batch).
 """
 from __future__ import annotations
 
@@ -67,6 +67,15 @@ class ChrStats(ctypes.Structure):
 _lib = None
 
 
+class ChrBatchItem(ctypes.Structure):
+    _fields_ = [("h", c_void_p), ("level", c_uint32), ("isovalue", c_float)]
+
+
+class ChrBatchConfig(ctypes.Structure):
+    _fields_ = [("count_blocks_per_sm", ctypes.c_int32), ("emit_blocks_per_sm", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32)]
+
+
 def lib():
     """The loaded libchr.so; raises if it was not built."""
     global _lib
@@ -115,6 +124,24 @@ def lib():
         L.chr_stats.argtypes = [c_void_p, POINTER(ChrStats)]
         L.chr_free.restype = None
         L.chr_free.argtypes = [c_void_p]
+        L.chr_batch_create.restype = st
+        L.chr_batch_create.argtypes = [POINTER(ChrBatchItem), c_uint32, c_void_p, c_uint64, c_void_p, c_void_p,
+                                       POINTER(ChrAllocator), c_void_p, POINTER(c_void_p)]
+        L.chr_batch_run.restype = st
+        L.chr_batch_run.argtypes = [c_void_p, c_void_p]
+        L.chr_batch_autotune.restype = st
+        L.chr_batch_autotune.argtypes = [c_void_p, c_uint32, c_void_p, POINTER(ChrBatchConfig)]
+        L.chr_batch_get_config.restype = st
+        L.chr_batch_get_config.argtypes = [c_void_p, POINTER(ChrBatchConfig)]
+        L.chr_batch_set_config.restype = st
+        L.chr_batch_set_config.argtypes = [c_void_p, POINTER(ChrBatchConfig)]
+        L.chr_batch_field.restype = st
+        L.chr_batch_field.argtypes = [c_void_p, c_uint32, POINTER(c_void_p), POINTER(ctypes.c_int64),
+                                      POINTER(ctypes.c_int64)]
+        L.chr_batch_field_copy.restype = st
+        L.chr_batch_field_copy.argtypes = [c_void_p, c_uint32, c_void_p, c_void_p]
+        L.chr_batch_free.restype = None
+        L.chr_batch_free.argtypes = [c_void_p]
         _lib = L
     return _lib
 
@@ -392,6 +419,73 @@ def chr_stats(h: Chr) -> dict:
 
 def chr_free(h: Chr):
     h.free()
+
+
+class Batch:
+    """Many CHRs decoded and meshed by one captured launch sequence (chr.h:
+    chr_batch_*).  items: (Chr, level, isovalue) triples; the handles must
+    outlive the batch.  Outputs (tris [cap, 3, 3], box_start [n+1], err [1])
+    are torch tensors owned here and rewritten by every run."""
+
+    def __init__(self, items, cap: int, stream=None):
+        self.items = list(items)
+        n = len(self.items)
+        arr = (ChrBatchItem * max(n, 1))(*[ChrBatchItem(h.ptr.value, int(l), float(k)) for h, l, k in self.items])
+        self.cap = int(cap)
+        self.tris = torch.empty((max(self.cap, 1), 3, 3), dtype=torch.float32, device="cuda")
+        self.box_start = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
+        self.err = torch.zeros(1, dtype=torch.int32, device="cuda")
+        out = c_void_p()
+        _check(lib().chr_batch_create(arr, n, self.tris.data_ptr() if self.cap > 0 else None, self.cap,
+                                      self.box_start.data_ptr(), self.err.data_ptr(), ctypes.byref(TORCH_ALLOCATOR),
+                                      _stream(stream), ctypes.byref(out)))
+        self._ptr = out
+
+    def run(self, stream=None):
+        _check(lib().chr_batch_run(self._ptr, _stream(stream)))
+
+    def autotune(self, reps: int = 3, stream=None) -> dict:
+        c = ChrBatchConfig()
+        _check(lib().chr_batch_autotune(self._ptr, int(reps), _stream(stream), ctypes.byref(c)))
+        return {"count_blocks_per_sm": c.count_blocks_per_sm, "emit_blocks_per_sm": c.emit_blocks_per_sm,
+                "use_graph": c.use_graph}
+
+    @property
+    def config(self) -> dict:
+        c = ChrBatchConfig()
+        _check(lib().chr_batch_get_config(self._ptr, ctypes.byref(c)))
+        return {"count_blocks_per_sm": c.count_blocks_per_sm, "emit_blocks_per_sm": c.emit_blocks_per_sm,
+                "use_graph": c.use_graph}
+
+    @config.setter
+    def config(self, cfg: dict):
+        c = ChrBatchConfig(int(cfg.get("count_blocks_per_sm", 0)), int(cfg.get("emit_blocks_per_sm", 0)),
+                           int(cfg.get("use_graph", 1)))
+        _check(lib().chr_batch_set_config(self._ptr, ctypes.byref(c)))
+
+    def field(self, i: int, stream=None) -> torch.Tensor:
+        """Item i's decoded field as a dense [nz, ny, nx] tensor (a copy)."""
+        h = self.items[i][0]
+        out = torch.empty(h.shape, dtype=torch.float32, device="cuda")
+        _check(lib().chr_batch_field_copy(self._ptr, int(i), out.data_ptr(), _stream(stream)))
+        return out
+
+    def triangles(self, i: int) -> torch.Tensor:
+        """Item i's triangles (a view; synchronises to read box_start)."""
+        bs = self.box_start.cpu()
+        a, b = int(bs[i]), min(int(bs[i + 1]), self.cap)
+        return self.tris[a:max(a, b)]
+
+    def free(self):
+        if self._ptr is not None and self._ptr.value:
+            lib().chr_batch_free(self._ptr)
+        self._ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 def parse_serialized(data: bytes) -> dict:

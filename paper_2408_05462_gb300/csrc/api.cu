@@ -16,47 +16,6 @@ static thread_local std::string g_last_error;
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 
-namespace {
-
-struct Alloc {
-    chr_allocator a{};
-    bool dflt = true;
-    cudaStream_t s = nullptr;
-
-    Alloc(const chr_allocator *al, cudaStream_t st) : s(st)
-    {
-        if (al) {
-            a = *al;
-            dflt = false;
-        }
-    }
-    void *get(size_t n)
-    {
-        if (n == 0) n = 16;
-        n = (n + 255) & ~size_t(255);
-        void *p = nullptr;
-        if (dflt) {
-            if (cudaMallocAsync(&p, n, s) != cudaSuccess) {
-                cudaGetLastError();
-                return nullptr;
-            }
-        } else {
-            p = a.alloc(n, s, a.ctx);
-        }
-        return p;
-    }
-    void put(void *p, size_t n)
-    {
-        if (!p) return;
-        if (n == 0) n = 16;
-        n = (n + 255) & ~size_t(255);
-        if (dflt)
-            cudaFreeAsync(p, s);
-        else
-            a.free(p, n, s, a.ctx);
-    }
-};
-
 chr_status fail(chr_status st, const std::string &msg)
 {
     set_error(msg);
@@ -67,6 +26,8 @@ chr_status cuda_fail(cudaError_t e, const char *where)
 {
     return fail(CHR_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
+
+namespace {
 
 #define CHR_CUDA(call, where)                         \
     do {                                              \
@@ -116,6 +77,8 @@ chr_handle *new_handle(chr_dims dims, const chr_allocator *alloc, cudaStream_t s
     return h;
 }
 
+}  // namespace
+
 void fill_codec_params(const chr_handle *h, CodecParams &p)
 {
     memset(&p, 0, sizeof(p));
@@ -150,8 +113,12 @@ void set_box(CodecParams &p, const Grid &g, int64_t x0, int64_t y0, int64_t z0, 
         p.box_brick0[a] = (int32_t)(org[a] / 8);
         p.box_bricks[a] = (int32_t)((org[a] + dim[a] - 1) / 8 - org[a] / 8 + 1);
     }
+    p.out_sx = bx;
+    p.out_sy = bx * by;
     (void)g;
 }
+
+namespace {
 
 void set_constants(chr_handle *h)
 {

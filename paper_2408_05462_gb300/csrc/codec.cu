@@ -289,23 +289,54 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // the packed words (cp.async straight into shared memory) and the first 64
 // exception entries of each level (registers), so a brick costs about two
 // memory round trips instead of three per level.
+__device__ __forceinline__ void decode_brick(const CodecParams &p, const BrickCoord &c, uint32_t *s_dyn);
+
 __global__ void __launch_bounds__(256) k_decode(const __grid_constant__ CodecParams p)
 {
     extern __shared__ __align__(16) uint32_t s_dyn[];
     BrickCoord c;
-    {   // bricks of the output box: groups of 8 along x inside the box's brick range
-        const int warp = threadIdx.x >> 5;
-        const int ngx = (p.box_bricks[0] + kWarpsPerBlock - 1) / kWarpsPerBlock;
-        const int64_t g = blockIdx.x;
-        const int32_t gx = (int32_t)(g % ngx);
-        const int64_t rest = g / ngx;
-        const int32_t lbx = gx * kWarpsPerBlock + warp;
-        if (lbx >= p.box_bricks[0]) return;
-        c.bx = p.box_brick0[0] + lbx;
-        c.by = p.box_brick0[1] + (int32_t)(rest % p.box_bricks[1]);
-        c.bz = p.box_brick0[2] + (int32_t)(rest / p.box_bricks[1]);
-        c.b = c.bx + (int64_t)p.nbx * (c.by + (int64_t)p.nby * c.bz);
+    // bricks of the output box: groups of 8 along x inside the box's brick range
+    const int warp = threadIdx.x >> 5;
+    const int ngx = (p.box_bricks[0] + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const int64_t g = blockIdx.x;
+    const int32_t gx = (int32_t)(g % ngx);
+    const int64_t rest = g / ngx;
+    const int32_t lbx = gx * kWarpsPerBlock + warp;
+    if (lbx >= p.box_bricks[0]) return;
+    c.bx = p.box_brick0[0] + lbx;
+    c.by = p.box_brick0[1] + (int32_t)(rest % p.box_bricks[1]);
+    c.bz = p.box_brick0[2] + (int32_t)(rest / p.box_bricks[1]);
+    c.b = c.bx + (int64_t)p.nbx * (c.by + (int64_t)p.nby * c.bz);
+    decode_brick(p, c, s_dyn);
+}
+
+// Many CHRs in one launch: warp w of the grid decodes brick w of the
+// concatenated brick list (box i owns bricks brick_start[i] ..
+// brick_start[i+1]-1, x fastest), so small boxes leave no warp idle.
+__global__ void __launch_bounds__(256) k_decode_batched(const CodecParams *__restrict__ descs,
+                                                        const int64_t *__restrict__ brick_start, int32_t nboxes)
+{
+    extern __shared__ __align__(16) uint32_t s_dyn[];
+    const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (w >= brick_start[nboxes]) return;
+    int lo = 0, hi = nboxes - 1;  // the last box whose start is <= w
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (brick_start[mid] <= w) lo = mid; else hi = mid - 1;
     }
+    const CodecParams &p = descs[lo];
+    const int64_t lb = w - brick_start[lo];
+    BrickCoord c;
+    c.bx = (int32_t)(lb % p.nbx);
+    c.by = (int32_t)((lb / p.nbx) % p.nby);
+    c.bz = (int32_t)(lb / ((int64_t)p.nbx * p.nby));
+    c.b = lb;
+    decode_brick(p, c, s_dyn);
+}
+
+// Decode brick c of p into p.out (and its value range into p.range), by one warp.
+__device__ __forceinline__ void decode_brick(const CodecParams &p, const BrickCoord &c, uint32_t *s_dyn)
+{
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ly = lane & 7;
 
@@ -479,15 +510,15 @@ __global__ void __launch_bounds__(256) k_decode(const __grid_constant__ CodecPar
     int xlo = (int)(bx0 < 0 ? -bx0 : 0);
     int xhi = (int)((p.nx - x0) < 8 ? (p.nx - x0) : 8);
     if (bx0 + xhi > p.box_dim[0]) xhi = (int)(p.box_dim[0] - bx0);
-    const bool vec = (xlo == 0) && (xhi == 8) && ((p.box_dim[0] & 3) == 0) && ((bx0 & 3) == 0) &&
-                     ((reinterpret_cast<uintptr_t>(p.out) & 15u) == 0);
+    const bool vec = (xlo == 0) && (xhi == 8) && ((p.out_sx & 3) == 0) && ((p.out_sy & 3) == 0) &&
+                     ((bx0 & 3) == 0) && ((reinterpret_cast<uintptr_t>(p.out) & 15u) == 0);
 #pragma unroll
     for (int s = 0; s < 2; s++) {
         const int64_t y = (int64_t)c.by * 8 + ly - p.box_org[1];
         const int64_t z = (int64_t)c.bz * 8 + (lane >> 3) + 4 * s - p.box_org[2];
         if (y < 0 || z < 0 || y >= p.box_dim[1] || z >= p.box_dim[2]) continue;
         if (y + p.box_org[1] >= p.ny || z + p.box_org[2] >= p.nz) continue;
-        float *row = p.out + bx0 + p.box_dim[0] * (y + p.box_dim[1] * z);
+        float *row = p.out + bx0 + p.out_sx * y + p.out_sy * z;
         if (vec) {
             __stcs(reinterpret_cast<float4 *>(row), make_float4(R[s][0], R[s][1], R[s][2], R[s][3]));
             __stcs(reinterpret_cast<float4 *>(row + 4), make_float4(R[s][4], R[s][5], R[s][6], R[s][7]));
@@ -635,6 +666,22 @@ cudaError_t launch_decode(const CodecParams &p, cudaStream_t s)
         attr = true;
     }
     k_decode<<<grid, 256, kDecodeSmem, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decode_batched(const CodecParams *d_descs, const int64_t *d_brick_start, int32_t nboxes,
+                                  int64_t total_bricks, cudaStream_t s)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_decode_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, kDecodeSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if (total_bricks == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((total_bricks + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    k_decode_batched<<<grid, 256, kDecodeSmem, s>>>(d_descs, d_brick_start, nboxes);
     return cudaGetLastError();
 }
 

@@ -51,6 +51,7 @@ struct CodecParams {
     // written x-fastest with the box's own strides; bricks box_brick0 ..
     // box_brick0 + box_bricks cover it (the whole grid for chr_reconstruct)
     int64_t box_org[3], box_dim[3];
+    int64_t out_sx, out_sy;  // output row and plane pitch in floats
     int32_t box_brick0[3], box_bricks[3];
     float2 *range;  // optional per-brick (min, max) of the decoded values
     // encode scratch: fixed per-brick slots (512 words, 512 exception entries)
@@ -65,6 +66,9 @@ inline size_t encode_slot_bytes(int64_t nbricks) { return (size_t)nbricks * 512 
 cudaError_t launch_encode(const CodecParams &p, cudaStream_t s);
 cudaError_t launch_compact(const CodecParams &p, cudaStream_t s);
 cudaError_t launch_decode(const CodecParams &p, cudaStream_t s);
+// Decode of many CHRs in one launch (descs, brick_start [nboxes+1] on the device).
+cudaError_t launch_decode_batched(const CodecParams *d_descs, const int64_t *d_brick_start, int32_t nboxes,
+                                  int64_t total_bricks, cudaStream_t s);
 // Exclusive scans of the widths and exception counts of each level's records;
 // totals[2*l] = sum of w, totals[2*l+1] = exceptions.  scratch needs
 // scan_scratch_bytes(nbricks, nlevels).
@@ -76,6 +80,33 @@ cudaError_t launch_scan_records(uint4 *const *recs, int nlevels, int64_t nbricks
 size_t mc_workspace_bytes(const Grid &g, int n_iso);
 cudaError_t launch_mc(const float *field, const Grid &g, const float *iso, int n_iso, float *tris, uint64_t cap,
                       uint64_t *ntris, uint32_t *err, void *workspace, cudaStream_t s);
+
+// Marching cubes of many fields (each with its own isovalue and pitch) in one
+// launch sequence: count over the concatenated tile list, one scan, emit.
+// Every field's triangles land in one buffer, field i's from box_start[i];
+// box_start[nboxes] = total (> cap: CHR_ERR_OVERFLOW in err).
+struct McBatchLaunch {
+    const void *params;      // device McParams [nboxes] (mc_batch_fill)
+    const void *maps;        // device CUtensorMap [nboxes], 64-byte aligned
+    const int64_t *tile_start;  // device [nboxes + 1]
+    int32_t nboxes;
+    int64_t ntiles;
+    void *scratch;           // mc_batch_scratch_bytes(ntiles)
+    uint64_t *total;         // device [1]
+    uint64_t *box_start;     // device [nboxes + 1]
+    uint64_t cap;
+    uint32_t *err;
+    int count_blocks, emit_blocks;  // grid sizes of the two tile kernels
+};
+size_t mc_batch_param_bytes();
+int64_t mc_tile_count(int64_t nx, int64_t ny, int64_t nz);
+size_t mc_batch_scratch_bytes(int64_t ntiles);
+// Host: field i's parameters and tensor map (false if no tensor map can be made).
+bool mc_batch_fill(void *params, void *map, const float *field, int64_t nx, int64_t ny, int64_t nz, int64_t sx,
+                   int64_t sy, float k, float *tris, uint64_t cap, void *scratch, int64_t total_tiles, int64_t tile0,
+                   uint32_t *err);
+cudaError_t mc_batch_prepare(int &count_per_sm, int &emit_per_sm, int &sms);
+cudaError_t launch_mc_batched(const McBatchLaunch &L, cudaStream_t s);
 
 // Adjoint of the vertex positions: dL/dfield from dL/dtris (forward layout).
 size_t mc_adjoint_workspace_bytes(const Grid &g, int n_iso);
@@ -98,6 +129,58 @@ cudaError_t launch_translate_pass(const float *field, const Grid &g, const float
                                   uint32_t prefix, bool min_only, TranslateScratch sc, cudaStream_t s);
 
 void set_error(const std::string &msg);
+
+}  // namespace chr
+
+struct chr_handle;
+
+namespace chr {
+
+// Device memory from a caller's chr_allocator, or stream-ordered cudaMallocAsync.
+struct Alloc {
+    chr_allocator a{};
+    bool dflt = true;
+    cudaStream_t s = nullptr;
+
+    Alloc(const chr_allocator *al, cudaStream_t st) : s(st)
+    {
+        if (al) {
+            a = *al;
+            dflt = false;
+        }
+    }
+    void *get(size_t n)
+    {
+        if (n == 0) n = 16;
+        n = (n + 255) & ~size_t(255);
+        void *p = nullptr;
+        if (dflt) {
+            if (cudaMallocAsync(&p, n, s) != cudaSuccess) {
+                cudaGetLastError();
+                return nullptr;
+            }
+        } else {
+            p = a.alloc(n, s, a.ctx);
+        }
+        return p;
+    }
+    void put(void *p, size_t n)
+    {
+        if (!p) return;
+        if (n == 0) n = 16;
+        n = (n + 255) & ~size_t(255);
+        if (dflt)
+            cudaFreeAsync(p, s);
+        else
+            a.free(p, n, s, a.ctx);
+    }
+};
+
+chr_status fail(chr_status st, const std::string &msg);
+chr_status cuda_fail(cudaError_t e, const char *where);
+// Decode parameters of a handle (every level, whole grid as the output box).
+void fill_codec_params(const chr_handle *h, CodecParams &p);
+void set_box(CodecParams &p, const Grid &g, int64_t x0, int64_t y0, int64_t z0, int64_t bx, int64_t by, int64_t bz);
 
 }  // namespace chr
 

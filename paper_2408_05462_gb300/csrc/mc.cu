@@ -57,6 +57,7 @@ constexpr int kEmitSmem = kOffStage + 8 * kWarpStage * 4 + 128;  // + alignment 
 struct McParams {
     const float *f;
     int64_t nx, ny, nz;
+    int64_t sx, sy;           // row and plane pitch of f in floats (plain loads)
     int32_t ntx, ncby, ncbz;  // tiles along x; cell bricks along y, z
     int32_t use_tma;
     int64_t ntiles;
@@ -90,7 +91,7 @@ __device__ void load_box_plain(float *buf, const McParams &p, const TileXYZ &o)
     for (int i = threadIdx.x; i < kRows * kVX; i += blockDim.x) {
         const int lx = i % kVX, r = i / kVX, ly = r % 9, lz = r / 9;
         const int64_t gx = o.x0 + lx, gy = o.y0 + ly, gz = o.z0 + lz;
-        buf[i] = (gx < p.nx && gy < p.ny && gz < p.nz) ? __ldg(p.f + gx + p.nx * (gy + p.ny * gz)) : 0.0f;
+        buf[i] = (gx < p.nx && gy < p.ny && gz < p.nz) ? __ldg(p.f + gx + p.sx * gy + p.sy * gz) : 0.0f;
     }
 }
 
@@ -160,54 +161,112 @@ __device__ __forceinline__ int valid_cells(const McParams &p, const TileXYZ &o)
     return 0;
 }
 
-// Persistent tile loop shared by both kernels: the next box is fetched while
-// `body` processes the current one.  A copy that never arrives (bounded
-// wait) raises CHR_ERR_TIMEOUT and the block stops.
-template <class Body>
-__device__ __forceinline__ void tile_loop(const McParams &p, const CUtensorMap *map, float *bufs, uint64_t *mbar,
-                                          Body body)
+// Where tiles come from.  One field: tile t of p.  A batch: tile t of the
+// concatenated tile list of many fields, each with its own McParams and
+// tensor map (tile_start[i] = first tile of field i).
+struct SrcOne {
+    const McParams *p;
+    const CUtensorMap *map;
+    __device__ __forceinline__ int64_t ntiles() const { return p->ntiles; }
+    __device__ __forceinline__ bool use_tma() const { return p->use_tma != 0; }
+    __device__ __forceinline__ void at(int64_t tile, const McParams *&bp, const CUtensorMap *&m, int64_t &local) const
+    {
+        bp = p;
+        m = map;
+        local = tile;
+    }
+};
+
+struct McBatch {
+    const McParams *boxes;   // [nboxes]
+    const CUtensorMap *maps; // [nboxes], 64-byte aligned
+    const int64_t *tile_start;  // [nboxes + 1]
+    int32_t nboxes;
+    int64_t ntiles;
+};
+
+struct SrcMany {
+    const McBatch *b;
+    __device__ __forceinline__ int64_t ntiles() const { return b->ntiles; }
+    __device__ __forceinline__ bool use_tma() const { return true; }
+    __device__ __forceinline__ void at(int64_t tile, const McParams *&bp, const CUtensorMap *&m, int64_t &local) const
+    {
+        const int64_t *ts = b->tile_start;
+        int lo = 0, hi = b->nboxes - 1;  // the last field whose first tile is <= tile
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(ts + mid) <= tile) lo = mid; else hi = mid - 1;
+        }
+        bp = b->boxes + lo;
+        m = b->maps + lo;
+        local = tile - __ldg(ts + lo);
+    }
+};
+
+// Persistent tile loop shared by the tile kernels: the next box is fetched
+// while `body` processes the current one.  A copy that never arrives
+// (bounded wait) raises CHR_ERR_TIMEOUT and the block stops.
+// body(tile, local tile, field params, box).
+template <class Src, class Body>
+__device__ __forceinline__ void tile_loop(const Src &src, uint32_t *err, float *bufs, uint64_t *mbar, Body body)
 {
     const int tid = threadIdx.x;
-    const int64_t G = gridDim.x;
+    const int64_t G = gridDim.x, ntiles = src.ntiles();
+    const bool tma = src.use_tma();
     int64_t tile = blockIdx.x;
-    if (p.use_tma) {
+    if (tma) {
         if (tid == 0) {
             mbar_init(&mbar[0], 1);
             mbar_init(&mbar[1], 1);
             fence_mbar_init();
         }
         __syncthreads();
-        if (tid == 0 && tile < p.ntiles) issue_box(bufs, map, &mbar[0], p, tile);
+        if (tid == 0 && tile < ntiles) {
+            const McParams *bp;
+            const CUtensorMap *m;
+            int64_t local;
+            src.at(tile, bp, m, local);
+            issue_box(bufs, m, &mbar[0], *bp, local);
+        }
     }
     uint32_t phase0 = 0, phase1 = 0;
     int cur = 0;
-    for (; tile < p.ntiles; tile += G) {
+    for (; tile < ntiles; tile += G) {
         float *buf = bufs + cur * (kBufBytes / 4);
         const int64_t next = tile + G;
+        const McParams *bp;
+        const CUtensorMap *m;
+        int64_t local;
+        src.at(tile, bp, m, local);
         bool ok = true;
-        if (p.use_tma) {
-            if (tid == 0 && next < p.ntiles) issue_box(bufs + (cur ^ 1) * (kBufBytes / 4), map, &mbar[cur ^ 1], p, next);
+        if (tma) {
+            if (tid == 0 && next < ntiles) {
+                const McParams *nbp;
+                const CUtensorMap *nm;
+                int64_t nlocal;
+                src.at(next, nbp, nm, nlocal);
+                issue_box(bufs + (cur ^ 1) * (kBufBytes / 4), nm, &mbar[cur ^ 1], *nbp, nlocal);
+            }
             ok = mbar_wait(&mbar[cur], cur ? phase1 : phase0);
             if (cur)
                 phase1 ^= 1u;
             else
                 phase0 ^= 1u;
         } else {
-            load_box_plain(buf, p, tile_origin(p, tile));
+            load_box_plain(buf, *bp, tile_origin(*bp, local));
         }
         if (!__syncthreads_and(ok)) {
-            if (tid == 0 && p.err) atomicOr(p.err, 1u << CHR_ERR_TIMEOUT);
+            if (tid == 0 && err) atomicOr(err, 1u << CHR_ERR_TIMEOUT);
             return;
         }
-        body(tile, buf);
+        body(tile, local, *bp, buf);
         __syncthreads();  // every read of buf is done before it is refilled
         cur ^= 1;
     }
 }
 
-template <int NISO>
-__global__ void __launch_bounds__(256) k_mc_count(const __grid_constant__ McParams p,
-                                                 const __grid_constant__ CUtensorMap map)
+template <int NISO, class Src>
+__device__ __forceinline__ void mc_count_run(const Src &src, uint32_t *err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
@@ -219,7 +278,7 @@ __global__ void __launch_bounds__(256) k_mc_count(const __grid_constant__ McPara
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     s_cnt[tid] = (uint8_t)(g_mc_case[tid] >> 60);
 
-    tile_loop(p, &map, bufs, mbar, [&](int64_t tile, const float *buf) {
+    tile_loop(src, err, bufs, mbar, [&](int64_t, int64_t tile, const McParams &p, const float *buf) {
         row_masks<NISO>(buf, s_row, p);
         __syncthreads();
         const TileXYZ o = tile_origin(p, tile);
@@ -246,6 +305,18 @@ __global__ void __launch_bounds__(256) k_mc_count(const __grid_constant__ McPara
             p.tile_cnt[tile] = make_uint4(t[0], t[1], t[2], t[3]);
         }
     });
+}
+
+template <int NISO>
+__global__ void __launch_bounds__(256) k_mc_count(const __grid_constant__ McParams p,
+                                                 const __grid_constant__ CUtensorMap map)
+{
+    mc_count_run<NISO>(SrcOne{&p, &map}, p.err);
+}
+
+__global__ void __launch_bounds__(256) k_mc_count_batched(const __grid_constant__ McBatch b, uint32_t *err)
+{
+    mc_count_run<1>(SrcMany{&b}, err);
 }
 
 // Edge e of a cell: the float offsets (ox, oy, oz) of its lower corner, the
@@ -306,9 +377,8 @@ __device__ __forceinline__ void make_triangle(float *dst, const float *box, cons
     }
 }
 
-template <int NISO>
-__global__ void __launch_bounds__(256, 4) k_mc_emit(const __grid_constant__ McParams p,
-                                                   const __grid_constant__ CUtensorMap map)
+template <int NISO, class Src>
+__device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
@@ -334,7 +404,7 @@ __global__ void __launch_bounds__(256, 4) k_mc_emit(const __grid_constant__ McPa
     }
     if (tid < 12) s_edge[tid] = edge_vec(tid);
 
-    tile_loop(p, &map, bufs, mbar, [&](int64_t tile, const float *box) {
+    tile_loop(src, err, bufs, mbar, [&](int64_t, int64_t tile, const McParams &p, const float *box) {
         row_masks<NISO>(box, s_row, p);
         __syncthreads();
         const TileXYZ o = tile_origin(p, tile);
@@ -427,6 +497,18 @@ __global__ void __launch_bounds__(256, 4) k_mc_emit(const __grid_constant__ McPa
     });
 }
 
+template <int NISO>
+__global__ void __launch_bounds__(256, 4) k_mc_emit(const __grid_constant__ McParams p,
+                                                   const __grid_constant__ CUtensorMap map)
+{
+    mc_emit_run<NISO>(SrcOne{&p, &map}, p.err);
+}
+
+__global__ void __launch_bounds__(256, 4) k_mc_emit_batched(const __grid_constant__ McBatch b, uint32_t *err)
+{
+    mc_emit_run<1>(SrcMany{&b}, err);
+}
+
 // ---- adjoint of the vertex positions ----------------------------------------
 //
 // A vertex on edge (i0, i1) along `axis` sits at p_axis = x0 + t with
@@ -485,7 +567,7 @@ __global__ void __launch_bounds__(256, 4) k_mc_adjoint(const __grid_constant__ M
     const double S = (a.pass == 1) ? adj_scale(*a.maxbits) : 1.0;
     float lane_max = 0.0f;
 
-    tile_loop(p, &map, bufs, mbar, [&](int64_t tile, const float *box) {
+    tile_loop(SrcOne{&p, &map}, p.err, bufs, mbar, [&](int64_t, int64_t tile, const McParams &, const float *box) {
         row_masks<NISO>(box, s_row, p);
         __syncthreads();
         const TileXYZ o = tile_origin(p, tile);
@@ -734,6 +816,17 @@ __global__ void __launch_bounds__(kTScanThreads) k_tscan_apply(const __grid_cons
     }
 }
 
+// First triangle of every field of a batch (the scan value at its first
+// tile) and the total at index nboxes.
+__global__ void k_box_starts(const uint64_t *off, const int64_t *tile_start, int32_t nboxes, int64_t ntiles,
+                             const uint64_t *total, uint64_t *box_start)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= nboxes; i += gridDim.x * blockDim.x) {
+        const int64_t t = tile_start[i];
+        box_start[i] = (i < nboxes && t < ntiles) ? off[t * kMcIsoPerPass] : *total;
+    }
+}
+
 }  // namespace
 
 static void mc_tiles(const Grid &g, int32_t &ntx, int32_t &ncby, int32_t &ncbz, int64_t &ntiles)
@@ -865,6 +958,8 @@ cudaError_t launch_mc(const float *field, const Grid &g, const float *iso, int n
     p.nx = g.nx;
     p.ny = g.ny;
     p.nz = g.nz;
+    p.sx = g.nx;
+    p.sy = g.nx * g.ny;
     mc_tiles(g, p.ntx, p.ncby, p.ncbz, p.ntiles);
     p.cap = cap;
     p.err = err;
@@ -908,6 +1003,8 @@ cudaError_t launch_mc_adjoint(const float *field, const Grid &g, const float *is
     p.nx = g.nx;
     p.ny = g.ny;
     p.nz = g.nz;
+    p.sx = g.nx;
+    p.sy = g.nx * g.ny;
     mc_tiles(g, p.ntx, p.ncby, p.ncbz, p.ntiles);
     p.cap = cap;
     p.err = nullptr;
@@ -950,6 +1047,113 @@ cudaError_t launch_mc_adjoint(const float *field, const Grid &g, const float *is
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     k_adj_finalize<<<(unsigned)(sms * 8), 256, 0, s>>>(a.acc, a.maxbits, grad_field, g.N);
+    return cudaGetLastError();
+}
+
+// ---- many fields in one launch sequence ------------------------------------
+
+size_t mc_batch_param_bytes() { return sizeof(McParams); }
+
+int64_t mc_tile_count(int64_t nx, int64_t ny, int64_t nz)
+{
+    Grid g = make_grid(chr_dims{nx, ny, nz});
+    int32_t ntx, ncby, ncbz;
+    int64_t ntiles;
+    mc_tiles(g, ntx, ncby, ncbz, ntiles);
+    return ntiles;
+}
+
+size_t mc_batch_scratch_bytes(int64_t ntiles)
+{
+    const int64_t nchunks = (ntiles + kTScanChunk - 1) / kTScanChunk;
+    return ((ntiles * 16 + 255) / 256) * 256 + ((ntiles * 32 + 255) / 256) * 256 + ((nchunks * 32 + 255) / 256) * 256;
+}
+
+bool mc_batch_fill(void *params, void *map, const float *field, int64_t nx, int64_t ny, int64_t nz, int64_t sx,
+                   int64_t sy, float k, float *tris, uint64_t cap, void *scratch, int64_t total_tiles, int64_t tile0,
+                   uint32_t *err)
+{
+    McParams &p = *reinterpret_cast<McParams *>(params);
+    memset(&p, 0, sizeof(p));
+    p.f = field;
+    p.nx = nx;
+    p.ny = ny;
+    p.nz = nz;
+    p.sx = sx;
+    p.sy = sy;
+    mc_tiles(make_grid(chr_dims{nx, ny, nz}), p.ntx, p.ncby, p.ncbz, p.ntiles);
+    p.k[0] = k;
+    p.tris[0] = tris;
+    p.cap = cap;
+    p.err = err;
+    char *b = reinterpret_cast<char *>(scratch);
+    p.tile_cnt = reinterpret_cast<uint4 *>(b) + tile0;
+    p.tile_off = reinterpret_cast<uint64_t *>(b + ((total_tiles * 16 + 255) / 256) * 256) + tile0 * kMcIsoPerPass;
+    p.use_tma = make_field_tensor_map_pitched(reinterpret_cast<CUtensorMap *>(map), field, nx, ny, nz, sx, sy, kBoxX,
+                                              9, 9)
+                    ? 1
+                    : 0;
+    return p.use_tma != 0;
+}
+
+cudaError_t mc_batch_prepare(int &count_per_sm, int &emit_per_sm, int &sms)
+{
+    static int bc = 0, be = 0, ns = 0;
+    if (!ns) {
+        cudaError_t e = cudaFuncSetAttribute(k_mc_emit_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_mc_count_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, kCountSmem);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&ns, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bc, k_mc_count_batched, 256, kCountSmem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&be, k_mc_emit_batched, 256, kEmitSmem);
+        if (bc < 1) bc = 1;
+        if (be < 1) be = 1;
+    }
+    count_per_sm = bc;
+    emit_per_sm = be;
+    sms = ns;
+    return cudaSuccess;
+}
+
+cudaError_t launch_mc_batched(const McBatchLaunch &L, cudaStream_t s)
+{
+    if (L.ntiles == 0) {
+        cudaError_t e = cudaMemsetAsync(L.total, 0, sizeof(uint64_t), s);
+        if (e != cudaSuccess) return e;
+        k_box_starts<<<1, 256, 0, s>>>(nullptr, L.tile_start, L.nboxes, 0, L.total, L.box_start);
+        return cudaGetLastError();
+    }
+    McBatch b;
+    b.boxes = reinterpret_cast<const McParams *>(L.params);
+    b.maps = reinterpret_cast<const CUtensorMap *>(L.maps);
+    b.tile_start = L.tile_start;
+    b.nboxes = L.nboxes;
+    b.ntiles = L.ntiles;
+    char *sc = reinterpret_cast<char *>(L.scratch);
+    const size_t o_off = ((L.ntiles * 16 + 255) / 256) * 256;
+    const size_t o_chunk = o_off + ((L.ntiles * 32 + 255) / 256) * 256;
+    TScanArgs a;
+    a.cnt = reinterpret_cast<const uint4 *>(sc);
+    a.off = reinterpret_cast<uint64_t *>(sc + o_off);
+    a.chunk = reinterpret_cast<Sum4 *>(sc + o_chunk);
+    a.ntiles = L.ntiles;
+    a.nchunks = (L.ntiles + kTScanChunk - 1) / kTScanChunk;
+    a.ntris = L.total;
+    a.niso = 1;
+    a.cap = L.cap;
+    a.err = L.err;
+    const unsigned gc = (unsigned)(L.ntiles < L.count_blocks ? L.ntiles : L.count_blocks);
+    const unsigned ge = (unsigned)(L.ntiles < L.emit_blocks ? L.ntiles : L.emit_blocks);
+    k_mc_count_batched<<<gc, 256, kCountSmem, s>>>(b, L.err);
+    k_tscan_reduce<<<(unsigned)a.nchunks, kTScanThreads, 0, s>>>(a);
+    k_tscan_chunks<<<1, kTScanThreads, 0, s>>>(a);
+    k_tscan_apply<<<(unsigned)a.nchunks, kTScanThreads, 0, s>>>(a);
+    k_mc_emit_batched<<<ge, 256, kEmitSmem, s>>>(b, L.err);
+    k_box_starts<<<(unsigned)((L.nboxes + 256) / 256), 256, 0, s>>>(a.off, L.tile_start, L.nboxes, L.ntiles, L.total,
+                                                                    L.box_start);
     return cudaGetLastError();
 }
 

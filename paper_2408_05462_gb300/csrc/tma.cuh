@@ -14,10 +14,12 @@ namespace chr {
 // the field cannot be described (nx*4 not a multiple of 16, base not 16-byte
 // aligned, or the driver entry point is missing); callers then fall back to
 // plain loads.
-inline bool make_field_tensor_map(CUtensorMap *map, const float *f, int64_t nx, int64_t ny, int64_t nz, uint32_t bx,
-                                  uint32_t by, uint32_t bz)
+// The field may be pitched: row y of plane z starts at f + sx*y + sy*z
+// (sx >= nx, sy >= sx*ny, both multiples of 4 floats).
+inline bool make_field_tensor_map_pitched(CUtensorMap *map, const float *f, int64_t nx, int64_t ny, int64_t nz,
+                                          int64_t sx, int64_t sy, uint32_t bx, uint32_t by, uint32_t bz)
 {
-    if ((nx & 3) != 0 || (reinterpret_cast<uintptr_t>(f) & 15u) != 0) return false;
+    if ((sx & 3) != 0 || (sy & 3) != 0 || (reinterpret_cast<uintptr_t>(f) & 15u) != 0) return false;
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     static bool looked_up = false;
     if (!looked_up) {
@@ -33,13 +35,19 @@ inline bool make_field_tensor_map(CUtensorMap *map, const float *f, int64_t nx, 
     }
     if (!encode) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
-    const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
+    const cuuint64_t strides[2] = {(cuuint64_t)sx * 4, (cuuint64_t)sy * 4};
     const cuuint32_t box[3] = {bx, by, bz};
     const cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(f), dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
+}
+
+inline bool make_field_tensor_map(CUtensorMap *map, const float *f, int64_t nx, int64_t ny, int64_t nz, uint32_t bx,
+                                  uint32_t by, uint32_t bz)
+{
+    return make_field_tensor_map_pitched(map, f, nx, ny, nz, nx, nx * ny, bx, by, bz);
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
