@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--serve-size", type=int, default=1024, help="grid side of the served timesteps")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 256-box batched measurement")
     return ap.parse_args()
 
 
@@ -435,6 +436,11 @@ def main():
                                         "field_GBps": passes * 4.0 * N / (t_ms * 1e-3) / 1e9}
 
     adjoint = None if args.no_adjoint or world > 1 else adjoint_timing()
+    batch = None
+    if not args.no_batched and world == 1:
+        from paper_2408_05462_gb300 import batched
+
+        batch = batched.measure(256, 256, reps=20)
     serving = None if args.no_serve or world > 1 else serve_measurement(args)
 
     peak, peak_kind = measured_peaks()
@@ -478,6 +484,8 @@ def main():
     }
     if adjoint is not None:
         out["adjoint"] = adjoint
+    if batch is not None:
+        out["batched"] = batch
     if serving is not None:
         out["serve"] = serving
     if rank == 0:
