@@ -52,7 +52,16 @@ constexpr int kOffEdge = kOffTri + 256 * CHR_MC_MAX_TRI * 4;     // EdgeVec [12]
 constexpr int kOffCase = kOffEdge + 12 * 32;                     // uint8 [4][2048] case bytes
 constexpr int kOffPre = kOffCase + kMcIsoPerPass * kCells;       // uint16 [2048] per-cell prefix counts
 constexpr int kOffStage = kOffPre + kCells * 2;                  // float [8][32*9+4]
-constexpr int kEmitSmem = kOffStage + 8 * kWarpStage * 4 + 128;  // + alignment slack
+constexpr int kAdjSmem = kOffStage + 8 * kWarpStage * 4 + 128;   // adjoint kernel (+ alignment slack)
+
+// dynamic shared memory of the emit kernel (bytes)
+constexpr int kMaxChunks = kCells * CHR_MC_MAX_TRI / 32;           // 32-triangle chunks per tile and isovalue
+constexpr int kEOffEdge = kOffTri + 256 * CHR_MC_MAX_TRI * 4;      // uint32 [16] packed edge words
+constexpr int kEOffAct = kEOffEdge + 64;                           // uint32 [2048] active cell | case << 11
+constexpr int kEOffAPre = kEOffAct + kCells * 4;                   // uint16 [2048 + 32] first triangle of each active cell
+constexpr int kEOffChunk = kEOffAPre + (kCells + 32) * 2;          // uint16 [320] active cell holding triangle 32q
+constexpr int kEOffStage = ((kEOffChunk + kMaxChunks * 2 + 15) / 16) * 16;  // float [8][32*9+4]
+constexpr int kEmitSmem = kEOffStage + 8 * kWarpStage * 4 + 128;   // + alignment slack
 
 struct McParams {
     const float *f;
@@ -377,6 +386,71 @@ __device__ __forceinline__ void make_triangle(float *dst, const float *box, cons
     }
 }
 
+// Edge e of a cell as one word: bits 0-10 the byte offset of its lower
+// corner in the box, 11-21 the byte step to its upper corner, 22-23 its axis,
+// 24-26 the lower corner's offsets (ox, oy, oz).
+__device__ __forceinline__ uint32_t edge_word(int e)
+{
+    const int axis = e >> 2, m = e & 3;
+    const int ox = (axis == 0) ? 0 : (m & 1);
+    const int oy = (axis == 1) ? 0 : ((axis == 0) ? (m & 1) : (m >> 1));
+    const int oz = (axis == 2) ? 0 : (m >> 1);
+    const int step = (axis == 0) ? 1 : (axis == 1) ? kVX : kPlane;
+    return (uint32_t)(4 * (ox + oy * kVX + oz * kPlane)) | ((uint32_t)(4 * step) << 11) | ((uint32_t)axis << 22) |
+           ((uint32_t)ox << 24) | ((uint32_t)oy << 25) | ((uint32_t)oz << 26);
+}
+
+__device__ __forceinline__ float lds_f32(uint32_t addr)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+    return v;
+}
+
+// Triangle `tri` (three edge numbers, one per byte) of the cell whose lower
+// corner is at shared address cellB and grid position (cx, cy, cz), into
+// dst[0..8].  A crossing sits at the edge's lower corner plus t along its
+// axis; the corner's coordinates are integers, exact in float.
+__device__ __forceinline__ void make_triangle_s(float *dst, uint32_t cellB, const uint32_t *s_edgew, uint32_t tri,
+                                                float k, float cx, float cy, float cz)
+{
+    const float cx1 = cx + 1.0f, cy1 = cy + 1.0f, cz1 = cz + 1.0f;
+#pragma unroll
+    for (int v = 0; v < 3; v++) {
+        const uint32_t E = s_edgew[(tri >> (8 * v)) & 0xffu];
+        const uint32_t a0 = cellB + (E & 0x7ffu);
+        const float f0 = lds_f32(a0), f1 = lds_f32(a0 + ((E >> 11) & 0x7ffu));
+        const float tv = edge_t(k, f0, f1);
+        float x = (E & (1u << 24)) ? cx1 : cx;
+        float y = (E & (1u << 25)) ? cy1 : cy;
+        float z = (E & (1u << 26)) ? cz1 : cz;
+        const uint32_t axis = (E >> 22) & 3u;
+        if (axis == 0) x = __fadd_rn(x, tv);
+        else if (axis == 1) y = __fadd_rn(y, tv);
+        else z = __fadd_rn(z, tv);
+        dst[3 * v + 0] = x;
+        dst[3 * v + 1] = y;
+        dst[3 * v + 2] = z;
+    }
+}
+
+// Bytes of w that are neither 0 nor 0xff (active cells): bit 7 of each byte.
+__device__ __forceinline__ uint32_t active_bytes(uint32_t w)
+{
+    const uint32_t nz = ((w & 0x7f7f7f7fu) + 0x7f7f7f7fu) | w;     // bit 7: byte != 0
+    const uint32_t nw = ~w;
+    const uint32_t nf = ((nw & 0x7f7f7f7fu) + 0x7f7f7f7fu) | nw;   // bit 7: byte != 0xff
+    return nz & nf & 0x80808080u;
+}
+
+// Emit, one isovalue at a time: case bytes of the thread's 8 cells, a block
+// scan of (triangles, active cells), the active cells compacted in cell
+// order with their first triangle, and the first active cell of every
+// 32-triangle chunk noted.  Warps take chunks round-robin; a lane finds its
+// triangle's cell from the chunk's window of 32 active cells (a cell that
+// starts at window position s marks bit s; the lane's cell is the number of
+// marks at or below it), builds the triangle in the warp's staging buffer,
+// and the warp writes the chunk with aligned 16-byte stores.
 template <int NISO, class Src>
 __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
 {
@@ -386,13 +460,14 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
     uint64_t *s_row = reinterpret_cast<uint64_t *>(smem + kOffRow);
     uint8_t *s_cnt = smem + kOffCnt;
     uint32_t *s_tri = reinterpret_cast<uint32_t *>(smem + kOffTri);
-    EdgeVec *s_edge = reinterpret_cast<EdgeVec *>(smem + kOffEdge);
-    uint8_t *s_case = smem + kOffCase;
+    uint32_t *s_edgew = reinterpret_cast<uint32_t *>(smem + kEOffEdge);
+    uint32_t *s_act = reinterpret_cast<uint32_t *>(smem + kEOffAct);
+    uint16_t *s_apre = reinterpret_cast<uint16_t *>(smem + kEOffAPre);
+    uint16_t *s_chunk = reinterpret_cast<uint16_t *>(smem + kEOffChunk);
     __shared__ uint64_t mbar[2];
-    __shared__ uint64_t s_warp[9];
+    __shared__ uint32_t s_w[2][9];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    uint16_t *s_pre = reinterpret_cast<uint16_t *>(smem + kOffPre);  // per-cell triangle prefix of the tile
-    float *s_stage = reinterpret_cast<float *>(smem + kOffStage) + warp * kWarpStage;
+    float *s_stage = reinterpret_cast<float *>(smem + kEOffStage) + warp * kWarpStage;
     s_cnt[tid] = (uint8_t)(g_mc_case[tid] >> 60);
     for (int i = tid; i < 256 * CHR_MC_MAX_TRI; i += 256) {
         const uint64_t word = g_mc_case[i / CHR_MC_MAX_TRI];
@@ -402,7 +477,7 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
             for (int v = 0; v < 3; v++) tri |= (uint32_t)((word >> (12 * t + 4 * v)) & 15u) << (8 * v);
         s_tri[i] = tri;
     }
-    if (tid < 12) s_edge[tid] = edge_vec(tid);
+    if (tid < 12) s_edgew[tid] = edge_word(tid);
 
     tile_loop(src, err, bufs, mbar, [&](int64_t, int64_t tile, const McParams &p, const float *box) {
         row_masks<NISO>(box, s_row, p);
@@ -411,50 +486,49 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
         const int nvalid = valid_cells(p, o);
         const int j = tid >> 6, ly = tid & 7, lz = (tid >> 3) & 7;
         const int r00 = lz * 9 + ly;
-        uint64_t packed = 0;
-#pragma unroll
+        const uint32_t boxB = smem_addr(box);
+        const float fx0 = (float)o.x0, fy0 = (float)o.y0, fz0 = (float)o.z0;
+
+#pragma unroll 1
         for (int i = 0; i < NISO; i++) {
             uint32_t lo, hi;
             cases8(s_row + i * kRows, r00, j, nvalid, lo, hi);
             uint32_t cnt = 0;
 #pragma unroll
             for (int x = 0; x < 4; x++) cnt += s_cnt[(lo >> (8 * x)) & 0xffu] + s_cnt[(hi >> (8 * x)) & 0xffu];
-            *reinterpret_cast<uint2 *>(s_case + i * kCells + tid * 8) = make_uint2(lo, hi);
-            packed |= (uint64_t)cnt << (16 * i);
-        }
-        // block scan of the four 16-bit counts
-        const uint64_t inc = warp_incl_scan_u64(packed, lane);
-        if (lane == 31) s_warp[warp] = inc;
-        __syncthreads();
-        if (warp == 0) {
-            const uint64_t t = (lane < 8) ? s_warp[lane] : 0ull;
-            const uint64_t ti = warp_incl_scan_u64(t, lane);
-            if (lane < 8) s_warp[lane] = ti - t;
-            if (lane == 7) s_warp[8] = ti;
-        }
-        __syncthreads();
-        const uint64_t thread_excl = s_warp[warp] + inc - packed;
-        const uint64_t block_total = s_warp[8];
-        const float fx0 = (float)o.x0, fy0 = (float)o.y0, fz0 = (float)o.z0;
-
-#pragma unroll 1
-        for (int i = 0; i < NISO; i++) {
-            const int n = (int)((block_total >> (16 * i)) & 0xffffull);
+            const uint32_t na = __popc(active_bytes(lo)) + __popc(active_bytes(hi));
+            // block scan of (triangles | active cells << 16); s_w alternates between isovalues
+            const uint32_t packed = cnt | (na << 16);
+            const uint32_t inc = warp_incl_scan_u32(packed, lane);
+            uint32_t *sw = s_w[i & 1];
+            if (lane == 31) sw[warp] = inc;
+            __syncthreads();
+            if (warp == 0) {
+                const uint32_t t = (lane < 8) ? sw[lane] : 0u;
+                const uint32_t ti = warp_incl_scan_u32(t, lane);
+                if (lane < 8) sw[lane] = ti - t;
+                if (lane == 7) sw[8] = ti;
+            }
+            __syncthreads();
+            const uint32_t excl = sw[warp] + inc - packed, total = sw[8];
+            const int n = (int)(total & 0xffffu);
             if (n == 0) continue;  // uniform across the block
-            {   // per-cell exclusive prefix of the tile's triangles, 8 cells per thread in one 16-byte store
-                const uint2 cw = *reinterpret_cast<const uint2 *>(s_case + i * kCells + tid * 8);
-                uint32_t run = (uint32_t)((thread_excl >> (16 * i)) & 0xffffull);
-                uint32_t pk[4];
+            {   // compaction of this thread's active cells, in cell order
+                uint32_t a = excl >> 16, pre = excl & 0xffffu;
 #pragma unroll
-                for (int x = 0; x < 8; x += 2) {
-                    const uint32_t c0 = ((x < 4 ? cw.x : cw.y) >> (8 * (x & 3))) & 0xffu;
-                    const uint32_t c1 = ((x < 4 ? cw.x : cw.y) >> (8 * ((x + 1) & 3))) & 0xffu;
-                    const uint32_t a = run;
-                    run += s_cnt[c0];
-                    pk[x >> 1] = a | (run << 16);
-                    run += s_cnt[c1];
+                for (int x = 0; x < 8; x++) {
+                    const uint32_t cb = ((x < 4 ? lo : hi) >> (8 * (x & 3))) & 0xffu;
+                    const uint32_t c = s_cnt[cb];
+                    if (c) {
+                        s_act[a] = (uint32_t)(tid * 8 + x) | (cb << 11);
+                        s_apre[a] = (uint16_t)pre;
+                        const uint32_t q = (pre + 31u) >> 5;
+                        if ((q << 5) < pre + c) s_chunk[q] = (uint16_t)a;
+                        a++;
+                        pre += c;
+                    }
                 }
-                *reinterpret_cast<uint4 *>(s_pre + tid * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                if (tid < 32) s_apre[(total >> 16) + tid] = 0xffffu;  // window tail past the last active cell
             }
             __syncthreads();
             const uint64_t g0 = __ldg(p.tile_off + tile * kMcIsoPerPass + i);
@@ -462,37 +536,43 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
             // triangles of this tile that fit below cap (the rest are counted, not written)
             const int lim = (g0 >= p.cap) ? 0 : (int)((p.cap - g0) < (uint64_t)n ? (p.cap - g0) : (uint64_t)n);
             float *tout = p.tris[i] + 9ull * g0;
-            const uint8_t *icase = s_case + i * kCells;
-            // 32-triangle chunks dealt round-robin to the warps
-            for (int base = warp * 32; base < lim; base += 8 * 32) {
+            // a chunk is 288 floats, so every chunk of the tile has the same 16-byte phase
+            const int pad = (int)((reinterpret_cast<uintptr_t>(tout) >> 2) & 3u);
+            const int head = (4 - pad) & 3;
+            float *stage = s_stage + pad;
+            for (int q = warp; 32 * q < lim; q += 8) {
+                const int base = 32 * q;
                 const int mm = (lim - base) < 32 ? (lim - base) : 32;
-                float *dst = tout + 9 * base;
-                const int pad = (int)((reinterpret_cast<uintptr_t>(dst) >> 2) & 3u);
+                const int a_lo = s_chunk[q];
+                const int s0 = (int)s_apre[a_lo + lane] - base;
+                const uint32_t mark = (s0 > 0 && s0 < 32) ? (1u << s0) : 0u;
+                const uint32_t starts = __reduce_or_sync(CHR_FULL_MASK, mark);
+                const int jj = __popc(starts & (0xffffffffu >> (31 - lane)));
                 if (lane < mm) {
-                    // the last cell whose prefix is <= m owns triangle m
-                    const int m = base + lane;
-                    int c = 0;
-#pragma unroll
-                    for (int step = 1024; step > 0; step >>= 1)
-                        if ((int)s_pre[c + step] <= m) c += step;
-                    const int t = m - (int)s_pre[c];
-                    const uint32_t tri = s_tri[icase[c] * CHR_MC_MAX_TRI + t];
-                    make_triangle(s_stage + pad + 9 * lane, box, s_edge, tri, c, k, fx0, fy0, fz0);
+                    const int a = a_lo + jj;
+                    const uint32_t e = s_act[a];
+                    const int t = base + lane - (int)s_apre[a];
+                    const uint32_t tri = s_tri[(e >> 11) * CHR_MC_MAX_TRI + t];
+                    const uint32_t c = e & 2047u;
+                    const uint32_t lx = c & 7u, cly = (c >> 3) & 7u, clz = (c >> 6) & 7u, jb = c >> 9;
+                    make_triangle_s(stage + 9 * lane, boxB + 4u * (clz * kPlane + cly * kVX + 8u * jb + lx), s_edgew,
+                                    tri, k, fx0 + (float)(8u * jb + lx), fy0 + (float)cly, fz0 + (float)clz);
                 }
                 __syncwarp();
-                // dst[q] = s_stage[pad + q]; dst + q is 16-byte aligned when (pad + q) % 4 == 0
+                // dst[u] = stage[u]; dst + u is 16-byte aligned when (pad + u) % 4 == 0
+                float *dst = tout + 9 * base;
                 const int F = 9 * mm;
-                const int head = min((4 - pad) & 3, F);
-                if (lane < head) __stcs(dst + lane, s_stage[pad + lane]);
-                const int nbody = (F - head) >> 2;
-                const float4 *src4 = reinterpret_cast<const float4 *>(s_stage + pad + head);
-                float4 *dst4 = reinterpret_cast<float4 *>(dst + head);
-                for (int q = lane; q < nbody; q += 32) __stcs(dst4 + q, src4[q]);
-                const int tail0 = head + 4 * nbody;
-                if (lane < F - tail0) __stcs(dst + tail0 + lane, s_stage[pad + tail0 + lane]);
+                const int h = min(head, F);
+                if (lane < h) __stcs(dst + lane, stage[lane]);
+                const int nbody = (F - h) >> 2;
+                const float4 *src4 = reinterpret_cast<const float4 *>(stage + h);
+                float4 *dst4 = reinterpret_cast<float4 *>(dst + h);
+                for (int u = lane; u < nbody; u += 32) __stcs(dst4 + u, src4[u]);
+                const int tail0 = h + 4 * nbody;
+                if (lane < F - tail0) __stcs(dst + tail0 + lane, stage[tail0 + lane]);
                 __syncwarp();
             }
-            __syncthreads();  // the prefix array is rewritten for the next isovalue
+            __syncthreads();  // the compacted lists are rewritten for the next isovalue
         }
     });
 }
@@ -877,7 +957,7 @@ static cudaError_t mc_prepare(int &grid_count, int &grid_emit)
     if (!ge) {
         cudaError_t e = cudaFuncSetAttribute(k_mc_emit<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_mc_adjoint<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
+        e = cudaFuncSetAttribute(k_mc_adjoint<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAdjSmem);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(k_mc_count<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCountSmem);
         if (e != cudaSuccess) return e;
@@ -945,7 +1025,7 @@ static cudaError_t launch_adjoint_group(const McParams &p, const AdjParams &a, c
     cudaError_t e = mc_prepare<NISO>(grid_count, grid_emit);
     if (e != cudaSuccess) return e;
     const unsigned ge = (unsigned)(p.ntiles < grid_emit ? p.ntiles : grid_emit);
-    k_mc_adjoint<NISO><<<ge, 256, kEmitSmem, s>>>(p, a, map);
+    k_mc_adjoint<NISO><<<ge, 256, kAdjSmem, s>>>(p, a, map);
     return cudaGetLastError();
 }
 
