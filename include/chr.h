@@ -170,11 +170,19 @@ chr_status chr_topo_translate(const float *d_field, chr_dims dims, const float *
                               uint64_t *count_out);
 
 /*
- * isosurface_workspace_size — bytes of device scratch isosurface_extract
- * needs for these dims and number of isovalues (a tile counter and one
- * look-back status word per 8x8x32-cell tile and isovalue).
+ * isosurface_workspace_size — bytes of device scratch for isosurface_extract
+ * with these dims and number of isovalues: per 32x8x8-cell tile its
+ * triangle counts and output offsets, and the counting pass's classification
+ * (12 bytes per 8 cells and isovalue, at most 4 isovalues at a time) that
+ * the emitting pass reads instead of classifying again.  A workspace of at
+ * least the tile arrays alone (48 bytes per tile plus the scan chunks) is
+ * also accepted; the emitting pass then classifies again (slower, same
+ * output).
  */
 size_t isosurface_workspace_size(chr_dims dims, uint32_t n_iso);
+
+/* isosurface_workspace_min_size — the smallest workspace isosurface_extract accepts (the slower layout). */
+size_t isosurface_workspace_min_size(chr_dims dims, uint32_t n_iso);
 
 /*
  * isosurface_extract — marching cubes (Sec. 2.2, Lorensen & Cline) of
@@ -193,8 +201,10 @@ size_t isosurface_workspace_size(chr_dims dims, uint32_t n_iso);
  * receives isovalue j's true triangle count even when it exceeds cap_tris;
  * triangles beyond cap_tris are not written and bit CHR_ERR_OVERFLOW is set in
  * *d_err.  d_err (device uint32) is cleared by the call; may be NULL.
- * d_workspace: at least isosurface_workspace_size() bytes of device scratch,
- * reused by the call (it is cleared on `stream` first).  Asynchronous.
+ * d_workspace: device scratch of workspace_bytes, reused by the call;
+ * isosurface_workspace_size() bytes select the faster layout, a smaller
+ * workspace that still holds the tile arrays the slower one, anything
+ * smaller is CHR_ERR_INVALID.  Asynchronous.
  */
 chr_status isosurface_extract(const float *d_field, chr_dims dims, const float *isovalues, uint32_t n_iso,
                               float *d_tris, uint64_t cap_tris, uint64_t *d_ntris, uint32_t *d_err, void *d_workspace,

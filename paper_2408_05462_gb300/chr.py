@@ -8,7 +8,7 @@ CPU path: if libchr.so is missing or cannot load, every call raises.
 
 Names follow the C ABI: chr_compress, chr_reconstruct, chr_reconstruct_box, chr_brick_range,
 chr_topo_translate,
-isosurface_extract, isosurface_workspace_size, isosurface_extract_noalloc,
+isosurface_extract, isosurface_workspace_size, isosurface_workspace_min_size, isosurface_extract_noalloc,
 isosurface_backward, isosurface_distance_loss, chr_serialize, chr_deserialize,
 chr_stats, chr_free, and the chr_batch_* calls (class Batch).
 """
@@ -100,6 +100,8 @@ def lib():
                                          POINTER(ChrAllocator), c_void_p, POINTER(c_float), POINTER(c_uint64)]
         L.isosurface_workspace_size.restype = c_size_t
         L.isosurface_workspace_size.argtypes = [ChrDims, c_uint32]
+        L.isosurface_workspace_min_size.restype = c_size_t
+        L.isosurface_workspace_min_size.argtypes = [ChrDims, c_uint32]
         L.isosurface_extract.restype = st
         L.isosurface_extract.argtypes = [c_void_p, ChrDims, POINTER(c_float), c_uint32, c_void_p, c_uint64, c_void_p,
                                          c_void_p, c_void_p, c_size_t, c_void_p]
@@ -300,6 +302,12 @@ def isosurface_workspace_size(shape, n_iso: int) -> int:
     return int(lib().isosurface_workspace_size(ChrDims(nx, ny, nz), int(n_iso)))
 
 
+def isosurface_workspace_min_size(shape, n_iso: int) -> int:
+    """Smallest workspace isosurface_extract accepts (chr.h: isosurface_workspace_min_size)."""
+    nz, ny, nx = shape
+    return int(lib().isosurface_workspace_min_size(ChrDims(nx, ny, nz), int(n_iso)))
+
+
 def isosurface_extract(field: torch.Tensor, isovalues, cap: int, tris: torch.Tensor | None = None,
                        counts: torch.Tensor | None = None, err: torch.Tensor | None = None,
                        workspace: torch.Tensor | None = None, stream=None):
@@ -316,9 +324,10 @@ def isosurface_extract(field: torch.Tensor, isovalues, cap: int, tris: torch.Ten
         counts = torch.empty(ni, dtype=torch.int64, device="cuda")
     if err is None:
         err = torch.empty(1, dtype=torch.int32, device="cuda")
-    need = isosurface_workspace_size(field.shape, ni)
-    if workspace is None or workspace.numel() < need:
-        workspace = torch.empty(need, dtype=torch.uint8, device="cuda")
+    if workspace is None:
+        workspace = torch.empty(isosurface_workspace_size(field.shape, ni), dtype=torch.uint8, device="cuda")
+    elif workspace.numel() < isosurface_workspace_min_size(field.shape, ni):
+        raise ValueError("workspace smaller than isosurface_workspace_min_size")
     if tris.numel() < ni * int(cap) * 9:
         raise ValueError("tris too small for n_iso * cap triangles")
     _check(lib().isosurface_extract(field.data_ptr(), _dims(field), iso, ni, tris.data_ptr() if cap > 0 else None,

@@ -432,6 +432,13 @@ size_t isosurface_workspace_size(chr_dims dims, uint32_t n_iso)
     return mc_workspace_bytes(make_grid(dims), (int)n_iso);
 }
 
+size_t isosurface_workspace_min_size(chr_dims dims, uint32_t n_iso)
+{
+    std::string why;
+    if (!dims_ok(dims, why)) return 0;
+    return mc_workspace_min_bytes(make_grid(dims), (int)n_iso);
+}
+
 chr_status isosurface_extract(const float *d_field, chr_dims dims, const float *isovalues, uint32_t n_iso,
                               float *d_tris, uint64_t cap_tris, uint64_t *d_ntris, uint32_t *d_err, void *d_workspace,
                               size_t workspace_bytes, void *stream)
@@ -449,12 +456,13 @@ chr_status isosurface_extract(const float *d_field, chr_dims dims, const float *
         return fail(CHR_ERR_INVALID, "isosurface_extract: misaligned pointer");
     if (cap_tris > (1ull << 58)) return fail(CHR_ERR_INVALID, "isosurface_extract: cap_tris too large");
     const Grid g = make_grid(dims);
-    if (!d_workspace || workspace_bytes < mc_workspace_bytes(g, (int)n_iso))
-        return fail(CHR_ERR_INVALID, "isosurface_extract: workspace smaller than isosurface_workspace_size()");
+    if (!d_workspace || workspace_bytes < mc_workspace_min_bytes(g, (int)n_iso))
+        return fail(CHR_ERR_INVALID, "isosurface_extract: workspace smaller than the minimum (see isosurface_workspace_size)");
     cudaStream_t s = (cudaStream_t)stream;
     CHR_CUDA(cudaMemsetAsync(d_ntris, 0, sizeof(uint64_t) * n_iso, s), "isosurface_extract");
     if (d_err) CHR_CUDA(cudaMemsetAsync(d_err, 0, sizeof(uint32_t), s), "isosurface_extract");
-    CHR_CUDA(launch_mc(d_field, g, isovalues, (int)n_iso, d_tris, cap_tris, d_ntris, d_err, d_workspace, s),
+    CHR_CUDA(launch_mc(d_field, g, isovalues, (int)n_iso, d_tris, cap_tris, d_ntris, d_err, d_workspace,
+                       workspace_bytes, s),
              "isosurface_extract");
     return CHR_OK;
 }

@@ -77,9 +77,13 @@ cudaError_t launch_scan_records(uint4 *const *recs, int nlevels, int64_t nbricks
                                 cudaStream_t s);
 
 // Marching cubes over a plain field.
+// mc_workspace_bytes: the layout in which the count pass keeps its
+// classification for the emit pass; mc_workspace_min_bytes: the smallest
+// workspace accepted (the emit pass then classifies again).
 size_t mc_workspace_bytes(const Grid &g, int n_iso);
+size_t mc_workspace_min_bytes(const Grid &g, int n_iso);
 cudaError_t launch_mc(const float *field, const Grid &g, const float *iso, int n_iso, float *tris, uint64_t cap,
-                      uint64_t *ntris, uint32_t *err, void *workspace, cudaStream_t s);
+                      uint64_t *ntris, uint32_t *err, void *workspace, size_t workspace_bytes, cudaStream_t s);
 
 // Marching cubes of many fields (each with its own isovalue and pitch) in one
 // launch sequence: count over the concatenated tile list, one scan, emit.

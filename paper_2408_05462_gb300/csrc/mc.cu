@@ -76,6 +76,12 @@ struct McParams {
     uint32_t *err;
     uint4 *tile_cnt;     // [ntiles]: triangles per isovalue slot
     uint64_t *tile_off;  // [ntiles][4]: global index of the tile's first triangle
+    // classification kept by the count pass for the emit pass (null: emit
+    // classifies again): per tile, isovalue slot (cstride slots) and thread,
+    // the case bytes of the thread's 8 cells and its triangles | active cells << 16
+    uint2 *cases;
+    uint32_t *tcnt;
+    int32_t cstride;
 };
 
 struct TileXYZ {
@@ -159,6 +165,15 @@ __device__ __forceinline__ void cases8(const uint64_t *R, int r00, int j, int nv
         lo &= (uint32_t)keep;
         hi &= (uint32_t)(keep >> 32);
     }
+}
+
+// Bytes of w that are neither 0 nor 0xff (active cells): bit 7 of each byte.
+__device__ __forceinline__ uint32_t active_bytes(uint32_t w)
+{
+    const uint32_t nz = ((w & 0x7f7f7f7fu) + 0x7f7f7f7fu) | w;     // bit 7: byte != 0
+    const uint32_t nw = ~w;
+    const uint32_t nf = ((nw & 0x7f7f7f7fu) + 0x7f7f7f7fu) | nw;   // bit 7: byte != 0xff
+    return nz & nf & 0x80808080u;
 }
 
 __device__ __forceinline__ int valid_cells(const McParams &p, const TileXYZ &o)
@@ -301,6 +316,12 @@ __device__ __forceinline__ void mc_count_run(const Src &src, uint32_t *err)
             uint32_t c = 0;
 #pragma unroll
             for (int x = 0; x < 4; x++) c += s_cnt[(lo >> (8 * x)) & 0xffu] + s_cnt[(hi >> (8 * x)) & 0xffu];
+            if (p.cases) {
+                const uint32_t na = __popc(active_bytes(lo)) + __popc(active_bytes(hi));
+                const size_t at = ((size_t)tile * p.cstride + i) * 256 + tid;
+                p.cases[at] = make_uint2(lo, hi);
+                p.tcnt[at] = c | (na << 16);
+            }
             c = __reduce_add_sync(CHR_FULL_MASK, c);
             if (lane == 0) s_sum[warp][i] = c;
         }
@@ -434,14 +455,6 @@ __device__ __forceinline__ void make_triangle_s(float *dst, uint32_t cellB, cons
     }
 }
 
-// Bytes of w that are neither 0 nor 0xff (active cells): bit 7 of each byte.
-__device__ __forceinline__ uint32_t active_bytes(uint32_t w)
-{
-    const uint32_t nz = ((w & 0x7f7f7f7fu) + 0x7f7f7f7fu) | w;     // bit 7: byte != 0
-    const uint32_t nw = ~w;
-    const uint32_t nf = ((nw & 0x7f7f7f7fu) + 0x7f7f7f7fu) | nw;   // bit 7: byte != 0xff
-    return nz & nf & 0x80808080u;
-}
 
 // Emit, one isovalue at a time: case bytes of the thread's 8 cells, a block
 // scan of (triangles, active cells), the active cells compacted in cell
@@ -451,7 +464,7 @@ __device__ __forceinline__ uint32_t active_bytes(uint32_t w)
 // starts at window position s marks bit s; the lane's cell is the number of
 // marks at or below it), builds the triangle in the warp's staging buffer,
 // and the warp writes the chunk with aligned 16-byte stores.
-template <int NISO, class Src>
+template <int NISO, bool STORED, class Src>
 __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -480,25 +493,44 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
     if (tid < 12) s_edgew[tid] = edge_word(tid);
 
     tile_loop(src, err, bufs, mbar, [&](int64_t, int64_t tile, const McParams &p, const float *box) {
-        row_masks<NISO>(box, s_row, p);
-        __syncthreads();
+        if (!STORED) {
+            row_masks<NISO>(box, s_row, p);
+            __syncthreads();
+        }
         const TileXYZ o = tile_origin(p, tile);
-        const int nvalid = valid_cells(p, o);
         const int j = tid >> 6, ly = tid & 7, lz = (tid >> 3) & 7;
         const int r00 = lz * 9 + ly;
         const uint32_t boxB = smem_addr(box);
         const float fx0 = (float)o.x0, fy0 = (float)o.y0, fz0 = (float)o.z0;
+        // the count pass's classification, one isovalue ahead
+        const size_t at0 = (size_t)tile * p.cstride * 256 + tid;
+        uint2 cw_next = make_uint2(0u, 0u);
+        uint32_t pk_next = 0;
+        if (STORED) {
+            cw_next = __ldg(p.cases + at0);
+            pk_next = __ldg(p.tcnt + at0);
+        }
 
 #pragma unroll 1
         for (int i = 0; i < NISO; i++) {
-            uint32_t lo, hi;
-            cases8(s_row + i * kRows, r00, j, nvalid, lo, hi);
-            uint32_t cnt = 0;
+            uint32_t lo, hi, packed;
+            if (STORED) {
+                lo = cw_next.x;
+                hi = cw_next.y;
+                packed = pk_next;
+                if (i + 1 < NISO) {
+                    cw_next = __ldg(p.cases + at0 + 256 * (i + 1));
+                    pk_next = __ldg(p.tcnt + at0 + 256 * (i + 1));
+                }
+            } else {
+                cases8(s_row + i * kRows, r00, j, valid_cells(p, o), lo, hi);
+                uint32_t cnt = 0;
 #pragma unroll
-            for (int x = 0; x < 4; x++) cnt += s_cnt[(lo >> (8 * x)) & 0xffu] + s_cnt[(hi >> (8 * x)) & 0xffu];
-            const uint32_t na = __popc(active_bytes(lo)) + __popc(active_bytes(hi));
+                for (int x = 0; x < 4; x++) cnt += s_cnt[(lo >> (8 * x)) & 0xffu] + s_cnt[(hi >> (8 * x)) & 0xffu];
+                const uint32_t na = __popc(active_bytes(lo)) + __popc(active_bytes(hi));
+                packed = cnt | (na << 16);
+            }
             // block scan of (triangles | active cells << 16); s_w alternates between isovalues
-            const uint32_t packed = cnt | (na << 16);
             const uint32_t inc = warp_incl_scan_u32(packed, lane);
             uint32_t *sw = s_w[i & 1];
             if (lane == 31) sw[warp] = inc;
@@ -577,16 +609,16 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
     });
 }
 
-template <int NISO>
+template <int NISO, bool STORED>
 __global__ void __launch_bounds__(256, 4) k_mc_emit(const __grid_constant__ McParams p,
                                                    const __grid_constant__ CUtensorMap map)
 {
-    mc_emit_run<NISO>(SrcOne{&p, &map}, p.err);
+    mc_emit_run<NISO, STORED>(SrcOne{&p, &map}, p.err);
 }
 
 __global__ void __launch_bounds__(256, 4) k_mc_emit_batched(const __grid_constant__ McBatch b, uint32_t *err)
 {
-    mc_emit_run<1>(SrcMany{&b}, err);
+    mc_emit_run<1, true>(SrcMany{&b}, err);
 }
 
 // ---- adjoint of the vertex positions ----------------------------------------
@@ -923,54 +955,83 @@ struct McWorkspace {
     uint64_t *off;
     Sum4 *chunk;
     int64_t nchunks;
+    uint2 *cases;    // null in the compact layout
+    uint32_t *tcnt;
 };
 
-static size_t mc_layout(const Grid &g, void *base, McWorkspace *w)
+static size_t align256(size_t n) { return ((n + 255) / 256) * 256; }
+
+// Scratch of one marching-cubes call: tile counts, offsets and scan chunks,
+// plus (stored layout) the count pass's classification for cstride isovalue
+// slots per tile, 12 bytes per thread and slot.
+static size_t mc_layout(const Grid &g, int cstride, void *base, McWorkspace *w)
 {
     int32_t ntx, ncby, ncbz;
     int64_t ntiles;
     mc_tiles(g, ntx, ncby, ncbz, ntiles);
     const int64_t nchunks = (ntiles + kTScanChunk - 1) / kTScanChunk;
-    const size_t o_cnt = 0, o_off = o_cnt + ((ntiles * 16 + 255) / 256) * 256;
-    const size_t o_chunk = o_off + ((ntiles * 32 + 255) / 256) * 256;
-    const size_t total = o_chunk + ((nchunks * 32 + 255) / 256) * 256;
+    const size_t o_cnt = 0, o_off = o_cnt + align256(ntiles * 16);
+    const size_t o_chunk = o_off + align256(ntiles * 32);
+    const size_t o_cases = o_chunk + align256(nchunks * 32);
+    const size_t o_tcnt = o_cases + align256((size_t)ntiles * cstride * 256 * 8);
+    const size_t total = o_tcnt + align256((size_t)ntiles * cstride * 256 * 4);
     if (w) {
         char *b = reinterpret_cast<char *>(base);
         w->cnt = reinterpret_cast<uint4 *>(b + o_cnt);
         w->off = reinterpret_cast<uint64_t *>(b + o_off);
         w->chunk = reinterpret_cast<Sum4 *>(b + o_chunk);
         w->nchunks = nchunks;
+        w->cases = cstride ? reinterpret_cast<uint2 *>(b + o_cases) : nullptr;
+        w->tcnt = cstride ? reinterpret_cast<uint32_t *>(b + o_tcnt) : nullptr;
     }
     return total;
 }
 
+static int stored_slots(int n_iso) { return n_iso < kMcIsoPerPass ? (n_iso > 0 ? n_iso : 1) : kMcIsoPerPass; }
+
 size_t mc_workspace_bytes(const Grid &g, int n_iso)
 {
-    (void)n_iso;  // groups of 4 isovalues reuse the same scratch in turn
-    return mc_layout(g, nullptr, nullptr);
+    // groups of 4 isovalues reuse the same scratch in turn
+    return mc_layout(g, stored_slots(n_iso), nullptr, nullptr);
 }
 
-template <int NISO>
-static cudaError_t mc_prepare(int &grid_count, int &grid_emit)
+size_t mc_workspace_min_bytes(const Grid &g, int n_iso)
 {
-    static int gc = 0, ge = 0;  // resident blocks per device, computed once per process
-    if (!ge) {
-        cudaError_t e = cudaFuncSetAttribute(k_mc_emit<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
+    (void)n_iso;
+    return mc_layout(g, 0, nullptr, nullptr);
+}
+
+struct McGrids {
+    int count, emit, emit_compact, adjoint;
+};
+
+template <int NISO>
+static cudaError_t mc_prepare(McGrids &out)
+{
+    static McGrids G = {0, 0, 0, 0};  // resident blocks per device, computed once per process
+    if (!G.emit) {
+        cudaError_t e = cudaFuncSetAttribute(k_mc_emit<NISO, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kEmitSmem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_mc_emit<NISO, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(k_mc_adjoint<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAdjSmem);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(k_mc_count<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCountSmem);
         if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, bc = 0, be = 0;
+        int dev = 0, sms = 0, bc = 0, be = 0, bf = 0, ba = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bc, k_mc_count<NISO>, 256, kCountSmem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&be, k_mc_emit<NISO>, 256, kEmitSmem);
-        gc = sms * (bc > 0 ? bc : 1);
-        ge = sms * (be > 0 ? be : 1);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&be, k_mc_emit<NISO, true>, 256, kEmitSmem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_mc_emit<NISO, false>, 256, kEmitSmem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ba, k_mc_adjoint<NISO>, 256, kAdjSmem);
+        G.count = sms * (bc > 0 ? bc : 1);
+        G.emit_compact = sms * (bf > 0 ? bf : 1);
+        G.adjoint = sms * (ba > 0 ? ba : 1);
+        G.emit = sms * (be > 0 ? be : 1);
     }
-    grid_count = gc;
-    grid_emit = ge;
+    out = G;
     return cudaSuccess;
 }
 
@@ -979,10 +1040,10 @@ template <int NISO>
 static cudaError_t launch_count_scan(const McParams &p, const CUtensorMap &map, const McWorkspace &w, uint64_t *ntris,
                                      int niso, cudaStream_t s)
 {
-    int grid_count, grid_emit;
-    cudaError_t e = mc_prepare<NISO>(grid_count, grid_emit);
+    McGrids G;
+    cudaError_t e = mc_prepare<NISO>(G);
     if (e != cudaSuccess) return e;
-    const unsigned gc = (unsigned)(p.ntiles < grid_count ? p.ntiles : grid_count);
+    const unsigned gc = (unsigned)(p.ntiles < G.count ? p.ntiles : G.count);
     k_mc_count<NISO><<<gc, 256, kCountSmem, s>>>(p, map);
     TScanArgs a;
     a.cnt = w.cnt;
@@ -1006,10 +1067,15 @@ static cudaError_t launch_mc_group(const McParams &p, const CUtensorMap &map, co
 {
     cudaError_t e = launch_count_scan<NISO>(p, map, w, ntris, niso, s);
     if (e != cudaSuccess) return e;
-    int grid_count, grid_emit;
-    mc_prepare<NISO>(grid_count, grid_emit);
-    const unsigned ge = (unsigned)(p.ntiles < grid_emit ? p.ntiles : grid_emit);
-    k_mc_emit<NISO><<<ge, 256, kEmitSmem, s>>>(p, map);
+    McGrids G;
+    mc_prepare<NISO>(G);
+    if (p.cases) {
+        const unsigned ge = (unsigned)(p.ntiles < G.emit ? p.ntiles : G.emit);
+        k_mc_emit<NISO, true><<<ge, 256, kEmitSmem, s>>>(p, map);
+    } else {
+        const unsigned ge = (unsigned)(p.ntiles < G.emit_compact ? p.ntiles : G.emit_compact);
+        k_mc_emit<NISO, false><<<ge, 256, kEmitSmem, s>>>(p, map);
+    }
     return cudaGetLastError();
 }
 
@@ -1021,16 +1087,16 @@ static cudaError_t launch_adjoint_group(const McParams &p, const AdjParams &a, c
         cudaError_t e = launch_count_scan<NISO>(p, map, w, ntris, niso, s);
         if (e != cudaSuccess) return e;
     }
-    int grid_count, grid_emit;
-    cudaError_t e = mc_prepare<NISO>(grid_count, grid_emit);
+    McGrids G;
+    cudaError_t e = mc_prepare<NISO>(G);
     if (e != cudaSuccess) return e;
-    const unsigned ge = (unsigned)(p.ntiles < grid_emit ? p.ntiles : grid_emit);
+    const unsigned ge = (unsigned)(p.ntiles < G.adjoint ? p.ntiles : G.adjoint);
     k_mc_adjoint<NISO><<<ge, 256, kAdjSmem, s>>>(p, a, map);
     return cudaGetLastError();
 }
 
 cudaError_t launch_mc(const float *field, const Grid &g, const float *iso, int n_iso, float *tris, uint64_t cap,
-                      uint64_t *ntris, uint32_t *err, void *workspace, cudaStream_t s)
+                      uint64_t *ntris, uint32_t *err, void *workspace, size_t workspace_bytes, cudaStream_t s)
 {
     McParams p;
     memset(&p, 0, sizeof(p));
@@ -1043,10 +1109,15 @@ cudaError_t launch_mc(const float *field, const Grid &g, const float *iso, int n
     mc_tiles(g, p.ntx, p.ncby, p.ncbz, p.ntiles);
     p.cap = cap;
     p.err = err;
+    // the stored layout when the workspace holds it, else the emit pass classifies again
+    const int cstride = (workspace_bytes >= mc_workspace_bytes(g, n_iso)) ? stored_slots(n_iso) : 0;
     McWorkspace w;
-    mc_layout(g, workspace, &w);
+    mc_layout(g, cstride, workspace, &w);
     p.tile_cnt = w.cnt;
     p.tile_off = w.off;
+    p.cases = w.cases;
+    p.tcnt = w.tcnt;
+    p.cstride = cstride;
     CUtensorMap map;
     memset(&map, 0, sizeof(map));
     p.use_tma = make_field_tensor_map(&map, field, g.nx, g.ny, g.nz, kBoxX, 9, 9) ? 1 : 0;
@@ -1070,7 +1141,7 @@ cudaError_t launch_mc(const float *field, const Grid &g, const float *iso, int n
 
 size_t mc_adjoint_workspace_bytes(const Grid &g, int n_iso)
 {
-    const size_t base = ((mc_workspace_bytes(g, n_iso) + 255) / 256) * 256;
+    const size_t base = ((mc_workspace_min_bytes(g, n_iso) + 255) / 256) * 256;
     return base + (size_t)g.N * 8 + 256;
 }
 
@@ -1089,10 +1160,10 @@ cudaError_t launch_mc_adjoint(const float *field, const Grid &g, const float *is
     p.cap = cap;
     p.err = nullptr;
     McWorkspace w;
-    mc_layout(g, workspace, &w);
+    mc_layout(g, 0, workspace, &w);
     p.tile_cnt = w.cnt;
     p.tile_off = w.off;
-    const size_t base = ((mc_workspace_bytes(g, n_iso) + 255) / 256) * 256;
+    const size_t base = ((mc_workspace_min_bytes(g, n_iso) + 255) / 256) * 256;
     AdjParams a;
     memset(&a, 0, sizeof(a));
     a.acc = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(workspace) + base);
@@ -1143,10 +1214,22 @@ int64_t mc_tile_count(int64_t nx, int64_t ny, int64_t nz)
     return ntiles;
 }
 
-size_t mc_batch_scratch_bytes(int64_t ntiles)
+// Batch scratch: tile counts, offsets, scan chunks, then the count pass's
+// classification (one isovalue slot per tile).
+static size_t batch_offsets(int64_t ntiles, size_t &o_off, size_t &o_chunk, size_t &o_cases, size_t &o_tcnt)
 {
     const int64_t nchunks = (ntiles + kTScanChunk - 1) / kTScanChunk;
-    return ((ntiles * 16 + 255) / 256) * 256 + ((ntiles * 32 + 255) / 256) * 256 + ((nchunks * 32 + 255) / 256) * 256;
+    o_off = align256(ntiles * 16);
+    o_chunk = o_off + align256(ntiles * 32);
+    o_cases = o_chunk + align256(nchunks * 32);
+    o_tcnt = o_cases + align256((size_t)ntiles * 256 * 8);
+    return o_tcnt + align256((size_t)ntiles * 256 * 4);
+}
+
+size_t mc_batch_scratch_bytes(int64_t ntiles)
+{
+    size_t a, b, c, d;
+    return batch_offsets(ntiles, a, b, c, d);
 }
 
 bool mc_batch_fill(void *params, void *map, const float *field, int64_t nx, int64_t ny, int64_t nz, int64_t sx,
@@ -1167,8 +1250,13 @@ bool mc_batch_fill(void *params, void *map, const float *field, int64_t nx, int6
     p.cap = cap;
     p.err = err;
     char *b = reinterpret_cast<char *>(scratch);
+    size_t o_off, o_chunk, o_cases, o_tcnt;
+    batch_offsets(total_tiles, o_off, o_chunk, o_cases, o_tcnt);
     p.tile_cnt = reinterpret_cast<uint4 *>(b) + tile0;
-    p.tile_off = reinterpret_cast<uint64_t *>(b + ((total_tiles * 16 + 255) / 256) * 256) + tile0 * kMcIsoPerPass;
+    p.tile_off = reinterpret_cast<uint64_t *>(b + o_off) + tile0 * kMcIsoPerPass;
+    p.cases = reinterpret_cast<uint2 *>(b + o_cases) + tile0 * 256;
+    p.tcnt = reinterpret_cast<uint32_t *>(b + o_tcnt) + tile0 * 256;
+    p.cstride = 1;
     p.use_tma = make_field_tensor_map_pitched(reinterpret_cast<CUtensorMap *>(map), field, nx, ny, nz, sx, sy, kBoxX,
                                               9, 9)
                     ? 1
@@ -1213,8 +1301,8 @@ cudaError_t launch_mc_batched(const McBatchLaunch &L, cudaStream_t s)
     b.nboxes = L.nboxes;
     b.ntiles = L.ntiles;
     char *sc = reinterpret_cast<char *>(L.scratch);
-    const size_t o_off = ((L.ntiles * 16 + 255) / 256) * 256;
-    const size_t o_chunk = o_off + ((L.ntiles * 32 + 255) / 256) * 256;
+    size_t o_off, o_chunk, o_cases, o_tcnt;
+    batch_offsets(L.ntiles, o_off, o_chunk, o_cases, o_tcnt);
     TScanArgs a;
     a.cnt = reinterpret_cast<const uint4 *>(sc);
     a.off = reinterpret_cast<uint64_t *>(sc + o_off);

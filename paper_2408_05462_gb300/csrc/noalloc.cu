@@ -63,7 +63,7 @@ extern "C" chr_status isosurface_extract_noalloc(const float *d_field, chr_dims 
 {
     if (dims.nx >= 2 && dims.ny >= 2 && dims.nz >= 2 && dims.nx < (1ll << 31) && dims.ny < (1ll << 31) &&
         dims.nz < (1ll << 31) && (double)dims.nx * (double)dims.ny * (double)dims.nz < 4294967295.0) {
-        const size_t need = mc_workspace_bytes(make_grid(dims), (int)n_iso);
+        const size_t need = mc_workspace_min_bytes(make_grid(dims), (int)n_iso);
         if (need > kNoallocScratchBytes) {
             set_error("isosurface_extract_noalloc: grid needs " + std::to_string(need) +
                       " bytes of scratch, more than the fixed " + std::to_string(kNoallocScratchBytes) +

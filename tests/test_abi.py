@@ -79,10 +79,11 @@ def test_other_calls_reject_bad_arguments(L):
     assert L.chr_reconstruct(None, 0, ctypes.c_void_p(0x1000), None) == 1
     assert L.isosurface_extract(None, d, iso, 1, None, 0, None, None, None, 0, None) == 1
     ws = L.isosurface_workspace_size(d, 1)
-    assert ws > 0
+    ws_min = L.isosurface_workspace_min_size(d, 1)
+    assert 0 < ws_min < ws
     # too small a workspace, zero or too many isovalues, non-finite isovalue
     p = ctypes.c_void_p(0x1000)
-    assert L.isosurface_extract(p, d, iso, 1, p, 10, p, None, p, ws - 1, None) == 1
+    assert L.isosurface_extract(p, d, iso, 1, p, 10, p, None, p, ws_min - 1, None) == 1
     assert L.isosurface_extract(p, d, iso, 0, p, 10, p, None, p, ws, None) == 1
     assert L.isosurface_extract(p, d, iso, 17, p, 10, p, None, p, ws, None) == 1
     bad = (ctypes.c_float * 1)(float("inf"))

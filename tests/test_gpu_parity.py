@@ -102,6 +102,25 @@ def test_mc_overflow_reports_true_count_and_stays_in_bounds():
     assert np.array_equal(tris.cpu().numpy()[0], full[0, :cap])
 
 
+@pytest.mark.parametrize("isos", [[0.3], [-1.0, 0.5], [-1.0, -0.5, 0.5, 1.0], [-1.2, -0.6, 0.0, 0.2, 0.7, 1.1]])
+def test_mc_workspace_layouts_agree(isos):
+    # the stored-classification layout (full workspace) and the compact one
+    # (minimum workspace: the emit pass classifies again) give the same bits
+    f = synth.turbulence((70, 45, 33), seed=12)
+    fd = _dev(f)
+    cap = 5 * 69 * 44 * 32
+    full = torch.empty(chr.isosurface_workspace_size(f.shape, len(isos)), dtype=torch.uint8, device="cuda")
+    small = torch.empty(chr.isosurface_workspace_min_size(f.shape, len(isos)), dtype=torch.uint8, device="cuda")
+    assert small.numel() < full.numel()
+    t1, c1, e1 = chr.isosurface_extract(fd, isos, cap, workspace=full)
+    t2, c2, e2 = chr.isosurface_extract(fd, isos, cap, workspace=small)
+    torch.cuda.synchronize()
+    assert torch.equal(c1, c2) and int(e1.item()) == 0 and int(e2.item()) == 0
+    for j in range(len(isos)):
+        n = int(c1[j])
+        assert torch.equal(t1[j, :n].view(torch.int32), t2[j, :n].view(torch.int32)), j
+
+
 def _compare_codec(h, enc, f, label):
     parsed = chr.parse_serialized(chr.chr_serialize(h))
     assert parsed["nlevels"] == enc.nlevels
