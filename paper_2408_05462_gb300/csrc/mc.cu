@@ -580,6 +580,8 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
                 const uint32_t mark = (s0 > 0 && s0 < 32) ? (1u << s0) : 0u;
                 const uint32_t starts = __reduce_or_sync(CHR_FULL_MASK, mark);
                 const int jj = __popc(starts & (0xffffffffu >> (31 - lane)));
+                if (lane == 0) bulk_wait_read_all();  // the previous chunk's bulk store has read the staging buffer
+                __syncwarp();
                 if (lane < mm) {
                     const int a = a_lo + jj;
                     const uint32_t e = s_act[a];
@@ -590,23 +592,26 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
                     make_triangle_s(stage + 9 * lane, boxB + 4u * (clz * kPlane + cly * kVX + 8u * jb + lx), s_edgew,
                                     tri, k, fx0 + (float)(8u * jb + lx), fy0 + (float)cly, fz0 + (float)clz);
                 }
+                fence_proxy_async_smem();
                 __syncwarp();
-                // dst[u] = stage[u]; dst + u is 16-byte aligned when (pad + u) % 4 == 0
+                // dst[u] = stage[u]; dst + u and stage + u are 16-byte aligned when (pad + u) % 4 == 0: the
+                // aligned middle goes out as one bulk store, the ragged ends as plain stores
                 float *dst = tout + 9 * base;
                 const int F = 9 * mm;
                 const int h = min(head, F);
                 if (lane < h) __stcs(dst + lane, stage[lane]);
-                const int nbody = (F - h) >> 2;
-                const float4 *src4 = reinterpret_cast<const float4 *>(stage + h);
-                float4 *dst4 = reinterpret_cast<float4 *>(dst + h);
-                for (int u = lane; u < nbody; u += 32) __stcs(dst4 + u, src4[u]);
-                const int tail0 = h + 4 * nbody;
+                const int nb16 = (F - h) >> 2;
+                if (lane == 0 && nb16 > 0) {
+                    bulk_store(dst + h, stage + h, (uint32_t)nb16 * 16u);
+                    bulk_commit();
+                }
+                const int tail0 = h + 4 * nb16;
                 if (lane < F - tail0) __stcs(dst + tail0 + lane, stage[tail0 + lane]);
-                __syncwarp();
             }
             __syncthreads();  // the compacted lists are rewritten for the next isovalue
         }
     });
+    if (lane == 0) bulk_wait_all();  // shared memory stays valid until every bulk store is done
 }
 
 template <int NISO, bool STORED>
