@@ -21,6 +21,8 @@
 // (y, z) = (t&7, (t>>3)&7), so thread order is output order.
 #include <string.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "internal.h"
 #include "mc_table.h"
@@ -56,7 +58,7 @@ constexpr int kAdjSmem = kOffStage + 8 * kWarpStage * 4 + 128;   // adjoint kern
 
 // dynamic shared memory of the emit kernel (bytes)
 constexpr int kMaxChunks = kCells * CHR_MC_MAX_TRI / 32;           // 32-triangle chunks per tile and isovalue
-constexpr int kEOffEdge = kOffTri + 256 * CHR_MC_MAX_TRI * 4;      // uint32 [16] packed edge words
+constexpr int kEOffEdge = kOffTri + 256 * CHR_MC_MAX_TRI * 4;      // uint32 [16] edge words
 constexpr int kEOffAct = kEOffEdge + 64;                           // uint32 [2048] active cell | case << 11
 constexpr int kEOffAPre = kEOffAct + kCells * 4;                   // uint16 [2048 + 32] first triangle of each active cell
 constexpr int kEOffChunk = kEOffAPre + (kCells + 32) * 2;          // uint16 [320] active cell holding triangle 32q
@@ -407,9 +409,9 @@ __device__ __forceinline__ void make_triangle(float *dst, const float *box, cons
     }
 }
 
-// Edge e of a cell as one word: bits 0-10 the byte offset of its lower
-// corner in the box, 11-21 the byte step to its upper corner, 22-23 its axis,
-// 24-26 the lower corner's offsets (ox, oy, oz).
+// Edge e of a cell as one word for the emit pass: bits 0-10 the byte offset
+// of its lower corner in the box, 11-21 the byte step to its upper corner,
+// 24-26 the lower corner's offsets (ox, oy, oz), 27-29 its axis, one-hot.
 __device__ __forceinline__ uint32_t edge_word(int e)
 {
     const int axis = e >> 2, m = e & 3;
@@ -417,8 +419,8 @@ __device__ __forceinline__ uint32_t edge_word(int e)
     const int oy = (axis == 1) ? 0 : ((axis == 0) ? (m & 1) : (m >> 1));
     const int oz = (axis == 2) ? 0 : (m >> 1);
     const int step = (axis == 0) ? 1 : (axis == 1) ? kVX : kPlane;
-    return (uint32_t)(4 * (ox + oy * kVX + oz * kPlane)) | ((uint32_t)(4 * step) << 11) | ((uint32_t)axis << 22) |
-           ((uint32_t)ox << 24) | ((uint32_t)oy << 25) | ((uint32_t)oz << 26);
+    return (uint32_t)(4 * (ox + oy * kVX + oz * kPlane)) | ((uint32_t)(4 * step) << 11) | ((uint32_t)ox << 24) |
+           ((uint32_t)oy << 25) | ((uint32_t)oz << 26) | (1u << (27 + axis));
 }
 
 __device__ __forceinline__ float lds_f32(uint32_t addr)
@@ -431,8 +433,11 @@ __device__ __forceinline__ float lds_f32(uint32_t addr)
 // Triangle `tri` (three edge numbers, one per byte) of the cell whose lower
 // corner is at shared address cellB and grid position (cx, cy, cz), into
 // dst[0..8].  A crossing sits at the edge's lower corner plus t along its
-// axis; the corner's coordinates are integers, exact in float.
-__device__ __forceinline__ void make_triangle_s(float *dst, uint32_t cellB, const uint32_t *s_edgew, uint32_t tri,
+// axis; the corner's coordinates are integers, exact in float.  FAST: every
+// value of the tile's box is below 2^125 in magnitude, so |f1 - f0| < 2^126
+// and the fast quotient applies everywhere.
+template <bool FAST>
+__device__ __forceinline__ void make_triangle_w(float *dst, uint32_t cellB, const uint32_t *s_edgew, uint32_t tri,
                                                 float k, float cx, float cy, float cz)
 {
     const float cx1 = cx + 1.0f, cy1 = cy + 1.0f, cz1 = cz + 1.0f;
@@ -441,20 +446,18 @@ __device__ __forceinline__ void make_triangle_s(float *dst, uint32_t cellB, cons
         const uint32_t E = s_edgew[(tri >> (8 * v)) & 0xffu];
         const uint32_t a0 = cellB + (E & 0x7ffu);
         const float f0 = lds_f32(a0), f1 = lds_f32(a0 + ((E >> 11) & 0x7ffu));
-        const float tv = edge_t(k, f0, f1);
+        const float tv = FAST ? __fdividef(__fsub_rn(k, f0), __fsub_rn(f1, f0)) : edge_t(k, f0, f1);
         float x = (E & (1u << 24)) ? cx1 : cx;
         float y = (E & (1u << 25)) ? cy1 : cy;
         float z = (E & (1u << 26)) ? cz1 : cz;
-        const uint32_t axis = (E >> 22) & 3u;
-        if (axis == 0) x = __fadd_rn(x, tv);
-        else if (axis == 1) y = __fadd_rn(y, tv);
-        else z = __fadd_rn(z, tv);
+        if (E & (1u << 27)) x = __fadd_rn(x, tv);
+        if (E & (1u << 28)) y = __fadd_rn(y, tv);
+        if (E & (1u << 29)) z = __fadd_rn(z, tv);
         dst[3 * v + 0] = x;
         dst[3 * v + 1] = y;
         dst[3 * v + 2] = z;
     }
 }
-
 
 // Emit, one isovalue at a time: case bytes of the thread's 8 cells, a block
 // scan of (triangles, active cells), the active cells compacted in cell
@@ -493,6 +496,13 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
     if (tid < 12) s_edgew[tid] = edge_word(tid);
 
     tile_loop(src, err, bufs, mbar, [&](int64_t, int64_t tile, const McParams &p, const float *box) {
+        // fast quotients unless some value of the box is 2^125 or more in magnitude (or infinite)
+        bool huge = false;
+        for (int u = tid; u < kRows * kVX / 4; u += 256) {
+            const float4 v = reinterpret_cast<const float4 *>(box)[u];
+            huge |= fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))) >= 4.2535296e37f;
+        }
+        const bool fast = !__syncthreads_or(huge);
         if (!STORED) {
             row_masks<NISO>(box, s_row, p);
             __syncthreads();
@@ -572,42 +582,50 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
             const int pad = (int)((reinterpret_cast<uintptr_t>(tout) >> 2) & 3u);
             const int head = (4 - pad) & 3;
             float *stage = s_stage + pad;
-            for (int q = warp; 32 * q < lim; q += 8) {
-                const int base = 32 * q;
-                const int mm = (lim - base) < 32 ? (lim - base) : 32;
-                const int a_lo = s_chunk[q];
-                const int s0 = (int)s_apre[a_lo + lane] - base;
-                const uint32_t mark = (s0 > 0 && s0 < 32) ? (1u << s0) : 0u;
-                const uint32_t starts = __reduce_or_sync(CHR_FULL_MASK, mark);
-                const int jj = __popc(starts & (0xffffffffu >> (31 - lane)));
-                if (lane == 0) bulk_wait_read_all();  // the previous chunk's bulk store has read the staging buffer
-                __syncwarp();
-                if (lane < mm) {
-                    const int a = a_lo + jj;
-                    const uint32_t e = s_act[a];
-                    const int t = base + lane - (int)s_apre[a];
-                    const uint32_t tri = s_tri[(e >> 11) * CHR_MC_MAX_TRI + t];
-                    const uint32_t c = e & 2047u;
-                    const uint32_t lx = c & 7u, cly = (c >> 3) & 7u, clz = (c >> 6) & 7u, jb = c >> 9;
-                    make_triangle_s(stage + 9 * lane, boxB + 4u * (clz * kPlane + cly * kVX + 8u * jb + lx), s_edgew,
-                                    tri, k, fx0 + (float)(8u * jb + lx), fy0 + (float)cly, fz0 + (float)clz);
+            auto chunks = [&](auto fast_tag) {
+                constexpr bool FAST = decltype(fast_tag)::value;
+                for (int q = warp; 32 * q < lim; q += 8) {
+                    const int base = 32 * q;
+                    const int mm = (lim - base) < 32 ? (lim - base) : 32;
+                    const int a_lo = s_chunk[q];
+                    const int s0 = (int)s_apre[a_lo + lane] - base;
+                    const uint32_t mark = (s0 > 0 && s0 < 32) ? (1u << s0) : 0u;
+                    const uint32_t starts = __reduce_or_sync(CHR_FULL_MASK, mark);
+                    const int jj = __popc(starts & (0xffffffffu >> (31 - lane)));
+                    if (lane == 0) bulk_wait_read_all();  // the previous chunk's bulk store has read the staging buffer
+                    __syncwarp();
+                    if (lane < mm) {
+                        const int a = a_lo + jj;
+                        const uint32_t e = s_act[a];
+                        const int t = base + lane - (int)s_apre[a];
+                        const uint32_t tri = s_tri[(e >> 11) * CHR_MC_MAX_TRI + t];
+                        const uint32_t c = e & 2047u;
+                        const uint32_t lx = c & 7u, cly = (c >> 3) & 7u, clz = (c >> 6) & 7u, jb = c >> 9;
+                        make_triangle_w<FAST>(stage + 9 * lane, boxB + 4u * (clz * kPlane + cly * kVX + 8u * jb + lx),
+                                              s_edgew, tri, k, fx0 + (float)(8u * jb + lx), fy0 + (float)cly,
+                                              fz0 + (float)clz);
+                    }
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    // dst[u] = stage[u]; dst + u and stage + u are 16-byte aligned when (pad + u) % 4 == 0: the
+                    // aligned middle goes out as one bulk store, the ragged ends as plain stores
+                    float *dst = tout + 9 * base;
+                    const int F = 9 * mm;
+                    const int h = min(head, F);
+                    if (lane < h) __stcs(dst + lane, stage[lane]);
+                    const int nb16 = (F - h) >> 2;
+                    if (lane == 0 && nb16 > 0) {
+                        bulk_store(dst + h, stage + h, (uint32_t)nb16 * 16u);
+                        bulk_commit();
+                    }
+                    const int tail0 = h + 4 * nb16;
+                    if (lane < F - tail0) __stcs(dst + tail0 + lane, stage[tail0 + lane]);
                 }
-                fence_proxy_async_smem();
-                __syncwarp();
-                // dst[u] = stage[u]; dst + u and stage + u are 16-byte aligned when (pad + u) % 4 == 0: the
-                // aligned middle goes out as one bulk store, the ragged ends as plain stores
-                float *dst = tout + 9 * base;
-                const int F = 9 * mm;
-                const int h = min(head, F);
-                if (lane < h) __stcs(dst + lane, stage[lane]);
-                const int nb16 = (F - h) >> 2;
-                if (lane == 0 && nb16 > 0) {
-                    bulk_store(dst + h, stage + h, (uint32_t)nb16 * 16u);
-                    bulk_commit();
-                }
-                const int tail0 = h + 4 * nb16;
-                if (lane < F - tail0) __stcs(dst + tail0 + lane, stage[tail0 + lane]);
-            }
+            };
+            if (fast)
+                chunks(std::true_type{});
+            else
+                chunks(std::false_type{});
             __syncthreads();  // the compacted lists are rewritten for the next isovalue
         }
     });
