@@ -123,19 +123,25 @@ __device__ __forceinline__ void issue_box(float *buf, const CUtensorMap *map, ui
 }
 
 // Inside masks (v < k) of the box rows: bit x of s_row[i*81 + row], x < 33.
+// Lane i (i < NISO) keeps isovalue i's ballot and writes its row mask.
 template <int NISO>
 __device__ __forceinline__ void row_masks(const float *buf, uint64_t *s_row, const McParams &p)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float k[NISO];
+#pragma unroll
+    for (int i = 0; i < NISO; i++) k[i] = p.k[i];
+    const float kl = p.k[lane < NISO ? lane : 0];
     for (int row = warp; row < kRows; row += 8) {
         const float v = buf[row * kVX + lane];
         const float vh = buf[row * kVX + kTX];
+        uint32_t mine = 0;
 #pragma unroll
         for (int i = 0; i < NISO; i++) {
-            const float k = p.k[i];
-            const uint32_t lo = __ballot_sync(CHR_FULL_MASK, v < k);
-            if (lane == 0) s_row[i * kRows + row] = (uint64_t)lo | ((uint64_t)(vh < k) << 32);
+            const uint32_t b = __ballot_sync(CHR_FULL_MASK, v < k[i]);
+            mine = (lane == i) ? b : mine;
         }
+        if (lane < NISO) s_row[lane * kRows + row] = (uint64_t)mine | ((uint64_t)(vh < kl) << 32);
     }
 }
 
