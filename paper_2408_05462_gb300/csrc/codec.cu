@@ -46,8 +46,12 @@ __device__ __forceinline__ int count_above(float v, const float *K, int nK)
 // levels; Sec. 2.2 sign preservation).  Every float operation is one IEEE
 // binary32 operation rounded to nearest-even.  Returns true for a vertex
 // stored exactly (bound or sign check failed, or not quantisable).
+// The sign check compares the count of candidates above R with f's count cf.
+// Both counts agree exactly when kdn <= R < kup, kup the smallest candidate
+// above f (+inf if none) and kdn the largest at or below it (-inf if none):
+// the same test without a second count.
 __device__ __forceinline__ bool encode_step(float f, float Rprev, bool first, float e, float two_e, float inv2e,
-                                            const float *K, int nK, bool fix, int cf, int32_t &q, float &R)
+                                            bool fix, float kdn, float kup, int32_t &q, float &R)
 {
     const float r = first ? f : __fsub_rn(f, Rprev);
     const float x = __fmul_rn(r, inv2e);
@@ -58,7 +62,7 @@ __device__ __forceinline__ bool encode_step(float f, float Rprev, bool first, fl
     const float P = __fmul_rn(__int2float_rn(qi), two_e);
     const float Rn = first ? P : __fadd_rn(Rprev, P);
     if (!(fabsf(__fsub_rn(f, Rn)) < e)) return true;
-    if (fix && count_above(Rn, K, nK) != cf) return true;
+    if (fix && !(Rn >= kdn && Rn < kup)) return true;
     q = qi;
     R = Rn;
     return false;
@@ -76,9 +80,10 @@ constexpr int kEncBricks = 4;  // bricks per block
 template <bool FULL>
 __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ CodecParams p)
 {
-    __shared__ __align__(16) uint32_t s_zz[kEncBricks][512];
     __shared__ __align__(16) int32_t s_zrow[kEncBricks][8][8];  // z = 3 rows after the x and y differences
     __shared__ uint32_t s_red[kEncBricks][2][4];                // per warp: max L, max plain, exceptions, -
+    __shared__ __align__(16) uint32_t s_pk[kEncBricks][512];    // packed words of each brick (zero between levels)
+    __shared__ float s_kup[CHR_MAX_ISO + 1], s_kdn[CHR_MAX_ISO + 1];  // by count of candidates above f
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int j = tid >> 6, r = tid & 63, wb = r >> 5;
@@ -96,6 +101,22 @@ __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ Codec
         const bool full = ((int64_t)c.bx * 8 + 8 <= p.nx) && ((int64_t)c.by * 8 + 8 <= p.ny) && ((int64_t)c.bz * 8 + 8 <= p.nz);
         mine = (full == FULL);
     }
+    if (tid == 0 && p.fix) {
+        float ks[CHR_MAX_ISO];
+        const int nK = p.nK;
+        for (int a = 0; a < nK; a++) {  // insertion sort of the candidate isovalues
+            float v = p.K[a];
+            int b = a;
+            for (; b > 0 && ks[b - 1] > v; b--) ks[b] = ks[b - 1];
+            ks[b] = v;
+        }
+        for (int cnt = 0; cnt <= nK; cnt++) {
+            s_kup[cnt] = (cnt > 0) ? ks[nK - cnt] : __int_as_float(0x7f800000);
+            s_kdn[cnt] = (cnt < nK) ? ks[nK - cnt - 1] : __int_as_float(0xff800000);
+        }
+    }
+    *reinterpret_cast<uint4 *>(&s_pk[j][8 * r]) = make_uint4(0u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4 *>(&s_pk[j][8 * r + 4]) = make_uint4(0u, 0u, 0u, 0u);
     if (!__syncthreads_or(mine)) return;  // uniform: no brick of this block is ours
 
     // load this thread's row
@@ -144,8 +165,9 @@ __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ Codec
             if ((valid >> x) & 1u) {
                 float Rn;
                 int32_t qq;
-                const bool ex = encode_step(f[x], R[x], l == 0, e, two_e, inv2e, p.K, p.nK, fix,
-                                            (int)((cfp[x >> 2] >> (8 * (x & 3))) & 0xffu), qq, Rn);
+                const int cf = (int)((cfp[x >> 2] >> (8 * (x & 3))) & 0xffu);
+                const bool ex = encode_step(f[x], R[x], l == 0, e, two_e, inv2e, fix, fix ? s_kdn[cf] : 0.0f,
+                                            fix ? s_kup[cf] : 0.0f, qq, Rn);
                 q[x] = qq;
                 R[x] = Rn;
                 if (ex) excm |= 1u << x;
@@ -206,33 +228,38 @@ __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ Codec
         if (mine && r == 0)
             p.recs[l][c.b] = make_uint4(0u, 0u, (uint32_t)q[0], (uint32_t)w | ((uint32_t)mode << 8) | (nexc << 16));
 
-        // pack: every row's zig-zag codes into shared memory, then 16*w words
-        uint32_t *zb = s_zz[j];
+        // pack: row r's 8 codes are bits [8*r*w, 8*r*w + 8*w) of the brick's
+        // stream; each thread ORs its bits into the zeroed shared words, then
+        // the brick's 16*w words are copied out (and zeroed for the next level)
         {
-            uint32_t zz[8];
+            const uint32_t bit0 = 8u * (uint32_t)r * (uint32_t)w;
+            uint32_t wi = bit0 >> 5;
+            int pos = (int)(bit0 & 31u);
+            uint64_t acc = 0;
+            if (w > 0) {
 #pragma unroll
-            for (int x = 0; x < 8; x++) {
-                const bool live = ((valid >> x) & 1u) && !(r == 0 && x == 0);
-                zz[x] = mode ? zigzag(d[x]) : (live ? zigzag(q[x]) : 0u);
+                for (int x = 0; x < 8; x++) {
+                    const bool live = ((valid >> x) & 1u) && !(r == 0 && x == 0);
+                    const uint32_t zz = mode ? zigzag(d[x]) : (live ? zigzag(q[x]) : 0u);
+                    acc |= (uint64_t)zz << pos;
+                    pos += w;
+                    if (pos >= 32) {
+                        if ((uint32_t)acc) atomicOr(&s_pk[j][wi], (uint32_t)acc);
+                        acc >>= 32;
+                        pos -= 32;
+                        wi++;
+                    }
+                }
+                if (pos > 0 && (uint32_t)acc) atomicOr(&s_pk[j][wi], (uint32_t)acc);
             }
-            *reinterpret_cast<uint4 *>(zb + 8 * r) = make_uint4(zz[0], zz[1], zz[2], zz[3]);
-            *reinterpret_cast<uint4 *>(zb + 8 * r + 4) = make_uint4(zz[4], zz[5], zz[6], zz[7]);
         }
         __syncthreads();
-        if (mine && w > 0) {
+        {
             uint32_t *dst = p.slot_words[l] + 512ull * c.b;
             const int nw = 16 * w;
             for (int jw = r; jw < nw; jw += 64) {
-                const int bit0 = 32 * jw;
-                const int s0 = bit0 / w;
-                const int s1 = min(511, (bit0 + 31) / w);
-                uint32_t word = 0;
-                for (int s = s0; s <= s1; s++) {
-                    const int pos = s * w - bit0;
-                    const uint32_t v = zb[s];
-                    word |= (pos >= 0) ? (v << pos) : (v >> (-pos));
-                }
-                dst[jw] = word;
+                if (mine) dst[jw] = s_pk[j][jw];
+                s_pk[j][jw] = 0u;
             }
         }
         if (mine && cnt) {
@@ -246,7 +273,7 @@ __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ Codec
                 }
             }
         }
-        __syncthreads();  // s_zz, s_zrow and s_red are reused by the next level
+        __syncthreads();  // s_pk, s_zrow and s_red are reused by the next level
     }
 }
 
