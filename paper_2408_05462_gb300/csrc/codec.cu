@@ -318,7 +318,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // memory round trips instead of three per level.
 __device__ __forceinline__ void decode_brick(const CodecParams &p, const BrickCoord &c, uint32_t *s_dyn);
 
-__global__ void __launch_bounds__(256) k_decode(const __grid_constant__ CodecParams p)
+__global__ void __launch_bounds__(256, 4) k_decode(const __grid_constant__ CodecParams p)
 {
     extern __shared__ __align__(16) uint32_t s_dyn[];
     BrickCoord c;
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(256) k_decode(const __grid_constant__ CodecPar
 // Many CHRs in one launch: warp w of the grid decodes brick w of the
 // concatenated brick list (box i owns bricks brick_start[i] ..
 // brick_start[i+1]-1, x fastest), so small boxes leave no warp idle.
-__global__ void __launch_bounds__(256) k_decode_batched(const CodecParams *__restrict__ descs,
+__global__ void __launch_bounds__(256, 4) k_decode_batched(const CodecParams *__restrict__ descs,
                                                         const int64_t *__restrict__ brick_start, int32_t nboxes)
 {
     extern __shared__ __align__(16) uint32_t s_dyn[];
