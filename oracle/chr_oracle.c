@@ -66,7 +66,9 @@ int64_t orc_nbricks(int64_t nx, int64_t ny, int64_t nz)
  * reconstruction R is checked strictly against the bound (|f - R| < e), and
  * with the topology fix on, against every candidate isovalue k: the inside
  * bit (v < k) of R must equal that of f (Sec. 2.2).  A vertex that fails any
- * check becomes an exception: code 0, and R takes f exactly.
+ * check becomes an exception: R takes f exactly, and the code keeps the
+ * rounded value when there is one (0 when r cannot be quantised), so the
+ * prediction of its neighbours is not disturbed.
  * Returns 1 for an exception.
  */
 static int level_step(float f, float Rprev, int lvl, float e, float two_e, float inv2e,
@@ -95,10 +97,7 @@ static int level_step(float f, float Rprev, int lvl, float e, float two_e, float
             }
         }
     }
-    if (exc) {
-        q = 0;
-        R = f;
-    }
+    if (exc) R = f; /* q stays the rounded code, or 0 if r was not quantisable */
     *q_out = q;
     *R_out = R;
     return exc;

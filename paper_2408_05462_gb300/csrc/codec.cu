@@ -45,7 +45,8 @@ __device__ __forceinline__ int count_above(float v, const float *K, int nK)
 // One level of the residual chain for one vertex (paper Sec. 2 accuracy
 // levels; Sec. 2.2 sign preservation).  Every float operation is one IEEE
 // binary32 operation rounded to nearest-even.  Returns true for a vertex
-// stored exactly (bound or sign check failed, or not quantisable).
+// stored exactly (bound or sign check failed, or not quantisable); its code
+// is the rounded value (0 when not quantisable) and R takes f.
 // The sign check compares the count of candidates above R with f's count cf.
 // Both counts agree exactly when kdn <= R < kup, kup the smallest candidate
 // above f (+inf if none) and kdn the largest at or below it (-inf if none):
@@ -59,11 +60,11 @@ __device__ __forceinline__ bool encode_step(float f, float Rprev, bool first, fl
     R = f;
     if (!(fabsf(x) <= CHR_QMAX)) return true;
     const int32_t qi = __float2int_rn(x);  // round half to even
+    q = qi;  // kept by an exception too, so the neighbours' prediction stays smooth
     const float P = __fmul_rn(__int2float_rn(qi), two_e);
     const float Rn = first ? P : __fadd_rn(Rprev, P);
     if (!(fabsf(__fsub_rn(f, Rn)) < e)) return true;
     if (fix && !(Rn >= kdn && Rn < kup)) return true;
-    q = qi;
     R = Rn;
     return false;
 }
