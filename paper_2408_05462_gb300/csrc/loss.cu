@@ -10,7 +10,8 @@
 // Points where G vanishes count as distance 0 with zero gradient.  The mean
 // is reduced in a fixed order (per-thread sums over a fixed stride, a
 // fixed-shape block tree, then one block over the block partials), so the
-// result does not depend on scheduling.  Arithmetic in float64.
+// result does not depend on scheduling.  Arithmetic in float64, the
+// interpolation separable (x, then y, then z) and one reciprocal per point.
 #include "common.cuh"
 #include "internal.h"
 
@@ -51,35 +52,45 @@ __global__ void __launch_bounds__(kLossThreads) k_dist_loss(const __grid_constan
             u[a] = x - fl;
         }
         const float *base = p.f + c[0] + p.nx * (c[1] + p.ny * c[2]);
-        double F = 0, G0 = 0, G1 = 0, G2 = 0, H01 = 0, H02 = 0, H12 = 0;
+        // separable trilinear interpolation: along x for the four (y, z)
+        // edges, then y, then z, carrying the derivatives along
+        double a[2][2], b[2][2];  // [dz][dy]: value and x-derivative on the x-edge
 #pragma unroll
         for (int dz = 0; dz < 2; dz++)
 #pragma unroll
-            for (int dy = 0; dy < 2; dy++)
+            for (int dy = 0; dy < 2; dy++) {
+                const float *e = base + p.nx * (dy + p.ny * dz);
+                const double f0 = (double)__ldg(e), f1 = (double)__ldg(e + 1);
+                b[dz][dy] = f1 - f0;
+                a[dz][dy] = fma(u[0], b[dz][dy], f0);
+            }
+        double Fz[2], Gyz[2], Gxz[2], Hxyz[2];
 #pragma unroll
-                for (int dx = 0; dx < 2; dx++) {
-                    const double fv = (double)__ldg(base + dx + p.nx * (dy + p.ny * dz));
-                    const double wx = dx ? u[0] : 1.0 - u[0], wy = dy ? u[1] : 1.0 - u[1], wz = dz ? u[2] : 1.0 - u[2];
-                    const double sx = dx ? 1.0 : -1.0, sy = dy ? 1.0 : -1.0, sz = dz ? 1.0 : -1.0;
-                    F += wx * wy * wz * fv;
-                    G0 += sx * wy * wz * fv;
-                    G1 += wx * sy * wz * fv;
-                    G2 += wx * wy * sz * fv;
-                    H01 += sx * sy * wz * fv;
-                    H02 += sx * wy * sz * fv;
-                    H12 += wx * sy * sz * fv;
-                }
+        for (int dz = 0; dz < 2; dz++) {
+            Gyz[dz] = a[dz][1] - a[dz][0];
+            Fz[dz] = fma(u[1], Gyz[dz], a[dz][0]);
+            Hxyz[dz] = b[dz][1] - b[dz][0];
+            Gxz[dz] = fma(u[1], Hxyz[dz], b[dz][0]);
+        }
+        const double G2 = Fz[1] - Fz[0];
+        const double F = fma(u[2], G2, Fz[0]);
+        const double H12 = Gyz[1] - Gyz[0], H02 = Gxz[1] - Gxz[0], H01d = Hxyz[1] - Hxyz[0];
+        const double G1 = fma(u[2], H12, Gyz[0]);
+        const double G0 = fma(u[2], H02, Gxz[0]);
+        const double H01 = fma(u[2], H01d, Hxyz[0]);
         const double gn = sqrt(G0 * G0 + G1 * G1 + G2 * G2);
         const double r = F - p.k;
         double g[3] = {0.0, 0.0, 0.0};
         if (gn > 0.0) {
-            acc += fabs(r) / gn;
+            const double inv = 1.0 / gn;
+            const double ar = fabs(r) * inv;
+            acc += ar;
             const double s = (r > 0.0) ? 1.0 : (r < 0.0) ? -1.0 : 0.0;
             const double hg0 = H01 * G1 + H02 * G2, hg1 = H01 * G0 + H12 * G2, hg2 = H02 * G0 + H12 * G1;
-            const double a3 = fabs(r) / (gn * gn * gn);
-            g[0] = (s * G0 / gn - a3 * hg0) * invn;
-            g[1] = (s * G1 / gn - a3 * hg1) * invn;
-            g[2] = (s * G2 / gn - a3 * hg2) * invn;
+            const double a3 = ar * inv * inv;
+            g[0] = (s * G0 * inv - a3 * hg0) * invn;
+            g[1] = (s * G1 * inv - a3 * hg1) * invn;
+            g[2] = (s * G2 * inv - a3 * hg2) * invn;
         }
         if (p.grad) {
             p.grad[3 * v + 0] = (float)g[0];
