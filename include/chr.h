@@ -314,9 +314,10 @@ typedef struct chr_batch_item {
 } chr_batch_item;
 
 typedef struct chr_batch_config {
-    int32_t count_blocks_per_sm; /* resident blocks per SM of the tile-count pass (0: the most that fit) */
-    int32_t emit_blocks_per_sm;  /* the same for the emit pass */
-    int32_t use_graph;           /* 1: capture the sequence once and replay it */
+    int32_t count_blocks_per_sm;    /* resident blocks per SM of the tile-count pass (0: the most that fit) */
+    int32_t emit_blocks_per_sm;     /* the same for the emit pass */
+    int32_t use_graph;              /* 1: capture the sequence once and replay it */
+    int32_t decode_warps_per_block; /* bricks (one per warp) per decode block: 4 or 8 (0: 8) */
 } chr_batch_config;
 
 /*
@@ -339,8 +340,8 @@ chr_status chr_batch_run(chr_batch *b, void *stream);
 
 /*
  * chr_batch_autotune — time every candidate configuration (tile-kernel grid
- * sizes) on this batch, reps runs each, keep the fastest and remember it for
- * the batch's size-class signature.  Synchronises stream.  The outputs then
+ * sizes and the decode brick-group size) on this batch, reps runs each, keep
+ * the fastest and remember it for the batch's size-class signature.  Synchronises stream.  The outputs then
  * hold the last candidate's (identical) results.
  */
 chr_status chr_batch_autotune(chr_batch *b, uint32_t reps, void *stream, chr_batch_config *chosen);

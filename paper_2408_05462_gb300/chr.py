@@ -73,7 +73,10 @@ class ChrBatchItem(ctypes.Structure):
 
 class ChrBatchConfig(ctypes.Structure):
     _fields_ = [("count_blocks_per_sm", ctypes.c_int32), ("emit_blocks_per_sm", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("decode_warps_per_block", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 def lib():
@@ -456,20 +459,18 @@ class Batch:
     def autotune(self, reps: int = 3, stream=None) -> dict:
         c = ChrBatchConfig()
         _check(lib().chr_batch_autotune(self._ptr, int(reps), _stream(stream), ctypes.byref(c)))
-        return {"count_blocks_per_sm": c.count_blocks_per_sm, "emit_blocks_per_sm": c.emit_blocks_per_sm,
-                "use_graph": c.use_graph}
+        return c.as_dict()
 
     @property
     def config(self) -> dict:
         c = ChrBatchConfig()
         _check(lib().chr_batch_get_config(self._ptr, ctypes.byref(c)))
-        return {"count_blocks_per_sm": c.count_blocks_per_sm, "emit_blocks_per_sm": c.emit_blocks_per_sm,
-                "use_graph": c.use_graph}
+        return c.as_dict()
 
     @config.setter
     def config(self, cfg: dict):
         c = ChrBatchConfig(int(cfg.get("count_blocks_per_sm", 0)), int(cfg.get("emit_blocks_per_sm", 0)),
-                           int(cfg.get("use_graph", 1)))
+                           int(cfg.get("use_graph", 1)), int(cfg.get("decode_warps_per_block", 0)))
         _check(lib().chr_batch_set_config(self._ptr, ctypes.byref(c)))
 
     def field(self, i: int, stream=None) -> torch.Tensor:

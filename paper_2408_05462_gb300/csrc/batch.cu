@@ -10,10 +10,11 @@
 // parameters and tensor map, with one scan of the tile counts in between.
 // The whole sequence is captured once into a CUDA graph and replayed.
 //
-// The grid sizes of the two tile kernels are picked by a small autotuner
-// that times the candidates on the batch itself; the choice is remembered per
-// size-class signature of the batch (how many boxes fall in each volume
-// class), so a later batch of the same mix reuses it without timing.
+// The grid sizes of the two tile kernels and the decoder's brick-group size
+// (bricks per block) are picked by a small autotuner that times the
+// candidates on the batch itself; the choice is remembered per size-class
+// signature of the batch (how many boxes fall in each volume class), so a
+// later batch of the same mix reuses it without timing.
 #include <cuda.h>
 #include <string.h>
 
@@ -35,7 +36,7 @@ struct chr_batch {
     std::string key;                // size-class signature
     int64_t ntiles = 0, nbricks = 0;
     uint64_t cap = 0;
-    chr_batch_config cfg{0, 0, 1};
+    chr_batch_config cfg{0, 0, 1, 8};
     int sms = 0, count_max = 1, emit_max = 1;
     // device buffers
     Alloc *al = nullptr;
@@ -98,7 +99,8 @@ cudaError_t record_work(chr_batch *b, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(b->d_err, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    e = launch_decode_batched(b->d_descs, b->d_brick_start, (int32_t)b->n, b->nbricks, s);
+    e = launch_decode_batched(b->d_descs, b->d_brick_start, (int32_t)b->n, b->nbricks, b->cfg.decode_warps_per_block,
+                              s);
     if (e != cudaSuccess) return e;
     McBatchLaunch L;
     L.params = b->d_params;
@@ -123,6 +125,7 @@ chr_status clamp_config(const chr_batch *b, chr_batch_config &c)
     if (c.count_blocks_per_sm == 0 || c.count_blocks_per_sm > b->count_max) c.count_blocks_per_sm = b->count_max;
     if (c.emit_blocks_per_sm == 0 || c.emit_blocks_per_sm > b->emit_max) c.emit_blocks_per_sm = b->emit_max;
     c.use_graph = c.use_graph ? 1 : 0;
+    c.decode_warps_per_block = (c.decode_warps_per_block == 4) ? 4 : 8;
     return CHR_OK;
 }
 
@@ -188,7 +191,7 @@ chr_status chr_batch_create(const chr_batch_item *items, uint32_t n, float *d_tr
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(b->key);
-        b->cfg = (it != g_tuned.end()) ? it->second : chr_batch_config{0, 0, 1};
+        b->cfg = (it != g_tuned.end()) ? it->second : chr_batch_config{0, 0, 1, 8};
     }
     clamp_config(b, b->cfg);
 
@@ -299,12 +302,13 @@ chr_status chr_batch_autotune(chr_batch *b, uint32_t reps, void *stream, chr_bat
     if (reps == 0) reps = 3;
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<chr_batch_config> cand;
-    const int cc[4] = {1, 2, 4, 8}, ec[4] = {1, 2, 3, 4};
-    for (int i = 0; i < 4; i++) {
-        if (cc[i] > b->count_max) continue;
-        for (int j = 0; j < 4; j++)
-            if (ec[j] <= b->emit_max) cand.push_back(chr_batch_config{cc[i], ec[j], 1});
-    }
+    const int cc[4] = {1, 2, 4, 8}, ec[4] = {1, 2, 3, 4}, dw[2] = {4, 8};
+    for (int d = 0; d < 2; d++)
+        for (int i = 0; i < 4; i++) {
+            if (cc[i] > b->count_max) continue;
+            for (int j = 0; j < 4; j++)
+                if (ec[j] <= b->emit_max) cand.push_back(chr_batch_config{cc[i], ec[j], 1, dw[d]});
+        }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return cuda_fail(cudaGetLastError(), "chr_batch_autotune");

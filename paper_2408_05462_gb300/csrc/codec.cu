@@ -341,11 +341,13 @@ __global__ void __launch_bounds__(256, 4) k_decode(const __grid_constant__ Codec
 // Many CHRs in one launch: warp w of the grid decodes brick w of the
 // concatenated brick list (box i owns bricks brick_start[i] ..
 // brick_start[i+1]-1, x fastest), so small boxes leave no warp idle.
-__global__ void __launch_bounds__(256, 4) k_decode_batched(const CodecParams *__restrict__ descs,
-                                                        const int64_t *__restrict__ brick_start, int32_t nboxes)
+template <int WPB>
+__global__ void __launch_bounds__(WPB * 32, 32 / WPB) k_decode_batched(const CodecParams *__restrict__ descs,
+                                                                      const int64_t *__restrict__ brick_start,
+                                                                      int32_t nboxes)
 {
     extern __shared__ __align__(16) uint32_t s_dyn[];
-    const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int64_t w = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5);
     if (w >= brick_start[nboxes]) return;
     int lo = 0, hi = nboxes - 1;  // the last box whose start is <= w
     while (lo < hi) {
@@ -698,18 +700,26 @@ cudaError_t launch_decode(const CodecParams &p, cudaStream_t s)
 }
 
 cudaError_t launch_decode_batched(const CodecParams *d_descs, const int64_t *d_brick_start, int32_t nboxes,
-                                  int64_t total_bricks, cudaStream_t s)
+                                  int64_t total_bricks, int warps_per_block, cudaStream_t s)
 {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_decode_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, kDecodeSmem);
+        cudaError_t e = cudaFuncSetAttribute(k_decode_batched<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             8 * kDecGroup * kLevelWords * 4);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_decode_batched<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 4 * kDecGroup * kLevelWords * 4);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     if (total_bricks == 0) return cudaSuccess;
-    const unsigned grid = (unsigned)((total_bricks + kWarpsPerBlock - 1) / kWarpsPerBlock);
-    k_decode_batched<<<grid, 256, kDecodeSmem, s>>>(d_descs, d_brick_start, nboxes);
+    if (warps_per_block == 4) {
+        const unsigned grid = (unsigned)((total_bricks + 3) / 4);
+        k_decode_batched<4><<<grid, 128, 4 * kDecGroup * kLevelWords * 4, s>>>(d_descs, d_brick_start, nboxes);
+    } else {
+        const unsigned grid = (unsigned)((total_bricks + 7) / 8);
+        k_decode_batched<8><<<grid, 256, 8 * kDecGroup * kLevelWords * 4, s>>>(d_descs, d_brick_start, nboxes);
+    }
     return cudaGetLastError();
 }
 

@@ -68,7 +68,7 @@ cudaError_t launch_compact(const CodecParams &p, cudaStream_t s);
 cudaError_t launch_decode(const CodecParams &p, cudaStream_t s);
 // Decode of many CHRs in one launch (descs, brick_start [nboxes+1] on the device).
 cudaError_t launch_decode_batched(const CodecParams *d_descs, const int64_t *d_brick_start, int32_t nboxes,
-                                  int64_t total_bricks, cudaStream_t s);
+                                  int64_t total_bricks, int warps_per_block, cudaStream_t s);
 // Exclusive scans of the widths and exception counts of each level's records;
 // totals[2*l] = sum of w, totals[2*l+1] = exceptions.  scratch needs
 // scan_scratch_bytes(nbricks, nlevels).

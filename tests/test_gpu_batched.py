@@ -84,14 +84,15 @@ def test_graph_direct_and_tuned_agree(small):
     b.run()
     ref_t, ref_s = b.tris.clone(), b.box_start.clone()
     for cfg in ({"use_graph": 0}, {"count_blocks_per_sm": 1, "emit_blocks_per_sm": 1, "use_graph": 1},
-                {"count_blocks_per_sm": 99, "emit_blocks_per_sm": 2, "use_graph": 0}):
+                {"count_blocks_per_sm": 99, "emit_blocks_per_sm": 2, "use_graph": 0},
+                {"decode_warps_per_block": 4, "use_graph": 1}, {"decode_warps_per_block": 4, "use_graph": 0}):
         b.config = cfg
         b.tris.zero_()
         b.run()
         assert torch.equal(b.box_start, ref_s)
         assert torch.equal(b.tris.view(torch.int32), ref_t.view(torch.int32))
     c = b.config
-    assert 1 <= c["count_blocks_per_sm"] and 1 <= c["emit_blocks_per_sm"]
+    assert 1 <= c["count_blocks_per_sm"] and 1 <= c["emit_blocks_per_sm"] and c["decode_warps_per_block"] == 4
     tuned = b.autotune(reps=2)
     assert tuned == b.config
     b.run()
