@@ -144,6 +144,25 @@ chr_status chr_reconstruct_box(const chr_handle *h, uint32_t level, int64_t x0, 
                                float *d_out, void *stream);
 
 /*
+ * chr_serve_request — one request of the visualization side in one call:
+ * decode the box [x0, x0+box.nx) x [y0, ...) x [z0, ...) of level `level`
+ * (every side >= 2 and inside the grid), run marching cubes on it at
+ * `isovalue` with room for cap_tris triangles, and copy (triangle count,
+ * error word) as two uint64 to h_result (host memory, pinned for a truly
+ * asynchronous copy) when the stream gets there.  d_mem: caller-owned device
+ * memory, 256-byte aligned, of at least chr_serve_request_bytes(box,
+ * cap_tris) bytes; the triangles (box-local grid coordinates, the layout of
+ * isosurface_extract with one isovalue) start at d_mem, the rest is scratch
+ * (the box field, pitched to 16-byte rows, and the marching-cubes
+ * workspace).  Equal, bit for bit, to chr_reconstruct_box +
+ * isosurface_extract of the box.  Asynchronous.
+ */
+size_t chr_serve_request_bytes(chr_dims box, uint64_t cap_tris);
+chr_status chr_serve_request(const chr_handle *h, uint32_t level, int64_t x0, int64_t y0, int64_t z0, chr_dims box,
+                             float isovalue, void *d_mem, size_t mem_bytes, uint64_t cap_tris, uint64_t *h_result,
+                             void *stream);
+
+/*
  * chr_brick_range — per-brick value range of level `level`: d_range
  * (caller-owned, 2 floats per 8^3 brick, brick (bx, by, bz) at index
  * bx + nbx*(by + nby*bz), nbx = ceil(nx/8) and so on) receives the (min, max)

@@ -7,6 +7,7 @@ to the library as a chr_allocator) and the current CUDA stream.  There is no
 CPU path: if libchr.so is missing or cannot load, every call raises.
 
 Names follow the C ABI: chr_compress, chr_reconstruct, chr_reconstruct_box, chr_brick_range,
+chr_serve_request, chr_serve_request_bytes,
 chr_topo_translate,
 isosurface_extract, isosurface_workspace_size, isosurface_workspace_min_size, isosurface_extract_noalloc,
 isosurface_backward, isosurface_distance_loss, chr_serialize, chr_deserialize,
@@ -96,6 +97,11 @@ def lib():
         L.chr_reconstruct.argtypes = [c_void_p, c_uint32, c_void_p, c_void_p]
         L.chr_reconstruct_box.restype = st
         L.chr_reconstruct_box.argtypes = [c_void_p, c_uint32, c_int64, c_int64, c_int64, ChrDims, c_void_p, c_void_p]
+        L.chr_serve_request_bytes.restype = c_size_t
+        L.chr_serve_request_bytes.argtypes = [ChrDims, c_uint64]
+        L.chr_serve_request.restype = st
+        L.chr_serve_request.argtypes = [c_void_p, c_uint32, c_int64, c_int64, c_int64, ChrDims, c_float, c_void_p,
+                                        c_size_t, c_uint64, c_void_p, c_void_p]
         L.chr_brick_range.restype = st
         L.chr_brick_range.argtypes = [c_void_p, c_uint32, c_void_p, c_void_p]
         L.chr_topo_translate.restype = st
@@ -273,6 +279,29 @@ def chr_reconstruct_box(h: Chr, level: int, origin, size, out: torch.Tensor | No
     _check(lib().chr_reconstruct_box(h.ptr, int(level), x0, y0, z0, ChrDims(bx, by, bz), out.data_ptr(),
                                      _stream(stream)))
     return out
+
+
+def chr_serve_request_bytes(size, cap: int) -> int:
+    """Device bytes chr_serve_request needs for a box of `size` (x, y, z) and
+    room for `cap` triangles (chr.h: chr_serve_request_bytes)."""
+    bx, by, bz = (int(v) for v in size)
+    return int(lib().chr_serve_request_bytes(ChrDims(bx, by, bz), int(cap)))
+
+
+def chr_serve_request(h: Chr, level: int, origin, size, isovalue: float, mem: torch.Tensor, cap: int,
+                      result: torch.Tensor, stream=None):
+    """Decode the box and mesh it at `isovalue` in one call (chr.h:
+    chr_serve_request).  mem: uint8 CUDA tensor of chr_serve_request_bytes
+    bytes whose first 36*cap bytes receive the triangles; result: int64 CPU
+    tensor of 2 (pinned) that receives (count, error word)."""
+    x0, y0, z0 = (int(v) for v in origin)
+    bx, by, bz = (int(v) for v in size)
+    if not (mem.is_cuda and mem.dtype == torch.uint8 and mem.is_contiguous()):
+        raise ValueError("mem must be a contiguous uint8 CUDA tensor")
+    if result.is_cuda or result.dtype != torch.int64 or result.numel() < 2 or not result.is_contiguous():
+        raise ValueError("result must be a contiguous int64 CPU tensor of 2")
+    _check(lib().chr_serve_request(h.ptr, int(level), x0, y0, z0, ChrDims(bx, by, bz), float(isovalue),
+                                   mem.data_ptr(), mem.numel(), int(cap), result.data_ptr(), _stream(stream)))
 
 
 def chr_brick_range(h: Chr, level: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:

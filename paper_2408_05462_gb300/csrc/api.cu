@@ -408,6 +408,72 @@ chr_status chr_reconstruct_box(const chr_handle *h, uint32_t level, int64_t x0, 
     return CHR_OK;
 }
 
+namespace {
+
+struct ServeLayout {
+    size_t tris, field, ws, result, total;  // byte offsets of each part, total size
+    int64_t sx, sy;
+};
+
+ServeLayout serve_layout(chr_dims box, uint64_t cap_tris)
+{
+    ServeLayout L;
+    L.sx = (box.nx + 3) & ~int64_t(3);  // rows start on 16 bytes: the marching cubes always have a tensor map
+    L.sy = L.sx * box.ny;
+    auto up = [](size_t n) { return (n + 255) & ~size_t(255); };
+    L.tris = 0;
+    L.field = up((size_t)cap_tris * 36);
+    L.ws = L.field + up((size_t)L.sy * box.nz * 4);
+    L.result = L.ws + up(mc_workspace_bytes(make_grid(box), 1));
+    L.total = L.result + 256;
+    return L;
+}
+
+}  // namespace
+
+size_t chr_serve_request_bytes(chr_dims box, uint64_t cap_tris)
+{
+    std::string why;
+    if (!dims_ok(box, why) || cap_tris > (1ull << 58)) return 0;
+    return serve_layout(box, cap_tris).total;
+}
+
+chr_status chr_serve_request(const chr_handle *h, uint32_t level, int64_t x0, int64_t y0, int64_t z0, chr_dims box,
+                             float isovalue, void *d_mem, size_t mem_bytes, uint64_t cap_tris, uint64_t *h_result,
+                             void *stream)
+{
+    std::string why;
+    if (!h || !d_mem || !h_result) return fail(CHR_ERR_INVALID, "chr_serve_request: NULL handle, memory or result");
+    if (level >= h->nlevels) return fail(CHR_ERR_INVALID, "chr_serve_request: level out of range");
+    if (!dims_ok(box, why)) return fail(CHR_ERR_INVALID, "chr_serve_request: " + why);
+    if (x0 < 0 || y0 < 0 || z0 < 0 || x0 + box.nx > h->g.nx || y0 + box.ny > h->g.ny || z0 + box.nz > h->g.nz)
+        return fail(CHR_ERR_INVALID, "chr_serve_request: box outside the grid");
+    if (!isfinite(isovalue)) return fail(CHR_ERR_INVALID, "chr_serve_request: isovalue must be finite");
+    if (reinterpret_cast<uintptr_t>(d_mem) & 255u) return fail(CHR_ERR_INVALID, "chr_serve_request: misaligned memory");
+    if (cap_tris > (1ull << 58)) return fail(CHR_ERR_INVALID, "chr_serve_request: cap_tris too large");
+    const ServeLayout L = serve_layout(box, cap_tris);
+    if (mem_bytes < L.total) return fail(CHR_ERR_INVALID, "chr_serve_request: memory smaller than chr_serve_request_bytes()");
+    cudaStream_t s = (cudaStream_t)stream;
+    char *base = reinterpret_cast<char *>(d_mem);
+    float *field = reinterpret_cast<float *>(base + L.field);
+    uint64_t *res = reinterpret_cast<uint64_t *>(base + L.result);
+    CodecParams p;
+    fill_codec_params(h, p);
+    p.out = field;
+    p.nlevels = (int32_t)level + 1;
+    set_box(p, h->g, x0, y0, z0, box.nx, box.ny, box.nz);
+    p.out_sx = L.sx;
+    p.out_sy = L.sy;
+    CHR_CUDA(cudaMemsetAsync(res, 0, 16, s), "chr_serve_request");
+    CHR_CUDA(launch_decode(p, s), "chr_serve_request");
+    CHR_CUDA(launch_mc_pitched(field, make_grid(box), L.sx, L.sy, &isovalue, 1,
+                               cap_tris ? reinterpret_cast<float *>(base + L.tris) : nullptr, cap_tris, res,
+                               reinterpret_cast<uint32_t *>(res + 1), base + L.ws, L.result - L.ws, s),
+             "chr_serve_request");
+    CHR_CUDA(cudaMemcpyAsync(h_result, res, 16, cudaMemcpyDeviceToHost, s), "chr_serve_request");
+    return CHR_OK;
+}
+
 chr_status chr_topo_translate(const float *d_field, chr_dims dims, const float *isovalues, uint32_t n_iso,
                               float accuracy, const chr_allocator *alloc, void *stream, float *eb_out,
                               uint64_t *count_out)

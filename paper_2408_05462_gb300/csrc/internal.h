@@ -84,6 +84,10 @@ size_t mc_workspace_bytes(const Grid &g, int n_iso);
 size_t mc_workspace_min_bytes(const Grid &g, int n_iso);
 cudaError_t launch_mc(const float *field, const Grid &g, const float *iso, int n_iso, float *tris, uint64_t cap,
                       uint64_t *ntris, uint32_t *err, void *workspace, size_t workspace_bytes, cudaStream_t s);
+// The same over a pitched field: value (x, y, z) at field[x + sx*y + sy*z].
+cudaError_t launch_mc_pitched(const float *field, const Grid &g, int64_t sx, int64_t sy, const float *iso, int n_iso,
+                              float *tris, uint64_t cap, uint64_t *ntris, uint32_t *err, void *workspace,
+                              size_t workspace_bytes, cudaStream_t s);
 
 // Marching cubes of many fields (each with its own isovalue and pitch) in one
 // launch sequence: count over the concatenated tile list, one scan, emit.

@@ -1127,14 +1127,22 @@ static cudaError_t launch_adjoint_group(const McParams &p, const AdjParams &a, c
 cudaError_t launch_mc(const float *field, const Grid &g, const float *iso, int n_iso, float *tris, uint64_t cap,
                       uint64_t *ntris, uint32_t *err, void *workspace, size_t workspace_bytes, cudaStream_t s)
 {
+    return launch_mc_pitched(field, g, g.nx, g.nx * g.ny, iso, n_iso, tris, cap, ntris, err, workspace,
+                             workspace_bytes, s);
+}
+
+cudaError_t launch_mc_pitched(const float *field, const Grid &g, int64_t sx, int64_t sy, const float *iso, int n_iso,
+                              float *tris, uint64_t cap, uint64_t *ntris, uint32_t *err, void *workspace,
+                              size_t workspace_bytes, cudaStream_t s)
+{
     McParams p;
     memset(&p, 0, sizeof(p));
     p.f = field;
     p.nx = g.nx;
     p.ny = g.ny;
     p.nz = g.nz;
-    p.sx = g.nx;
-    p.sy = g.nx * g.ny;
+    p.sx = sx;
+    p.sy = sy;
     mc_tiles(g, p.ntx, p.ncby, p.ncbz, p.ntiles);
     p.cap = cap;
     p.err = err;
@@ -1149,7 +1157,7 @@ cudaError_t launch_mc(const float *field, const Grid &g, const float *iso, int n
     p.cstride = cstride;
     CUtensorMap map;
     memset(&map, 0, sizeof(map));
-    p.use_tma = make_field_tensor_map(&map, field, g.nx, g.ny, g.nz, kBoxX, 9, 9) ? 1 : 0;
+    p.use_tma = make_field_tensor_map_pitched(&map, field, g.nx, g.ny, g.nz, sx, sy, kBoxX, 9, 9) ? 1 : 0;
     for (int i0 = 0; i0 < n_iso; i0 += kMcIsoPerPass) {
         const int n = (n_iso - i0) < kMcIsoPerPass ? (n_iso - i0) : kMcIsoPerPass;
         for (int i = 0; i < kMcIsoPerPass; i++) {

@@ -3,9 +3,9 @@ device, and requests for (timestep, isovalue, accuracy level, subvolume)
 arrive over time (Sec. 2: the analysis side asks for the data it needs at
 the accuracy it needs; Sec. 1, in-transit visualization).
 
-Every request runs chr_reconstruct_box (decode only the bricks of its box at
-its level) and isosurface_extract (marching cubes of the box) on one of a few
-CUDA streams ("slots").  Scheduling is continuous: whenever a request
+Every request is one chr_serve_request call (decode only the bricks of its
+box at its level into a pitched box field, marching cubes of the box, the
+count copied back) on one of a few CUDA streams ("slots").  Scheduling is continuous: whenever a request
 finishes, its slot and memory are released and the next waiting requests are
 admitted in arrival order, so new work starts while older work is still on the
 device.  Admission is by a device-memory budget: a request holds its box
@@ -126,8 +126,8 @@ class _Flight:
     bound: int
     admit_ms: float
     done: torch.cuda.Event
-    count_host: tuple  # (pinned count, pinned error word)
-    tris: torch.Tensor | None
+    count_host: torch.Tensor  # pinned (triangle count, error word)
+    tris: torch.Tensor | None  # the request's device memory, triangles first (keep_results)
     keep: list = dc_field(default_factory=list)  # buffers alive until done
 
 
@@ -152,13 +152,10 @@ class Server:
         self.host_ms = 0.0  # host time spent on admission and launches in the last run
 
     def _bufs(self, slot: int):
-        """Per-slot device count/error words and their pinned host copies,
-        reused request after request (a slot runs one request at a time)."""
+        """Per-slot pinned host words (triangle count, error word), reused
+        request after request (a slot runs one request at a time)."""
         while len(self._slot_bufs) <= slot:
-            self._slot_bufs.append((torch.zeros(1, dtype=torch.int64, device="cuda"),
-                                    torch.zeros(1, dtype=torch.int32, device="cuda"),
-                                    torch.zeros(1, dtype=torch.int64, pin_memory=True),
-                                    torch.zeros(1, dtype=torch.int32, pin_memory=True)))
+            self._slot_bufs.append(torch.zeros(2, dtype=torch.int64, pin_memory=True))
         return self._slot_bufs[slot]
 
     def with_slots(self, slots: int) -> "Server":
@@ -195,28 +192,19 @@ class Server:
 
     # ---- one request ------------------------------------------------------
     def request_bytes(self, req: Request, bound: int) -> int:
-        bx, by, bz = req.size
-        ws = chr.isosurface_workspace_size((bz, by, bx), 1)
-        return 4 * bx * by * bz + 36 * bound + ws + 512
+        return chr.chr_serve_request_bytes(req.size, max(bound, 1))
 
     def _launch(self, req: Request, slot: int, bound: int, nbytes: int, t0: float, keep_results: bool) -> _Flight:
         ts = self.steps[req.step]
         s = self.streams[slot]
-        counts, err, counts_h, err_h = self._bufs(slot)
-        bx, by, bz = req.size
+        result = self._bufs(slot)
         with torch.cuda.stream(s):
-            box = torch.empty((bz, by, bx), dtype=torch.float32, device="cuda")
-            chr.chr_reconstruct_box(ts.handle, req.level, req.origin, req.size, out=box, stream=s)
-            tris = torch.empty((1, max(bound, 1), 3, 3), dtype=torch.float32, device="cuda")
-            ws = torch.empty(chr.isosurface_workspace_size(box.shape, 1), dtype=torch.uint8, device="cuda")
-            chr.isosurface_extract(box, [req.k], bound, tris=tris, counts=counts, err=err, workspace=ws, stream=s)
-            counts_h.copy_(counts, non_blocking=True)
-            err_h.copy_(err, non_blocking=True)
+            mem = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            chr.chr_serve_request(ts.handle, req.level, req.origin, req.size, req.k, mem, bound, result, stream=s)
             done = torch.cuda.Event(enable_timing=True)
             done.record(s)
         admit_ms = (time.perf_counter() - t0) * 1e3
-        return _Flight(req, slot, nbytes, bound, admit_ms, done, (counts_h, err_h), tris if keep_results else None,
-                       [box, ws] + ([] if keep_results else [tris]))
+        return _Flight(req, slot, nbytes, bound, admit_ms, done, result, mem if keep_results else None, [mem])
 
     # ---- the loop ---------------------------------------------------------
     def run(self, requests, keep_results: bool = False, poll_s: float = 20e-6):
@@ -250,7 +238,7 @@ class Server:
             progressed = False
             for slot, fl in list(flights.items()):
                 if fl.done.query():
-                    n, e = int(fl.count_host[0][0]), int(fl.count_host[1][0])
+                    n, e = int(fl.count_host[0]), int(fl.count_host[1])
                     if e != 0 or n > fl.bound:
                         raise RuntimeError("request %d: device error %d, %d triangles for capacity %d"
                                            % (fl.req.rid, e, n, fl.bound))
@@ -258,7 +246,8 @@ class Server:
                     results[fl.req.rid] = Result(fl.req.rid, n, fl.bound, fl.admit_ms, done_ms,
                                                  done_ms - 1e3 * fl.req.arrival,
                                                  (time.perf_counter() - t0) * 1e3, fl.nbytes,
-                                                 fl.tris[0, :n] if fl.tris is not None else None)
+                                                 fl.tris[:36 * n].view(torch.float32).view(n, 3, 3)
+                                                 if fl.tris is not None else None)
                     used -= fl.nbytes
                     free_slots.append(slot)
                     del flights[slot]

@@ -71,6 +71,28 @@ def test_brick_range_is_the_brick_extrema(handle):
                     assert got[bz, by, bx, 0] == blk.min() and got[bz, by, bx, 1] == blk.max()
 
 
+def test_serve_request_equals_the_box_path(handle):
+    # one call (pitched box field, tensor-map marching cubes) against
+    # chr_reconstruct_box + isosurface_extract (dense box) of the same box
+    _, h = handle
+    result = torch.zeros(2, dtype=torch.int64, pin_memory=True)
+    for (o, s), level, k in [(((3, 5, 7), (64, 33, 17)), 0, 0.1), (((9, 1, 2), (70, 69, 59)), 3, -0.4),
+                             (((0, 0, 0), (83, 70, 61)), 2, 0.8), (((40, 0, 30), (2, 70, 2)), 1, 0.0),
+                             (((77, 13, 0), (6, 9, 61)), 0, -1.0)]:
+        box = h.reconstruct_box(level, o, s)
+        cap = 5 * (s[0] - 1) * (s[1] - 1) * (s[2] - 1) + 8
+        tris, counts, err = chr.isosurface_extract(box, [k], cap)
+        mem = torch.empty(chr.chr_serve_request_bytes(s, cap), dtype=torch.uint8, device="cuda")
+        chr.chr_serve_request(h, level, o, s, k, mem, cap, result)
+        torch.cuda.synchronize()
+        n = int(counts[0])
+        assert int(result[0]) == n and int(result[1]) == 0 and int(err.item()) == 0
+        got = mem[:36 * n].view(torch.int32)
+        assert torch.equal(got, tris[0, :n].reshape(-1).view(torch.int32)), (o, s, level, k)
+    with pytest.raises(chr.ChrError):
+        chr.chr_serve_request(h, 0, (80, 0, 0), (8, 8, 8), 0.0, mem, 16, result)
+
+
 def _server(f, slots):
     srv = serve.Server(budget_bytes=8 << 30, slots=slots, max_resident=2)
     fd = torch.from_numpy(f).cuda()
