@@ -689,11 +689,12 @@ cudaError_t launch_decode(const CodecParams &p, cudaStream_t s)
 {
     const dim3 grid((unsigned)((int64_t)((p.box_bricks[0] + kWarpsPerBlock - 1) / kWarpsPerBlock) * p.box_bricks[1] *
                                p.box_bricks[2]));
-    static bool attr = false;
-    if (!attr) {
+    static bool attr[kMaxDevices] = {};
+    const int dev = current_device();
+    if (!attr[dev]) {
         cudaError_t e = cudaFuncSetAttribute(k_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, kDecodeSmem);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr[dev] = true;
     }
     k_decode<<<grid, 256, kDecodeSmem, s>>>(p);
     return cudaGetLastError();
@@ -702,15 +703,16 @@ cudaError_t launch_decode(const CodecParams &p, cudaStream_t s)
 cudaError_t launch_decode_batched(const CodecParams *d_descs, const int64_t *d_brick_start, int32_t nboxes,
                                   int64_t total_bricks, int warps_per_block, cudaStream_t s)
 {
-    static bool attr = false;
-    if (!attr) {
+    static bool attr[kMaxDevices] = {};
+    const int dev = current_device();
+    if (!attr[dev]) {
         cudaError_t e = cudaFuncSetAttribute(k_decode_batched<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              8 * kDecGroup * kLevelWords * 4);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(k_decode_batched<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  4 * kDecGroup * kLevelWords * 4);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr[dev] = true;
     }
     if (total_bricks == 0) return cudaSuccess;
     if (warps_per_block == 4) {

@@ -138,6 +138,19 @@ cudaError_t launch_translate_pass(const float *field, const Grid &g, const float
 
 void set_error(const std::string &msg);
 
+// Per-device one-time setup (kernel attributes, occupancy): the current
+// device's index, clamped to the table size used by the launchers.
+constexpr int kMaxDevices = 64;
+inline int current_device()
+{
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess) {
+        cudaGetLastError();
+        d = 0;
+    }
+    return (d >= 0 && d < kMaxDevices) ? d : 0;
+}
+
 }  // namespace chr
 
 struct chr_handle;

@@ -1037,7 +1037,8 @@ struct McGrids {
 template <int NISO>
 static cudaError_t mc_prepare(McGrids &out)
 {
-    static McGrids G = {0, 0, 0, 0};  // resident blocks per device, computed once per process
+    static McGrids Gd[kMaxDevices] = {};  // resident blocks, computed once per device
+    McGrids &G = Gd[current_device()];
     if (!G.emit) {
         cudaError_t e = cudaFuncSetAttribute(k_mc_emit<NISO, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              kEmitSmem);
@@ -1048,8 +1049,7 @@ static cudaError_t mc_prepare(McGrids &out)
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(k_mc_count<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCountSmem);
         if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, bc = 0, be = 0, bf = 0, ba = 0;
-        cudaGetDevice(&dev);
+        int dev = current_device(), sms = 0, bc = 0, be = 0, bf = 0, ba = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bc, k_mc_count<NISO>, 256, kCountSmem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&be, k_mc_emit<NISO, true>, 256, kEmitSmem);
@@ -1303,14 +1303,14 @@ bool mc_batch_fill(void *params, void *map, const float *field, int64_t nx, int6
 
 cudaError_t mc_batch_prepare(int &count_per_sm, int &emit_per_sm, int &sms)
 {
-    static int bc = 0, be = 0, ns = 0;
+    static int bcd[kMaxDevices] = {}, bed[kMaxDevices] = {}, nsd[kMaxDevices] = {};
+    const int dev = current_device();
+    int &bc = bcd[dev], &be = bed[dev], &ns = nsd[dev];
     if (!ns) {
         cudaError_t e = cudaFuncSetAttribute(k_mc_emit_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(k_mc_count_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, kCountSmem);
         if (e != cudaSuccess) return e;
-        int dev = 0;
-        cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&ns, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bc, k_mc_count_batched, 256, kCountSmem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&be, k_mc_emit_batched, 256, kEmitSmem);
