@@ -145,34 +145,51 @@ __device__ __forceinline__ void row_masks(const float *buf, uint64_t *s_row, con
     }
 }
 
-// Byte x of the result = bit x of v (v < 16): the four shifted copies of v
-// made by the multiply do not overlap, so masking keeps one bit per byte.
-__device__ __forceinline__ uint32_t spread4(uint32_t v) { return (v * 0x00204081u) & 0x01010101u; }
-
-// Bytes x = 0..3 (lo) and 4..7 (hi) hold b(x) | b(x+1) << 1 of a 9-bit row mask.
-__device__ __forceinline__ void pair_bytes(uint32_t m, uint32_t &lo, uint32_t &hi)
+// Bit i of v (i < 8) moves to bit 4i.
+__device__ __forceinline__ uint32_t nib_spread(uint32_t v)
 {
-    lo = spread4(m & 15u) | (spread4((m >> 1) & 15u) << 1);
-    hi = spread4((m >> 4) & 15u) | (spread4((m >> 5) & 15u) << 1);
+    v &= 0xffu;
+    v = (v | (v << 12)) & 0x000f000fu;
+    v = (v | (v << 6)) & 0x03030303u;
+    v = (v | (v << 3)) & 0x11111111u;
+    return v;
 }
 
 // Case bytes of this thread's 8 cells from the inside masks of its four rows
-// (y, z), (y+1, z), (y, z+1), (y+1, z+1): corner j = ox + 2*oy + 4*oz is bit j.
+// A = (y, z), B = (y+1, z), C = (y, z+1), D = (y+1, z+1), in the kernels'
+// own bit order: corner (ox, oy, oz) is bit 4*ox + oy + 2*oz, so a cell's
+// byte is the nibble (A, B, C, D) of its x column with the nibble of column
+// x+1 above it.  Interleaving the four rows gives every column's nibble at
+// once; byte x is then bits 4x..4x+7 of that word, picked by two byte
+// permutes.  The case tables are stored in the same order (case_order).
 // Cells past `nvalid` get case 0.
 __device__ __forceinline__ void cases8(const uint64_t *R, int r00, int j, int nvalid, uint32_t &lo, uint32_t &hi)
 {
-    uint32_t l0, h0, l1, h1, l2, h2, l3, h3;
-    pair_bytes((uint32_t)(R[r00] >> (8 * j)) & 511u, l0, h0);
-    pair_bytes((uint32_t)(R[r00 + 1] >> (8 * j)) & 511u, l1, h1);
-    pair_bytes((uint32_t)(R[r00 + 9] >> (8 * j)) & 511u, l2, h2);
-    pair_bytes((uint32_t)(R[r00 + 10] >> (8 * j)) & 511u, l3, h3);
-    lo = l0 | (l1 << 2) | (l2 << 4) | (l3 << 6);
-    hi = h0 | (h1 << 2) | (h2 << 4) | (h3 << 6);
+    const uint32_t a = (uint32_t)(R[r00] >> (8 * j)) & 511u, b = (uint32_t)(R[r00 + 1] >> (8 * j)) & 511u;
+    const uint32_t c = (uint32_t)(R[r00 + 9] >> (8 * j)) & 511u, d = (uint32_t)(R[r00 + 10] >> (8 * j)) & 511u;
+    const uint32_t q = nib_spread(a) | (nib_spread(b) << 1) | (nib_spread(c) << 2) | (nib_spread(d) << 3);
+    const uint32_t n8 = (a >> 8) | ((b >> 8) << 1) | ((c >> 8) << 2) | ((d >> 8) << 3);  // column 8
+    const uint32_t y = (q >> 4) | (n8 << 28);
+    lo = __byte_perm(q, y, 0x5140);
+    hi = __byte_perm(q, y, 0x7362);
     if (nvalid < 8) {
         const uint64_t keep = (nvalid <= 0) ? 0ull : ((1ull << (8 * nvalid)) - 1ull);
         lo &= (uint32_t)keep;
         hi &= (uint32_t)(keep >> 32);
     }
+}
+
+// The table's case index (corner ox + 2*oy + 4*oz is bit ox + 2*oy + 4*oz)
+// of a case byte in the kernels' order (that corner is bit 4*ox + oy + 2*oz).
+__device__ __forceinline__ int case_order(int c)
+{
+    int r = 0;
+#pragma unroll
+    for (int jc = 0; jc < 8; jc++) {
+        const int ox = jc & 1, oy = (jc >> 1) & 1, oz = jc >> 2;
+        r |= ((c >> (4 * ox + oy + 2 * oz)) & 1) << jc;
+    }
+    return r;
 }
 
 // Bytes of w that are neither 0 nor 0xff (active cells): bit 7 of each byte.
@@ -308,7 +325,7 @@ __device__ __forceinline__ void mc_count_run(const Src &src, uint32_t *err)
     __shared__ uint64_t mbar[2];
     __shared__ uint32_t s_sum[8][kMcIsoPerPass];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    s_cnt[tid] = (uint8_t)(g_mc_case[tid] >> 60);
+    s_cnt[tid] = (uint8_t)(g_mc_case[case_order(tid)] >> 60);
 
     tile_loop(src, err, bufs, mbar, [&](int64_t, int64_t tile, const McParams &p, const float *buf) {
         row_masks<NISO>(buf, s_row, p);
@@ -490,9 +507,9 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
     __shared__ uint32_t s_w[2][9];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float *s_stage = reinterpret_cast<float *>(smem + kEOffStage) + warp * kWarpStage;
-    s_cnt[tid] = (uint8_t)(g_mc_case[tid] >> 60);
+    s_cnt[tid] = (uint8_t)(g_mc_case[case_order(tid)] >> 60);
     for (int i = tid; i < 256 * CHR_MC_MAX_TRI; i += 256) {
-        const uint64_t word = g_mc_case[i / CHR_MC_MAX_TRI];
+        const uint64_t word = g_mc_case[case_order(i / CHR_MC_MAX_TRI)];
         const int t = i % CHR_MC_MAX_TRI;
         uint32_t tri = 0;
         if (t < (int)(word >> 60))
@@ -695,9 +712,9 @@ __global__ void __launch_bounds__(256, 4) k_mc_adjoint(const __grid_constant__ M
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint16_t *s_pre = reinterpret_cast<uint16_t *>(smem + kOffPre);
     float *s_stage = reinterpret_cast<float *>(smem + kOffStage) + warp * kWarpStage;
-    s_cnt[tid] = (uint8_t)(g_mc_case[tid] >> 60);
+    s_cnt[tid] = (uint8_t)(g_mc_case[case_order(tid)] >> 60);
     for (int i = tid; i < 256 * CHR_MC_MAX_TRI; i += 256) {
-        const uint64_t word = g_mc_case[i / CHR_MC_MAX_TRI];
+        const uint64_t word = g_mc_case[case_order(i / CHR_MC_MAX_TRI)];
         const int t = i % CHR_MC_MAX_TRI;
         uint32_t tri = 0;
         if (t < (int)(word >> 60))
