@@ -78,6 +78,13 @@ __device__ __forceinline__ bool encode_step(float f, float Rprev, bool first, fl
 // exception counts.
 constexpr int kEncBricks = 4;  // bricks per block
 
+// The two warps of brick j meet at their own barrier (1 + j): bricks of a
+// block share nothing inside the level loop, so none waits for another.
+__device__ __forceinline__ void brick_sync(int j)
+{
+    asm volatile("bar.sync %0, 64;" ::"r"(1 + j) : "memory");
+}
+
 template <bool FULL>
 __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ CodecParams p)
 {
@@ -192,7 +199,7 @@ __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ Codec
         int32_t below[8];
 #pragma unroll
         for (int x = 0; x < 8; x++) below[x] = __shfl_up_sync(CHR_FULL_MASK, d[x], 8);
-        __syncthreads();
+        brick_sync(j);
         if (lz == 4)
 #pragma unroll
             for (int x = 0; x < 8; x++) below[x] = s_zrow[j][ly][x];
@@ -217,7 +224,7 @@ __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ Codec
             s_red[j][wb][1] = maxn;
             s_red[j][wb][2] = inc;
         }
-        __syncthreads();
+        brick_sync(j);
         maxl = max(s_red[j][0][0], s_red[j][1][0]);
         maxn = max(s_red[j][0][1], s_red[j][1][1]);
         const uint32_t tot0 = s_red[j][0][2];
@@ -254,7 +261,7 @@ __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ Codec
                 if (pos > 0 && (uint32_t)acc) atomicOr(&s_pk[j][wi], (uint32_t)acc);
             }
         }
-        __syncthreads();
+        brick_sync(j);
         {
             uint32_t *dst = p.slot_words[l] + 512ull * c.b;
             const int nw = 16 * w;
@@ -274,7 +281,7 @@ __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ Codec
                 }
             }
         }
-        __syncthreads();  // s_pk, s_zrow and s_red are reused by the next level
+        brick_sync(j);  // s_pk, s_zrow and s_red are reused by the next level
     }
 }
 
