@@ -273,9 +273,32 @@ def adjoint_timing(n=256, seed=256256, reps=10):
     ms = timed(lambda: chr.isosurface_distance_loss(f0, 0.0, pts))
     nb = 2 * 12.0 * 3 * T
     out["isosurface_distance_loss"] = {"ms": ms, "points": 3 * T, "points_per_s": 3 * T / (ms * 1e-3)}
+    peak, peak_kind = measured_peaks()
+    gbps = out["isosurface_backward"]["GBps"]
+    out["roofline"] = {"kernel": "isosurface_backward", "bound": "hbm", "achieved": gbps, "peak": peak,
+                       "unit": "GB/s", "frac": gbps / peak, "peak_kind": peak_kind}
     del f0, R, tris, G, pts, gf
     h.free()
     return out
+
+
+def adjoint_cpu_baseline(n=64, seed=256256):
+    """The oracle's adjoints (single thread) on an n^3 sample of the
+    differentiation field: marching cubes, the position adjoint and the
+    distance loss with its gradient."""
+    import oracle
+    from paper_2408_05462_gb300 import synth
+
+    oracle.build()
+    f = synth.turbulence(n, seed=seed)
+    t0 = time.perf_counter()
+    m = oracle.mc(f, 0.0)
+    L, gp = oracle.dist_loss(f, 0.0, m.pos.reshape(-1, 3))
+    oracle.mc_backward(f, 0.0, gp.reshape(m.pos.shape))
+    dt = time.perf_counter() - t0
+    return {"value": m.ntri / dt, "unit": "triangles/s", "cores": 1, "kind": "oracle",
+            "sample": "%d^3 turbulence, k=0: oracle mc + distance loss + position adjoint, %d triangles, single "
+                      "thread, %.2f s" % (n, m.ntri, dt)}
 
 
 def viz_full_grid(h, n, reps=5):
@@ -318,6 +341,29 @@ def viz_full_grid(h, n, reps=5):
            "error_word": int(err.item())}
     del R, tris, ws
     return out
+
+
+def batched_cpu_baseline(n_boxes=12):
+    """The oracle (single thread) on the smallest boxes of the 256-box
+    workload: encode with the box's bound and k fixed, decode, marching cubes
+    at k; field GB/s over those boxes."""
+    import oracle
+    from paper_2408_05462_gb300 import batched
+
+    specs = sorted(batched.make_specs(256, 256), key=lambda sp: int(np.prod(sp.size)))[:n_boxes]
+    oracle.build()
+    vox = 0
+    t0 = time.perf_counter()
+    for sp in specs:
+        f = batched.box_field(sp)
+        k, eb = batched.box_params(sp, f)
+        R = oracle.decode(oracle.encode(f, [eb], [k], fix=True), 0)
+        oracle.mc_count(R, k)
+        vox += f.size
+    dt = time.perf_counter() - t0
+    return {"value": 4.0 * vox / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": "%d smallest boxes of the workload (%d vertices), oracle encode + decode + marching-cubes "
+                      "count, single thread, %.1f s" % (len(specs), vox, dt)}
 
 
 def serve_measurement(args):
@@ -515,11 +561,18 @@ def main():
                                         "field_GBps": passes * 4.0 * N / (t_ms * 1e-3) / 1e9}
 
     adjoint = None if args.no_adjoint or world > 1 else adjoint_timing()
+    if adjoint is not None and not args.no_cpu_baseline:
+        adjoint["cpu_baseline"] = adjoint_cpu_baseline()
     batch = None
     if not args.no_batched and world == 1:
         from paper_2408_05462_gb300 import batched
 
         batch = batched.measure(256, 256, reps=20)
+        peak, peak_kind = measured_peaks()
+        batch["roofline"] = {"bound": "hbm", "achieved": batch["batched_algorithmic_GBps"], "peak": peak,
+                             "unit": "GB/s", "frac": batch["batched_algorithmic_GBps"] / peak, "peak_kind": peak_kind}
+        if not args.no_cpu_baseline:
+            batch["cpu_baseline"] = batched_cpu_baseline()
     serving = None if args.no_serve or world > 1 else serve_measurement(args)
 
     peak, peak_kind = measured_peaks()

@@ -135,6 +135,10 @@ def measure(n: int = 256, seed: int = 256, reps: int = 20):
     t_plain = _time(plain.run, reps)
     vertices = sum(int(np.prod(sp.size)) for sp in specs)
     total = int(bs[-1])
+    comp = sum(int(h.stats()["level_bytes"][0]) for h, _, _ in items)
+    # decode reads the compressed stream and writes the field; marching cubes
+    # reads the field and writes 36 B per triangle
+    alg = comp + 8.0 * vertices + 36.0 * total
     return {
         "workload": "%d boxes, sides U{32..192}, blobs/turbulence, own k and eb in [1e-4,1e-2] x range, seed %d"
                     % (n, seed),
@@ -145,6 +149,8 @@ def measure(n: int = 256, seed: int = 256, reps: int = 20):
         "per_box_field_GBps": 4.0 * vertices / (t_plain * 1e-3) / 1e9,
         "tuned_config": tuned, "default_config": default_cfg,
         "launches_batched": 7, "launches_per_box": 6 * n,
+        "compressed_bytes": comp, "algorithmic_bytes": alg,
+        "batched_algorithmic_GBps": alg / (t_tuned * 1e-3) / 1e9,
     }
 
 
