@@ -3,11 +3,14 @@
 // Three launches per group of up to 4 isovalues, none of which waits on
 // another block:
 //   k_mc_count  per 32x8x8-cell tile: inside masks by warp ballot, case bytes,
-//               triangle counts per isovalue -> tile_cnt
+//               triangle counts per isovalue -> tile_cnt (and, when the
+//               workspace holds it, the classification for the emit pass)
 //   k_tscan_*   exclusive scan of the tile counts -> tile_off, totals
-//   k_mc_emit   per tile again: case bytes, block scan, triangle -> cell map,
-//               edge interpolation, aligned 16-byte streaming stores at
-//               tile_off + local offset
+//   k_mc_emit   per tile again: the classification (stored, or computed
+//               again), block scan, active cells compacted per isovalue,
+//               triangle -> cell by a 32-triangle window, edge
+//               interpolation, each chunk written at tile_off + local offset
+//               by one TMA bulk store
 // Both tile kernels are persistent (one wave of blocks striding over tiles)
 // and prefetch the next tile's 36x9x9 vertex box with a TMA bulk tensor copy
 // into a second shared-memory buffer while the current tile is processed;
@@ -50,11 +53,6 @@ constexpr int kOffRow = 2 * kBufBytes;                           // uint64 [4][8
 constexpr int kOffCnt = kOffRow + kMcIsoPerPass * kRows * 8;     // uint8 [256] triangles per case
 constexpr int kCountSmem = kOffCnt + 256 + 128;                  // + alignment slack
 constexpr int kOffTri = kOffCnt + 256;                           // uint32 [256][5] edges of each triangle
-constexpr int kOffEdge = kOffTri + 256 * CHR_MC_MAX_TRI * 4;     // EdgeVec [12]
-constexpr int kOffCase = kOffEdge + 12 * 32;                     // uint8 [4][2048] case bytes
-constexpr int kOffPre = kOffCase + kMcIsoPerPass * kCells;       // uint16 [2048] per-cell prefix counts
-constexpr int kOffStage = kOffPre + kCells * 2;                  // float [8][32*9+4]
-constexpr int kAdjSmem = kOffStage + 8 * kWarpStage * 4 + 128;   // adjoint kernel (+ alignment slack)
 
 // dynamic shared memory of the emit kernel (bytes)
 constexpr int kMaxChunks = kCells * CHR_MC_MAX_TRI / 32;           // 32-triangle chunks per tile and isovalue
@@ -374,35 +372,6 @@ __global__ void __launch_bounds__(256) k_mc_count_batched(const __grid_constant_
     mc_count_run<1>(SrcMany{&b}, err);
 }
 
-// Edge e of a cell: the float offsets (ox, oy, oz) of its lower corner, the
-// corner's offset in the box, the unit vector along the edge, and the box
-// step to the upper corner.  A crossing at parameter t then sits at
-// fma(t, dir, cell + off), i.e. (cell + off) + t along the edge axis.
-struct __align__(16) EdgeVec {
-    float ox, oy, oz;
-    int delta;
-    float dx, dy, dz;
-    int step;
-};
-
-__device__ __forceinline__ EdgeVec edge_vec(int e)
-{
-    const int axis = e >> 2, m = e & 3;
-    const int ox = (axis == 0) ? 0 : (m & 1);
-    const int oy = (axis == 1) ? 0 : ((axis == 0) ? (m & 1) : (m >> 1));
-    const int oz = (axis == 2) ? 0 : (m >> 1);
-    EdgeVec v;
-    v.ox = (float)ox;
-    v.oy = (float)oy;
-    v.oz = (float)oz;
-    v.delta = ox + oy * kVX + oz * kPlane;
-    v.dx = (axis == 0) ? 1.0f : 0.0f;
-    v.dy = (axis == 1) ? 1.0f : 0.0f;
-    v.dz = (axis == 2) ? 1.0f : 0.0f;
-    v.step = (axis == 0) ? 1 : (axis == 1) ? kVX : kPlane;
-    return v;
-}
-
 // t = (k - f0) / (f1 - f0): the edge parameter of a crossing.  f0 and f1 lie
 // on opposite sides of k, so the quotient is in (0, 1]; the fast reciprocal
 // quotient is within 2 ulp of the rounded one, and the IEEE quotient is used
@@ -413,24 +382,6 @@ __device__ __forceinline__ float edge_t(float k, float f0, float f1)
     return (fabsf(den) < 8.5e37f) ? __fdividef(num, den) : __fdiv_rn(num, den);
 }
 
-// Triangle `tri` (three edge numbers, one per byte) of cell c (tile-local
-// index) into dst[0..8].
-__device__ __forceinline__ void make_triangle(float *dst, const float *box, const EdgeVec *s_edge, uint32_t tri, int c,
-                                              float k, float fx0, float fy0, float fz0)
-{
-    const int lx = c & 7, tt = c >> 3, ly = tt & 7, lz = (tt >> 3) & 7, j = tt >> 6;
-    const float *cell = box + lz * kPlane + ly * kVX + 8 * j + lx;
-    const float cx = fx0 + (float)(8 * j + lx), cy = fy0 + (float)ly, cz = fz0 + (float)lz;
-#pragma unroll
-    for (int v = 0; v < 3; v++) {
-        const EdgeVec E = s_edge[(tri >> (8 * v)) & 0xffu];
-        const float *p0 = cell + E.delta;
-        const float tv = edge_t(k, p0[0], p0[E.step]);
-        dst[3 * v + 0] = __fmaf_rn(tv, E.dx, cx + E.ox);
-        dst[3 * v + 1] = __fmaf_rn(tv, E.dy, cy + E.oy);
-        dst[3 * v + 2] = __fmaf_rn(tv, E.dz, cz + E.oz);
-    }
-}
 
 // Edge e of a cell as one word for the emit pass: bits 0-10 the byte offset
 // of its lower corner in the box, 11-21 the byte step to its upper corner,
@@ -673,7 +624,8 @@ __global__ void __launch_bounds__(256, 4) k_mc_emit_batched(const __grid_constan
 // t = (k - f0)/(f1 - f0): dp_axis/df0 = (t - 1)/(f1 - f0) and
 // dp_axis/df1 = -t/(f1 - f0); the other coordinates do not depend on the
 // field.  The adjoint walks the triangles in exactly the emit order (same
-// tiles, scan and search), reads dL/dp where the forward pass wrote p, and
+// tiles, classification, compaction and window), reads dL/dp where the
+// forward pass wrote p, and
 // adds each contribution to both edge ends.  Sums are made deterministic by
 // fixed-point int64 atomics: pass 0 finds the largest |contribution|, pass 1
 // adds round(c * S) with S = 2^(52 - exponent of that maximum), so every
@@ -694,6 +646,9 @@ __device__ __forceinline__ double adj_scale(unsigned int maxbits)
     return ldexp(1.0, 52 - ilogbf(m));
 }
 
+// The adjoint walks each tile and isovalue exactly like the emit pass (the
+// count pass's classification, the compacted active cells, the chunk window)
+// so lane m of a chunk meets triangle m of the forward output.
 template <int NISO>
 __global__ void __launch_bounds__(256, 4) k_mc_adjoint(const __grid_constant__ McParams p,
                                                       const __grid_constant__ AdjParams a,
@@ -702,16 +657,15 @@ __global__ void __launch_bounds__(256, 4) k_mc_adjoint(const __grid_constant__ M
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     float *bufs = reinterpret_cast<float *>(smem + kOffBuf);
-    uint64_t *s_row = reinterpret_cast<uint64_t *>(smem + kOffRow);
     uint8_t *s_cnt = smem + kOffCnt;
     uint32_t *s_tri = reinterpret_cast<uint32_t *>(smem + kOffTri);
-    EdgeVec *s_edge = reinterpret_cast<EdgeVec *>(smem + kOffEdge);
-    uint8_t *s_case = smem + kOffCase;
+    uint32_t *s_edgew = reinterpret_cast<uint32_t *>(smem + kEOffEdge);
+    uint32_t *s_act = reinterpret_cast<uint32_t *>(smem + kEOffAct);
+    uint16_t *s_apre = reinterpret_cast<uint16_t *>(smem + kEOffAPre);
+    uint16_t *s_chunk = reinterpret_cast<uint16_t *>(smem + kEOffChunk);
     __shared__ uint64_t mbar[2];
-    __shared__ uint64_t s_warp[9];
+    __shared__ uint32_t s_w[2][9];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    uint16_t *s_pre = reinterpret_cast<uint16_t *>(smem + kOffPre);
-    float *s_stage = reinterpret_cast<float *>(smem + kOffStage) + warp * kWarpStage;
     s_cnt[tid] = (uint8_t)(g_mc_case[case_order(tid)] >> 60);
     for (int i = tid; i < 256 * CHR_MC_MAX_TRI; i += 256) {
         const uint64_t word = g_mc_case[case_order(i / CHR_MC_MAX_TRI)];
@@ -721,109 +675,97 @@ __global__ void __launch_bounds__(256, 4) k_mc_adjoint(const __grid_constant__ M
             for (int v = 0; v < 3; v++) tri |= (uint32_t)((word >> (12 * t + 4 * v)) & 15u) << (8 * v);
         s_tri[i] = tri;
     }
-    if (tid < 12) s_edge[tid] = edge_vec(tid);
+    if (tid < 12) s_edgew[tid] = edge_word(tid);
     const double S = (a.pass == 1) ? adj_scale(*a.maxbits) : 1.0;
     float lane_max = 0.0f;
+    const int64_t step_g[3] = {1, p.nx, p.nx * p.ny};
 
     tile_loop(SrcOne{&p, &map}, p.err, bufs, mbar, [&](int64_t, int64_t tile, const McParams &, const float *box) {
-        row_masks<NISO>(box, s_row, p);
-        __syncthreads();
         const TileXYZ o = tile_origin(p, tile);
-        const int nvalid = valid_cells(p, o);
-        const int j = tid >> 6, ly = tid & 7, lz = (tid >> 3) & 7;
-        const int r00 = lz * 9 + ly;
-        uint64_t packed = 0;
-#pragma unroll
-        for (int i = 0; i < NISO; i++) {
-            uint32_t lo, hi;
-            cases8(s_row + i * kRows, r00, j, nvalid, lo, hi);
-            uint32_t cnt = 0;
-#pragma unroll
-            for (int x = 0; x < 4; x++) cnt += s_cnt[(lo >> (8 * x)) & 0xffu] + s_cnt[(hi >> (8 * x)) & 0xffu];
-            *reinterpret_cast<uint2 *>(s_case + i * kCells + tid * 8) = make_uint2(lo, hi);
-            packed |= (uint64_t)cnt << (16 * i);
-        }
-        const uint64_t inc = warp_incl_scan_u64(packed, lane);
-        if (lane == 31) s_warp[warp] = inc;
-        __syncthreads();
-        if (warp == 0) {
-            const uint64_t t = (lane < 8) ? s_warp[lane] : 0ull;
-            const uint64_t ti = warp_incl_scan_u64(t, lane);
-            if (lane < 8) s_warp[lane] = ti - t;
-            if (lane == 7) s_warp[8] = ti;
-        }
-        __syncthreads();
-        const uint64_t thread_excl = s_warp[warp] + inc - packed;
-        const uint64_t block_total = s_warp[8];
+        const uint32_t boxB = smem_addr(box);
+        const size_t at0 = (size_t)tile * p.cstride * 256 + tid;
+        uint2 cw_next = __ldg(p.cases + at0);
+        uint32_t pk_next = __ldg(p.tcnt + at0);
 
 #pragma unroll 1
         for (int i = 0; i < NISO; i++) {
-            const int n = (int)((block_total >> (16 * i)) & 0xffffull);
-            if (n == 0) continue;
+            const uint32_t lo = cw_next.x, hi = cw_next.y, packed = pk_next;
+            if (i + 1 < NISO) {
+                cw_next = __ldg(p.cases + at0 + 256 * (i + 1));
+                pk_next = __ldg(p.tcnt + at0 + 256 * (i + 1));
+            }
+            const uint32_t inc = warp_incl_scan_u32(packed, lane);
+            uint32_t *sw = s_w[i & 1];
+            if (lane == 31) sw[warp] = inc;
+            __syncthreads();
+            if (warp == 0) {
+                const uint32_t t = (lane < 8) ? sw[lane] : 0u;
+                const uint32_t ti = warp_incl_scan_u32(t, lane);
+                if (lane < 8) sw[lane] = ti - t;
+                if (lane == 7) sw[8] = ti;
+            }
+            __syncthreads();
+            const uint32_t excl = sw[warp] + inc - packed, total = sw[8];
+            const int n = (int)(total & 0xffffu);
+            if (n == 0) continue;  // uniform across the block
             {
-                const uint2 cw = *reinterpret_cast<const uint2 *>(s_case + i * kCells + tid * 8);
-                uint32_t run = (uint32_t)((thread_excl >> (16 * i)) & 0xffffull);
-                uint32_t pk[4];
+                uint32_t ai = excl >> 16, pre = excl & 0xffffu;
 #pragma unroll
-                for (int x = 0; x < 8; x += 2) {
-                    const uint32_t c0 = ((x < 4 ? cw.x : cw.y) >> (8 * (x & 3))) & 0xffu;
-                    const uint32_t c1 = ((x < 4 ? cw.x : cw.y) >> (8 * ((x + 1) & 3))) & 0xffu;
-                    const uint32_t a0 = run;
-                    run += s_cnt[c0];
-                    pk[x >> 1] = a0 | (run << 16);
-                    run += s_cnt[c1];
+                for (int x = 0; x < 8; x++) {
+                    const uint32_t cb = ((x < 4 ? lo : hi) >> (8 * (x & 3))) & 0xffu;
+                    const uint32_t c = s_cnt[cb];
+                    if (c) {
+                        s_act[ai] = (uint32_t)(tid * 8 + x) | (cb << 11);
+                        s_apre[ai] = (uint16_t)pre;
+                        const uint32_t q = (pre + 31u) >> 5;
+                        if ((q << 5) < pre + c) s_chunk[q] = (uint16_t)ai;
+                        ai++;
+                        pre += c;
+                    }
                 }
-                *reinterpret_cast<uint4 *>(s_pre + tid * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                if (tid < 32) s_apre[(total >> 16) + tid] = 0xffffu;
             }
             __syncthreads();
             const uint64_t g0 = __ldg(p.tile_off + tile * kMcIsoPerPass + i);
             const float k = p.k[i];
             const int lim = (g0 >= p.cap) ? 0 : (int)((p.cap - g0) < (uint64_t)n ? (p.cap - g0) : (uint64_t)n);
             const float *gin = a.grad[i] + 9ull * g0;
-            const uint8_t *icase = s_case + i * kCells;
-            for (int base = warp * 32; base < lim; base += 8 * 32) {
-                const int mm = (lim - base) < 32 ? (lim - base) : 32;
-                const float *src = gin + 9 * base;
-                const int pad = (int)((reinterpret_cast<uintptr_t>(src) >> 2) & 3u);
-                // s_stage[pad + q] = src[q]: the same alignment split as the forward stores
-                const int F = 9 * mm;
-                const int head = min((4 - pad) & 3, F);
-                if (lane < head) s_stage[pad + lane] = __ldg(src + lane);
-                const int nbody = (F - head) >> 2;
-                const float4 *src4 = reinterpret_cast<const float4 *>(src + head);
-                float4 *dst4 = reinterpret_cast<float4 *>(s_stage + pad + head);
-                for (int q = lane; q < nbody; q += 32) dst4[q] = ld_stream_f4(src4 + q);
-                const int tail0 = head + 4 * nbody;
-                if (lane < F - tail0) s_stage[pad + tail0 + lane] = __ldg(src + tail0 + lane);
-                __syncwarp();
-                if (lane < mm) {
-                    const int m = base + lane;
-                    int c = 0;
-#pragma unroll
-                    for (int step = 1024; step > 0; step >>= 1)
-                        if ((int)s_pre[c + step] <= m) c += step;
-                    const int t = m - (int)s_pre[c];
-                    const uint32_t tri = s_tri[icase[c] * CHR_MC_MAX_TRI + t];
-                    const int lx = c & 7, tt = c >> 3, cly = tt & 7, clz = (tt >> 3) & 7, cj = tt >> 6;
-                    const float *cell = box + clz * kPlane + cly * kVX + 8 * cj + lx;
-                    const int64_t gx = o.x0 + 8 * cj + lx, gy = o.y0 + cly, gz = o.z0 + clz;
-                    const float *g9 = s_stage + pad + 9 * lane;
+            for (int q = warp; 32 * q < lim; q += 8) {
+                const int base = 32 * q;
+                const int a_lo = s_chunk[q];
+                const int s0 = (int)s_apre[a_lo + lane] - base;
+                const uint32_t mark = (s0 > 0 && s0 < 32) ? (1u << s0) : 0u;
+                const uint32_t starts = __reduce_or_sync(CHR_FULL_MASK, mark);
+                const int jj = __popc(starts & (0xffffffffu >> (31 - lane)));
+                const int m = base + lane;
+                if (m < lim) {
+                    const int aa = a_lo + jj;
+                    const uint32_t e = s_act[aa];
+                    const int t = m - (int)s_apre[aa];
+                    const uint32_t tri = s_tri[(e >> 11) * CHR_MC_MAX_TRI + t];
+                    const uint32_t c = e & 2047u;
+                    const uint32_t lx = c & 7u, cly = (c >> 3) & 7u, clz = (c >> 6) & 7u, jb = c >> 9;
+                    const uint32_t cellB = boxB + 4u * (clz * kPlane + cly * kVX + 8u * jb + lx);
+                    const int64_t gx = o.x0 + 8 * jb + lx, gy = o.y0 + cly, gz = o.z0 + clz;
+                    const float *g9 = gin + 9ull * m;
 #pragma unroll
                     for (int v = 0; v < 3; v++) {
-                        const EdgeVec E = s_edge[(tri >> (8 * v)) & 0xffu];
-                        const float *p0 = cell + E.delta;
-                        const float f0 = p0[0], f1 = p0[E.step];
+                        const uint32_t E = s_edgew[(tri >> (8 * v)) & 0xffu];
+                        const uint32_t a0 = cellB + (E & 0x7ffu);
+                        const float f0 = lds_f32(a0), f1 = lds_f32(a0 + ((E >> 11) & 0x7ffu));
                         const float tv = edge_t(k, f0, f1);
-                        const int axis = (E.dx != 0.0f) ? 0 : (E.dy != 0.0f) ? 1 : 2;
-                        const float gax = g9[3 * v + axis];
+                        const int axis = (E & (1u << 27)) ? 0 : (E & (1u << 28)) ? 1 : 2;
+                        const float gax = __ldg(g9 + 3 * v + axis);
                         const float inv = 1.0f / __fsub_rn(f1, f0);
                         const float c0 = gax * (tv - 1.0f) * inv, c1 = -gax * tv * inv;
                         if (a.pass == 0) {
                             if (isfinite(c0)) lane_max = fmaxf(lane_max, fabsf(c0));
                             if (isfinite(c1)) lane_max = fmaxf(lane_max, fabsf(c1));
                         } else {
-                            const int64_t i0 = (gx + (int64_t)E.ox) + p.nx * ((gy + (int64_t)E.oy) + p.ny * (gz + (int64_t)E.oz));
-                            const int64_t i1 = i0 + ((axis == 0) ? 1 : (axis == 1) ? p.nx : p.nx * p.ny);
+                            const int64_t i0 = (gx + (int64_t)((E >> 24) & 1u)) +
+                                               p.nx * ((gy + (int64_t)((E >> 25) & 1u)) +
+                                                       p.ny * (gz + (int64_t)((E >> 26) & 1u)));
+                            const int64_t i1 = i0 + step_g[axis];
                             if (isfinite(c0))
                                 atomicAdd(a.acc + i0, (unsigned long long)(long long)llrint((double)c0 * S));
                             if (isfinite(c1))
@@ -831,9 +773,8 @@ __global__ void __launch_bounds__(256, 4) k_mc_adjoint(const __grid_constant__ M
                         }
                     }
                 }
-                __syncwarp();
             }
-            __syncthreads();
+            __syncthreads();  // the compacted lists are rewritten for the next isovalue
         }
     });
     if (a.pass == 0) {
@@ -1062,7 +1003,7 @@ static cudaError_t mc_prepare(McGrids &out)
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(k_mc_emit<NISO, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_mc_adjoint<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAdjSmem);
+        e = cudaFuncSetAttribute(k_mc_adjoint<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(k_mc_count<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCountSmem);
         if (e != cudaSuccess) return e;
@@ -1071,7 +1012,7 @@ static cudaError_t mc_prepare(McGrids &out)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bc, k_mc_count<NISO>, 256, kCountSmem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&be, k_mc_emit<NISO, true>, 256, kEmitSmem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_mc_emit<NISO, false>, 256, kEmitSmem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ba, k_mc_adjoint<NISO>, 256, kAdjSmem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ba, k_mc_adjoint<NISO>, 256, kEmitSmem);
         G.count = sms * (bc > 0 ? bc : 1);
         G.emit_compact = sms * (bf > 0 ? bf : 1);
         G.adjoint = sms * (ba > 0 ? ba : 1);
@@ -1137,7 +1078,7 @@ static cudaError_t launch_adjoint_group(const McParams &p, const AdjParams &a, c
     cudaError_t e = mc_prepare<NISO>(G);
     if (e != cudaSuccess) return e;
     const unsigned ge = (unsigned)(p.ntiles < G.adjoint ? p.ntiles : G.adjoint);
-    k_mc_adjoint<NISO><<<ge, 256, kAdjSmem, s>>>(p, a, map);
+    k_mc_adjoint<NISO><<<ge, 256, kEmitSmem, s>>>(p, a, map);
     return cudaGetLastError();
 }
 
@@ -1195,7 +1136,7 @@ cudaError_t launch_mc_pitched(const float *field, const Grid &g, int64_t sx, int
 
 size_t mc_adjoint_workspace_bytes(const Grid &g, int n_iso)
 {
-    const size_t base = ((mc_workspace_min_bytes(g, n_iso) + 255) / 256) * 256;
+    const size_t base = ((mc_workspace_bytes(g, n_iso) + 255) / 256) * 256;
     return base + (size_t)g.N * 8 + 256;
 }
 
@@ -1213,11 +1154,15 @@ cudaError_t launch_mc_adjoint(const float *field, const Grid &g, const float *is
     mc_tiles(g, p.ntx, p.ncby, p.ncbz, p.ntiles);
     p.cap = cap;
     p.err = nullptr;
+    const int cstride = stored_slots(n_iso);
     McWorkspace w;
-    mc_layout(g, 0, workspace, &w);
+    mc_layout(g, cstride, workspace, &w);
     p.tile_cnt = w.cnt;
     p.tile_off = w.off;
-    const size_t base = ((mc_workspace_min_bytes(g, n_iso) + 255) / 256) * 256;
+    p.cases = w.cases;
+    p.tcnt = w.tcnt;
+    p.cstride = cstride;
+    const size_t base = ((mc_workspace_bytes(g, n_iso) + 255) / 256) * 256;
     AdjParams a;
     memset(&a, 0, sizeof(a));
     a.acc = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(workspace) + base);
