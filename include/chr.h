@@ -163,6 +163,18 @@ chr_status chr_serve_request(const chr_handle *h, uint32_t level, int64_t x0, in
                              void *stream);
 
 /*
+ * chr_box_tri_bound — host-side upper bound on the triangles of the box
+ * [x0, x0+box.nx) x [y0, ...) x [z0, ...) at `isovalue`, from a per-brick
+ * index on the host: h_min/h_max [nbz][nby][nbx] hold each brick's value
+ * range widened by its +x, +y and +z neighbours (the vertices its cells
+ * touch, as from chr_brick_range).  Counts 5 triangles for every cell of
+ * the box in a brick whose range straddles the isovalue (min < k <= max);
+ * 0 for bad arguments.  No device work.
+ */
+uint64_t chr_box_tri_bound(const float *h_min, const float *h_max, int64_t nbx, int64_t nby, int64_t nbz, int64_t x0,
+                           int64_t y0, int64_t z0, chr_dims box, float isovalue);
+
+/*
  * chr_brick_range — per-brick value range of level `level`: d_range
  * (caller-owned, 2 floats per 8^3 brick, brick (bx, by, bz) at index
  * bx + nbx*(by + nby*bz), nbx = ceil(nx/8) and so on) receives the (min, max)

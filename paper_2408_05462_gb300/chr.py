@@ -7,7 +7,7 @@ to the library as a chr_allocator) and the current CUDA stream.  There is no
 CPU path: if libchr.so is missing or cannot load, every call raises.
 
 Names follow the C ABI: chr_compress, chr_reconstruct, chr_reconstruct_box, chr_brick_range,
-chr_serve_request, chr_serve_request_bytes,
+chr_serve_request, chr_serve_request_bytes, chr_box_tri_bound,
 chr_topo_translate,
 isosurface_extract, isosurface_workspace_size, isosurface_workspace_min_size, isosurface_extract_noalloc,
 isosurface_backward, isosurface_distance_loss, chr_serialize, chr_deserialize,
@@ -102,6 +102,9 @@ def lib():
         L.chr_serve_request.restype = st
         L.chr_serve_request.argtypes = [c_void_p, c_uint32, c_int64, c_int64, c_int64, ChrDims, c_float, c_void_p,
                                         c_size_t, c_uint64, c_void_p, c_void_p]
+        L.chr_box_tri_bound.restype = c_uint64
+        L.chr_box_tri_bound.argtypes = [c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int64, c_int64, c_int64,
+                                        ChrDims, c_float]
         L.chr_brick_range.restype = st
         L.chr_brick_range.argtypes = [c_void_p, c_uint32, c_void_p, c_void_p]
         L.chr_topo_translate.restype = st
@@ -302,6 +305,16 @@ def chr_serve_request(h: Chr, level: int, origin, size, isovalue: float, mem: to
         raise ValueError("result must be a contiguous int64 CPU tensor of 2")
     _check(lib().chr_serve_request(h.ptr, int(level), x0, y0, z0, ChrDims(bx, by, bz), float(isovalue),
                                    mem.data_ptr(), mem.numel(), int(cap), result.data_ptr(), _stream(stream)))
+
+
+def chr_box_tri_bound(mn, mx, origin, size, isovalue: float) -> int:
+    """Triangle bound of a box from a host brick index (chr.h:
+    chr_box_tri_bound); mn, mx: contiguous float32 numpy arrays [nbz, nby, nbx]."""
+    nbz, nby, nbx = mn.shape
+    x0, y0, z0 = (int(v) for v in origin)
+    bx, by, bz = (int(v) for v in size)
+    return int(lib().chr_box_tri_bound(mn.ctypes.data, mx.ctypes.data, nbx, nby, nbz, x0, y0, z0,
+                                       ChrDims(bx, by, bz), float(isovalue)))
 
 
 def chr_brick_range(h: Chr, level: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:

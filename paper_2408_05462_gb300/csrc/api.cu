@@ -431,6 +431,41 @@ ServeLayout serve_layout(chr_dims box, uint64_t cap_tris)
 
 }  // namespace
 
+uint64_t chr_box_tri_bound(const float *h_min, const float *h_max, int64_t nbx, int64_t nby, int64_t nbz, int64_t x0,
+                           int64_t y0, int64_t z0, chr_dims box, float isovalue)
+{
+    if (!h_min || !h_max || nbx < 1 || nby < 1 || nbz < 1 || box.nx < 2 || box.ny < 2 || box.nz < 2 || x0 < 0 ||
+        y0 < 0 || z0 < 0)
+        return 0;
+    // cells [o, o + n - 1) along each axis; brick b holds cells [8b, 8b + 8)
+    const int64_t o[3] = {x0, y0, z0}, n[3] = {box.nx, box.ny, box.nz}, nb[3] = {nbx, nby, nbz};
+    int64_t b0[3], b1[3];
+    for (int a = 0; a < 3; a++) {
+        b0[a] = o[a] / 8;
+        b1[a] = (o[a] + n[a] - 2) / 8 + 1;
+        if (b1[a] > nb[a]) b1[a] = nb[a];
+        if (b0[a] >= b1[a]) return 0;
+    }
+    auto cells = [&](int a, int64_t b) {
+        const int64_t lo = (8 * b > o[a]) ? 8 * b : o[a];
+        const int64_t hi = (8 * b + 8 < o[a] + n[a] - 1) ? 8 * b + 8 : o[a] + n[a] - 1;
+        return hi - lo;
+    };
+    uint64_t total = 0;
+    for (int64_t bz = b0[2]; bz < b1[2]; bz++) {
+        const int64_t cz = cells(2, bz);
+        for (int64_t by = b0[1]; by < b1[1]; by++) {
+            const int64_t cyz = cz * cells(1, by);
+            const float *mn = h_min + nbx * (by + nby * bz), *mx = h_max + nbx * (by + nby * bz);
+            uint64_t row = 0;
+            for (int64_t bx = b0[0]; bx < b1[0]; bx++)
+                if (mn[bx] < isovalue && mx[bx] >= isovalue) row += (uint64_t)cells(0, bx);
+            total += row * (uint64_t)cyz;
+        }
+    }
+    return 5 * total;
+}
+
 size_t chr_serve_request_bytes(chr_dims box, uint64_t cap_tris)
 {
     std::string why;

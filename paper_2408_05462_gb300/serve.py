@@ -83,18 +83,6 @@ def dilate_range(rng: np.ndarray):
     return mn, mx
 
 
-def _cells_per_brick(o: int, s: int, nb: int):
-    """Brick range and the number of the box's cells in each brick along one
-    axis: the box [o, o+s) of vertices has cells o .. o+s-2."""
-    if s < 2:
-        return 0, 0, np.zeros(0, np.int64)
-    c0, c1 = o, o + s - 1  # cells [c0, c1)
-    b0, b1 = c0 // 8, (c1 - 1) // 8 + 1
-    starts = np.maximum(np.arange(b0, b1) * 8, c0)
-    ends = np.minimum(np.arange(b0, b1) * 8 + 8, c1)
-    return b0, b1, (ends - starts).astype(np.int64)
-
-
 @dataclass
 class Timestep:
     step: int
@@ -105,17 +93,7 @@ class Timestep:
 
     def tri_bound(self, level: int, k: float, origin, size) -> int:
         mn, mx = self.index[level]
-        rx = _cells_per_brick(origin[0], size[0], mn.shape[2])
-        ry = _cells_per_brick(origin[1], size[1], mn.shape[1])
-        rz = _cells_per_brick(origin[2], size[2], mn.shape[0])
-        if min(len(rx[2]), len(ry[2]), len(rz[2])) == 0:
-            return 0
-        sl = (slice(rz[0], rz[1]), slice(ry[0], ry[1]), slice(rx[0], rx[1]))
-        k32 = np.float32(k)
-        act = ((mn[sl] < k32) & (mx[sl] >= k32)).astype(np.float64)
-        # sum over bricks of active * cells-in-box, one axis at a time (exact in float64)
-        cells = float(((act @ rx[2].astype(np.float64)) @ ry[2].astype(np.float64)) @ rz[2].astype(np.float64))
-        return int(cells) * MAX_TRIS_PER_CELL
+        return chr.chr_box_tri_bound(mn, mx, origin, size, k)
 
 
 @dataclass

@@ -2,8 +2,15 @@
 triangle bound of a box against brute force over a field, and the request
 generator.  No GPU."""
 import numpy as np
+import pytest
 
-from paper_2408_05462_gb300 import serve, synth
+from paper_2408_05462_gb300 import build as chr_build
+from paper_2408_05462_gb300 import chr, serve, synth
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    chr_build.build()  # the native bound lives in libchr; nvcc builds it without a GPU
 
 
 def _range_index(f):
@@ -35,12 +42,34 @@ def _timestep(f):
     return serve.Timestep(0, None, f.shape, [serve.dilate_range(_range_index(f))], 0)
 
 
-def test_cells_per_brick():
-    b0, b1, n = serve._cells_per_brick(5, 20, 4)  # vertices 5..24, cells 5..23
-    assert (b0, b1) == (0, 3) and n.tolist() == [3, 8, 8] and n.sum() == 19
-    assert serve._cells_per_brick(0, 1, 4)[2].size == 0
-    b0, b1, n = serve._cells_per_brick(8, 9, 4)  # cells 8..15: one brick
-    assert (b0, b1) == (1, 2) and n.tolist() == [8]
+def _bound_reference(mn, mx, origin, size, k):
+    """The bound written out with numpy: 5 x the box's cells in bricks whose
+    widened range straddles k."""
+    total = 0
+    per_axis = []
+    for a, nb in zip(range(3), (mn.shape[2], mn.shape[1], mn.shape[0])):
+        o, n = origin[a], size[a]
+        cells = np.zeros(nb, np.int64)
+        for c in range(o, o + n - 1):
+            cells[c // 8] += 1
+        per_axis.append(cells)
+    act = (mn < np.float32(k)) & (mx >= np.float32(k))
+    total = np.einsum("zyx,z,y,x->", act.astype(np.int64), per_axis[2], per_axis[1], per_axis[0])
+    return 5 * int(total)
+
+
+def test_native_bound_equals_the_reference():
+    g = np.random.Generator(np.random.PCG64(4))
+    for shape in [(5, 7, 9), (1, 1, 1), (3, 1, 4)]:
+        mid = g.normal(size=shape).astype(np.float32)
+        mn, mx = (mid - 0.4).astype(np.float32), (mid + 0.4).astype(np.float32)
+        nbz, nby, nbx = shape
+        for _ in range(50):
+            size = tuple(int(g.integers(2, 8 * s + 1)) for s in (nbx, nby, nbz))
+            org = tuple(int(g.integers(0, 8 * s - b + 1)) for s, b in zip((nbx, nby, nbz), size))
+            k = float(g.uniform(-1.5, 1.5))
+            assert chr.chr_box_tri_bound(mn, mx, org, size, k) == _bound_reference(mn, mx, org, size, k)
+    assert chr.chr_box_tri_bound(mn, mx, (0, 0, 0), (1, 4, 4), 0.0) == 0
 
 
 def test_tri_bound_covers_every_active_cell():
