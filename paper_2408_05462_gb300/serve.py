@@ -26,7 +26,7 @@ import argparse
 import json
 import time
 from collections import OrderedDict, deque
-from dataclasses import dataclass, field as dc_field
+from dataclasses import dataclass
 
 import numpy as np
 import torch
@@ -100,21 +100,66 @@ class Timestep:
 class _Flight:
     req: Request
     slot: int
-    nbytes: int
+    block: tuple  # (offset, bytes) in the arena; the triangles come first
     bound: int
     admit_ms: float
     done: torch.cuda.Event
     count_host: torch.Tensor  # pinned (triangle count, error word)
-    tris: torch.Tensor | None  # the request's device memory, triangles first (keep_results)
-    keep: list = dc_field(default_factory=list)  # buffers alive until done
+    keep_results: bool
+
+
+class FreeList:
+    """First-fit allocation of byte ranges in 256-byte units, with freed
+    ranges merged back into their neighbours."""
+
+    def __init__(self, size: int):
+        self.size = int(size)
+        self.free = [(0, self.size)]  # (offset, bytes), sorted by offset, coalesced
+
+    def alloc(self, nbytes: int):
+        n = (int(nbytes) + 255) & ~255
+        for i, (off, size) in enumerate(self.free):
+            if size >= n:
+                if size == n:
+                    del self.free[i]
+                else:
+                    self.free[i] = (off + n, size - n)
+                return off, n
+        return None
+
+    def release(self, off: int, n: int):
+        i = 0
+        while i < len(self.free) and self.free[i][0] < off:
+            i += 1
+        self.free.insert(i, (off, n))
+        if i + 1 < len(self.free) and off + n == self.free[i + 1][0]:  # merge with the next range
+            self.free[i] = (off, n + self.free[i + 1][1])
+            del self.free[i + 1]
+        if i > 0 and self.free[i - 1][0] + self.free[i - 1][1] == self.free[i][0]:  # and the previous one
+            self.free[i - 1] = (self.free[i - 1][0], self.free[i - 1][1] + self.free[i][1])
+            del self.free[i]
+
+
+class Arena(FreeList):
+    """The requests' device memory: one allocation made once and handed out
+    by the free list, so serving never calls the device allocator."""
+
+    def __init__(self, nbytes: int):
+        super().__init__(nbytes)
+        self.buf = torch.empty(self.size, dtype=torch.uint8, device="cuda")
+
+    def view(self, off: int, n: int) -> torch.Tensor:
+        return self.buf[off:off + n]
 
 
 class Server:
     """Resident CHR timesteps and a continuous-batching request loop.
 
     budget_bytes bounds the device memory of the requests in flight (box
-    fields, workspaces and triangle capacity); the resident CHRs are counted
-    in `resident_bytes` and limited by max_resident timesteps."""
+    fields, workspaces and triangle capacity): it is the size of the arena the
+    requests' memory comes from, allocated at the first run.  The resident
+    CHRs are counted in `resident_bytes` and limited by max_resident
+    timesteps."""
 
     def __init__(self, budget_bytes: int = 96 << 30, slots: int = 4, max_resident: int = 2,
                  levels_rel=LEVELS_REL, fix_isovalues=FIX_ISOVALUES):
@@ -127,6 +172,7 @@ class Server:
         self.fix_isovalues = tuple(fix_isovalues)
         self.steps: OrderedDict[int, Timestep] = OrderedDict()
         self._slot_bufs = []
+        self.arena = None
         self.host_ms = 0.0  # host time spent on admission and launches in the last run
 
     def _bufs(self, slot: int):
@@ -144,6 +190,7 @@ class Server:
         other.streams = self.streams[:slots] if slots <= len(self.streams) else \
             self.streams + [torch.cuda.Stream() for _ in range(slots - len(self.streams))]
         other._slot_bufs = []
+        other.arena = None
         return other
 
     @property
@@ -172,17 +219,17 @@ class Server:
     def request_bytes(self, req: Request, bound: int) -> int:
         return chr.chr_serve_request_bytes(req.size, max(bound, 1))
 
-    def _launch(self, req: Request, slot: int, bound: int, nbytes: int, t0: float, keep_results: bool) -> _Flight:
+    def _launch(self, req: Request, slot: int, bound: int, block, t0: float, keep_results: bool) -> _Flight:
         ts = self.steps[req.step]
         s = self.streams[slot]
         result = self._bufs(slot)
+        mem = self.arena.view(*block)
         with torch.cuda.stream(s):
-            mem = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
             chr.chr_serve_request(ts.handle, req.level, req.origin, req.size, req.k, mem, bound, result, stream=s)
             done = torch.cuda.Event(enable_timing=True)
             done.record(s)
         admit_ms = (time.perf_counter() - t0) * 1e3
-        return _Flight(req, slot, nbytes, bound, admit_ms, done, result, mem if keep_results else None, [mem])
+        return _Flight(req, slot, block, bound, admit_ms, done, result, keep_results)
 
     # ---- the loop ---------------------------------------------------------
     def run(self, requests, keep_results: bool = False, poll_s: float = 20e-6):
@@ -198,11 +245,13 @@ class Server:
             if min(r.size) < 2 or any(o < 0 for o in r.origin) or r.origin[0] + r.size[0] > nx or \
                     r.origin[1] + r.size[1] > ny or r.origin[2] + r.size[2] > nz:
                 raise ValueError("request %d: box outside the grid" % r.rid)
+        if self.arena is None or self.arena.size != self.budget:
+            self.arena = None
+            self.arena = Arena(self.budget)
         pending = deque(reqs)
         waiting: deque = deque()
         flights: dict[int, _Flight] = {}
         free_slots = list(range(len(self.streams)))[::-1]
-        used = 0
         results: dict[int, Result] = {}
         torch.cuda.synchronize()
         start = torch.cuda.Event(enable_timing=True)
@@ -221,12 +270,13 @@ class Server:
                         raise RuntimeError("request %d: device error %d, %d triangles for capacity %d"
                                            % (fl.req.rid, e, n, fl.bound))
                     done_ms = start.elapsed_time(fl.done)
+                    tris = None
+                    if fl.keep_results:  # copied out before the block goes back to the arena
+                        tris = self.arena.view(fl.block[0], 36 * n).clone().view(torch.float32).view(n, 3, 3)
                     results[fl.req.rid] = Result(fl.req.rid, n, fl.bound, fl.admit_ms, done_ms,
                                                  done_ms - 1e3 * fl.req.arrival,
-                                                 (time.perf_counter() - t0) * 1e3, fl.nbytes,
-                                                 fl.tris[:36 * n].view(torch.float32).view(n, 3, 3)
-                                                 if fl.tris is not None else None)
-                    used -= fl.nbytes
+                                                 (time.perf_counter() - t0) * 1e3, fl.block[1], tris)
+                    self.arena.release(*fl.block)
                     free_slots.append(slot)
                     del flights[slot]
                     progressed = True
@@ -239,13 +289,13 @@ class Server:
                     head[2] = self.request_bytes(r, head[1])
                     if head[2] > self.budget:
                         raise MemoryError("request %d needs %d bytes, above the budget" % (r.rid, head[2]))
-                if used + head[2] > self.budget:
+                block = self.arena.alloc(head[2])
+                if block is None:  # no room until a request in flight retires
                     host += time.perf_counter() - ta
                     break
-                r, b, nb = waiting.popleft()
+                r, b, _ = waiting.popleft()
                 slot = free_slots.pop()
-                flights[slot] = self._launch(r, slot, b, nb, t0, keep_results)
-                used += nb
+                flights[slot] = self._launch(r, slot, b, block, t0, keep_results)
                 progressed = True
                 host += time.perf_counter() - ta
             if not progressed:

@@ -125,3 +125,39 @@ def test_make_requests_is_seeded_and_in_bounds():
             assert 0 <= o and o + s <= n
     burst = serve.make_requests(10, 0.0, (100, 100, 100), [0])
     assert all(r.arrival == 0.0 for r in burst)
+
+
+def test_free_list_first_fit_and_merge():
+    fl = serve.FreeList(4096)
+    a = fl.alloc(100)
+    b = fl.alloc(1000)
+    c = fl.alloc(256)
+    assert a == (0, 256) and b == (256, 1024) and c == (1280, 256)
+    assert fl.alloc(4096) is None
+    fl.release(*b)
+    assert fl.alloc(2000) == (1536, 2048)       # the freed hole is too small; first fit goes past it
+    assert fl.alloc(512) == (256, 512)          # the hole is used from its start
+    fl.release(*a)
+    assert fl.free == [(0, 256), (768, 512), (3584, 512)]
+    fl.release(256, 512)                        # merges with both neighbours
+    assert fl.free == [(0, 1280), (3584, 512)]
+    fl.release(1280, 256)
+    assert fl.free == [(0, 1536), (3584, 512)]
+    fl.release(1536, 2048)
+    assert fl.free == [(0, 4096)]
+    g = np.random.Generator(np.random.PCG64(1))
+    fl = serve.FreeList(1 << 20)
+    live = []
+    for _ in range(2000):
+        if live and g.uniform() < 0.5:
+            fl.release(*live.pop(int(g.integers(0, len(live)))))
+        else:
+            blk = fl.alloc(int(g.integers(1, 40000)))
+            if blk is not None:
+                live.append(blk)
+        spans = sorted(live + fl.free)
+        assert sum(n for _, n in spans) == fl.size
+        assert all(o1 + n1 == o2 for (o1, n1), (o2, _) in zip(spans, spans[1:]))  # no overlap, no gap
+    for blk in live:
+        fl.release(*blk)
+    assert fl.free == [(0, fl.size)]
