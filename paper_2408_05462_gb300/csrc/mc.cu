@@ -55,11 +55,18 @@ constexpr int kCountSmem = kOffCnt + 256 + 128;                  // + alignment 
 constexpr int kOffTri = kOffCnt + 256;                           // uint32 [256][5] edges of each triangle
 
 // dynamic shared memory of the emit kernel (bytes)
-constexpr int kMaxChunks = kCells * CHR_MC_MAX_TRI / 32;           // 32-triangle chunks per tile and isovalue
+// The active cells of a tile's isovalues share one pool: each isovalue's list
+// is followed by 32 entries that read as "no cell here" to the chunk window.
+// All lists go in together when they fit; a tile whose lists do not (more
+// than about 2048 active cells over its isovalues) takes them one at a time.
+constexpr int kPool = kCells + 32 * kMcIsoPerPass;                 // 2176 entries
+// Chunk-table entries: at most 5 triangles per active cell, so the lists in
+// the pool hold at most 10,240 triangles, plus one partial chunk per list.
+constexpr int kMaxChunks = kCells * CHR_MC_MAX_TRI / 32 + 16;      // 336
 constexpr int kEOffEdge = kOffTri + 256 * CHR_MC_MAX_TRI * 4;      // uint32 [16] edge words
-constexpr int kEOffAct = kEOffEdge + 64;                           // uint32 [2048] active cell | case << 11
-constexpr int kEOffAPre = kEOffAct + kCells * 4;                   // uint16 [2048 + 32] first triangle of each active cell
-constexpr int kEOffChunk = kEOffAPre + (kCells + 32) * 2;          // uint16 [320] active cell holding triangle 32q
+constexpr int kEOffAct = kEOffEdge + 64;                           // uint32 [kPool] active cell | case << 11
+constexpr int kEOffAPre = kEOffAct + kPool * 4;                    // uint16 [kPool] first triangle of each active cell
+constexpr int kEOffChunk = kEOffAPre + kPool * 2;                  // uint16 [kMaxChunks] active cell holding triangle 32q
 constexpr int kEOffStage = ((kEOffChunk + kMaxChunks * 2 + 15) / 16) * 16;  // float [8][32*9+4]
 constexpr int kEmitSmem = kEOffStage + 8 * kWarpStage * 4 + 128;   // + alignment slack
 
@@ -143,31 +150,42 @@ __device__ __forceinline__ void row_masks(const float *buf, uint64_t *s_row, con
     }
 }
 
-// Bit i of v (i < 8) moves to bit 4i.
-__device__ __forceinline__ uint32_t nib_spread(uint32_t v)
+// Exchanges the bits of w at positions p and p + s for every p in m: with
+// s = 2^j - 2^i and m the positions whose index bit i is set and bit j clear,
+// this swaps index bits i and j of every bit position (a delta swap).
+__device__ __forceinline__ uint32_t delta_swap(uint32_t w, int s, uint32_t m)
 {
-    v &= 0xffu;
-    v = (v | (v << 12)) & 0x000f000fu;
-    v = (v | (v << 6)) & 0x03030303u;
-    v = (v | (v << 3)) & 0x11111111u;
-    return v;
+    const uint32_t t = ((w >> s) ^ w) & m;
+    return w ^ t ^ (t << s);
 }
 
 // Case bytes of this thread's 8 cells from the inside masks of its four rows
 // A = (y, z), B = (y+1, z), C = (y, z+1), D = (y+1, z+1), in the kernels'
 // own bit order: corner (ox, oy, oz) is bit 4*ox + oy + 2*oz, so a cell's
 // byte is the nibble (A, B, C, D) of its x column with the nibble of column
-// x+1 above it.  Interleaving the four rows gives every column's nibble at
-// once; byte x is then bits 4x..4x+7 of that word, picked by two byte
+// x+1 above it.  The columns 8j..8j+7 of the four rows, one byte each, form
+// a 4x8 bit matrix; transposing it (bit 8r + x to bit 4x + r: the five index
+// bits rotated by two, four delta swaps) gives every column's nibble at
+// once, and column 8's nibble comes from one multiply whose partial products
+// do not overlap.  Byte x is then bits 4x..4x+7, picked by two byte
 // permutes.  The case tables are stored in the same order (case_order).
 // Cells past `nvalid` get case 0.
 __device__ __forceinline__ void cases8(const uint64_t *R, int r00, int j, int nvalid, uint32_t &lo, uint32_t &hi)
 {
-    const uint32_t a = (uint32_t)(R[r00] >> (8 * j)) & 511u, b = (uint32_t)(R[r00 + 1] >> (8 * j)) & 511u;
-    const uint32_t c = (uint32_t)(R[r00 + 9] >> (8 * j)) & 511u, d = (uint32_t)(R[r00 + 10] >> (8 * j)) & 511u;
-    const uint32_t q = nib_spread(a) | (nib_spread(b) << 1) | (nib_spread(c) << 2) | (nib_spread(d) << 3);
-    const uint32_t n8 = (a >> 8) | ((b >> 8) << 1) | ((c >> 8) << 2) | ((d >> 8) << 3);  // column 8
-    const uint32_t y = (q >> 4) | (n8 << 28);
+    const int sh = 8 * j;
+    const uint64_t ra = R[r00], rb = R[r00 + 1], rc = R[r00 + 9], rd = R[r00 + 10];
+    const uint32_t a = __funnelshift_r((uint32_t)ra, (uint32_t)(ra >> 32), sh);
+    const uint32_t b = __funnelshift_r((uint32_t)rb, (uint32_t)(rb >> 32), sh);
+    const uint32_t c = __funnelshift_r((uint32_t)rc, (uint32_t)(rc >> 32), sh);
+    const uint32_t d = __funnelshift_r((uint32_t)rd, (uint32_t)(rd >> 32), sh);
+    const uint32_t ab = __byte_perm(a, b, 0x5140), cd = __byte_perm(c, d, 0x5140);
+    uint32_t q = __byte_perm(ab, cd, 0x5410);                       // byte r: row r, columns 0..7
+    const uint32_t c8 = __byte_perm(ab, cd, 0x7632) & 0x01010101u;  // bit 8r: row r, column 8
+    q = delta_swap(q, 7, 0x00AA00AAu);   // index bits 0 <-> 3
+    q = delta_swap(q, 14, 0x0000CCCCu);  // 1 <-> 4
+    q = delta_swap(q, 4, 0x00F000F0u);   // 2 <-> 3
+    q = delta_swap(q, 8, 0x0000FF00u);   // 3 <-> 4
+    const uint32_t y = (q >> 4) | ((c8 * 0x10204080u) & 0xF0000000u);  // bit 8r of c8 -> bit 28 + r
     lo = __byte_perm(q, y, 0x5140);
     hi = __byte_perm(q, y, 0x7362);
     if (nvalid < 8) {
@@ -433,10 +451,26 @@ __device__ __forceinline__ void make_triangle_w(float *dst, uint32_t cellB, cons
     }
 }
 
-// Emit, one isovalue at a time: case bytes of the thread's 8 cells, a block
-// scan of (triangles, active cells), the active cells compacted in cell
-// order with their first triangle, and the first active cell of every
-// 32-triangle chunk noted.  Warps take chunks round-robin; a lane finds its
+// A small non-negative integer as a float without the conversion unit:
+// 2^23 + u has u in its low mantissa bits, and subtracting 2^23 is exact.
+__device__ __forceinline__ float small_to_float(uint32_t u)
+{
+    return __fsub_rn(__uint_as_float(0x4B000000u | u), 8388608.0f);
+}
+
+__device__ __forceinline__ uint32_t lanemask_le()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_le;" : "=r"(m));
+    return m;
+}
+
+// Emit, per tile: case bytes of the thread's 8 cells for every isovalue, one
+// block scan of (triangles, active cells) for all of them, the active cells
+// of each isovalue compacted in cell order (with their first triangle) into
+// the shared pool, and the first active cell of every 32-triangle chunk
+// noted.  Warps then take the chunks of all the tile's isovalues
+// round-robin, with no barrier between isovalues; a lane finds its
 // triangle's cell from the chunk's window of 32 active cells (a cell that
 // starts at window position s marks bit s; the lane's cell is the number of
 // marks at or below it), builds the triangle in the warp's staging buffer,
@@ -455,8 +489,9 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
     uint16_t *s_apre = reinterpret_cast<uint16_t *>(smem + kEOffAPre);
     uint16_t *s_chunk = reinterpret_cast<uint16_t *>(smem + kEOffChunk);
     __shared__ uint64_t mbar[2];
-    __shared__ uint32_t s_w[2][9];
+    __shared__ uint32_t s_w[kMcIsoPerPass][9];  // per isovalue slot: warp offsets, then the tile total
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t le = lanemask_le();
     float *s_stage = reinterpret_cast<float *>(smem + kEOffStage) + warp * kWarpStage;
     s_cnt[tid] = (uint8_t)(g_mc_case[case_order(tid)] >> 60);
     for (int i = tid; i < 256 * CHR_MC_MAX_TRI; i += 256) {
@@ -484,69 +519,47 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
         const TileXYZ o = tile_origin(p, tile);
         const int j = tid >> 6, ly = tid & 7, lz = (tid >> 3) & 7;
         const int r00 = lz * 9 + ly;
+        const int nvalid = STORED ? 8 : valid_cells(p, o);
         const uint32_t boxB = smem_addr(box);
         const float fx0 = (float)o.x0, fy0 = (float)o.y0, fz0 = (float)o.z0;
-        // the count pass's classification, one isovalue ahead
         const size_t at0 = (size_t)tile * p.cstride * 256 + tid;
-        uint2 cw_next = make_uint2(0u, 0u);
-        uint32_t pk_next = 0;
-        if (STORED) {
-            cw_next = __ldg(p.cases + at0);
-            pk_next = __ldg(p.tcnt + at0);
-        }
 
-#pragma unroll 1
-        for (int i = 0; i < NISO; i++) {
-            uint32_t lo, hi, packed;
+        // isovalue slot i of this thread: case bytes, triangles | active cells << 16
+        auto classify = [&](int i, uint32_t &lo, uint32_t &hi) -> uint32_t {
             if (STORED) {
-                lo = cw_next.x;
-                hi = cw_next.y;
-                packed = pk_next;
-                if (i + 1 < NISO) {
-                    cw_next = __ldg(p.cases + at0 + 256 * (i + 1));
-                    pk_next = __ldg(p.tcnt + at0 + 256 * (i + 1));
-                }
-            } else {
-                cases8(s_row + i * kRows, r00, j, valid_cells(p, o), lo, hi);
-                uint32_t cnt = 0;
+                const uint2 cw = __ldg(p.cases + at0 + 256 * i);
+                lo = cw.x;
+                hi = cw.y;
+                return __ldg(p.tcnt + at0 + 256 * i);
+            }
+            cases8(s_row + i * kRows, r00, j, nvalid, lo, hi);
+            uint32_t cnt = 0;
 #pragma unroll
-                for (int x = 0; x < 4; x++) cnt += s_cnt[(lo >> (8 * x)) & 0xffu] + s_cnt[(hi >> (8 * x)) & 0xffu];
-                const uint32_t na = __popc(active_bytes(lo)) + __popc(active_bytes(hi));
-                packed = cnt | (na << 16);
-            }
-            // block scan of (triangles | active cells << 16); s_w alternates between isovalues
-            const uint32_t inc = warp_incl_scan_u32(packed, lane);
-            uint32_t *sw = s_w[i & 1];
-            if (lane == 31) sw[warp] = inc;
-            __syncthreads();
-            if (warp == 0) {
-                const uint32_t t = (lane < 8) ? sw[lane] : 0u;
-                const uint32_t ti = warp_incl_scan_u32(t, lane);
-                if (lane < 8) sw[lane] = ti - t;
-                if (lane == 7) sw[8] = ti;
-            }
-            __syncthreads();
-            const uint32_t excl = sw[warp] + inc - packed, total = sw[8];
-            const int n = (int)(total & 0xffffu);
-            if (n == 0) continue;  // uniform across the block
-            {   // compaction of this thread's active cells, in cell order
-                uint32_t a = excl >> 16, pre = excl & 0xffffu;
+            for (int x = 0; x < 4; x++) cnt += s_cnt[(lo >> (8 * x)) & 0xffu] + s_cnt[(hi >> (8 * x)) & 0xffu];
+            return cnt | ((__popc(active_bytes(lo)) + __popc(active_bytes(hi))) << 16);
+        };
+        // this thread's active cells of slot i into the pool from entry `a` on,
+        // triangle prefix `pre`; chunk q of the slot is entry cq + q of the table
+        auto compact = [&](uint32_t lo, uint32_t hi, uint32_t a, uint32_t pre, uint32_t cq) {
 #pragma unroll
-                for (int x = 0; x < 8; x++) {
-                    const uint32_t cb = ((x < 4 ? lo : hi) >> (8 * (x & 3))) & 0xffu;
-                    const uint32_t c = s_cnt[cb];
-                    if (c) {
-                        s_act[a] = (uint32_t)(tid * 8 + x) | (cb << 11);
-                        s_apre[a] = (uint16_t)pre;
-                        const uint32_t q = (pre + 31u) >> 5;
-                        if ((q << 5) < pre + c) s_chunk[q] = (uint16_t)a;
-                        a++;
-                        pre += c;
-                    }
+            for (int x = 0; x < 8; x++) {
+                const uint32_t cb = ((x < 4 ? lo : hi) >> (8 * (x & 3))) & 0xffu;
+                const uint32_t c = s_cnt[cb];
+                if (c) {
+                    s_act[a] = (uint32_t)(tid * 8 + x) | (cb << 11);
+                    s_apre[a] = (uint16_t)pre;
+                    const uint32_t q = (pre + 31u) >> 5;
+                    if ((q << 5) < pre + c) s_chunk[cq + q] = (uint16_t)a;
+                    a++;
+                    pre += c;
                 }
-                if (tid < 32) s_apre[(total >> 16) + tid] = 0xffffu;  // window tail past the last active cell
             }
-            __syncthreads();
+        };
+        // the chunks of slot i (list from pool entry ab, chunk table from cq);
+        // warp w takes the chunks whose index counted from the first chunk
+        // of the group is w modulo 8
+        auto chunks = [&](int i, uint32_t n, uint32_t cq, auto fast_tag) {
+            constexpr bool FAST = decltype(fast_tag)::value;
             const uint64_t g0 = __ldg(p.tile_off + tile * kMcIsoPerPass + i);
             const float k = p.k[i];
             // triangles of this tile that fit below cap (the rest are counted, not written)
@@ -556,51 +569,123 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
             const int pad = (int)((reinterpret_cast<uintptr_t>(tout) >> 2) & 3u);
             const int head = (4 - pad) & 3;
             float *stage = s_stage + pad;
-            auto chunks = [&](auto fast_tag) {
-                constexpr bool FAST = decltype(fast_tag)::value;
-                for (int q = warp; 32 * q < lim; q += 8) {
-                    const int base = 32 * q;
-                    const int mm = (lim - base) < 32 ? (lim - base) : 32;
-                    const int a_lo = s_chunk[q];
-                    const int s0 = (int)s_apre[a_lo + lane] - base;
-                    const uint32_t mark = (s0 > 0 && s0 < 32) ? (1u << s0) : 0u;
-                    const uint32_t starts = __reduce_or_sync(CHR_FULL_MASK, mark);
-                    const int jj = __popc(starts & (0xffffffffu >> (31 - lane)));
-                    if (lane == 0) bulk_wait_read_all();  // the previous chunk's bulk store has read the staging buffer
-                    __syncwarp();
-                    if (lane < mm) {
-                        const int a = a_lo + jj;
-                        const uint32_t e = s_act[a];
-                        const int t = base + lane - (int)s_apre[a];
-                        const uint32_t tri = s_tri[(e >> 11) * CHR_MC_MAX_TRI + t];
-                        const uint32_t c = e & 2047u;
-                        const uint32_t lx = c & 7u, cly = (c >> 3) & 7u, clz = (c >> 6) & 7u, jb = c >> 9;
-                        make_triangle_w<FAST>(stage + 9 * lane, boxB + 4u * (clz * kPlane + cly * kVX + 8u * jb + lx),
-                                              s_edgew, tri, k, fx0 + (float)(8u * jb + lx), fy0 + (float)cly,
-                                              fz0 + (float)clz);
-                    }
-                    fence_proxy_async_smem();
-                    __syncwarp();
-                    // dst[u] = stage[u]; dst + u and stage + u are 16-byte aligned when (pad + u) % 4 == 0: the
-                    // aligned middle goes out as one bulk store, the ragged ends as plain stores
-                    float *dst = tout + 9 * base;
-                    const int F = 9 * mm;
-                    const int h = min(head, F);
-                    if (lane < h) __stcs(dst + lane, stage[lane]);
-                    const int nb16 = (F - h) >> 2;
-                    if (lane == 0 && nb16 > 0) {
-                        bulk_store(dst + h, stage + h, (uint32_t)nb16 * 16u);
-                        bulk_commit();
-                    }
-                    const int tail0 = h + 4 * nb16;
-                    if (lane < F - tail0) __stcs(dst + tail0 + lane, stage[tail0 + lane]);
+            for (int q = (warp - (int)cq) & 7; 32 * q < lim; q += 8) {
+                const int base = 32 * q;
+                const int mm = (lim - base) < 32 ? (lim - base) : 32;
+                const int a_lo = s_chunk[cq + q];
+                const int s0 = (int)s_apre[a_lo + lane] - base;
+                const uint32_t mark = (s0 > 0 && s0 < 32) ? (1u << s0) : 0u;
+                const uint32_t starts = __reduce_or_sync(CHR_FULL_MASK, mark);
+                const int jj = __popc(starts & le);
+                if (lane == 0) bulk_wait_read_all();  // the previous chunk's bulk store has read the staging buffer
+                __syncwarp();
+                if (lane < mm) {
+                    const int a = a_lo + jj;
+                    const uint32_t e = s_act[a];
+                    const int t = base + lane - (int)s_apre[a];
+                    const uint32_t tri = s_tri[(e >> 11) * CHR_MC_MAX_TRI + t];
+                    const uint32_t c = e & 2047u;
+                    const uint32_t lx = (c & 7u) + ((c >> 6) & 0x18u), cly = (c >> 3) & 7u, clz = (c >> 6) & 7u;
+                    make_triangle_w<FAST>(stage + 9 * lane, boxB + 4u * (clz * kPlane + cly * kVX + lx), s_edgew, tri,
+                                          k, fx0 + small_to_float(lx), fy0 + small_to_float(cly),
+                                          fz0 + small_to_float(clz));
                 }
-            };
+                fence_proxy_async_smem();
+                __syncwarp();
+                // dst[u] = stage[u]; dst + u and stage + u are 16-byte aligned when (pad + u) % 4 == 0: the
+                // aligned middle goes out as one bulk store, the ragged ends as plain stores
+                float *dst = tout + 9 * base;
+                const int F = 9 * mm;
+                const int h = min(head, F);
+                if (lane < h) __stcs(dst + lane, stage[lane]);
+                const int nb16 = (F - h) >> 2;
+                if (lane == 0 && nb16 > 0) {
+                    bulk_store(dst + h, stage + h, (uint32_t)nb16 * 16u);
+                    bulk_commit();
+                }
+                const int tail0 = h + 4 * nb16;
+                if (lane < F - tail0) __stcs(dst + tail0 + lane, stage[tail0 + lane]);
+            }
+        };
+        auto chunks_any = [&](int i, uint32_t n, uint32_t cq) {
             if (fast)
-                chunks(std::true_type{});
+                chunks(i, n, cq, std::true_type{});
             else
-                chunks(std::false_type{});
-            __syncthreads();  // the compacted lists are rewritten for the next isovalue
+                chunks(i, n, cq, std::false_type{});
+        };
+
+        // one block scan of every slot's (triangles | active cells << 16)
+        uint32_t lo[NISO], hi[NISO], excl[NISO];
+#pragma unroll
+        for (int i = 0; i < NISO; i++) {
+            const uint32_t packed = classify(i, lo[i], hi[i]);
+            const uint32_t inc = warp_incl_scan_u32(packed, lane);
+            excl[i] = inc - packed;
+            if (lane == 31) s_w[i][warp] = inc;
+        }
+        __syncthreads();
+        if (warp == 0) {  // lane 8i + w scans warp w's total of slot i over the 8 warps
+            const int ii = lane >> 3, wi = lane & 7;
+            const uint32_t t = (ii < NISO) ? s_w[ii][wi] : 0u;
+            uint32_t ti = t;
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                const uint32_t u = __shfl_up_sync(CHR_FULL_MASK, ti, o, 8);
+                if (wi >= o) ti += u;
+            }
+            if (ii < NISO) {
+                s_w[ii][wi] = ti - t;
+                if (wi == 7) s_w[ii][8] = ti;
+            }
+        }
+        __syncthreads();
+        // pool entries and chunk-table entries of the slots, all lists together
+        uint32_t used = 0;
+#pragma unroll
+        for (int i = 0; i < NISO; i++) {
+            const uint32_t na = s_w[i][8] >> 16;
+            used += na ? na + 32u : 0u;
+        }
+        if (used <= (uint32_t)kPool) {
+            uint32_t ab = 0, cq = 0;
+#pragma unroll
+            for (int i = 0; i < NISO; i++) {
+                const uint32_t tot = s_w[i][8], n = tot & 0xffffu, na = tot >> 16;
+                if (n) {
+                    const uint32_t ex = s_w[i][warp] + excl[i];
+                    // without a stored classification the case bytes are made again rather than kept
+                    if (!STORED) cases8(s_row + i * kRows, r00, j, nvalid, lo[i], hi[i]);
+                    compact(lo[i], hi[i], ab + (ex >> 16), ex & 0xffffu, cq);
+                    if (tid < 32) s_apre[ab + na + tid] = 0xffffu;  // window tail past the last active cell
+                    ab += na + 32u;
+                    cq += (n + 31u) >> 5;
+                }
+            }
+            __syncthreads();
+            cq = 0;
+#pragma unroll 1
+            for (int i = 0; i < NISO; i++) {
+                const uint32_t n = s_w[i][8] & 0xffffu;
+                if (n) {
+                    chunks_any(i, n, cq);
+                    cq += (n + 31u) >> 5;
+                }
+            }
+            // (the tile loop's barrier keeps the pool until every chunk is written)
+        } else {
+#pragma unroll 1
+            for (int i = 0; i < NISO; i++) {  // one slot at a time
+                const uint32_t tot = s_w[i][8], n = tot & 0xffffu, na = tot >> 16;
+                if (n == 0) continue;  // uniform across the block
+                uint32_t l, h;
+                const uint32_t packed = classify(i, l, h);
+                const uint32_t ex = s_w[i][warp] + warp_incl_scan_u32(packed, lane) - packed;
+                compact(l, h, ex >> 16, ex & 0xffffu, 0u);
+                if (tid < 32) s_apre[na + tid] = 0xffffu;
+                __syncthreads();
+                chunks_any(i, n, 0u);
+                __syncthreads();  // the pool is rewritten for the next slot
+            }
         }
     });
     if (lane == 0) bulk_wait_all();  // shared memory stays valid until every bulk store is done

@@ -121,6 +121,33 @@ def test_mc_workspace_layouts_agree(isos):
         assert torch.equal(t1[j, :n].view(torch.int32), t2[j, :n].view(torch.int32)), j
 
 
+def test_mc_dense_tiles_take_their_isovalues_one_at_a_time():
+    # The emit pass compacts the active cells of all of a tile's isovalues
+    # into one shared pool when they fit (about 2048 cells in all) and takes
+    # the isovalues one at a time when they do not.  White noise at four
+    # isovalues fills every tile's lists several times over (the slot-by-slot
+    # path); the smooth part of the field leaves its tiles on the pooled
+    # path.  Both layouts of the workspace, against the oracle.
+    f = synth.turbulence((70, 19, 20), seed=21)
+    f = (f / np.abs(f).max()).astype(np.float32)
+    f[:, :, :34] = synth.uniform_noise((20, 19, 34), 22)
+    isos = [-0.6, -0.2, 0.2, 0.6]
+    fd = _dev(f)
+    nz, ny, nx = f.shape
+    cap = 5 * (nx - 1) * (ny - 1) * (nz - 1) + 64
+    meshes = [oracle.mc(f, k) for k in isos]
+    assert min(m.ntri for m in meshes) > 4 * 2048  # the noise tiles alone overflow the pool
+    for size in (chr.isosurface_workspace_size, chr.isosurface_workspace_min_size):
+        ws = torch.empty(size(f.shape, len(isos)), dtype=torch.uint8, device="cuda")
+        tris, counts, err = chr.isosurface_extract(fd, isos, cap, workspace=ws)
+        torch.cuda.synchronize()
+        assert int(err.item()) == 0
+        t = tris.cpu().numpy()
+        for j, (k, mesh) in enumerate(zip(isos, meshes)):
+            assert int(counts[j]) == mesh.ntri, (size.__name__, k)
+            compare_mesh(t[j, :mesh.ntri], mesh, (nx, ny, nz), f"dense {size.__name__} k={k}")
+
+
 def _compare_codec(h, enc, f, label):
     parsed = chr.parse_serialized(chr.chr_serialize(h))
     assert parsed["nlevels"] == enc.nlevels
