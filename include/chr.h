@@ -57,7 +57,9 @@ typedef struct chr_dims {
  * Stream-ordered device allocator supplied by the caller.  alloc returns a
  * device pointer of at least `bytes` bytes (256-byte aligned) usable on
  * `stream`, or NULL; free releases it after the work already enqueued on
- * `stream`.  A NULL chr_allocator* selects cudaMallocAsync/cudaFreeAsync.
+ * `stream`.  A NULL chr_allocator* selects the library's own stream-ordered
+ * pool on the current device (cudaMallocFromPoolAsync / cudaFreeAsync),
+ * which keeps freed memory for later calls; chr_pool_trim gives it back.
  */
 typedef struct chr_allocator {
     void *(*alloc)(size_t bytes, void *stream, void *ctx);
@@ -116,7 +118,7 @@ typedef struct chr_stats_t {
  * coded and bit-packed at the brick's width.
  *
  * Synchronises `stream` once (to size the packed stream).  *out receives a
- * handle whose buffers come from `alloc` (NULL: cudaMallocAsync); release it
+ * handle whose buffers come from `alloc` (NULL: the library pool); release it
  * with chr_free.  d_field is only read.
  */
 chr_status chr_compress(const float *d_field, chr_dims dims, const chr_params *params, const chr_allocator *alloc,
@@ -194,7 +196,7 @@ chr_status chr_brick_range(const chr_handle *h, uint32_t level, float *d_range, 
  * float32.  *eb_out = element of rank floor((1 - accuracy)*|D|) of D in
  * ascending order (min D for accuracy 1), +inf when D is empty;
  * *count_out = |D| (may be NULL).  Exact (radix selection on the float bits).
- * Synchronises `stream`; scratch comes from `alloc` (NULL: cudaMallocAsync).
+ * Synchronises `stream`; scratch comes from `alloc` (NULL: the library pool).
  */
 chr_status chr_topo_translate(const float *d_field, chr_dims dims, const float *isovalues, uint32_t n_iso,
                               float accuracy, const chr_allocator *alloc, void *stream, float *eb_out,
@@ -358,7 +360,7 @@ typedef struct chr_batch_config {
  * d_box_start (n+1 uint64) and d_err (one uint32 error word, reset by each
  * run).  The library allocates the pitched field buffer (rows padded to 16
  * bytes), the per-item parameters and tensor maps and the scan scratch from
- * `alloc` (NULL: cudaMallocAsync) on `stream`, which it synchronises once.
+ * `alloc` (NULL: the library pool) on `stream`, which it synchronises once.
  * The configuration is the one the autotuner last chose for a batch with the
  * same size-class signature, else the defaults.
  */
@@ -394,6 +396,15 @@ chr_status chr_stats(const chr_handle *h, chr_stats_t *out);
 
 /* chr_free — release a handle's buffers (stream-ordered on its stream). NULL ok. */
 void chr_free(chr_handle *h);
+
+/*
+ * chr_pool_trim — give all but `keep_bytes` of the unused memory held by the
+ * library's pool on the current device (the NULL-allocator path) back to the
+ * driver (cudaMemPoolTrimTo).  Memory freed by work still in flight is not
+ * unused yet: synchronise its stream first.  CHR_ERR_CUDA if the pool cannot
+ * be made or trimmed.
+ */
+chr_status chr_pool_trim(size_t keep_bytes);
 
 /* chr_last_error — message for the last failing call on this thread. */
 const char *chr_last_error(void);

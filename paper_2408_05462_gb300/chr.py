@@ -11,7 +11,7 @@ chr_serve_request, chr_serve_request_bytes, chr_box_tri_bound,
 chr_topo_translate,
 isosurface_extract, isosurface_workspace_size, isosurface_workspace_min_size, isosurface_extract_noalloc,
 isosurface_backward, isosurface_distance_loss, chr_serialize, chr_deserialize,
-chr_stats, chr_free, and the chr_batch_* calls (class Batch).
+chr_stats, chr_free, chr_pool_trim, and the chr_batch_* calls (class Batch).
 """
 from __future__ import annotations
 
@@ -138,6 +138,8 @@ def lib():
         L.chr_stats.argtypes = [c_void_p, POINTER(ChrStats)]
         L.chr_free.restype = None
         L.chr_free.argtypes = [c_void_p]
+        L.chr_pool_trim.restype = st
+        L.chr_pool_trim.argtypes = [c_size_t]
         L.chr_batch_create.restype = st
         L.chr_batch_create.argtypes = [POINTER(ChrBatchItem), c_uint32, c_void_p, c_uint64, c_void_p, c_void_p,
                                        POINTER(ChrAllocator), c_void_p, POINTER(c_void_p)]
@@ -246,16 +248,25 @@ class Chr:
 
 
 def chr_compress(field: torch.Tensor, error_bounds, isovalues=(), topo: str = "fix", accuracy: float = 1.0,
-                 stream=None) -> Chr:
-    """Compress a [nz, ny, nx] float32 CUDA field into a CHR (chr.h: chr_compress)."""
+                 stream=None, library_pool: bool = False) -> Chr:
+    """Compress a [nz, ny, nx] float32 CUDA field into a CHR (chr.h: chr_compress).
+    The CHR's buffers come from torch's caching allocator, or with
+    library_pool=True from the library's own pool (a NULL chr_allocator)."""
     _check_field(field)
     eb, ne = _floats(error_bounds)
     iso, ni = _floats(isovalues)
     prm = ChrParams(ne, eb, iso, ni, TOPO[topo], float(accuracy), 0)
     out = c_void_p()
-    _check(lib().chr_compress(field.data_ptr(), _dims(field), ctypes.byref(prm), ctypes.byref(TORCH_ALLOCATOR),
-                              _stream(stream), ctypes.byref(out)))
+    alloc = None if library_pool else ctypes.byref(TORCH_ALLOCATOR)
+    _check(lib().chr_compress(field.data_ptr(), _dims(field), ctypes.byref(prm), alloc, _stream(stream),
+                              ctypes.byref(out)))
     return Chr(out.value, field.shape)
+
+
+def chr_pool_trim(keep_bytes: int = 0) -> None:
+    """Give the unused memory of the library's pool on the current device back
+    to the driver, keeping `keep_bytes` (chr.h: chr_pool_trim)."""
+    _check(lib().chr_pool_trim(int(keep_bytes)))
 
 
 def chr_reconstruct(h: Chr, level: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:

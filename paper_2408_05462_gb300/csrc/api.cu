@@ -4,7 +4,9 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cstdio>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -102,6 +104,14 @@ void fill_codec_params(const chr_handle *h, CodecParams &p)
     p.nK = (int32_t)h->n_iso;
     for (uint32_t j = 0; j < h->n_iso; j++) p.K[j] = h->iso[j];
     p.fix = (h->topo_mode == CHR_TOPO_FIX) ? 1 : 0;
+    float ks[CHR_MAX_ISO];
+    const int nK = (int)h->n_iso;
+    for (int j = 0; j < nK; j++) ks[j] = h->iso[j];
+    std::sort(ks, ks + nK);
+    for (int c = 0; c <= nK; c++) {
+        p.kup[c] = (c > 0) ? ks[nK - c] : INFINITY;
+        p.kdn[c] = (c < nK) ? ks[nK - c - 1] : -INFINITY;
+    }
 }
 
 void set_box(CodecParams &p, const Grid &g, int64_t x0, int64_t y0, int64_t z0, int64_t bx, int64_t by, int64_t bz)
@@ -225,6 +235,32 @@ size_t level_bytes(const chr_handle *h, uint32_t l)
 }
 
 }  // namespace
+
+cudaMemPool_t library_pool()
+{
+    static std::mutex mu;
+    static cudaMemPool_t pools[kMaxDevices] = {};
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps pr;
+        memset(&pr, 0, sizeof(pr));
+        pr.allocType = cudaMemAllocationTypePinned;
+        pr.handleTypes = cudaMemHandleTypeNone;
+        pr.location.type = cudaMemLocationTypeDevice;
+        pr.location.id = dev;
+        cudaMemPool_t mp = nullptr;
+        if (cudaMemPoolCreate(&mp, &pr) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = UINT64_MAX;  // freed memory stays in the pool until chr_pool_trim
+        if (cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) cudaGetLastError();
+        pools[dev] = mp;
+    }
+    return pools[dev];
+}
+
 }  // namespace chr
 
 using namespace chr;
@@ -232,6 +268,15 @@ using namespace chr;
 extern "C" {
 
 int chr_version(void) { return 1; }
+
+chr_status chr_pool_trim(size_t keep_bytes)
+{
+    cudaMemPool_t mp = library_pool();
+    if (!mp) return fail(CHR_ERR_CUDA, "chr_pool_trim: the library's memory pool could not be made");
+    const cudaError_t e = cudaMemPoolTrimTo(mp, keep_bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "chr_pool_trim");
+    return CHR_OK;
+}
 
 const char *chr_last_error(void) { return g_last_error.c_str(); }
 
@@ -290,10 +335,22 @@ chr_status chr_compress(const float *d_field, chr_dims dims, const chr_params *p
     set_constants(h);
 
     const Grid &g = h->g;
+    // scratch first (the per-brick slots of every level, then the
+    // record-scan buffers), so that a pool that keeps freed memory hands the
+    // same block back to the next call; then the handle's records
+    const size_t slot_bytes = encode_slot_bytes(g.nbricks);
+    const size_t scan_bytes = scan_scratch_bytes(g.nbricks, (int)h->nlevels);
+    const size_t scr_bytes = slot_bytes * h->nlevels + scan_bytes + 16 * CHR_MAX_LEVELS;
+    char *scr = (char *)al.get(scr_bytes);
+    if (!scr) {
+        delete h;
+        return fail(CHR_ERR_OOM, "chr_compress: allocator returned NULL");
+    }
     h->sz_recs = (size_t)g.nbricks * sizeof(uint4);
     for (uint32_t l = 0; l < h->nlevels; l++) {
         h->d_recs[l] = (uint4 *)al.get(h->sz_recs);
         if (!h->d_recs[l]) {
+            al.put(scr, scr_bytes);
             free_handle_buffers(h);
             delete h;
             return fail(CHR_ERR_OOM, "chr_compress: allocator returned NULL");
@@ -302,14 +359,8 @@ chr_status chr_compress(const float *d_field, chr_dims dims, const chr_params *p
     CodecParams p;
     fill_codec_params(h, p);
     p.f = d_field;
-    // scratch: the per-brick slots of every level, then the record-scan buffers
-    const size_t slot_bytes = encode_slot_bytes(g.nbricks);
-    const size_t scan_bytes = scan_scratch_bytes(g.nbricks, (int)h->nlevels);
-    const size_t scr_bytes = slot_bytes * h->nlevels + scan_bytes + 16 * CHR_MAX_LEVELS;
-    char *scr = (char *)al.get(scr_bytes);
     cudaError_t e = cudaSuccess;
     uint64_t totals[2 * CHR_MAX_LEVELS] = {0};
-    if (!scr) st = fail(CHR_ERR_OOM, "chr_compress: allocator returned NULL");
     if (st == CHR_OK) {
         const size_t nb512 = (size_t)g.nbricks * 512;
         for (uint32_t l = 0; l < h->nlevels; l++) {

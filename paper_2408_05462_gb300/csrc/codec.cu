@@ -109,19 +109,9 @@ __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ Codec
         const bool full = ((int64_t)c.bx * 8 + 8 <= p.nx) && ((int64_t)c.by * 8 + 8 <= p.ny) && ((int64_t)c.bz * 8 + 8 <= p.nz);
         mine = (full == FULL);
     }
-    if (tid == 0 && p.fix) {
-        float ks[CHR_MAX_ISO];
-        const int nK = p.nK;
-        for (int a = 0; a < nK; a++) {  // insertion sort of the candidate isovalues
-            float v = p.K[a];
-            int b = a;
-            for (; b > 0 && ks[b - 1] > v; b--) ks[b] = ks[b - 1];
-            ks[b] = v;
-        }
-        for (int cnt = 0; cnt <= nK; cnt++) {
-            s_kup[cnt] = (cnt > 0) ? ks[nK - cnt] : __int_as_float(0x7f800000);
-            s_kdn[cnt] = (cnt < nK) ? ks[nK - cnt - 1] : __int_as_float(0xff800000);
-        }
+    if (tid <= CHR_MAX_ISO) {  // sign-check intervals by count of candidates above (sorted on the host)
+        s_kup[tid] = p.kup[tid];
+        s_kdn[tid] = p.kdn[tid];
     }
     *reinterpret_cast<uint4 *>(&s_pk[j][8 * r]) = make_uint4(0u, 0u, 0u, 0u);
     *reinterpret_cast<uint4 *>(&s_pk[j][8 * r + 4]) = make_uint4(0u, 0u, 0u, 0u);

@@ -43,6 +43,11 @@ struct CodecParams {
     int32_t fix;
     float e[CHR_MAX_LEVELS], two_e[CHR_MAX_LEVELS], inv2e[CHR_MAX_LEVELS];
     float K[CHR_MAX_ISO];
+    // encoder sign check: a vertex with c candidates strictly above its value
+    // keeps every sign exactly when its reconstruction lies in
+    // [kdn[c], kup[c]): kup[c] the smallest of those c candidates (+inf if
+    // c = 0), kdn[c] the largest of the others (-inf if there are none)
+    float kup[CHR_MAX_ISO + 1], kdn[CHR_MAX_ISO + 1];
     uint4 *recs[CHR_MAX_LEVELS];
     uint32_t *words[CHR_MAX_LEVELS];
     uint16_t *exc_idx[CHR_MAX_LEVELS];
@@ -157,7 +162,13 @@ struct chr_handle;
 
 namespace chr {
 
-// Device memory from a caller's chr_allocator, or stream-ordered cudaMallocAsync.
+// The library's own stream-ordered memory pool on the current device (for a
+// NULL chr_allocator): freed blocks stay in the pool for the next call
+// instead of going back to the driver at every synchronisation; NULL if the
+// pool cannot be made.
+cudaMemPool_t library_pool();
+
+// Device memory from a caller's chr_allocator, or the library pool.
 struct Alloc {
     chr_allocator a{};
     bool dflt = true;
@@ -176,7 +187,8 @@ struct Alloc {
         n = (n + 255) & ~size_t(255);
         void *p = nullptr;
         if (dflt) {
-            if (cudaMallocAsync(&p, n, s) != cudaSuccess) {
+            cudaMemPool_t mp = library_pool();
+            if (!mp || cudaMallocFromPoolAsync(&p, n, mp, s) != cudaSuccess) {
                 cudaGetLastError();
                 return nullptr;
             }

@@ -148,6 +148,27 @@ def test_mc_dense_tiles_take_their_isovalues_one_at_a_time():
             compare_mesh(t[j, :mesh.ntri], mesh, (nx, ny, nz), f"dense {size.__name__} k={k}")
 
 
+def test_library_pool_allocator_gives_the_same_chr():
+    # a NULL chr_allocator takes the library's own stream-ordered pool; the
+    # CHR is the same bytes as with torch's allocator, and trimming the pool
+    # after the handles are freed succeeds
+    f = synth.turbulence((40, 33, 27), seed=5)
+    r = synth.value_range(f)
+    fd = _dev(f)
+    eb, isos = [1e-2 * r, 1e-3 * r], [-0.5, 0.5]
+    ref = chr.chr_compress(fd, eb, isos)
+    want = chr.chr_serialize(ref)
+    for _ in range(3):
+        h = chr.chr_compress(fd, eb, isos, library_pool=True)
+        assert chr.chr_serialize(h) == want
+        R = h.reconstruct(1)
+        assert torch.equal(R.view(torch.int32), ref.reconstruct(1).view(torch.int32))
+        h.free()
+    torch.cuda.synchronize()
+    chr.chr_pool_trim(0)
+    ref.free()
+
+
 def _compare_codec(h, enc, f, label):
     parsed = chr.parse_serialized(chr.chr_serialize(h))
     assert parsed["nlevels"] == enc.nlevels
