@@ -586,13 +586,14 @@ def main():
     for v in stages.values():
         v["GBps"] = v["algorithmic_bytes"] / (v["ms"] * 1e-3) / 1e9
         v["frac_of_measured_hbm"] = v["GBps"] / peak
-    # the dominant stage: isosurface_extract (k_mc_count + tile scan + k_mc_emit,
-    # timed together by the events around the call); algorithmic bytes =
+    # the dominant stage: isosurface_extract (one k_mc_fused launch for the 4
+    # isovalues, after a clear of its tile status words; timed by the events
+    # around the call); algorithmic bytes =
     # the field read once + 36 B per triangle written
     dom = "isosurface_extract"
     achieved = stages[dom]["GBps"]
     ratio = profiled_traffic_ratio()
-    roofline = {"bound": "hbm", "kernel": "isosurface_extract (k_mc_count + tile scan + k_mc_emit)",
+    roofline = {"bound": "hbm", "kernel": "isosurface_extract (k_mc_fused)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (ratio * mc_bytes) if ratio else None, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": mc_bytes,
@@ -611,7 +612,9 @@ def main():
         "triangles": ntri, "compressed_bytes": comp_bytes, "compression_ratio": 4.0 * N / comp_bytes,
         "exceptions": st["exceptions"],
         "translate": translate,
-        "gpu_launches": 11 * args.steps,  # encode, 3 record scans, compact, decode, MC count, 3 tile scans, emit
+        # per step: encode (a second launch for partial bricks when a side is not a multiple of 8),
+        # 3 record scans, compact, decode, one single-pass marching-cubes launch for the 4 isovalues
+        "gpu_launches": (7 + (1 if args.size % 8 else 0)) * args.steps,
         "e2e": e2e,
     }
     if adjoint is not None:

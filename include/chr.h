@@ -204,17 +204,19 @@ chr_status chr_topo_translate(const float *d_field, chr_dims dims, const float *
 
 /*
  * isosurface_workspace_size — bytes of device scratch for isosurface_extract
- * with these dims and number of isovalues: per 32x8x8-cell tile its
- * triangle counts and output offsets, and the counting pass's classification
- * (12 bytes per 8 cells and isovalue, at most 4 isovalues at a time) that
- * the emitting pass reads instead of classifying again.  A workspace of at
- * least the tile arrays alone (48 bytes per tile plus the scan chunks) is
- * also accepted; the emitting pass then classifies again (slower, same
- * output).
+ * with these dims and number of isovalues: per 32x8x8-cell tile a status
+ * word, its triangle counts and output offsets (the groups of 4 isovalues
+ * reuse them), and when the last group has 1 or 2 isovalues the counting
+ * pass's classification for that group (12 bytes per 8 cells and
+ * isovalue), which its emitting pass reads back.
  */
 size_t isosurface_workspace_size(chr_dims dims, uint32_t n_iso);
 
-/* isosurface_workspace_min_size — the smallest workspace isosurface_extract accepts (the slower layout). */
+/*
+ * isosurface_workspace_min_size — the smallest workspace isosurface_extract
+ * accepts: the tile arrays alone (every group then takes the single pass;
+ * same output).
+ */
 size_t isosurface_workspace_min_size(chr_dims dims, uint32_t n_iso);
 
 /*
@@ -234,10 +236,14 @@ size_t isosurface_workspace_min_size(chr_dims dims, uint32_t n_iso);
  * receives isovalue j's true triangle count even when it exceeds cap_tris;
  * triangles beyond cap_tris are not written and bit CHR_ERR_OVERFLOW is set in
  * *d_err.  d_err (device uint32) is cleared by the call; may be NULL.
- * d_workspace: device scratch of workspace_bytes, reused by the call;
- * isosurface_workspace_size() bytes select the faster layout, a smaller
- * workspace that still holds the tile arrays the slower one, anything
- * smaller is CHR_ERR_INVALID.  Asynchronous.
+ * d_workspace: device scratch of workspace_bytes (at least
+ * isosurface_workspace_min_size(), else CHR_ERR_INVALID), overwritten by the
+ * call.  Groups of 3-4 isovalues (or any group, with the minimum workspace)
+ * take one launch (k_mc_fused): blocks claim tiles in order and find each
+ * tile's output offset from the counts the tiles before it publish (bounded
+ * waits; a wait that gives up sets CHR_ERR_TIMEOUT).  A group of 1-2 with
+ * isosurface_workspace_size() bytes takes a counting pass, a scan of the
+ * tile counts and an emitting pass.  Same output either way.  Asynchronous.
  */
 chr_status isosurface_extract(const float *d_field, chr_dims dims, const float *isovalues, uint32_t n_iso,
                               float *d_tris, uint64_t cap_tris, uint64_t *d_ntris, uint32_t *d_err, void *d_workspace,

@@ -81,10 +81,10 @@ size_t scan_scratch_bytes(int64_t nbricks, int nlevels);
 cudaError_t launch_scan_records(uint4 *const *recs, int nlevels, int64_t nbricks, void *scratch, uint64_t *totals,
                                 cudaStream_t s);
 
-// Marching cubes over a plain field.
-// mc_workspace_bytes: the layout in which the count pass keeps its
-// classification for the emit pass; mc_workspace_min_bytes: the smallest
-// workspace accepted (the emit pass then classifies again).
+// Marching cubes over a plain field, per group of up to 4 isovalues one
+// single-pass launch, or count + scan + emit for a group of 1-2 when the
+// workspace holds its classification.  mc_workspace_bytes: the tile arrays
+// plus that classification; mc_workspace_min_bytes: the tile arrays alone.
 size_t mc_workspace_bytes(const Grid &g, int n_iso);
 size_t mc_workspace_min_bytes(const Grid &g, int n_iso);
 cudaError_t launch_mc(const float *field, const Grid &g, const float *iso, int n_iso, float *tris, uint64_t cap,

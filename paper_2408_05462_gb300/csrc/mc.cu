@@ -1,22 +1,30 @@
 // Marching cubes over a float32 field (paper Sec. 2.2; Lorensen & Cline).
 //
-// Three launches per group of up to 4 isovalues, none of which waits on
-// another block:
-//   k_mc_count  per 32x8x8-cell tile: inside masks by warp ballot, case bytes,
-//               triangle counts per isovalue -> tile_cnt (and, when the
-//               workspace holds it, the classification for the emit pass)
+// isosurface_extract: per group of up to 4 isovalues (groups of 3-4, or any
+// group when the workspace holds only the tile arrays) one launch,
+//   k_mc_fused  persistent blocks claim 32x8x8-cell tiles in increasing
+//               order; per tile: inside masks by warp ballot, case bytes,
+//               one block scan of (triangles, active cells) for every
+//               isovalue, the tile's counts published and its output offset
+//               found by a decoupled look-back over the tiles before it,
+//               active cells compacted, triangle -> cell by a 32-triangle
+//               window, edge interpolation, each chunk written by one TMA
+//               bulk store
+// The two-pass form serves groups of 1-2 isovalues (a tile has too little
+// triangle work there to hide the single pass's per-tile waits), the
+// adjoint and the batched path, which keep the classification for a second
+// walk over the same tiles:
+//   k_mc_count  per tile: case bytes and triangle counts -> tile_cnt (and
+//               the classification, 12 bytes per 8 cells and isovalue)
 //   k_tscan_*   exclusive scan of the tile counts -> tile_off, totals
-//   k_mc_emit   per tile again: the classification (stored, or computed
-//               again), block scan, active cells compacted per isovalue,
-//               triangle -> cell by a 32-triangle window, edge
-//               interpolation, each chunk written at tile_off + local offset
-//               by one TMA bulk store
-// Both tile kernels are persistent (one wave of blocks striding over tiles)
-// and prefetch the next tile's 36x9x9 vertex box with a TMA bulk tensor copy
-// into a second shared-memory buffer while the current tile is processed;
-// the box is zero-filled past the grid edge.  When the field cannot be
-// described by a tensor map (nx*4 not a multiple of 16, or a base address
-// not 16-byte aligned) the same kernels load the box with plain loads.
+//   k_mc_emit_stored / k_mc_emit_batched / k_mc_adjoint  per tile again,
+//               from the stored classification
+// Every tile kernel fetches a tile's 36x9x9 vertex box with a TMA bulk
+// tensor copy into one of two shared-memory buffers while another tile is
+// processed; the box is zero-filled past the grid edge.  When the field
+// cannot be described by a tensor map (nx*4 not a multiple of 16, or a base
+// address not 16-byte aligned) the same kernels load the box with plain
+// loads.
 //
 // Output order: 8^3-cell bricks in x-fastest order, cells of a brick
 // x-fastest, triangles of a cell in table order.  A tile is 4 bricks along
@@ -83,12 +91,20 @@ struct McParams {
     uint32_t *err;
     uint4 *tile_cnt;     // [ntiles]: triangles per isovalue slot
     uint64_t *tile_off;  // [ntiles][4]: global index of the tile's first triangle
-    // classification kept by the count pass for the emit pass (null: emit
-    // classifies again): per tile, isovalue slot (cstride slots) and thread,
-    // the case bytes of the thread's 8 cells and its triangles | active cells << 16
+    // two-pass form (batched emit, adjoint): the count pass's classification
+    // per tile, isovalue slot (cstride slots) and thread, the case bytes of
+    // the thread's 8 cells and its triangles | active cells << 16
     uint2 *cases;
     uint32_t *tcnt;
     int32_t cstride;
+    // single pass (k_mc_fused): per tile a status word (tile_status), its
+    // inclusive prefix in tile_off once published, the tile counter blocks
+    // claim tiles from, a word that a gave-up wait sets so that no other
+    // block waits on it, and where the totals of the isovalue slots go
+    uint64_t *tstat;
+    uint32_t *tctr;
+    uint32_t *tabort;
+    uint64_t *ntris;
 };
 
 struct TileXYZ {
@@ -451,6 +467,161 @@ __device__ __forceinline__ void make_triangle_w(float *dst, uint32_t cellB, cons
     }
 }
 
+// ---- single pass: tile offsets by decoupled look-back -------------------------
+//
+// Blocks claim tiles in increasing order from a counter.  A tile publishes
+// its own triangle counts as soon as it has classified its cells, then adds
+// up the counts of the tiles before it, walking back 32 at a time, until it
+// meets a tile that has published its inclusive prefix; it then publishes its
+// own.  A tile's counts never wait on anything and every claimed tile belongs
+// to a running block, so every wait ends; each is bounded all the same, and
+// one that gives up sets the abort word so that no block waits after it.
+//
+// Tile status word: bits 62-63 the state (0 nothing yet, 1 the tile's own
+// counts, 2 its inclusive prefix is in tile_off), bits 14i..14i+13 the
+// tile's triangles at isovalue slot i (at most 2048 cells x 5 < 2^14).
+constexpr uint64_t kTileOwn = 1ull << 62, kTilePrefix = 2ull << 62;
+
+__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t *a)
+{
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(a) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *a)
+{
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(a) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *a)
+{
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64(uint64_t *a, uint64_t v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(a), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_release_u64(uint64_t *a, uint64_t v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(a), "l"(v) : "memory");
+}
+
+// Triangles before tile t at each isovalue slot, by one warp; false when a
+// wait gave up or another block's did.
+template <int NISO>
+__device__ __forceinline__ bool look_back(const McParams &p, int64_t t, uint64_t (&excl)[NISO])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < NISO; i++) excl[i] = 0;
+    for (int64_t pos = t - 1; pos >= 0; pos -= 32) {
+        const int64_t idx = pos - lane;
+        uint64_t w = kTilePrefix;  // before tile 0: a prefix of zero
+        bool ok = true;
+        if (idx >= 0) {
+            w = ld_acquire_u64(p.tstat + idx);
+            for (uint32_t it = 0; (w >> 62) == 0; it++) {
+                if (it >= CHR_SPIN_LIMIT || ld_relaxed_u32(p.tabort) != 0u) {
+                    ok = false;
+                    break;
+                }
+                if (it > 16) __nanosleep(64);
+                w = ld_acquire_u64(p.tstat + idx);
+            }
+        }
+        if (!__all_sync(CHR_FULL_MASK, ok)) return false;
+        const uint32_t pm = __ballot_sync(CHR_FULL_MASK, (w >> 62) == 2u);
+        const int first = pm ? __ffs(pm) - 1 : 32;  // nearest tile with its prefix
+#pragma unroll
+        for (int i = 0; i < NISO; i++) {
+            const uint32_t c = (lane < first) ? (uint32_t)(w >> (14 * i)) & 0x3fffu : 0u;
+            excl[i] += __reduce_add_sync(CHR_FULL_MASK, c);
+        }
+        if (pm) {
+#pragma unroll
+            for (int i = 0; i < NISO; i++) {
+                const uint64_t v = (lane == first && idx >= 0) ? ld_relaxed_u64(p.tile_off + idx * kMcIsoPerPass + i)
+                                                               : 0ull;
+                excl[i] += __shfl_sync(CHR_FULL_MASK, v, first);
+            }
+            return true;
+        }
+    }
+    return true;
+}
+
+// The single pass's tile loop: blocks claim tiles from p.tctr in increasing
+// order.  A block claims its next tile only near the end of the current one
+// (the first warp done with its share of the current tile's triangles calls
+// claim(), else thread 0 after the body): a tile that is claimed but not
+// started would hold up the look-back of every later tile until its block
+// got to it.  The next box is fetched into the other buffer meanwhile.
+// body(tile, tile, params, box, claim).
+template <class Body>
+__device__ __forceinline__ void tile_loop_claimed(const McParams &p, const CUtensorMap *map, float *bufs,
+                                                  uint64_t *mbar, Body body)
+{
+    __shared__ int64_t s_tile;
+    __shared__ uint32_t s_claimed;
+    const int tid = threadIdx.x;
+    const bool tma = p.use_tma != 0;
+    int cur = 0;
+    auto claim = [&]() {  // one thread per tile: the next tile, and its box on its way
+        if (atomicExch(&s_claimed, 1u) != 0u) return;
+        const int64_t t = (int64_t)atomicAdd(p.tctr, 1u);
+        s_tile = t;
+        if (tma && t < p.ntiles) issue_box(bufs + (cur ^ 1) * (kBufBytes / 4), map, &mbar[cur ^ 1], p, t);
+    };
+    if (tid == 0) {
+        if (tma) {
+            mbar_init(&mbar[0], 1);
+            mbar_init(&mbar[1], 1);
+            fence_mbar_init();
+        }
+        const int64_t t = (int64_t)atomicAdd(p.tctr, 1u);
+        s_tile = t;
+        s_claimed = 0u;
+        if (tma && t < p.ntiles) issue_box(bufs, map, &mbar[0], p, t);
+    }
+    __syncthreads();
+    int64_t tile = s_tile;
+    uint32_t phase0 = 0, phase1 = 0;
+    while (tile < p.ntiles) {
+        float *buf = bufs + cur * (kBufBytes / 4);
+        bool ok = true;
+        if (tma) {
+            ok = mbar_wait(&mbar[cur], cur ? phase1 : phase0);
+            if (cur)
+                phase1 ^= 1u;
+            else
+                phase0 ^= 1u;
+        } else {
+            load_box_plain(buf, p, tile_origin(p, tile));
+        }
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) {
+                atomicExch(p.tabort, 1u);
+                if (p.err) atomicOr(p.err, 1u << CHR_ERR_TIMEOUT);
+            }
+            return;
+        }
+        // (the other buffer's last reads ended at the previous barrier, so claim() may refill it)
+        body(tile, tile, p, buf, claim);
+        if (tid == 0) claim();  // unless a warp already did
+        __syncthreads();        // every read of buf is done, and s_tile holds the next tile
+        tile = s_tile;          // (read before the next tile's first barrier, so before the next claim)
+        if (tid == 0) s_claimed = 0u;
+        cur ^= 1;
+    }
+}
+
 // A small non-negative integer as a float without the conversion unit:
 // 2^23 + u has u in its low mantissa bits, and subtracting 2^23 is exact.
 __device__ __forceinline__ float small_to_float(uint32_t u)
@@ -475,9 +646,15 @@ __device__ __forceinline__ uint32_t lanemask_le()
 // starts at window position s marks bit s; the lane's cell is the number of
 // marks at or below it), builds the triangle in the warp's staging buffer,
 // and the warp writes the chunk with aligned 16-byte stores.
-template <int NISO, bool STORED, class Src>
+//
+// FUSED: the single pass (no count pass before it): the tiles come from the
+// claimed-tile loop and the case bytes from the box, and once the block scan
+// has the tile's totals, warp 0 publishes them and finds the tile's offsets
+// by the look-back while the other warps compact.
+template <int NISO, bool STORED, bool FUSED, class Src>
 __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
 {
+    static_assert(!(FUSED && STORED), "the single pass classifies from the box");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     float *bufs = reinterpret_cast<float *>(smem + kOffBuf);
@@ -490,6 +667,7 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
     uint16_t *s_chunk = reinterpret_cast<uint16_t *>(smem + kEOffChunk);
     __shared__ uint64_t mbar[2];
     __shared__ uint32_t s_w[kMcIsoPerPass][9];  // per isovalue slot: warp offsets, then the tile total
+    __shared__ uint64_t s_g0[kMcIsoPerPass];    // single pass: the tile's first triangle per slot
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t le = lanemask_le();
     float *s_stage = reinterpret_cast<float *>(smem + kEOffStage) + warp * kWarpStage;
@@ -504,7 +682,7 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
     }
     if (tid < 12) s_edgew[tid] = edge_word(tid);
 
-    tile_loop(src, err, bufs, mbar, [&](int64_t, int64_t tile, const McParams &p, const float *box) {
+    auto body = [&](int64_t, int64_t tile, const McParams &p, const float *box, auto &&claim) {
         // fast quotients unless some value of the box is 2^125 or more in magnitude (or infinite)
         bool huge = false;
         for (int u = tid; u < kRows * kVX / 4; u += 256) {
@@ -560,7 +738,7 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
         // of the group is w modulo 8
         auto chunks = [&](int i, uint32_t n, uint32_t cq, auto fast_tag) {
             constexpr bool FAST = decltype(fast_tag)::value;
-            const uint64_t g0 = __ldg(p.tile_off + tile * kMcIsoPerPass + i);
+            const uint64_t g0 = FUSED ? s_g0[i] : __ldg(p.tile_off + tile * kMcIsoPerPass + i);
             const float k = p.k[i];
             // triangles of this tile that fit below cap (the rest are counted, not written)
             const int lim = (g0 >= p.cap) ? 0 : (int)((p.cap - g0) < (uint64_t)n ? (p.cap - g0) : (uint64_t)n);
@@ -639,6 +817,38 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
             }
         }
         __syncthreads();
+        if (FUSED && warp == 0) {
+            // publish this tile's counts, find the triangles before it, publish its inclusive prefix
+            uint64_t own = 0;
+#pragma unroll
+            for (int i = 0; i < NISO; i++) own |= (uint64_t)(s_w[i][8] & 0xffffu) << (14 * i);
+            uint64_t ex[NISO];
+            bool ok = true;
+            if (tile == 0) {
+#pragma unroll
+                for (int i = 0; i < NISO; i++) ex[i] = 0;
+            } else {
+                if (lane == 0) st_relaxed_u64(p.tstat + tile, kTileOwn | own);
+                ok = look_back<NISO>(p, tile, ex);
+            }
+            if (lane == 0) {
+                if (!ok) {
+                    atomicExch(p.tabort, 1u);
+                    if (p.err) atomicOr(p.err, 1u << CHR_ERR_TIMEOUT);
+                }
+#pragma unroll
+                for (int i = 0; i < NISO; i++) {
+                    const uint64_t incl = ex[i] + (s_w[i][8] & 0xffffu);
+                    st_relaxed_u64(p.tile_off + tile * kMcIsoPerPass + i, incl);
+                    s_g0[i] = ex[i];
+                    if (tile == p.ntiles - 1) {  // the totals, and whether every triangle fitted below cap
+                        p.ntris[i] = incl;
+                        if (incl > p.cap && p.err) atomicOr(p.err, 1u << CHR_ERR_OVERFLOW);
+                    }
+                }
+                st_release_u64(p.tstat + tile, kTilePrefix | own);
+            }
+        }
         // pool entries and chunk-table entries of the slots, all lists together
         uint32_t used = 0;
 #pragma unroll
@@ -671,6 +881,7 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
                     cq += (n + 31u) >> 5;
                 }
             }
+            if (FUSED && lane == 0) claim();  // the first warp done claims the next tile
             // (the tile loop's barrier keeps the pool until every chunk is written)
         } else {
 #pragma unroll 1
@@ -687,20 +898,37 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
                 __syncthreads();  // the pool is rewritten for the next slot
             }
         }
-    });
+    };
+    if constexpr (FUSED)
+        tile_loop_claimed(*src.p, src.map, bufs, mbar, body);
+    else
+        tile_loop(src, err, bufs, mbar, [&](int64_t g, int64_t t, const McParams &p, const float *box) {
+            body(g, t, p, box, [] {});
+        });
     if (lane == 0) bulk_wait_all();  // shared memory stays valid until every bulk store is done
 }
 
-template <int NISO, bool STORED>
-__global__ void __launch_bounds__(256, 4) k_mc_emit(const __grid_constant__ McParams p,
-                                                   const __grid_constant__ CUtensorMap map)
+// Two-pass emit from the count pass's stored classification (groups of 1-2
+// isovalues, where a tile has too little triangle work to hide the single
+// pass's per-tile waits).
+template <int NISO>
+__global__ void __launch_bounds__(256, 4) k_mc_emit_stored(const __grid_constant__ McParams p,
+                                                          const __grid_constant__ CUtensorMap map)
 {
-    mc_emit_run<NISO, STORED>(SrcOne{&p, &map}, p.err);
+    mc_emit_run<NISO, true, false>(SrcOne{&p, &map}, p.err);
+}
+
+// Classification, tile offsets and emission in one launch (no count pass).
+template <int NISO>
+__global__ void __launch_bounds__(256, 4) k_mc_fused(const __grid_constant__ McParams p,
+                                                    const __grid_constant__ CUtensorMap map)
+{
+    mc_emit_run<NISO, false, true>(SrcOne{&p, &map}, p.err);
 }
 
 __global__ void __launch_bounds__(256, 4) k_mc_emit_batched(const __grid_constant__ McBatch b, uint32_t *err)
 {
-    mc_emit_run<1, true>(SrcMany{&b}, err);
+    mc_emit_run<1, true, false>(SrcMany{&b}, err);
 }
 
 // ---- adjoint of the vertex positions ----------------------------------------
@@ -1061,10 +1289,21 @@ static size_t mc_layout(const Grid &g, int cstride, void *base, McWorkspace *w)
 
 static int stored_slots(int n_iso) { return n_iso < kMcIsoPerPass ? (n_iso > 0 ? n_iso : 1) : kMcIsoPerPass; }
 
+// Isovalues go in groups of 4; a last group of 1 or 2 takes the two-pass
+// form, which stores the classification of that many slots.
+static int small_group_slots(int n_iso)
+{
+    const int r = n_iso - kMcIsoPerPass * ((n_iso - 1) / kMcIsoPerPass);
+    return (n_iso > 0 && r <= 2) ? r : 0;
+}
+
+// The single pass uses the tile arrays only (status words, counter and
+// abort word in the tile-count region, inclusive prefixes in the offsets);
+// the groups reuse them in turn.  The full workspace adds the stored
+// classification for a small last group.
 size_t mc_workspace_bytes(const Grid &g, int n_iso)
 {
-    // groups of 4 isovalues reuse the same scratch in turn
-    return mc_layout(g, stored_slots(n_iso), nullptr, nullptr);
+    return mc_layout(g, small_group_slots(n_iso), nullptr, nullptr);
 }
 
 size_t mc_workspace_min_bytes(const Grid &g, int n_iso)
@@ -1073,8 +1312,14 @@ size_t mc_workspace_min_bytes(const Grid &g, int n_iso)
     return mc_layout(g, 0, nullptr, nullptr);
 }
 
+// The adjoint's two passes keep the count pass's classification.
+static size_t mc_stored_workspace_bytes(const Grid &g, int n_iso)
+{
+    return mc_layout(g, stored_slots(n_iso), nullptr, nullptr);
+}
+
 struct McGrids {
-    int count, emit, emit_compact, adjoint;
+    int count, adjoint, fused, emit;  // resident blocks of each persistent kernel
 };
 
 template <int NISO>
@@ -1082,25 +1327,24 @@ static cudaError_t mc_prepare(McGrids &out)
 {
     static McGrids Gd[kMaxDevices] = {};  // resident blocks, computed once per device
     McGrids &G = Gd[current_device()];
-    if (!G.emit) {
-        cudaError_t e = cudaFuncSetAttribute(k_mc_emit<NISO, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kEmitSmem);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_mc_emit<NISO, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_mc_adjoint<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
+    if (!G.fused) {
+        cudaError_t e = cudaFuncSetAttribute(k_mc_adjoint<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(k_mc_count<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCountSmem);
         if (e != cudaSuccess) return e;
-        int dev = current_device(), sms = 0, bc = 0, be = 0, bf = 0, ba = 0;
+        e = cudaFuncSetAttribute(k_mc_fused<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_mc_emit_stored<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
+        if (e != cudaSuccess) return e;
+        int dev = current_device(), sms = 0, bc = 0, ba = 0, bu = 0, be = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bc, k_mc_count<NISO>, 256, kCountSmem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&be, k_mc_emit<NISO, true>, 256, kEmitSmem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_mc_emit<NISO, false>, 256, kEmitSmem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ba, k_mc_adjoint<NISO>, 256, kEmitSmem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu, k_mc_fused<NISO>, 256, kEmitSmem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&be, k_mc_emit_stored<NISO>, 256, kEmitSmem);
         G.count = sms * (bc > 0 ? bc : 1);
-        G.emit_compact = sms * (bf > 0 ? bf : 1);
         G.adjoint = sms * (ba > 0 ? ba : 1);
+        G.fused = sms * (bu > 0 ? bu : 1);
         G.emit = sms * (be > 0 ? be : 1);
     }
     out = G;
@@ -1133,21 +1377,36 @@ static cudaError_t launch_count_scan(const McParams &p, const CUtensorMap &map, 
     return cudaGetLastError();
 }
 
+// One group of up to 4 isovalues.  A group of 1-2 with room for its stored
+// classification: count pass, tile scan, emit from the stored
+// classification (a tile has too little triangle work there to hide the
+// single pass's per-tile waits: 512^3, 1 isovalue, 0.91 vs 1.23 ms).
+// Otherwise the single pass: the tile status words, the tile counter and
+// the abort word (the start of the tile-count region) are cleared, then
+// k_mc_fused classifies, offsets and emits every tile.
 template <int NISO>
-static cudaError_t launch_mc_group(const McParams &p, const CUtensorMap &map, const McWorkspace &w, uint64_t *ntris,
+static cudaError_t launch_mc_group(const McParams &p0, const CUtensorMap &map, const McWorkspace &w, uint64_t *ntris,
                                    int niso, cudaStream_t s)
 {
-    cudaError_t e = launch_count_scan<NISO>(p, map, w, ntris, niso, s);
-    if (e != cudaSuccess) return e;
     McGrids G;
-    mc_prepare<NISO>(G);
-    if (p.cases) {
-        const unsigned ge = (unsigned)(p.ntiles < G.emit ? p.ntiles : G.emit);
-        k_mc_emit<NISO, true><<<ge, 256, kEmitSmem, s>>>(p, map);
-    } else {
-        const unsigned ge = (unsigned)(p.ntiles < G.emit_compact ? p.ntiles : G.emit_compact);
-        k_mc_emit<NISO, false><<<ge, 256, kEmitSmem, s>>>(p, map);
+    cudaError_t e = mc_prepare<NISO>(G);
+    if (e != cudaSuccess) return e;
+    if (NISO <= 2 && p0.cases && p0.cstride >= NISO) {
+        e = launch_count_scan<NISO>(p0, map, w, ntris, niso, s);
+        if (e != cudaSuccess) return e;
+        const unsigned ge = (unsigned)(p0.ntiles < G.emit ? p0.ntiles : G.emit);
+        k_mc_emit_stored<NISO><<<ge, 256, kEmitSmem, s>>>(p0, map);
+        return cudaGetLastError();
     }
+    McParams p = p0;
+    p.tstat = reinterpret_cast<uint64_t *>(w.cnt);
+    p.tctr = reinterpret_cast<uint32_t *>(p.tstat + p.ntiles);
+    p.tabort = p.tctr + 1;
+    p.ntris = ntris;
+    e = cudaMemsetAsync(p.tstat, 0, (size_t)p.ntiles * 8 + 8, s);
+    if (e != cudaSuccess) return e;
+    const unsigned gf = (unsigned)(p.ntiles < G.fused ? p.ntiles : G.fused);
+    k_mc_fused<NISO><<<gf, 256, kEmitSmem, s>>>(p, map);
     return cudaGetLastError();
 }
 
@@ -1189,8 +1448,9 @@ cudaError_t launch_mc_pitched(const float *field, const Grid &g, int64_t sx, int
     mc_tiles(g, p.ntx, p.ncby, p.ncbz, p.ntiles);
     p.cap = cap;
     p.err = err;
-    // the stored layout when the workspace holds it, else the emit pass classifies again
-    const int cstride = (workspace_bytes >= mc_workspace_bytes(g, n_iso)) ? stored_slots(n_iso) : 0;
+    // the stored classification for a small last group when the workspace holds it
+    const int slots = small_group_slots(n_iso);
+    const int cstride = (slots && workspace_bytes >= mc_layout(g, slots, nullptr, nullptr)) ? slots : 0;
     McWorkspace w;
     mc_layout(g, cstride, workspace, &w);
     p.tile_cnt = w.cnt;
@@ -1221,7 +1481,7 @@ cudaError_t launch_mc_pitched(const float *field, const Grid &g, int64_t sx, int
 
 size_t mc_adjoint_workspace_bytes(const Grid &g, int n_iso)
 {
-    const size_t base = ((mc_workspace_bytes(g, n_iso) + 255) / 256) * 256;
+    const size_t base = ((mc_stored_workspace_bytes(g, n_iso) + 255) / 256) * 256;
     return base + (size_t)g.N * 8 + 256;
 }
 
@@ -1247,7 +1507,7 @@ cudaError_t launch_mc_adjoint(const float *field, const Grid &g, const float *is
     p.cases = w.cases;
     p.tcnt = w.tcnt;
     p.cstride = cstride;
-    const size_t base = ((mc_workspace_bytes(g, n_iso) + 255) / 256) * 256;
+    const size_t base = ((mc_stored_workspace_bytes(g, n_iso) + 255) / 256) * 256;
     AdjParams a;
     memset(&a, 0, sizeof(a));
     a.acc = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(workspace) + base);

@@ -102,23 +102,41 @@ def test_mc_overflow_reports_true_count_and_stays_in_bounds():
     assert np.array_equal(tris.cpu().numpy()[0], full[0, :cap])
 
 
-@pytest.mark.parametrize("isos", [[0.3], [-1.0, 0.5], [-1.0, -0.5, 0.5, 1.0], [-1.2, -0.6, 0.0, 0.2, 0.7, 1.1]])
+@pytest.mark.parametrize("isos", [[0.3], [-1.0, 0.5], [-1.0, -0.5, 0.5], [-1.0, -0.5, 0.5, 1.0],
+                                  [-1.2, -0.6, 0.0, 0.2, 0.7], [-1.2, -0.6, 0.0, 0.2, 0.7, 1.1]])
 def test_mc_workspace_layouts_agree(isos):
-    # the stored-classification layout (full workspace) and the compact one
-    # (minimum workspace: the emit pass classifies again) give the same bits
+    # The full workspace sends a last group of 1-2 isovalues through the
+    # count pass, tile scan and stored-classification emit; the minimum
+    # workspace (the tile arrays, about 40 bytes per 32x8x8-cell tile) sends
+    # every group through the single pass.  Same bits, the oracle's
+    # triangles, and a workspace full of stale bytes reused call after call.
     f = synth.turbulence((70, 45, 33), seed=12)
     fd = _dev(f)
     cap = 5 * 69 * 44 * 32
-    full = torch.empty(chr.isosurface_workspace_size(f.shape, len(isos)), dtype=torch.uint8, device="cuda")
-    small = torch.empty(chr.isosurface_workspace_min_size(f.shape, len(isos)), dtype=torch.uint8, device="cuda")
-    assert small.numel() < full.numel()
-    t1, c1, e1 = chr.isosurface_extract(fd, isos, cap, workspace=full)
-    t2, c2, e2 = chr.isosurface_extract(fd, isos, cap, workspace=small)
-    torch.cuda.synchronize()
-    assert torch.equal(c1, c2) and int(e1.item()) == 0 and int(e2.item()) == 0
-    for j in range(len(isos)):
+    full = chr.isosurface_workspace_size(f.shape, len(isos))
+    small = chr.isosurface_workspace_min_size(f.shape, len(isos))
+    ntiles = (69 + 31) // 32 * ((44 + 7) // 8) * ((32 + 7) // 8)
+    assert small <= 64 * ntiles + 1024
+    assert (full > small) == (len(isos) % 4 in (1, 2))
+    out = []
+    for nbytes in (full, small, small, full):
+        ws = torch.full((nbytes,), 0xA5, dtype=torch.uint8, device="cuda")
+        t, c, e = chr.isosurface_extract(fd, isos, cap, workspace=ws)
+        torch.cuda.synchronize()
+        assert int(e.item()) == 0
+        out.append((t, c))
+    t1, c1 = out[0]
+    for t2, c2 in out[1:]:
+        assert torch.equal(c1, c2)
+        for j in range(len(isos)):
+            n = int(c1[j])
+            assert torch.equal(t1[j, :n].view(torch.int32), t2[j, :n].view(torch.int32)), j
+    nz, ny, nx = f.shape
+    for j, k in enumerate(isos):
         n = int(c1[j])
-        assert torch.equal(t1[j, :n].view(torch.int32), t2[j, :n].view(torch.int32)), j
+        mesh = oracle.mc(f, k)
+        assert n == mesh.ntri, k
+        compare_mesh(t1[j, :n].cpu().numpy(), mesh, (nx, ny, nz), f"layouts k={k}")
 
 
 def test_mc_dense_tiles_take_their_isovalues_one_at_a_time():
@@ -127,7 +145,7 @@ def test_mc_dense_tiles_take_their_isovalues_one_at_a_time():
     # the isovalues one at a time when they do not.  White noise at four
     # isovalues fills every tile's lists several times over (the slot-by-slot
     # path); the smooth part of the field leaves its tiles on the pooled
-    # path.  Both layouts of the workspace, against the oracle.
+    # path.  Against the oracle, with a workspace full of stale bytes.
     f = synth.turbulence((70, 19, 20), seed=21)
     f = (f / np.abs(f).max()).astype(np.float32)
     f[:, :, :34] = synth.uniform_noise((20, 19, 34), 22)
@@ -138,7 +156,7 @@ def test_mc_dense_tiles_take_their_isovalues_one_at_a_time():
     meshes = [oracle.mc(f, k) for k in isos]
     assert min(m.ntri for m in meshes) > 4 * 2048  # the noise tiles alone overflow the pool
     for size in (chr.isosurface_workspace_size, chr.isosurface_workspace_min_size):
-        ws = torch.empty(size(f.shape, len(isos)), dtype=torch.uint8, device="cuda")
+        ws = torch.full((size(f.shape, len(isos)),), 0xFF, dtype=torch.uint8, device="cuda")
         tris, counts, err = chr.isosurface_extract(fd, isos, cap, workspace=ws)
         torch.cuda.synchronize()
         assert int(err.item()) == 0
