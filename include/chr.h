@@ -204,18 +204,17 @@ chr_status chr_topo_translate(const float *d_field, chr_dims dims, const float *
 
 /*
  * isosurface_workspace_size — bytes of device scratch for isosurface_extract
- * with these dims and number of isovalues: per 32x8x8-cell tile a status
- * word, its triangle counts and output offsets (the groups of 4 isovalues
- * reuse them), and when the last group has 1 or 2 isovalues the counting
- * pass's classification for that group (12 bytes per 8 cells and
- * isovalue), which its emitting pass reads back.
+ * with these dims and number of isovalues: per 32x8x8-cell tile its status
+ * word, triangle counts and output offsets, and the counting pass's
+ * classification (12 bytes per 8 cells and isovalue, at most 4 isovalues at
+ * a time) for grids large enough to take two passes.
  */
 size_t isosurface_workspace_size(chr_dims dims, uint32_t n_iso);
 
 /*
  * isosurface_workspace_min_size — the smallest workspace isosurface_extract
- * accepts: the tile arrays alone (every group then takes the single pass;
- * same output).
+ * accepts: the tile arrays alone (48 bytes per tile plus the scan chunks);
+ * every group then takes the single pass (same output).
  */
 size_t isosurface_workspace_min_size(chr_dims dims, uint32_t n_iso);
 
@@ -238,12 +237,13 @@ size_t isosurface_workspace_min_size(chr_dims dims, uint32_t n_iso);
  * *d_err.  d_err (device uint32) is cleared by the call; may be NULL.
  * d_workspace: device scratch of workspace_bytes (at least
  * isosurface_workspace_min_size(), else CHR_ERR_INVALID), overwritten by the
- * call.  Groups of 3-4 isovalues (or any group, with the minimum workspace)
- * take one launch (k_mc_fused): blocks claim tiles in order and find each
- * tile's output offset from the counts the tiles before it publish (bounded
- * waits; a wait that gives up sets CHR_ERR_TIMEOUT).  A group of 1-2 with
- * isosurface_workspace_size() bytes takes a counting pass, a scan of the
- * tile counts and an emitting pass.  Same output either way.  Asynchronous.
+ * call.  A group of n isovalues on fewer than 2048*n^3 tiles (or any group,
+ * with less than isosurface_workspace_size() bytes) takes one launch
+ * (k_mc_fused): blocks claim tiles in order and find each tile's output
+ * offset from the counts the tiles before it publish (bounded waits; a wait
+ * that gives up sets CHR_ERR_TIMEOUT).  Larger grids with the full
+ * workspace take a counting pass, a scan of the tile counts and an
+ * emitting pass.  Same output either way.  Asynchronous.
  */
 chr_status isosurface_extract(const float *d_field, chr_dims dims, const float *isovalues, uint32_t n_iso,
                               float *d_tris, uint64_t cap_tris, uint64_t *d_ntris, uint32_t *d_err, void *d_workspace,

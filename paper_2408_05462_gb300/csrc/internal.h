@@ -82,8 +82,8 @@ cudaError_t launch_scan_records(uint4 *const *recs, int nlevels, int64_t nbricks
                                 cudaStream_t s);
 
 // Marching cubes over a plain field, per group of up to 4 isovalues one
-// single-pass launch, or count + scan + emit for a group of 1-2 when the
-// workspace holds its classification.  mc_workspace_bytes: the tile arrays
+// single-pass launch, or count + scan + emit on large grids when the
+// workspace holds the classification.  mc_workspace_bytes: the tile arrays
 // plus that classification; mc_workspace_min_bytes: the tile arrays alone.
 size_t mc_workspace_bytes(const Grid &g, int n_iso);
 size_t mc_workspace_min_bytes(const Grid &g, int n_iso);

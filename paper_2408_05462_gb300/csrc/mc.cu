@@ -1,7 +1,8 @@
 // Marching cubes over a float32 field (paper Sec. 2.2; Lorensen & Cline).
 //
-// isosurface_extract: per group of up to 4 isovalues (groups of 3-4, or any
-// group when the workspace holds only the tile arrays) one launch,
+// isosurface_extract: per group of up to 4 isovalues one launch (below
+// 2048 n^3 tiles for a group of n, or whenever the workspace holds only the
+// tile arrays),
 //   k_mc_fused  persistent blocks claim 32x8x8-cell tiles in increasing
 //               order; per tile: inside masks by warp ballot, case bytes,
 //               one block scan of (triangles, active cells) for every
@@ -10,10 +11,9 @@
 //               active cells compacted, triangle -> cell by a 32-triangle
 //               window, edge interpolation, each chunk written by one TMA
 //               bulk store
-// The two-pass form serves groups of 1-2 isovalues (a tile has too little
-// triangle work there to hide the single pass's per-tile waits), the
-// adjoint and the batched path, which keep the classification for a second
-// walk over the same tiles:
+// The two-pass form serves larger grids (where the single pass's per-tile
+// waits cost more than a count pass), the adjoint and the batched path,
+// which keep the classification for a second walk over the same tiles:
 //   k_mc_count  per tile: case bytes and triangle counts -> tile_cnt (and
 //               the classification, 12 bytes per 8 cells and isovalue)
 //   k_tscan_*   exclusive scan of the tile counts -> tile_off, totals
@@ -908,9 +908,8 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
     if (lane == 0) bulk_wait_all();  // shared memory stays valid until every bulk store is done
 }
 
-// Two-pass emit from the count pass's stored classification (groups of 1-2
-// isovalues, where a tile has too little triangle work to hide the single
-// pass's per-tile waits).
+// Two-pass emit from the count pass's stored classification (large grids,
+// where the single pass's per-tile waits cost more than the count pass).
 template <int NISO>
 __global__ void __launch_bounds__(256, 4) k_mc_emit_stored(const __grid_constant__ McParams p,
                                                           const __grid_constant__ CUtensorMap map)
@@ -1289,21 +1288,14 @@ static size_t mc_layout(const Grid &g, int cstride, void *base, McWorkspace *w)
 
 static int stored_slots(int n_iso) { return n_iso < kMcIsoPerPass ? (n_iso > 0 ? n_iso : 1) : kMcIsoPerPass; }
 
-// Isovalues go in groups of 4; a last group of 1 or 2 takes the two-pass
-// form, which stores the classification of that many slots.
-static int small_group_slots(int n_iso)
-{
-    const int r = n_iso - kMcIsoPerPass * ((n_iso - 1) / kMcIsoPerPass);
-    return (n_iso > 0 && r <= 2) ? r : 0;
-}
-
-// The single pass uses the tile arrays only (status words, counter and
-// abort word in the tile-count region, inclusive prefixes in the offsets);
-// the groups reuse them in turn.  The full workspace adds the stored
-// classification for a small last group.
+// The full workspace holds the tile arrays and the count pass's
+// classification for up to 4 isovalue slots (the groups of 4 reuse it);
+// the minimum workspace the tile arrays alone, which is all the single
+// pass needs (status words, counter and abort word in the tile-count
+// region, inclusive prefixes in the offsets).
 size_t mc_workspace_bytes(const Grid &g, int n_iso)
 {
-    return mc_layout(g, small_group_slots(n_iso), nullptr, nullptr);
+    return mc_layout(g, stored_slots(n_iso), nullptr, nullptr);
 }
 
 size_t mc_workspace_min_bytes(const Grid &g, int n_iso)
@@ -1312,11 +1304,16 @@ size_t mc_workspace_min_bytes(const Grid &g, int n_iso)
     return mc_layout(g, 0, nullptr, nullptr);
 }
 
-// The adjoint's two passes keep the count pass's classification.
-static size_t mc_stored_workspace_bytes(const Grid &g, int n_iso)
-{
-    return mc_layout(g, stored_slots(n_iso), nullptr, nullptr);
-}
+// Tiles from which a group of n isovalues is faster in two passes than in
+// one, when the workspace allows both: the single pass saves the count
+// pass and its stored classification, but each tile waits for its claim,
+// its box and its look-back, which the triangle work of few isovalues or of
+// a small grid cannot hide.  Measured on 128^3..1024^3 turbulence: n = 1
+// from 1,024 (single faster) to 8,192 tiles (two-pass faster), n = 2 from
+// 8,192 to 65,536, n = 4 from 65,536 (512^3) to 221,184 (768^3).
+static int64_t two_pass_min_tiles(int n) { return (int64_t)2048 * n * n * n; }
+
+
 
 struct McGrids {
     int count, adjoint, fused, emit;  // resident blocks of each persistent kernel
@@ -1377,13 +1374,12 @@ static cudaError_t launch_count_scan(const McParams &p, const CUtensorMap &map, 
     return cudaGetLastError();
 }
 
-// One group of up to 4 isovalues.  A group of 1-2 with room for its stored
-// classification: count pass, tile scan, emit from the stored
-// classification (a tile has too little triangle work there to hide the
-// single pass's per-tile waits: 512^3, 1 isovalue, 0.91 vs 1.23 ms).
-// Otherwise the single pass: the tile status words, the tile counter and
-// the abort word (the start of the tile-count region) are cleared, then
-// k_mc_fused classifies, offsets and emits every tile.
+// One group of up to 4 isovalues.  With room for the stored classification
+// and at least two_pass_min_tiles tiles: count pass, tile scan, emit from
+// the stored classification.  Otherwise the single pass: the tile status
+// words, the tile counter and the abort word (the start of the tile-count
+// region) are cleared, then k_mc_fused classifies, offsets and emits every
+// tile.
 template <int NISO>
 static cudaError_t launch_mc_group(const McParams &p0, const CUtensorMap &map, const McWorkspace &w, uint64_t *ntris,
                                    int niso, cudaStream_t s)
@@ -1391,7 +1387,7 @@ static cudaError_t launch_mc_group(const McParams &p0, const CUtensorMap &map, c
     McGrids G;
     cudaError_t e = mc_prepare<NISO>(G);
     if (e != cudaSuccess) return e;
-    if (NISO <= 2 && p0.cases && p0.cstride >= NISO) {
+    if (p0.cases && p0.cstride >= NISO && p0.ntiles >= two_pass_min_tiles(NISO)) {
         e = launch_count_scan<NISO>(p0, map, w, ntris, niso, s);
         if (e != cudaSuccess) return e;
         const unsigned ge = (unsigned)(p0.ntiles < G.emit ? p0.ntiles : G.emit);
@@ -1448,9 +1444,8 @@ cudaError_t launch_mc_pitched(const float *field, const Grid &g, int64_t sx, int
     mc_tiles(g, p.ntx, p.ncby, p.ncbz, p.ntiles);
     p.cap = cap;
     p.err = err;
-    // the stored classification for a small last group when the workspace holds it
-    const int slots = small_group_slots(n_iso);
-    const int cstride = (slots && workspace_bytes >= mc_layout(g, slots, nullptr, nullptr)) ? slots : 0;
+    // the stored classification when the workspace holds it (large grids take two passes)
+    const int cstride = (workspace_bytes >= mc_workspace_bytes(g, n_iso)) ? stored_slots(n_iso) : 0;
     McWorkspace w;
     mc_layout(g, cstride, workspace, &w);
     p.tile_cnt = w.cnt;
@@ -1481,7 +1476,7 @@ cudaError_t launch_mc_pitched(const float *field, const Grid &g, int64_t sx, int
 
 size_t mc_adjoint_workspace_bytes(const Grid &g, int n_iso)
 {
-    const size_t base = ((mc_stored_workspace_bytes(g, n_iso) + 255) / 256) * 256;
+    const size_t base = ((mc_workspace_bytes(g, n_iso) + 255) / 256) * 256;
     return base + (size_t)g.N * 8 + 256;
 }
 
@@ -1507,7 +1502,7 @@ cudaError_t launch_mc_adjoint(const float *field, const Grid &g, const float *is
     p.cases = w.cases;
     p.tcnt = w.tcnt;
     p.cstride = cstride;
-    const size_t base = ((mc_stored_workspace_bytes(g, n_iso) + 255) / 256) * 256;
+    const size_t base = ((mc_workspace_bytes(g, n_iso) + 255) / 256) * 256;
     AdjParams a;
     memset(&a, 0, sizeof(a));
     a.acc = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(workspace) + base);

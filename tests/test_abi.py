@@ -80,10 +80,10 @@ def test_other_calls_reject_bad_arguments(L):
     assert L.isosurface_extract(None, d, iso, 1, None, 0, None, None, None, 0, None) == 1
     ws = L.isosurface_workspace_size(d, 1)
     ws_min = L.isosurface_workspace_min_size(d, 1)
-    # a last group of 1-2 isovalues adds its stored classification; groups of 3-4 need the tile arrays only
-    assert 0 < ws_min < ws
-    assert L.isosurface_workspace_size(d, 4) == L.isosurface_workspace_min_size(d, 4) == ws_min
-    assert L.isosurface_workspace_size(d, 6) == L.isosurface_workspace_size(d, 2) > ws
+    # the full workspace adds the stored classification of up to 4 isovalue slots to the tile arrays
+    assert 0 < ws_min < ws < L.isosurface_workspace_size(d, 2) < L.isosurface_workspace_size(d, 4)
+    assert L.isosurface_workspace_size(d, 4) == L.isosurface_workspace_size(d, 16)
+    assert L.isosurface_workspace_min_size(d, 16) == ws_min
     # too small a workspace, zero or too many isovalues, non-finite isovalue
     p = ctypes.c_void_p(0x1000)
     assert L.isosurface_extract(p, d, iso, 1, p, 10, p, None, p, ws_min - 1, None) == 1

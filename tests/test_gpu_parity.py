@@ -105,10 +105,9 @@ def test_mc_overflow_reports_true_count_and_stays_in_bounds():
 @pytest.mark.parametrize("isos", [[0.3], [-1.0, 0.5], [-1.0, -0.5, 0.5], [-1.0, -0.5, 0.5, 1.0],
                                   [-1.2, -0.6, 0.0, 0.2, 0.7], [-1.2, -0.6, 0.0, 0.2, 0.7, 1.1]])
 def test_mc_workspace_layouts_agree(isos):
-    # The full workspace sends a last group of 1-2 isovalues through the
-    # count pass, tile scan and stored-classification emit; the minimum
-    # workspace (the tile arrays, about 40 bytes per 32x8x8-cell tile) sends
-    # every group through the single pass.  Same bits, the oracle's
+    # A small grid takes the single pass with either workspace (the full one
+    # also holds the count pass's classification; the minimum one, the tile
+    # arrays, about 50 bytes per 32x8x8-cell tile).  Same bits, the oracle's
     # triangles, and a workspace full of stale bytes reused call after call.
     f = synth.turbulence((70, 45, 33), seed=12)
     fd = _dev(f)
@@ -117,7 +116,7 @@ def test_mc_workspace_layouts_agree(isos):
     small = chr.isosurface_workspace_min_size(f.shape, len(isos))
     ntiles = (69 + 31) // 32 * ((44 + 7) // 8) * ((32 + 7) // 8)
     assert small <= 64 * ntiles + 1024
-    assert (full > small) == (len(isos) % 4 in (1, 2))
+    assert full > small
     out = []
     for nbytes in (full, small, small, full):
         ws = torch.full((nbytes,), 0xA5, dtype=torch.uint8, device="cuda")
@@ -137,6 +136,40 @@ def test_mc_workspace_layouts_agree(isos):
         mesh = oracle.mc(f, k)
         assert n == mesh.ntri, k
         compare_mesh(t1[j, :n].cpu().numpy(), mesh, (nx, ny, nz), f"layouts k={k}")
+
+
+@pytest.mark.parametrize("shape,isos,with_oracle", [((257, 129, 129), [0.3], True),
+                                                    ((513, 257, 257), [-0.5, 0.5], False)])
+def test_mc_two_pass_and_single_pass_agree_on_large_grids(shape, isos, with_oracle):
+    # From 2048*n^3 tiles a group of n isovalues with the full workspace takes
+    # the count pass, tile scan and stored-classification emit (2048 tiles
+    # here for one isovalue, 16384 for two); the minimum workspace keeps the
+    # single pass.  The two give the same bits; one isovalue also against the
+    # oracle.
+    f = synth.turbulence(shape, seed=31)
+    fd = _dev(f)
+    nz, ny, nx = f.shape
+    ntiles = (nx - 1 + 31) // 32 * ((ny - 1 + 7) // 8) * ((nz - 1 + 7) // 8)
+    assert ntiles >= 2048 * len(isos) ** 3
+    _, c0, _ = chr.isosurface_extract(fd, isos, 0)
+    torch.cuda.synchronize()
+    cap = int(c0.max().item()) + 16
+    res = []
+    for size in (chr.isosurface_workspace_size, chr.isosurface_workspace_min_size):
+        ws = torch.full((size(f.shape, len(isos)),), 0x5A, dtype=torch.uint8, device="cuda")
+        t, c, e = chr.isosurface_extract(fd, isos, cap, workspace=ws)
+        torch.cuda.synchronize()
+        assert int(e.item()) == 0
+        res.append((t, c))
+    (t1, c1), (t2, c2) = res
+    assert torch.equal(c1, c2)
+    for j in range(len(isos)):
+        n = int(c1[j])
+        assert torch.equal(t1[j, :n].view(torch.int32), t2[j, :n].view(torch.int32)), j
+    if with_oracle:
+        mesh = oracle.mc(f, isos[0])
+        assert int(c1[0]) == mesh.ntri
+        compare_mesh(t1[0, :mesh.ntri].cpu().numpy(), mesh, (nx, ny, nz), "two-pass large grid")
 
 
 def test_mc_dense_tiles_take_their_isovalues_one_at_a_time():
