@@ -19,19 +19,6 @@ struct BrickCoord {
     int64_t b;  // linear brick index
 };
 
-__device__ __forceinline__ bool brick_of_warp(const CodecParams &p, BrickCoord &c)
-{
-    int warp = threadIdx.x >> 5;
-    int64_t g = blockIdx.x;
-    int32_t gx = (int32_t)(g % p.ngx);
-    int64_t rest = g / p.ngx;
-    c.by = (int32_t)(rest % p.nby);
-    c.bz = (int32_t)(rest / p.nby);
-    c.bx = gx * kWarpsPerBlock + warp;
-    c.b = c.bx + (int64_t)p.nbx * (c.by + (int64_t)p.nby * c.bz);
-    return c.bx < p.nbx;
-}
-
 // Number of candidate isovalues strictly above v (K sorted ascending).  Two
 // values lie on the same side of every k exactly when these counts agree,
 // because {j : v < K[j]} is always a suffix of the sorted K.
@@ -275,23 +262,60 @@ __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ Codec
     }
 }
 
-// Moves every brick's slot contents to its place in the dense stream (one
-// warp per brick and level): 16*w words to words + 16*wsum, and the
-// exceptions to exc_off.
+// Moves every brick's slot contents to its place in the dense stream: 16*w
+// words to words + 16*wsum, and the exceptions to exc_off.  A warp takes
+// kCompactBricks bricks in linear order at one level (blockIdx.y) and issues
+// the loads of all of them (records, then payloads and first exceptions)
+// before any store, so each warp keeps several bricks' bytes in flight.
+constexpr int kCompactBricks = 4;
+
 __global__ void __launch_bounds__(256) k_compact(const __grid_constant__ CodecParams p)
 {
-    BrickCoord c;
-    if (!brick_of_warp(p, c)) return;
     const int lane = threadIdx.x & 31;
     const int l = blockIdx.y;
-    const uint4 rec = p.recs[l][c.b];
-    const int w = min((int)(rec.w & 0xffu), 32), nexc = (int)(rec.w >> 16);
-    const uint4 *src = reinterpret_cast<const uint4 *>(p.slot_words[l] + 512ull * c.b);
-    uint4 *dst = reinterpret_cast<uint4 *>(p.words[l] + 16ull * rec.x);
-    for (int j = lane; j < 4 * w; j += 32) __stcs(dst + j, ld_stream_u4(src + j));
-    for (int j = lane; j < nexc; j += 32) {
-        p.exc_idx[l][rec.y + j] = p.slot_idx[l][512ull * c.b + j];
-        p.exc_val[l][rec.y + j] = p.slot_val[l][512ull * c.b + j];
+    const int64_t nbricks = (int64_t)p.nbx * p.nby * p.nbz;
+    const int64_t b0 = ((int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5)) * kCompactBricks;
+    if (b0 >= nbricks) return;
+    const int nb = (int)((nbricks - b0) < kCompactBricks ? (nbricks - b0) : kCompactBricks);
+    uint4 r = make_uint4(0u, 0u, 0u, 0u);
+    if (lane < nb) r = p.recs[l][b0 + lane];
+    uint4 rec[kCompactBricks], v[kCompactBricks];
+    uint16_t ei[kCompactBricks];
+    uint32_t ev[kCompactBricks];
+#pragma unroll
+    for (int k = 0; k < kCompactBricks; k++) {
+        v[k] = make_uint4(0u, 0u, 0u, 0u);
+        ei[k] = 0;
+        ev[k] = 0u;
+        rec[k].z = 0u;
+        rec[k].x = __shfl_sync(CHR_FULL_MASK, r.x, k);
+        rec[k].y = __shfl_sync(CHR_FULL_MASK, r.y, k);
+        rec[k].w = __shfl_sync(CHR_FULL_MASK, r.w, k);
+        const int w = min((int)(rec[k].w & 0xffu), 32), nexc = (int)(rec[k].w >> 16);
+        const size_t slot = 512ull * (uint64_t)(b0 + k);
+        if (k < nb && lane < 4 * w) v[k] = ld_stream_u4(reinterpret_cast<const uint4 *>(p.slot_words[l] + slot) + lane);
+        if (k < nb && lane < nexc) {
+            ei[k] = p.slot_idx[l][slot + lane];
+            ev[k] = p.slot_val[l][slot + lane];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kCompactBricks; k++) {
+        if (k >= nb) break;
+        const int w = min((int)(rec[k].w & 0xffu), 32), nexc = (int)(rec[k].w >> 16);
+        const size_t slot = 512ull * (uint64_t)(b0 + k);
+        const uint4 *src = reinterpret_cast<const uint4 *>(p.slot_words[l] + slot);
+        uint4 *dst = reinterpret_cast<uint4 *>(p.words[l] + 16ull * rec[k].x);
+        if (lane < 4 * w) __stcs(dst + lane, v[k]);
+        for (int j = lane + 32; j < 4 * w; j += 32) __stcs(dst + j, ld_stream_u4(src + j));  // w > 8
+        if (lane < nexc) {
+            p.exc_idx[l][rec[k].y + lane] = ei[k];
+            p.exc_val[l][rec[k].y + lane] = ev[k];
+        }
+        for (int j = lane + 32; j < nexc; j += 32) {
+            p.exc_idx[l][rec[k].y + j] = p.slot_idx[l][slot + j];
+            p.exc_val[l][rec[k].y + j] = p.slot_val[l][slot + j];
+        }
     }
 }
 
@@ -308,6 +332,30 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
 }
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// The 8 codes of packed row L (slots 8L..8L+7: bits [8WL, 8WL + 8W) of the
+// brick's stream) for a width W <= 8 known at compile time.  A row starts
+// on a byte boundary, so one 64-bit window cut from three words holds it
+// and every code sits at a fixed offset in the window.
+template <int W>
+__device__ __forceinline__ void unpack_row(const uint32_t *buf, int L, uint32_t (&q)[8])
+{
+    const uint32_t bit0 = 8u * W * (uint32_t)L;
+    const uint32_t wd = bit0 >> 5, off = bit0 & 31u;
+    const uint32_t a = buf[wd], b = buf[wd + 1];
+    const uint32_t lo = __funnelshift_r(a, b, off);
+    uint64_t win = lo;
+    if (W > 4) win |= (uint64_t)__funnelshift_r(b, buf[wd + 2], off) << 32;  // 8W > 32 bits
+#pragma unroll
+    for (int x = 0; x < 8; x++) q[x] = (uint32_t)unzigzag((uint32_t)(win >> (W * x)) & ((1u << W) - 1u));
+}
+
+template <int W>
+__device__ __forceinline__ void unpack_rows(const uint32_t *buf, int lane, uint32_t (&q)[2][8])
+{
+    unpack_row<W>(buf, lane, q[0]);
+    unpack_row<W>(buf, lane + 32, q[1]);
+}
 
 // Decode one brick per warp.  For each group of up to three levels every
 // load is issued before any is consumed: the records (one lane per level),
@@ -420,23 +468,34 @@ __device__ __forceinline__ void decode_brick(const CodecParams &p, const BrickCo
             const int nexc = (int)(rec[u].w >> 16);
             const uint32_t *buf = (s_dyn + warp * (kDecGroup * kLevelWords)) + u * kLevelWords;
             uint32_t q[2][8];  // unsigned: prefix sums wrap like the encoder's int32
-            if (w > 0) {
-                const uint32_t mask = width_mask(w);
+            switch (w) {  // (uniform across the warp) the common narrow widths with fixed offsets
+                case 1: unpack_rows<1>(buf, lane, q); break;
+                case 2: unpack_rows<2>(buf, lane, q); break;
+                case 3: unpack_rows<3>(buf, lane, q); break;
+                case 4: unpack_rows<4>(buf, lane, q); break;
+                case 5: unpack_rows<5>(buf, lane, q); break;
+                case 6: unpack_rows<6>(buf, lane, q); break;
+                case 7: unpack_rows<7>(buf, lane, q); break;
+                case 8: unpack_rows<8>(buf, lane, q); break;
+                case 0:
 #pragma unroll
-                for (int s = 0; s < 2; s++)
+                    for (int s = 0; s < 2; s++)
 #pragma unroll
-                    for (int x = 0; x < 8; x++) {
-                        const int slot = 8 * (lane + 32 * s) + x;
-                        const int pos = slot * w;
-                        const int wd = pos >> 5;
-                        const uint32_t z = __funnelshift_r(buf[wd], buf[wd + 1], pos & 31) & mask;
-                        q[s][x] = (uint32_t)unzigzag(z);
-                    }
-            } else {
+                        for (int x = 0; x < 8; x++) q[s][x] = 0u;
+                    break;
+                default: {
+                    const uint32_t mask = width_mask(w);
 #pragma unroll
-                for (int s = 0; s < 2; s++)
+                    for (int s = 0; s < 2; s++)
 #pragma unroll
-                    for (int x = 0; x < 8; x++) q[s][x] = 0u;
+                        for (int x = 0; x < 8; x++) {
+                            const int slot = 8 * (lane + 32 * s) + x;
+                            const int pos = slot * w;
+                            const int wd = pos >> 5;
+                            const uint32_t z = __funnelshift_r(buf[wd], buf[wd + 1], pos & 31) & mask;
+                            q[s][x] = (uint32_t)unzigzag(z);
+                        }
+                }
             }
             if (lane == 0) q[0][0] = rec[u].z;  // anchor
 
@@ -665,7 +724,6 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const __grid_consta
 
 }  // namespace
 
-static dim3 codec_grid(const CodecParams &p) { return dim3((unsigned)((int64_t)p.ngx * p.nby * p.nbz)); }
 
 cudaError_t launch_encode(const CodecParams &p, cudaStream_t s)
 {
@@ -677,8 +735,9 @@ cudaError_t launch_encode(const CodecParams &p, cudaStream_t s)
 
 cudaError_t launch_compact(const CodecParams &p, cudaStream_t s)
 {
-    const dim3 g = codec_grid(p);
-    k_compact<<<dim3(g.x, (unsigned)p.nlevels), 256, 0, s>>>(p);
+    const int64_t nbricks = (int64_t)p.nbx * p.nby * p.nbz;
+    const int64_t per_block = (int64_t)kWarpsPerBlock * kCompactBricks;
+    k_compact<<<dim3((unsigned)((nbricks + per_block - 1) / per_block), (unsigned)p.nlevels), 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 
