@@ -284,6 +284,16 @@ struct SrcMany {
     }
 };
 
+// After a box copy gave up: one more bounded wait for each copy this block
+// still has in flight (phase `par` of mbar[b], and of mbar[b ^ 1] when
+// `other` is set), so that no copy lands in shared memory the block has
+// left.  Kept out of line: it only runs on that failure path.
+__device__ __noinline__ void drain_box_copies(uint64_t *mbar, int b, uint32_t par, bool other, uint32_t par_other)
+{
+    mbar_wait(&mbar[b], par);
+    if (other) mbar_wait(&mbar[b ^ 1], par_other);
+}
+
 // Persistent tile loop shared by the tile kernels: the next box is fetched
 // while `body` processes the current one.  A copy that never arrives
 // (bounded wait) raises CHR_ERR_TIMEOUT and the block stops.
@@ -337,7 +347,11 @@ __device__ __forceinline__ void tile_loop(const Src &src, uint32_t *err, float *
             load_box_plain(buf, *bp, tile_origin(*bp, local));
         }
         if (!__syncthreads_and(ok)) {
-            if (tid == 0 && err) atomicOr(err, 1u << CHR_ERR_TIMEOUT);
+            if (tid == 0) {
+                if (err) atomicOr(err, 1u << CHR_ERR_TIMEOUT);
+                // (the phase of mbar[cur] was flipped after its wait; mbar[cur ^ 1]'s was not)
+                if (tma) drain_box_copies(mbar, cur, (cur ? phase1 : phase0) ^ 1u, next < ntiles, cur ? phase0 : phase1);
+            }
             return;
         }
         body(tile, local, *bp, buf);
@@ -609,6 +623,7 @@ __device__ __forceinline__ void tile_loop_claimed(const McParams &p, const CUten
             if (tid == 0) {
                 atomicExch(p.tabort, 1u);
                 if (p.err) atomicOr(p.err, 1u << CHR_ERR_TIMEOUT);
+                if (tma) drain_box_copies(mbar, cur, (cur ? phase1 : phase0) ^ 1u, false, 0u);
             }
             return;
         }
