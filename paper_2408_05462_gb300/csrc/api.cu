@@ -54,16 +54,58 @@ bool dims_ok(chr_dims d, std::string &why)
 void free_handle_buffers(chr_handle *h)
 {
     Alloc al(h->default_alloc ? nullptr : &h->alloc, h->stream);
+    al.put(h->d_rec_block, h->sz_rec_block);
+    al.put(h->d_pay_block, h->sz_pay_block);
+    h->d_rec_block = h->d_pay_block = nullptr;
     for (uint32_t l = 0; l < CHR_MAX_LEVELS; l++) {
-        al.put(h->d_recs[l], h->sz_recs);
-        al.put(h->d_words[l], h->sz_words[l]);
-        al.put(h->d_exc_idx[l], h->sz_exc_idx[l]);
-        al.put(h->d_exc_val[l], h->sz_exc_val[l]);
         h->d_recs[l] = nullptr;
         h->d_words[l] = nullptr;
         h->d_exc_idx[l] = nullptr;
         h->d_exc_val[l] = nullptr;
     }
+}
+
+size_t up256(size_t n) { return (n + 255) & ~size_t(255); }
+
+// Every level's records in one allocation; false if the allocator failed.
+bool alloc_records(chr_handle *h, Alloc &al)
+{
+    h->sz_recs = (size_t)h->g.nbricks * sizeof(uint4);
+    const size_t per = up256(h->sz_recs);
+    h->sz_rec_block = per * h->nlevels;
+    char *b = (char *)al.get(h->sz_rec_block);
+    h->d_rec_block = b;
+    if (!b) return false;
+    for (uint32_t l = 0; l < h->nlevels; l++) h->d_recs[l] = reinterpret_cast<uint4 *>(b + per * l);
+    return true;
+}
+
+// Every level's packed words, exception slots and exception values (sizes
+// from nwords and nexc, each with 64 bytes of read-ahead room) in one
+// allocation; false if the allocator failed.
+bool alloc_payload(chr_handle *h, Alloc &al)
+{
+    size_t total = 0;
+    for (uint32_t l = 0; l < h->nlevels; l++) {
+        h->sz_words[l] = h->nwords[l] * 4 + 64;
+        h->sz_exc_idx[l] = h->nexc[l] * 2 + 64;
+        h->sz_exc_val[l] = h->nexc[l] * 4 + 64;
+        total += up256(h->sz_words[l]) + up256(h->sz_exc_idx[l]) + up256(h->sz_exc_val[l]);
+    }
+    h->sz_pay_block = total;
+    char *b = (char *)al.get(total);
+    h->d_pay_block = b;
+    if (!b) return false;
+    size_t o = 0;
+    for (uint32_t l = 0; l < h->nlevels; l++) {
+        h->d_words[l] = reinterpret_cast<uint32_t *>(b + o);
+        o += up256(h->sz_words[l]);
+        h->d_exc_idx[l] = reinterpret_cast<uint16_t *>(b + o);
+        o += up256(h->sz_exc_idx[l]);
+        h->d_exc_val[l] = reinterpret_cast<uint32_t *>(b + o);
+        o += up256(h->sz_exc_val[l]);
+    }
+    return true;
 }
 
 chr_handle *new_handle(chr_dims dims, const chr_allocator *alloc, cudaStream_t s)
@@ -346,15 +388,11 @@ chr_status chr_compress(const float *d_field, chr_dims dims, const chr_params *p
         delete h;
         return fail(CHR_ERR_OOM, "chr_compress: allocator returned NULL");
     }
-    h->sz_recs = (size_t)g.nbricks * sizeof(uint4);
-    for (uint32_t l = 0; l < h->nlevels; l++) {
-        h->d_recs[l] = (uint4 *)al.get(h->sz_recs);
-        if (!h->d_recs[l]) {
-            al.put(scr, scr_bytes);
-            free_handle_buffers(h);
-            delete h;
-            return fail(CHR_ERR_OOM, "chr_compress: allocator returned NULL");
-        }
+    if (!alloc_records(h, al)) {
+        al.put(scr, scr_bytes);
+        free_handle_buffers(h);
+        delete h;
+        return fail(CHR_ERR_OOM, "chr_compress: allocator returned NULL");
     }
     CodecParams p;
     fill_codec_params(h, p);
@@ -377,18 +415,11 @@ chr_status chr_compress(const float *d_field, chr_dims dims, const chr_params *p
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     }
     if (e == cudaSuccess && st == CHR_OK) {
-        for (uint32_t l = 0; l < h->nlevels && st == CHR_OK; l++) {
+        for (uint32_t l = 0; l < h->nlevels; l++) {
             h->nwords[l] = 16 * totals[2 * l];
             h->nexc[l] = totals[2 * l + 1];
-            h->sz_words[l] = h->nwords[l] * 4 + 64;
-            h->sz_exc_idx[l] = h->nexc[l] * 2 + 64;
-            h->sz_exc_val[l] = h->nexc[l] * 4 + 64;
-            h->d_words[l] = (uint32_t *)al.get(h->sz_words[l]);
-            h->d_exc_idx[l] = (uint16_t *)al.get(h->sz_exc_idx[l]);
-            h->d_exc_val[l] = (uint32_t *)al.get(h->sz_exc_val[l]);
-            if (!h->d_words[l] || !h->d_exc_idx[l] || !h->d_exc_val[l])
-                st = fail(CHR_ERR_OOM, "chr_compress: allocator returned NULL");
         }
+        if (!alloc_payload(h, al)) st = fail(CHR_ERR_OOM, "chr_compress: allocator returned NULL");
     }
     if (e == cudaSuccess && st == CHR_OK) {
         for (uint32_t l = 0; l < h->nlevels; l++) {
@@ -833,20 +864,9 @@ chr_status chr_deserialize(const void *host_buf, size_t n, const chr_allocator *
         off += level_bytes(h, l);
     }
     Alloc al(alloc, s);
-    h->sz_recs = (size_t)g.nbricks * sizeof(uint4);
     chr_status st = CHR_OK;
+    if (!alloc_records(h, al) || !alloc_payload(h, al)) st = fail(CHR_ERR_OOM, "chr_deserialize: allocator returned NULL");
     for (uint32_t l = 0; l < nlevels && st == CHR_OK; l++) {
-        h->sz_words[l] = h->nwords[l] * 4 + 64;
-        h->sz_exc_idx[l] = h->nexc[l] * 2 + 64;
-        h->sz_exc_val[l] = h->nexc[l] * 4 + 64;
-        h->d_recs[l] = (uint4 *)al.get(h->sz_recs);
-        h->d_words[l] = (uint32_t *)al.get(h->sz_words[l]);
-        h->d_exc_idx[l] = (uint16_t *)al.get(h->sz_exc_idx[l]);
-        h->d_exc_val[l] = (uint32_t *)al.get(h->sz_exc_val[l]);
-        if (!h->d_recs[l] || !h->d_words[l] || !h->d_exc_idx[l] || !h->d_exc_val[l]) {
-            st = fail(CHR_ERR_OOM, "chr_deserialize: allocator returned NULL");
-            break;
-        }
         size_t o = level_off[l];
         const size_t nr = (size_t)g.nbricks * 16, nw = (size_t)h->nwords[l] * 4, ne = (size_t)h->nexc[l];
         cudaError_t e = cudaMemcpyAsync(h->d_recs[l], src + o, nr, cudaMemcpyHostToDevice, s);

@@ -231,6 +231,11 @@ struct chr_handle {
     uint16_t *d_exc_idx[CHR_MAX_LEVELS];
     uint32_t *d_exc_val[CHR_MAX_LEVELS];
     size_t sz_recs, sz_words[CHR_MAX_LEVELS], sz_exc_idx[CHR_MAX_LEVELS], sz_exc_val[CHR_MAX_LEVELS];
+    // the arrays above live in two allocations: every level's records in one
+    // block, every level's packed words and exception slots and values in
+    // the other (each array 256-byte aligned inside its block)
+    void *d_rec_block, *d_pay_block;
+    size_t sz_rec_block, sz_pay_block;
     chr_allocator alloc;
     bool default_alloc;
     cudaStream_t stream;
