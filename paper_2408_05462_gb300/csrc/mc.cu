@@ -32,6 +32,8 @@
 // (y, z) = (t&7, (t>>3)&7), so thread order is output order.
 #include <string.h>
 
+#include <atomic>
+#include <mutex>
 #include <type_traits>
 
 #include "common.cuh"
@@ -1337,29 +1339,39 @@ struct McGrids {
 template <int NISO>
 static cudaError_t mc_prepare(McGrids &out)
 {
-    static McGrids Gd[kMaxDevices] = {};  // resident blocks, computed once per device
-    McGrids &G = Gd[current_device()];
-    if (!G.fused) {
-        cudaError_t e = cudaFuncSetAttribute(k_mc_adjoint<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_mc_count<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCountSmem);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_mc_fused<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_mc_emit_stored<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
-        if (e != cudaSuccess) return e;
-        int dev = current_device(), sms = 0, bc = 0, ba = 0, bu = 0, be = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bc, k_mc_count<NISO>, 256, kCountSmem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ba, k_mc_adjoint<NISO>, 256, kEmitSmem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu, k_mc_fused<NISO>, 256, kEmitSmem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&be, k_mc_emit_stored<NISO>, 256, kEmitSmem);
-        G.count = sms * (bc > 0 ? bc : 1);
-        G.adjoint = sms * (ba > 0 ? ba : 1);
-        G.fused = sms * (bu > 0 ? bu : 1);
-        G.emit = sms * (be > 0 ? be : 1);
+    // resident blocks, computed once per device; filled under the lock and
+    // published with the flag, so a caller never sees a half-filled entry
+    static McGrids Gd[kMaxDevices] = {};
+    static std::atomic<bool> ready[kMaxDevices] = {};
+    static std::mutex mu;
+    const int dev = current_device();
+    if (!ready[dev].load(std::memory_order_acquire)) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!ready[dev].load(std::memory_order_relaxed)) {
+            cudaError_t e = cudaFuncSetAttribute(k_mc_adjoint<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
+            if (e != cudaSuccess) return e;
+            e = cudaFuncSetAttribute(k_mc_count<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCountSmem);
+            if (e != cudaSuccess) return e;
+            e = cudaFuncSetAttribute(k_mc_fused<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
+            if (e != cudaSuccess) return e;
+            e = cudaFuncSetAttribute(k_mc_emit_stored<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
+            if (e != cudaSuccess) return e;
+            int sms = 0, bc = 0, ba = 0, bu = 0, be = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bc, k_mc_count<NISO>, 256, kCountSmem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ba, k_mc_adjoint<NISO>, 256, kEmitSmem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu, k_mc_fused<NISO>, 256, kEmitSmem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&be, k_mc_emit_stored<NISO>, 256, kEmitSmem);
+            if (sms < 1) sms = 1;
+            McGrids &G = Gd[dev];
+            G.count = sms * (bc > 0 ? bc : 1);
+            G.adjoint = sms * (ba > 0 ? ba : 1);
+            G.fused = sms * (bu > 0 ? bu : 1);
+            G.emit = sms * (be > 0 ? be : 1);
+            ready[dev].store(true, std::memory_order_release);
+        }
     }
-    out = G;
+    out = Gd[dev];
     return cudaSuccess;
 }
 
@@ -1620,23 +1632,31 @@ bool mc_batch_fill(void *params, void *map, const float *field, int64_t nx, int6
 
 cudaError_t mc_batch_prepare(int &count_per_sm, int &emit_per_sm, int &sms)
 {
+    // computed once per device under the lock, published with the flag
     static int bcd[kMaxDevices] = {}, bed[kMaxDevices] = {}, nsd[kMaxDevices] = {};
+    static std::atomic<bool> ready[kMaxDevices] = {};
+    static std::mutex mu;
     const int dev = current_device();
-    int &bc = bcd[dev], &be = bed[dev], &ns = nsd[dev];
-    if (!ns) {
-        cudaError_t e = cudaFuncSetAttribute(k_mc_emit_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_mc_count_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, kCountSmem);
-        if (e != cudaSuccess) return e;
-        cudaDeviceGetAttribute(&ns, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bc, k_mc_count_batched, 256, kCountSmem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&be, k_mc_emit_batched, 256, kEmitSmem);
-        if (bc < 1) bc = 1;
-        if (be < 1) be = 1;
+    if (!ready[dev].load(std::memory_order_acquire)) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!ready[dev].load(std::memory_order_relaxed)) {
+            cudaError_t e = cudaFuncSetAttribute(k_mc_emit_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
+            if (e != cudaSuccess) return e;
+            e = cudaFuncSetAttribute(k_mc_count_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, kCountSmem);
+            if (e != cudaSuccess) return e;
+            int ns = 0, bc = 0, be = 0;
+            cudaDeviceGetAttribute(&ns, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bc, k_mc_count_batched, 256, kCountSmem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&be, k_mc_emit_batched, 256, kEmitSmem);
+            bcd[dev] = bc < 1 ? 1 : bc;
+            bed[dev] = be < 1 ? 1 : be;
+            nsd[dev] = ns < 1 ? 1 : ns;
+            ready[dev].store(true, std::memory_order_release);
+        }
     }
-    count_per_sm = bc;
-    emit_per_sm = be;
-    sms = ns;
+    count_per_sm = bcd[dev];
+    emit_per_sm = bed[dev];
+    sms = nsd[dev];
     return cudaSuccess;
 }
 
