@@ -30,6 +30,7 @@
 // x-fastest, triangles of a cell in table order.  A tile is 4 bricks along
 // x; thread t owns brick t>>6 of the tile and the 8 cells of row
 // (y, z) = (t&7, (t>>3)&7), so thread order is output order.
+#include <stdlib.h>
 #include <string.h>
 
 #include <atomic>
@@ -107,6 +108,9 @@ struct McParams {
     uint32_t *tctr;
     uint32_t *tabort;
     uint64_t *ntris;
+    // test only: a tile that never publishes its counts or prefix (-1: none),
+    // so that the tiles after it wait out their bounded look-back
+    int64_t unpublished_tile;
 };
 
 struct TileXYZ {
@@ -841,11 +845,12 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
             for (int i = 0; i < NISO; i++) own |= (uint64_t)(s_w[i][8] & 0xffffu) << (14 * i);
             uint64_t ex[NISO];
             bool ok = true;
+            const bool publish = tile != p.unpublished_tile;
             if (tile == 0) {
 #pragma unroll
                 for (int i = 0; i < NISO; i++) ex[i] = 0;
             } else {
-                if (lane == 0) st_relaxed_u64(p.tstat + tile, kTileOwn | own);
+                if (lane == 0 && publish) st_relaxed_u64(p.tstat + tile, kTileOwn | own);
                 ok = look_back<NISO>(p, tile, ex);
             }
             if (lane == 0) {
@@ -863,7 +868,7 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
                         if (incl > p.cap && p.err) atomicOr(p.err, 1u << CHR_ERR_OVERFLOW);
                     }
                 }
-                st_release_u64(p.tstat + tile, kTilePrefix | own);
+                if (publish) st_release_u64(p.tstat + tile, kTilePrefix | own);
             }
         }
         // pool entries and chunk-table entries of the slots, all lists together
@@ -1401,6 +1406,18 @@ static cudaError_t launch_count_scan(const McParams &p, const CUtensorMap &map, 
     return cudaGetLastError();
 }
 
+// Test only: CHR_TEST_UNPUBLISHED_TILE=<tile> makes that tile of the single
+// pass publish nothing, so the tiles after it give up their bounded
+// look-back and raise CHR_ERR_TIMEOUT (read at every call; -1 when unset).
+static int64_t test_unpublished_tile()
+{
+    const char *v = getenv("CHR_TEST_UNPUBLISHED_TILE");
+    if (!v || !*v) return -1;
+    char *end = nullptr;
+    const long long t = strtoll(v, &end, 10);
+    return (end && *end == '\0' && t >= 0) ? (int64_t)t : -1;
+}
+
 // One group of up to 4 isovalues.  With room for the stored classification
 // and at least two_pass_min_tiles tiles: count pass, tile scan, emit from
 // the stored classification.  Otherwise the single pass: the tile status
@@ -1422,6 +1439,7 @@ static cudaError_t launch_mc_group(const McParams &p0, const CUtensorMap &map, c
         return cudaGetLastError();
     }
     McParams p = p0;
+    p.unpublished_tile = test_unpublished_tile();
     p.tstat = reinterpret_cast<uint64_t *>(w.cnt);
     p.tctr = reinterpret_cast<uint32_t *>(p.tstat + p.ntiles);
     p.tabort = p.tctr + 1;
