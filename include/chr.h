@@ -412,6 +412,22 @@ void chr_free(chr_handle *h);
  */
 chr_status chr_pool_trim(size_t keep_bytes);
 
+/*
+ * chr_checked_build — 1 if this library was built with bounds checks
+ * (-DCHR_CHECKED: every data-dependent shared-memory index and output range
+ * on the hot paths is tested, and an access that fails is skipped), else 0.
+ */
+int chr_checked_build(void);
+
+/*
+ * chr_debug_bounds_word — in a checked build, which kernel families have
+ * seen an index fail its bounds test since the last reset: bit 0 marching
+ * cubes (extraction, batched, adjoint), bit 1 the codec (encode, decode).
+ * 0 in normal builds.  reset != 0 clears the record.  Synchronises the
+ * device.  CHR_ERR_INVALID if h_word is NULL.
+ */
+chr_status chr_debug_bounds_word(uint32_t *h_word, int reset);
+
 /* chr_last_error — message for the last failing call on this thread. */
 const char *chr_last_error(void);
 

@@ -11,7 +11,8 @@ chr_serve_request, chr_serve_request_bytes, chr_box_tri_bound,
 chr_topo_translate,
 isosurface_extract, isosurface_workspace_size, isosurface_workspace_min_size, isosurface_extract_noalloc,
 isosurface_backward, isosurface_distance_loss, chr_serialize, chr_deserialize,
-chr_stats, chr_free, chr_pool_trim, and the chr_batch_* calls (class Batch).
+chr_stats, chr_free, chr_pool_trim, chr_checked_build, chr_debug_bounds_word, and the chr_batch_*
+calls (class Batch).
 """
 from __future__ import annotations
 
@@ -140,6 +141,9 @@ def lib():
         L.chr_free.argtypes = [c_void_p]
         L.chr_pool_trim.restype = st
         L.chr_pool_trim.argtypes = [c_size_t]
+        L.chr_checked_build.restype = c_int
+        L.chr_debug_bounds_word.restype = st
+        L.chr_debug_bounds_word.argtypes = [POINTER(c_uint32), c_int]
         L.chr_batch_create.restype = st
         L.chr_batch_create.argtypes = [POINTER(ChrBatchItem), c_uint32, c_void_p, c_uint64, c_void_p, c_void_p,
                                        POINTER(ChrAllocator), c_void_p, POINTER(c_void_p)]
@@ -261,6 +265,20 @@ def chr_compress(field: torch.Tensor, error_bounds, isovalues=(), topo: str = "f
     _check(lib().chr_compress(field.data_ptr(), _dims(field), ctypes.byref(prm), alloc, _stream(stream),
                               ctypes.byref(out)))
     return Chr(out.value, field.shape)
+
+
+def chr_checked_build() -> bool:
+    """Whether the loaded library has the kernels' bounds tests compiled in
+    (chr.h: chr_checked_build; build.build(checked=True) makes it)."""
+    return bool(lib().chr_checked_build())
+
+
+def chr_debug_bounds_word(reset: bool = False) -> int:
+    """Kernel families that saw an index fail its bounds test in a checked
+    build: bit 0 marching cubes, bit 1 codec (chr.h: chr_debug_bounds_word)."""
+    w = c_uint32()
+    _check(lib().chr_debug_bounds_word(ctypes.byref(w), int(bool(reset))))
+    return int(w.value)
 
 
 def chr_pool_trim(keep_bytes: int = 0) -> None:

@@ -311,6 +311,22 @@ extern "C" {
 
 int chr_version(void) { return 1; }
 
+int chr_checked_build(void)
+{
+#ifdef CHR_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+chr_status chr_debug_bounds_word(uint32_t *h_word, int reset)
+{
+    if (!h_word) return fail(CHR_ERR_INVALID, "chr_debug_bounds_word: NULL output");
+    *h_word = (mc_bounds_word(reset != 0) ? 1u : 0u) | (codec_bounds_word(reset != 0) ? 2u : 0u);
+    return CHR_OK;
+}
+
 chr_status chr_pool_trim(size_t keep_bytes)
 {
     cudaMemPool_t mp = library_pool();

@@ -14,6 +14,8 @@ namespace chr {
 
 namespace {
 
+CHR_BOUNDS_WORD();
+
 struct BrickCoord {
     int32_t bx, by, bz;
     int64_t b;  // linear brick index
@@ -229,13 +231,13 @@ __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ Codec
                     acc |= (uint64_t)zz << pos;
                     pos += w;
                     if (pos >= 32) {
-                        if ((uint32_t)acc) atomicOr(&s_pk[j][wi], (uint32_t)acc);
+                        if ((uint32_t)acc && CHR_IN_BOUNDS(wi < 512u)) atomicOr(&s_pk[j][wi], (uint32_t)acc);
                         acc >>= 32;
                         pos -= 32;
                         wi++;
                     }
                 }
-                if (pos > 0 && (uint32_t)acc) atomicOr(&s_pk[j][wi], (uint32_t)acc);
+                if (pos > 0 && (uint32_t)acc && CHR_IN_BOUNDS(wi < 512u)) atomicOr(&s_pk[j][wi], (uint32_t)acc);
             }
         }
         brick_sync(j);
@@ -251,7 +253,7 @@ __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ Codec
             uint32_t pos = exc_rank;
 #pragma unroll
             for (int x = 0; x < 8; x++) {
-                if ((excm >> x) & 1u) {
+                if (((excm >> x) & 1u) && CHR_IN_BOUNDS(pos < 512u)) {
                     p.slot_idx[l][512ull * c.b + pos] = (uint16_t)(8 * r + x);
                     p.slot_val[l][512ull * c.b + pos] = __float_as_uint(f[x]);
                     pos++;
@@ -731,6 +733,19 @@ cudaError_t launch_encode(const CodecParams &p, cudaStream_t s)
     k_encode<true><<<g, 256, 0, s>>>(p);
     if ((p.nx & 7) || (p.ny & 7) || (p.nz & 7)) k_encode<false><<<g, 256, 0, s>>>(p);
     return cudaGetLastError();
+}
+
+uint32_t codec_bounds_word(bool reset)
+{
+#ifdef CHR_CHECKED
+    unsigned int v = 0u, z = 0u;
+    if (cudaMemcpyFromSymbol(&v, g_chr_bounds, sizeof(v)) != cudaSuccess) cudaGetLastError();
+    if (reset && cudaMemcpyToSymbol(g_chr_bounds, &z, sizeof(z)) != cudaSuccess) cudaGetLastError();
+    return v;
+#else
+    (void)reset;
+    return 0u;
+#endif
 }
 
 cudaError_t launch_compact(const CodecParams &p, cudaStream_t s)

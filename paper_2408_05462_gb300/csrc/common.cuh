@@ -12,7 +12,26 @@
 // a short sleep), raises CHR_ERR_TIMEOUT in the error word and moves on.
 #define CHR_SPIN_LIMIT (1u << 22)
 
+// Checked builds (-DCHR_CHECKED: libchr_checked.so, for tests): every
+// CHR_IN_BOUNDS(cond) on a hot path tests an index bound; a failed test sets
+// the translation unit's bounds word (declared by CHR_BOUNDS_WORD(), read
+// by chr_debug_bounds_word) and the caller skips the access.  Normal builds
+// compile the tests away.
+#ifdef CHR_CHECKED
+#define CHR_BOUNDS_WORD() __device__ unsigned int g_chr_bounds = 0u
+#define CHR_IN_BOUNDS(cond) ::chr::in_bounds_checked((cond), &g_chr_bounds)
+#else
+#define CHR_BOUNDS_WORD() static_assert(true, "")
+#define CHR_IN_BOUNDS(cond) true
+#endif
+
 namespace chr {
+
+__device__ __forceinline__ bool in_bounds_checked(bool c, unsigned int *word)
+{
+    if (!c) atomicOr(word, 1u);
+    return c;
+}
 
 __device__ __forceinline__ uint32_t zigzag(int32_t d) { return ((uint32_t)d << 1) ^ (uint32_t)(d >> 31); }
 

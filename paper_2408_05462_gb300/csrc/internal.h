@@ -81,6 +81,11 @@ size_t scan_scratch_bytes(int64_t nbricks, int nlevels);
 cudaError_t launch_scan_records(uint4 *const *recs, int nlevels, int64_t nbricks, void *scratch, uint64_t *totals,
                                 cudaStream_t s);
 
+// Checked builds: the bounds word of the marching-cubes and the codec kernels
+// (non-zero once an index failed its test); 0 in normal builds.  Synchronises.
+uint32_t mc_bounds_word(bool reset);
+uint32_t codec_bounds_word(bool reset);
+
 // Marching cubes over a plain field, per group of up to 4 isovalues one
 // single-pass launch, or count + scan + emit on large grids when the
 // workspace holds the classification.  mc_workspace_bytes: the tile arrays

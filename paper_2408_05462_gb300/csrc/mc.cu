@@ -46,6 +46,8 @@ namespace chr {
 
 namespace {
 
+CHR_BOUNDS_WORD();
+
 __device__ const uint64_t g_mc_case[256] = CHR_MC_CASE_INIT;
 
 constexpr int kTX = 8 * kMcBricksX;                    // cells per tile along x (32)
@@ -745,10 +747,12 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
                 const uint32_t cb = ((x < 4 ? lo : hi) >> (8 * (x & 3))) & 0xffu;
                 const uint32_t c = s_cnt[cb];
                 if (c) {
-                    s_act[a] = (uint32_t)(tid * 8 + x) | (cb << 11);
-                    s_apre[a] = (uint16_t)pre;
+                    if (CHR_IN_BOUNDS(a < (uint32_t)kPool)) {
+                        s_act[a] = (uint32_t)(tid * 8 + x) | (cb << 11);
+                        s_apre[a] = (uint16_t)pre;
+                    }
                     const uint32_t q = (pre + 31u) >> 5;
-                    if ((q << 5) < pre + c) s_chunk[cq + q] = (uint16_t)a;
+                    if ((q << 5) < pre + c && CHR_IN_BOUNDS(cq + q < (uint32_t)kMaxChunks)) s_chunk[cq + q] = (uint16_t)a;
                     a++;
                     pre += c;
                 }
@@ -771,23 +775,29 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
             for (int q = (warp - (int)cq) & 7; 32 * q < lim; q += 8) {
                 const int base = 32 * q;
                 const int mm = (lim - base) < 32 ? (lim - base) : 32;
+                // (uniform across the warp: a chunk whose table entry or output range is out of bounds is skipped)
+                if (!CHR_IN_BOUNDS(cq + q < (uint32_t)kMaxChunks && g0 + (uint64_t)(base + mm) <= p.cap)) continue;
                 const int a_lo = s_chunk[cq + q];
-                const int s0 = (int)s_apre[a_lo + lane] - base;
+                const int s0 = CHR_IN_BOUNDS(a_lo + lane < kPool) ? (int)s_apre[a_lo + lane] - base : 32;
                 const uint32_t mark = (s0 > 0 && s0 < 32) ? (1u << s0) : 0u;
                 const uint32_t starts = __reduce_or_sync(CHR_FULL_MASK, mark);
                 const int jj = __popc(starts & le);
                 if (lane == 0) bulk_wait_read_all();  // the previous chunk's bulk store has read the staging buffer
                 __syncwarp();
-                if (lane < mm) {
+                if (lane < mm && CHR_IN_BOUNDS(a_lo + jj < kPool)) {
                     const int a = a_lo + jj;
                     const uint32_t e = s_act[a];
                     const int t = base + lane - (int)s_apre[a];
-                    const uint32_t tri = s_tri[(e >> 11) * CHR_MC_MAX_TRI + t];
                     const uint32_t c = e & 2047u;
                     const uint32_t lx = (c & 7u) + ((c >> 6) & 0x18u), cly = (c >> 3) & 7u, clz = (c >> 6) & 7u;
-                    make_triangle_w<FAST>(stage + 9 * lane, boxB + 4u * (clz * kPlane + cly * kVX + lx), s_edgew, tri,
-                                          k, fx0 + small_to_float(lx), fy0 + small_to_float(cly),
-                                          fz0 + small_to_float(clz));
+                    // the triangle's table entry, and the cell's far corner inside the box
+                    if (CHR_IN_BOUNDS(t >= 0 && t < CHR_MC_MAX_TRI &&
+                                      4u * (clz * kPlane + cly * kVX + lx + 1u + kVX + kPlane) < (uint32_t)kTileBytes)) {
+                        const uint32_t tri = s_tri[(e >> 11) * CHR_MC_MAX_TRI + t];
+                        make_triangle_w<FAST>(stage + 9 * lane, boxB + 4u * (clz * kPlane + cly * kVX + lx), s_edgew,
+                                              tri, k, fx0 + small_to_float(lx), fy0 + small_to_float(cly),
+                                              fz0 + small_to_float(clz));
+                    }
                 }
                 fence_proxy_async_smem();
                 __syncwarp();
@@ -888,7 +898,8 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
                     // without a stored classification the case bytes are made again rather than kept
                     if (!STORED) cases8(s_row + i * kRows, r00, j, nvalid, lo[i], hi[i]);
                     compact(lo[i], hi[i], ab + (ex >> 16), ex & 0xffffu, cq);
-                    if (tid < 32) s_apre[ab + na + tid] = 0xffffu;  // window tail past the last active cell
+                    if (tid < 32 && CHR_IN_BOUNDS(ab + na + tid < (uint32_t)kPool))
+                        s_apre[ab + na + tid] = 0xffffu;  // window tail past the last active cell
                     ab += na + 32u;
                     cq += (n + 31u) >> 5;
                 }
@@ -914,7 +925,7 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
                 const uint32_t packed = classify(i, l, h);
                 const uint32_t ex = s_w[i][warp] + warp_incl_scan_u32(packed, lane) - packed;
                 compact(l, h, ex >> 16, ex & 0xffffu, 0u);
-                if (tid < 32) s_apre[na + tid] = 0xffffu;
+                if (tid < 32 && CHR_IN_BOUNDS(na + tid < (uint32_t)kPool)) s_apre[na + tid] = 0xffffu;
                 __syncthreads();
                 chunks_any(i, n, 0u);
                 __syncthreads();  // the pool is rewritten for the next slot
@@ -1049,15 +1060,17 @@ __global__ void __launch_bounds__(256, 4) k_mc_adjoint(const __grid_constant__ M
                     const uint32_t cb = ((x < 4 ? lo : hi) >> (8 * (x & 3))) & 0xffu;
                     const uint32_t c = s_cnt[cb];
                     if (c) {
-                        s_act[ai] = (uint32_t)(tid * 8 + x) | (cb << 11);
-                        s_apre[ai] = (uint16_t)pre;
+                        if (CHR_IN_BOUNDS(ai < (uint32_t)kPool)) {
+                            s_act[ai] = (uint32_t)(tid * 8 + x) | (cb << 11);
+                            s_apre[ai] = (uint16_t)pre;
+                        }
                         const uint32_t q = (pre + 31u) >> 5;
-                        if ((q << 5) < pre + c) s_chunk[q] = (uint16_t)ai;
+                        if ((q << 5) < pre + c && CHR_IN_BOUNDS(q < (uint32_t)kMaxChunks)) s_chunk[q] = (uint16_t)ai;
                         ai++;
                         pre += c;
                     }
                 }
-                if (tid < 32) s_apre[(total >> 16) + tid] = 0xffffu;
+                if (tid < 32 && CHR_IN_BOUNDS((total >> 16) + tid < (uint32_t)kPool)) s_apre[(total >> 16) + tid] = 0xffffu;
             }
             __syncthreads();
             const uint64_t g0 = __ldg(p.tile_off + tile * kMcIsoPerPass + i);
@@ -1066,17 +1079,19 @@ __global__ void __launch_bounds__(256, 4) k_mc_adjoint(const __grid_constant__ M
             const float *gin = a.grad[i] + 9ull * g0;
             for (int q = warp; 32 * q < lim; q += 8) {
                 const int base = 32 * q;
+                if (!CHR_IN_BOUNDS(q < kMaxChunks)) continue;  // uniform across the warp
                 const int a_lo = s_chunk[q];
-                const int s0 = (int)s_apre[a_lo + lane] - base;
+                const int s0 = CHR_IN_BOUNDS(a_lo + lane < kPool) ? (int)s_apre[a_lo + lane] - base : 32;
                 const uint32_t mark = (s0 > 0 && s0 < 32) ? (1u << s0) : 0u;
                 const uint32_t starts = __reduce_or_sync(CHR_FULL_MASK, mark);
                 const int jj = __popc(starts & (0xffffffffu >> (31 - lane)));
                 const int m = base + lane;
-                if (m < lim) {
+                if (m < lim && CHR_IN_BOUNDS(a_lo + jj < kPool)) {
                     const int aa = a_lo + jj;
                     const uint32_t e = s_act[aa];
                     const int t = m - (int)s_apre[aa];
-                    const uint32_t tri = s_tri[(e >> 11) * CHR_MC_MAX_TRI + t];
+                    const uint32_t tri =
+                        CHR_IN_BOUNDS(t >= 0 && t < CHR_MC_MAX_TRI) ? s_tri[(e >> 11) * CHR_MC_MAX_TRI + t] : 0u;
                     const uint32_t c = e & 2047u;
                     const uint32_t lx = c & 7u, cly = (c >> 3) & 7u, clz = (c >> 6) & 7u, jb = c >> 9;
                     const uint32_t cellB = boxB + 4u * (clz * kPlane + cly * kVX + 8u * jb + lx);
@@ -1676,6 +1691,19 @@ cudaError_t mc_batch_prepare(int &count_per_sm, int &emit_per_sm, int &sms)
     emit_per_sm = bed[dev];
     sms = nsd[dev];
     return cudaSuccess;
+}
+
+uint32_t mc_bounds_word(bool reset)
+{
+#ifdef CHR_CHECKED
+    unsigned int v = 0u, z = 0u;
+    if (cudaMemcpyFromSymbol(&v, g_chr_bounds, sizeof(v)) != cudaSuccess) cudaGetLastError();
+    if (reset && cudaMemcpyToSymbol(g_chr_bounds, &z, sizeof(z)) != cudaSuccess) cudaGetLastError();
+    return v;
+#else
+    (void)reset;
+    return 0u;
+#endif
 }
 
 cudaError_t launch_mc_batched(const McBatchLaunch &L, cudaStream_t s)
