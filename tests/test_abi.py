@@ -130,3 +130,29 @@ def test_deserialize_rejects_corrupt_bytes(L):
     rec = struct.pack("<IIiI", 0, 0, 0, 0 | (1 << 16))    # slot outside a 4x8x8 grid
     assert des(_header(nx=4, nwords=0, nexc=1) + rec + struct.pack("<H", 7) + b"\0\0" + b"\0" * 4) == 6
     assert out.value is None
+
+
+def test_deserialize_reports_a_failing_allocator(L):
+    # a valid one-brick, one-level CHR; the allocator returns NULL for the
+    # handle's record block, so the call fails with CHR_ERR_OOM before any
+    # device work and leaves no handle
+    blob = _header(nx=8, ny=8, nz=8, nlevels=1) + struct.pack("<IIiI", 0, 0, 0, 0)
+    calls = []
+
+    def alloc(n, s, c):
+        calls.append(n)
+        return None
+
+    fail = chr.ChrAllocator(chr.ALLOC_FN(alloc), chr.FREE_FN(lambda p, n, s, c: None), None)
+    out = ctypes.c_void_p()
+    assert L.chr_deserialize(blob, len(blob), ctypes.byref(fail), None, ctypes.byref(out)) == 2
+    assert out.value is None and len(calls) == 1
+
+
+def test_checked_build_is_a_separate_library():
+    # build(checked=True) makes libchr_checked.so with the kernels' bounds
+    # tests compiled in; the normal library reports none (no GPU needed)
+    normal = ctypes.CDLL(chr_build.build())
+    checked = ctypes.CDLL(chr_build.build(checked=True))
+    assert normal.chr_checked_build() == 0
+    assert checked.chr_checked_build() == 1
