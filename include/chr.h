@@ -243,7 +243,10 @@ size_t isosurface_workspace_min_size(chr_dims dims, uint32_t n_iso);
  * offset from the counts the tiles before it publish (bounded waits; a wait
  * that gives up sets CHR_ERR_TIMEOUT).  Larger grids with the full
  * workspace take a counting pass, a scan of the tile counts and an
- * emitting pass.  Same output either way.  Asynchronous.
+ * emitting pass.  Same output either way.  Asynchronous.  (Tests only: the
+ * environment variable CHR_TEST_UNPUBLISHED_TILE=<tile>, read at every
+ * call, keeps that tile of the single pass from publishing, so the tiles
+ * after it time out; leave it unset.)
  */
 chr_status isosurface_extract(const float *d_field, chr_dims dims, const float *isovalues, uint32_t n_iso,
                               float *d_tris, uint64_t cap_tris, uint64_t *d_ntris, uint32_t *d_err, void *d_workspace,
