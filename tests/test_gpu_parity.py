@@ -8,7 +8,7 @@ import pytest
 import torch
 
 import oracle
-from helpers import compare_mesh
+from helpers import brick_major_order, compare_mesh, vertex_tol
 from paper_2408_05462_gb300 import build as chr_build
 from paper_2408_05462_gb300 import chr, synth
 
@@ -170,6 +170,58 @@ def test_mc_two_pass_and_single_pass_agree_on_large_grids(shape, isos, with_orac
         mesh = oracle.mc(f, isos[0])
         assert int(c1[0]) == mesh.ntri
         compare_mesh(t1[0, :mesh.ntri].cpu().numpy(), mesh, (nx, ny, nz), "two-pass large grid")
+
+
+def test_mc_huge_values_take_the_ieee_quotient():
+    # Tiles holding a value of magnitude 2^125 or more divide with the IEEE
+    # quotient (|f1 - f0| may reach 2^126, past the fast reciprocal's
+    # range); the rest keep the fast one.  Half of this field is scaled by
+    # 5e37 (values up to about 2e38, neighbour differences far from
+    # overflow), half is not, so one call takes both paths.
+    f = synth.turbulence((80, 24, 20), seed=41)
+    f = (f / np.abs(f).max()).astype(np.float32)
+    f[:, :, 40:] *= np.float32(5e37)
+    nz, ny, nx = f.shape
+    cap = 5 * (nx - 1) * (ny - 1) * (nz - 1) + 64
+    for isos in ([-0.3, 0.3], [np.float32(-0.3) * np.float32(5e37), np.float32(0.3) * np.float32(5e37)]):
+        isos = [float(k) for k in isos]
+        for size in (chr.isosurface_workspace_size, chr.isosurface_workspace_min_size):
+            ws = torch.empty(size(f.shape, len(isos)), dtype=torch.uint8, device="cuda")
+            tris, counts, err = chr.isosurface_extract(_dev(f), isos, cap, workspace=ws)
+            torch.cuda.synchronize()
+            assert int(err.item()) == 0
+            t = tris.cpu().numpy()
+            for j, k in enumerate(isos):
+                mesh = oracle.mc(f, k)
+                assert int(counts[j]) == mesh.ntri, k
+                compare_mesh(t[j, :mesh.ntri], mesh, (nx, ny, nz), f"huge k={k}")
+
+
+def test_mc_nan_and_inf_vertices():
+    # NaN and +inf are outside (v < k is false), -inf inside.  The edge
+    # fraction t = (k - f0) / (f1 - f0) is 0 when only the far end f1 is
+    # infinite and NaN when the near end f0 is infinite (inf / inf) or either
+    # end is NaN; only the coordinate on the edge's axis carries t, so only
+    # that one may be NaN, on both sides alike
+    f = synth.turbulence((40, 30, 20), seed=43)
+    f.ravel()[::97] = np.nan
+    f.ravel()[5::89] = np.inf
+    f.ravel()[9::83] = -np.inf
+    nz, ny, nx = f.shape
+    isos = [-0.5, 0.5]
+    tris, counts, err = chr.isosurface_extract(_dev(f), isos, 5 * (nx - 1) * (ny - 1) * (nz - 1) + 64)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    t = tris.cpu().numpy()
+    for j, k in enumerate(isos):
+        mesh = oracle.mc(f, k)
+        assert int(counts[j]) == mesh.ntri, k
+        n = mesh.ntri
+        got = t[j, :n].astype(np.float64)
+        ref = mesh.pos[brick_major_order(mesh.cell, (nx, ny, nz))]
+        assert np.array_equal(np.isnan(got), np.isnan(ref)), k
+        ok = ~np.isnan(ref)
+        assert np.all(np.abs(got[ok] - ref[ok]) <= vertex_tol(ref)[ok]), k
 
 
 def test_mc_dense_tiles_take_their_isovalues_one_at_a_time():
