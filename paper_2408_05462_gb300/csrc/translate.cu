@@ -4,6 +4,25 @@
 // and either takes the minimum (accuracy 1) or builds a 256-bin histogram of
 // the next 8 bits of the float patterns that match the prefix chosen so far
 // (radix selection; non-negative floats order like their bit patterns).
+//
+// Each vertex v is summarised against the sorted isovalues by a = #{k < v}
+// and b = #{k > v}.  An edge (s, t) then holds c1 = a_t + b_s - nK isovalues
+// strictly between with s the lower end, and c2 = a_s + b_t - nK with t the
+// lower end (at most one is positive; a NaN end has a = b = 0, so neither
+// is); they are the sorted isovalues of index nK - b_s .. a_t - 1 (resp.
+// nK - b_t .. a_s - 1).  The smallest d0 of such an edge belongs to the
+// smallest isovalue above s and the smallest d1 to the largest below t, so
+// the minimum pass needs only up(s) = K[nK - b_s] - s and dn(t) = t - K[a_t - 1]
+// per vertex (both rounded down, like every element of D).
+//
+// Tiling: a block of 16 warps walks a tile of 32 x-columns by 16 rows along z.
+// Lane 31 and warp 15 are halo: they read the next tile's first column and
+// row so that every owned vertex (31 x 15 per plane) finds its +x neighbour
+// by a warp shuffle and its +y neighbour in shared memory; its +z neighbour
+// is the next plane, already in registers.  The field is read once per pass
+// (plus the one-column, one-row and one-plane halos).
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -11,23 +30,56 @@ namespace chr {
 
 namespace {
 
+constexpr int kTrWarps = 16;           // rows per tile, one warp each
+constexpr int kTrOwnX = 31;            // owned columns per tile (lane 31 is halo)
+constexpr int kTrOwnY = kTrWarps - 1;  // owned rows per tile (warp 15 is halo)
+constexpr int kTrG = 4;                // planes per shared-memory exchange
+constexpr int kTrBlocksPerSm = 2;
+
 struct TrParams {
     const float *f;
-    int64_t nx, ny, nz, N;
+    int64_t nx, ny, nz;
     int32_t nK;
-    float K[CHR_MAX_ISO];
-    int32_t pass;     // 0..3: histogram of bits [24-8*pass, 32-8*pass)
-    uint32_t prefix;  // the top 8*pass bits already selected
-    int32_t min_only;
+    float Klt[CHR_MAX_ISO];  // sorted isovalues, +inf past nK (never below a vertex)
+    float Kgt[CHR_MAX_ISO];  // sorted isovalues, -inf past nK (never above a vertex)
+    int32_t pass;            // 0..3: histogram of bits [24-8*pass, 32-8*pass)
+    uint32_t prefix;         // the top 8*pass bits already selected
+    int64_t tiles_x, tiles_y, zc, items;
     TranslateScratch sc;
 };
 
-__global__ void __launch_bounds__(256) k_translate(const __grid_constant__ TrParams p)
+// a = #{k < v} in bits 0-7, b = #{k > v} in bits 8-15 (NK >= nK, padded)
+template <int NK>
+__device__ __forceinline__ uint32_t below_above(float v, const TrParams &p)
 {
-    __shared__ unsigned int s_hist[8 * 256];  // one histogram per warp: fewer collisions
+    uint32_t a = 0, b = 0;
+#pragma unroll
+    for (int j = 0; j < NK; j++) {
+        a += (p.Klt[j] < v) ? 1u : 0u;
+        b += (v < p.Kgt[j]) ? 1u : 0u;
+    }
+    return a | (b << 8);
+}
+
+template <int NK, bool MIN>
+__global__ void __launch_bounds__(kTrWarps * 32, kTrBlocksPerSm) k_translate(const __grid_constant__ TrParams p)
+{
+    constexpr int kSlots = MIN ? 3 : 2;  // exchanged words per vertex: ab, up, dn | ab, value
+    __shared__ uint32_t s_x[kSlots][kTrG][kTrWarps][32];
+    __shared__ unsigned int s_hist[MIN ? 1 : kTrWarps * 256];  // one histogram per warp
+    __shared__ float s_kup[CHR_MAX_ISO + 1];  // sorted isovalues, +inf at nK
+    __shared__ float s_kdn[CHR_MAX_ISO + 1];  // -inf, then the sorted isovalues
     __shared__ unsigned long long s_cnt;
     __shared__ unsigned int s_min;
-    for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) s_hist[i] = 0u;
+
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (!MIN)
+        for (int i = threadIdx.x; i < kTrWarps * 256; i += blockDim.x) s_hist[i] = 0u;
+    if (threadIdx.x <= CHR_MAX_ISO) {
+        const int i = threadIdx.x;
+        s_kup[i] = (i < p.nK) ? p.Klt[i] : __int_as_float(0x7f800000);
+        s_kdn[i] = (i == 0) ? __int_as_float(0xff800000) : p.Klt[i - 1];
+    }
     if (threadIdx.x == 0) {
         s_cnt = 0ull;
         s_min = 0xffffffffu;
@@ -36,63 +88,135 @@ __global__ void __launch_bounds__(256) k_translate(const __grid_constant__ TrPar
 
     unsigned long long cnt = 0;
     unsigned int mn = 0xffffffffu;
-    unsigned int *wh = s_hist + 256 * (threadIdx.x >> 5);  // this warp's histogram
+    unsigned int *wh = s_hist + (MIN ? 0 : 256 * w);
     const int shift = 24 - 8 * p.pass;
-    // rows (y, z) are spread over the grid, x over the threads of a block
-    const int64_t nrows = p.ny * p.nz;
-    for (int64_t row = blockIdx.x; row < nrows; row += gridDim.x) {
-        const uint32_t y = (uint32_t)row % (uint32_t)p.ny;  // rows < 2^32
-        const bool has_y = (int64_t)y + 1 < p.ny, has_z = row + p.ny < nrows;
-        const float *src = p.f + row * p.nx;
-        for (int32_t x = threadIdx.x; x < p.nx; x += blockDim.x) {
-            const float s = __ldg(src + x);
-            const bool has[3] = {x + 1 < p.nx, has_y, has_z};
-            const int64_t off[3] = {1, p.nx, p.nx * p.ny};
-#pragma unroll
-            for (int a = 0; a < 3; a++) {
-                if (!has[a]) continue;
-                float lo = s, hi = __ldg(src + x + off[a]);
-                if (hi < lo) {
-                    const float t = lo;
-                    lo = hi;
-                    hi = t;
-                }
-                for (int j = 0; j < p.nK; j++) {
-                    const float k = p.K[j];
-                    if (!(lo < k && k < hi)) continue;
-                    const uint32_t d[2] = {__float_as_uint(__fsub_rd(k, lo)), __float_as_uint(__fsub_rd(hi, k))};
-#pragma unroll
-                    for (int u = 0; u < 2; u++) {
-                        cnt++;
-                        if (p.min_only) {
-                            mn = min(mn, d[u]);
-                        } else if (p.pass == 0 || (d[u] >> (shift + 8)) == p.prefix) {
-                            atomicAdd(&wh[(d[u] >> shift) & 255u], 1u);
-                        }
-                    }
+    const int nK = p.nK;
+    const int64_t plane = p.nx * p.ny;
+
+    auto put = [&](float d) {
+        const uint32_t bits = __float_as_uint(d);
+        if (p.pass == 0 || (bits >> (shift + 8)) == p.prefix) atomicAdd(&wh[(bits >> shift) & 255u], 1u);
+    };
+    // one edge: s the vertex, t its neighbour, each given by its exchanged words
+    auto edge = [&](uint32_t ab_s, uint32_t e1_s, uint32_t e2_s, uint32_t ab_t, uint32_t e1_t, uint32_t e2_t,
+                    uint32_t &c32) {
+        const int as = (int)(ab_s & 0xffu), bs = (int)(ab_s >> 8), at = (int)(ab_t & 0xffu), bt = (int)(ab_t >> 8);
+        const int c1 = at + bs - nK, c2 = as + bt - nK;
+        if (MIN) {
+            c32 += (uint32_t)(max(c1, 0) + max(c2, 0));
+            if (c1 > 0) mn = min(mn, min(e1_s, e2_t));  // up(s), dn(t)
+            if (c2 > 0) mn = min(mn, min(e1_t, e2_s));  // up(t), dn(s)
+        } else {
+            if (p.pass == 0) c32 += (uint32_t)(max(c1, 0) + max(c2, 0));
+            // one loop over the crossing isovalues (a single body keeps the
+            // unrolled kernel small enough for the instruction cache)
+            const bool s_low = c1 > 0;
+            const int c = s_low ? c1 : c2;
+            if (c > 0) {
+                const float lo = __uint_as_float(s_low ? e1_s : e1_t), hi = __uint_as_float(s_low ? e1_t : e1_s);
+                const int i0 = nK - (s_low ? bs : bt);
+                for (int i = i0; i < i0 + c; i++) {
+                    const float k = s_kup[i];
+                    put(__fsub_rd(k, lo));
+                    put(__fsub_rd(hi, k));
                 }
             }
         }
+    };
+
+    for (int64_t it = blockIdx.x; it < p.items; it += gridDim.x) {
+        const int64_t tx = it % p.tiles_x, r = it / p.tiles_x;
+        const int64_t ty = r % p.tiles_y, tz = r / p.tiles_y;
+        const int64_t x = tx * kTrOwnX + lane, y = ty * kTrOwnY + w;
+        const int64_t z0 = tz * p.zc, z1 = min(z0 + p.zc, p.nz);  // owned planes [z0, z1)
+        const int64_t zl = min(z1, p.nz - 1);                      // last plane read
+        const bool valid = x < p.nx && y < p.ny;
+        const bool own = valid && lane < kTrOwnX && w < kTrOwnY;
+        const bool hx = own && x + 1 < p.nx, hy = own && y + 1 < p.ny;
+        const float *src = p.f + (valid ? y * p.nx + x : 0);
+        auto ld = [&](int64_t z) -> float {
+            return (valid && z <= zl) ? __ldg(src + z * plane) : __int_as_float(0x7fffffff);
+        };
+        // per-vertex words: ab, then up/dn bits (MIN) or the value bits
+        auto attr = [&](float v, uint32_t &ab, uint32_t &e1, uint32_t &e2) {
+            ab = below_above<NK>(v, p);
+            if (MIN) {
+                e1 = __float_as_uint(__fsub_rd(s_kup[nK - (int)(ab >> 8)], v));
+                e2 = __float_as_uint(__fsub_rd(v, s_kdn[ab & 0xffu]));
+            } else {
+                e1 = __float_as_uint(v);
+                e2 = 0u;
+            }
+        };
+
+        uint32_t ab[kTrG + 1], e1[kTrG + 1], e2[kTrG + 1];
+        attr(ld(z0), ab[0], e1[0], e2[0]);
+        float vn[kTrG];
+#pragma unroll
+        for (int i = 0; i < kTrG; i++) vn[i] = ld(z0 + 1 + i);
+        uint32_t c32 = 0;
+        for (int64_t zb = z0; zb < z1; zb += kTrG) {
+#pragma unroll
+            for (int i = 0; i < kTrG; i++) attr(vn[i], ab[i + 1], e1[i + 1], e2[i + 1]);
+#pragma unroll
+            for (int i = 0; i < kTrG; i++) vn[i] = ld(zb + kTrG + 1 + i);  // in flight during the edges
+#pragma unroll
+            for (int i = 0; i < kTrG; i++) {
+                s_x[0][i][w][lane] = ab[i];
+                s_x[1][i][w][lane] = e1[i];
+                if (MIN) s_x[kSlots - 1][i][w][lane] = e2[i];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < kTrG; i++) {
+                const uint32_t xab = __shfl_down_sync(CHR_FULL_MASK, ab[i], 1);
+                const uint32_t xe1 = __shfl_down_sync(CHR_FULL_MASK, e1[i], 1);
+                const uint32_t xe2 = MIN ? __shfl_down_sync(CHR_FULL_MASK, e2[i], 1) : 0u;
+                const int64_t z = zb + i;
+                if (own && z < z1) {
+                    if (hx) edge(ab[i], e1[i], e2[i], xab, xe1, xe2, c32);
+                    if (hy)
+                        edge(ab[i], e1[i], e2[i], s_x[0][i][w + 1][lane], s_x[1][i][w + 1][lane],
+                             MIN ? s_x[kSlots - 1][i][w + 1][lane] : 0u, c32);
+                    if (z + 1 < p.nz) edge(ab[i], e1[i], e2[i], ab[i + 1], e1[i + 1], e2[i + 1], c32);
+                }
+            }
+            __syncthreads();
+            ab[0] = ab[kTrG];
+            e1[0] = e1[kTrG];
+            e2[0] = e2[kTrG];
+        }
+        cnt += 2ull * c32;  // d0 and d1 per crossing; c32 <= 3 * 16 per plane, and an item spans <= 2^20 planes
     }
+
     // block reduction, then one global update per block
     for (int o = 16; o > 0; o >>= 1) {
         cnt += __shfl_xor_sync(CHR_FULL_MASK, cnt, o);
         mn = min(mn, __shfl_xor_sync(CHR_FULL_MASK, mn, o));
     }
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
         if (cnt) atomicAdd(&s_cnt, cnt);
-        atomicMin(&s_min, mn);
+        if (MIN) atomicMin(&s_min, mn);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         if (s_cnt && p.pass == 0) atomicAdd(p.sc.count, s_cnt);
-        if (p.min_only) atomicMin(p.sc.minbits, s_min);
+        if (MIN) atomicMin(p.sc.minbits, s_min);
     }
-    if (!p.min_only) {
+    if (!MIN && threadIdx.x < 256) {
         unsigned long long h = 0;
-        for (int w = 0; w < 8; w++) h += s_hist[256 * w + threadIdx.x];
+        for (int v = 0; v < kTrWarps; v++) h += s_hist[256 * v + threadIdx.x];
         if (h) atomicAdd(p.sc.hist + threadIdx.x, h);
     }
+}
+
+template <int NK>
+void launch_nk(const TrParams &p, bool min_only, unsigned blocks, cudaStream_t s)
+{
+    if (min_only)
+        k_translate<NK, true><<<blocks, kTrWarps * 32, 0, s>>>(p);
+    else
+        k_translate<NK, false><<<blocks, kTrWarps * 32, 0, s>>>(p);
 }
 
 }  // namespace
@@ -102,25 +226,47 @@ size_t translate_scratch_bytes() { return 256 * sizeof(unsigned long long) + 64;
 cudaError_t launch_translate_pass(const float *field, const Grid &g, const float *K, int nK, int pass, uint32_t prefix,
                                   bool min_only, TranslateScratch sc, cudaStream_t s)
 {
+    if (nK < 1 || nK > CHR_MAX_ISO) return cudaErrorInvalidValue;
     TrParams p;
     p.f = field;
     p.nx = g.nx;
     p.ny = g.ny;
     p.nz = g.nz;
-    p.N = g.N;
     p.nK = nK;
-    for (int j = 0; j < CHR_MAX_ISO; j++) p.K[j] = (j < nK) ? K[j] : 0.0f;
+    float ks[CHR_MAX_ISO];
+    std::copy(K, K + nK, ks);
+    std::sort(ks, ks + nK);
+    for (int j = 0; j < CHR_MAX_ISO; j++) {
+        p.Klt[j] = (j < nK) ? ks[j] : INFINITY;
+        p.Kgt[j] = (j < nK) ? ks[j] : -INFINITY;
+    }
     p.pass = pass;
     p.prefix = prefix;
-    p.min_only = min_only ? 1 : 0;
     p.sc = sc;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int64_t blocks = g.ny * g.nz;
-    const int64_t cap = (int64_t)sms * 8;
-    if (blocks > cap) blocks = cap;
-    k_translate<<<(unsigned)blocks, 256, 0, s>>>(p);
+    // items: tiles x chunks of z, about 8 per resident block; a chunk's
+    // extent is capped so that a thread's per-item count fits 32 bits
+    const int64_t grid = (int64_t)sms * kTrBlocksPerSm;
+    p.tiles_x = (g.nx + kTrOwnX - 1) / kTrOwnX;
+    p.tiles_y = (g.ny + kTrOwnY - 1) / kTrOwnY;
+    const int64_t tiles = p.tiles_x * p.tiles_y;
+    int64_t chunks = std::min<int64_t>(std::max<int64_t>((8 * grid + tiles - 1) / tiles, 1), g.nz);
+    p.zc = std::min<int64_t>((g.nz + chunks - 1) / chunks, 1 << 20);
+    chunks = (g.nz + p.zc - 1) / p.zc;
+    p.items = tiles * chunks;
+    const unsigned blocks = (unsigned)std::min<int64_t>(p.items, grid);
+    if (nK <= 1)
+        launch_nk<1>(p, min_only, blocks, s);
+    else if (nK <= 2)
+        launch_nk<2>(p, min_only, blocks, s);
+    else if (nK <= 4)
+        launch_nk<4>(p, min_only, blocks, s);
+    else if (nK <= 8)
+        launch_nk<8>(p, min_only, blocks, s);
+    else
+        launch_nk<16>(p, min_only, blocks, s);
     return cudaGetLastError();
 }
 

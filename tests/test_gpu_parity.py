@@ -339,6 +339,53 @@ def test_translate_matches_oracle(acc):
     assert np.float32(eb_g).view(np.uint32) == np.float32(eb_o).view(np.uint32)
 
 
+_TRANSLATE_CASES = [
+    # (shape (nz, ny, nx), isovalues): several 31 x 15 tiles with ragged
+    # edges and z chunks; 1, 2, 3, 5, 9 and 16 isovalues (every padded
+    # count), unsorted and repeated ones
+    ((130, 61, 97), [0.3]),
+    ((70, 47, 64), [0.5, -0.5]),
+    ((33, 17, 93), [1.0, -0.5, 0.25]),
+    ((21, 90, 33), [-1.2, -0.4, 0.1, 0.6, 1.3]),
+    ((40, 31, 62), [-1.5, -1.0, -0.6, -0.2, 0.0, 0.2, 0.6, 1.0, 1.5]),
+    ((17, 29, 45), list(np.linspace(-1.6, 1.6, 15)) + [0.25]),
+    ((25, 16, 40), [0.25, -0.75, 0.25, 1.0, -0.75]),
+]
+
+
+@pytest.mark.parametrize("case", range(len(_TRANSLATE_CASES)))
+@pytest.mark.parametrize("acc", [1.0, 0.99, 0.8])
+def test_translate_tiles_and_isovalue_counts(case, acc):
+    shape, K = _TRANSLATE_CASES[case]
+    f = synth.turbulence(shape, seed=200 + case)
+    f = (f / np.abs(f).max() * 1.7).astype(np.float32)
+    eb_o, n_o = oracle.translate_eb(f, K, acc)
+    eb_g, n_g = chr.chr_topo_translate(_dev(f), [float(k) for k in K], acc)
+    assert n_g == n_o
+    assert np.float32(eb_g).view(np.uint32) == np.float32(eb_o).view(np.uint32)
+
+
+@pytest.mark.parametrize("acc", [1.0, 0.5, 0.2, 0.05])
+def test_translate_values_on_isovalues_and_non_finite(acc):
+    # an integer field with integer isovalues: many ends equal an isovalue
+    # (no crossing there: both inequalities are strict), D holds the small
+    # integers, each accuracy picks another; then NaN (never crosses) and
+    # -inf / +inf ends (d = +inf or a finite difference; at 0.05 the rank
+    # falls among the +inf elements)
+    rng = np.random.default_rng(9)
+    f = rng.integers(-3, 4, size=(23, 19, 37)).astype(np.float32)
+    K = [-2.0, 0.0, 1.0, 3.0]
+    for g in (f, f.copy()):
+        if g is not f:
+            g.ravel()[::53] = np.nan
+            g.ravel()[7::61] = np.inf
+            g.ravel()[11::67] = -np.inf
+        eb_o, n_o = oracle.translate_eb(g, K, acc)
+        eb_g, n_g = chr.chr_topo_translate(_dev(g), K, acc)
+        assert n_g == n_o
+        assert np.float32(eb_g).view(np.uint32) == np.float32(eb_o).view(np.uint32)
+
+
 def test_compress_translate_mode_matches_oracle():
     f = synth.turbulence(36, seed=77)
     K = [-0.5, 0.5]
