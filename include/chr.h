@@ -196,6 +196,8 @@ chr_status chr_brick_range(const chr_handle *h, uint32_t level, float *d_range, 
  * float32.  *eb_out = element of rank floor((1 - accuracy)*|D|) of D in
  * ascending order (min D for accuracy 1), +inf when D is empty;
  * *count_out = |D| (may be NULL).  Exact (radix selection on the float bits).
+ * An edge with a NaN end adds nothing; an infinite end makes its own
+ * difference +inf; an isovalue listed twice adds its elements twice.
  * Synchronises `stream`; scratch comes from `alloc` (NULL: the library pool).
  */
 chr_status chr_topo_translate(const float *d_field, chr_dims dims, const float *isovalues, uint32_t n_iso,
