@@ -4,8 +4,11 @@ element, or its n-th smallest to tolerate some wrong cells, is the bound).
 
 Checks: closed-form ramps whose D has known values and multiplicities,
 downward rounding of a gap that float32 cannot hold, the sign property the
-paper argues for, and the counter-example where min D does not protect a
-vertex that is on no crossing edge."""
+paper argues for, the counter-example where min D does not protect a
+vertex that is on no crossing edge, hand-worked NaN and infinite ends and a
+repeated isovalue, and D enumerated by brute force from exact rational gaps
+on tiny grids (rounding to nearest instead of down would change about a
+quarter of its elements)."""
 import numpy as np
 import pytest
 
@@ -110,3 +113,81 @@ def test_nth_smallest_rank(acc):
     # eb is the value at that rank: at most `rank` elements lie below it and
     # more than `rank` lie at or below it
     assert np.count_nonzero(D < eb) <= rank < np.count_nonzero(D <= eb)
+
+
+def test_nan_and_infinite_ends():
+    # NaN compares false with every k: an edge with a NaN end never crosses.
+    # An infinite end makes its own difference +inf and leaves the other one
+    # finite.
+    f = np.array([np.nan, 1.0, 3.0], np.float32).reshape(1, 1, 3)
+    assert sorted(oracle.translate_D(f, [2.0]).tolist()) == [1.0, 1.0]
+    f = np.array([-np.inf, 0.0], np.float32).reshape(1, 1, 2)
+    assert sorted(oracle.translate_D(f, [-1.0]).tolist()) == [1.0, np.inf]
+    f = np.array([0.0, np.inf], np.float32).reshape(1, 1, 2)
+    assert sorted(oracle.translate_D(f, [1.0]).tolist()) == [1.0, np.inf]
+    f = np.array([np.inf, -np.inf], np.float32).reshape(1, 1, 2)
+    assert oracle.translate_D(f, [5.0]).tolist() == [np.inf, np.inf]
+    f = np.array([np.nan, np.inf], np.float32).reshape(1, 1, 2)
+    assert oracle.translate_eb(f, [5.0], 1.0) == (np.inf, 0)
+
+
+def test_repeated_isovalue_counts_twice():
+    f = _ramp(7, 5, 3)
+    once = np.sort(oracle.translate_D(f, [2.25]))
+    twice = np.sort(oracle.translate_D(f, [2.25, 2.25]))
+    assert np.array_equal(twice, np.sort(np.concatenate([once, once])))
+    assert oracle.translate_eb(f, [2.25, 2.25], 1.0) == (0.25, 2 * once.size)
+
+
+def _f32_down(q):
+    """The largest float32 <= the rational q (math.inf stays inf)."""
+    from fractions import Fraction
+    if q == float("inf"):
+        return np.float32(np.inf)
+    c = np.float32(float(q))
+    while Fraction(float(c)) > q:
+        c = np.nextafter(c, np.float32(-np.inf))
+    while Fraction(float(np.nextafter(c, np.float32(np.inf)))) <= q:
+        c = np.nextafter(c, np.float32(np.inf))
+    return c
+
+
+def _brute_D(f, K):
+    """D from its definition: every edge, every listed k strictly between the
+    ends, both rounded-down gaps computed from exact rationals."""
+    from fractions import Fraction
+    nz, ny, nx = f.shape
+    out = []
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                for dz, dy, dx in ((0, 0, 1), (0, 1, 0), (1, 0, 0)):
+                    if x + dx >= nx or y + dy >= ny or z + dz >= nz:
+                        continue
+                    a, b = float(f[z, y, x]), float(f[z + dz, y + dy, x + dx])
+                    if np.isnan(a) or np.isnan(b):
+                        continue
+                    lo, hi = min(a, b), max(a, b)
+                    for k in K:
+                        k = float(np.float32(k))
+                        if lo < k < hi:
+                            d0 = float("inf") if lo == -np.inf else Fraction(k) - Fraction(lo)
+                            d1 = float("inf") if hi == np.inf else Fraction(hi) - Fraction(k)
+                            out += [_f32_down(d0), _f32_down(d1)]
+    return np.sort(np.array(out, np.float32))
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_brute_force_D_on_tiny_grids(seed):
+    # values on a coarse grid of thirds so that ends often equal an isovalue
+    # or each other, plus NaN and infinite vertices; isovalues unsorted and
+    # one repeated
+    rng = np.random.default_rng(seed)
+    f = (rng.integers(-9, 10, size=(4, 5, 6)) / 3.0).astype(np.float32)
+    f.ravel()[rng.choice(f.size, 6, replace=False)] = [np.nan, np.nan, np.inf, -np.inf, np.inf, -np.inf]
+    K = [1.0, -2.0 / 3.0, 0.1, 1.0, 2.5]
+    ref = _brute_D(f, K)
+    got = np.sort(oracle.translate_D(f, K))
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+    eb, n = oracle.translate_eb(f, K, 1.0)
+    assert n == ref.size and np.float32(eb) == ref[0]
