@@ -3,7 +3,8 @@
 Checks from outside the oracle: hand-derived single cells, closed oriented
 2-manifolds for all 256 cases and random grids, Euler characteristics of a
 sphere (2), two spheres (4) and a torus (0), exact planes, the enclosed volume
-of a sphere, and normals that point up the gradient."""
+of a sphere, normals that point up the gradient, and hand-worked cells with
+NaN and infinite corners."""
 import os
 from collections import Counter, deque
 
@@ -203,3 +204,40 @@ def test_value_equal_to_isovalue_is_outside():
     assert oracle.mc(f, 0.5).ntri == 0
     f[0, 0, 0] = np.nextafter(np.float32(0.5), np.float32(0))
     assert oracle.mc(f, 0.5).ntri == 1
+
+
+def _cell_vertices(f, k):
+    """{axis: position} of a one-cell mesh whose triangle sits on vertex 0's
+    three edges."""
+    m = oracle.mc(f, k)
+    assert m.ntri == 1
+    out = {}
+    for c in range(3):
+        i0, axis = divmod(int(m.edge_id[0, c]), 3)
+        assert i0 == 0
+        out[axis] = m.pos[0, c]
+    assert sorted(out) == [0, 1, 2]
+    return out
+
+
+def test_nan_and_infinite_corners():
+    # One cell, corner 0 inside (v < k), the rest outside.  A NaN corner is
+    # outside (NaN < k is false) and the fraction t = (k - f0) / (f1 - f0)
+    # on its edge is NaN; a +inf far end gives t = 0 (the vertex sits on the
+    # inside corner); a -inf near end gives inf / inf = NaN on every edge.
+    k = np.float32(0.5)
+    f = np.ones((2, 2, 2), np.float32)
+    f[0, 0, 0] = -1.0
+    f[0, 0, 1] = np.nan                      # the +x neighbour of corner 0
+    v = _cell_vertices(f, k)
+    assert np.isnan(v[0][0]) and v[0][1] == 0.0 and v[0][2] == 0.0
+    assert np.array_equal(v[1], [0.0, 0.75, 0.0]) and np.array_equal(v[2], [0.0, 0.0, 0.75])
+    f[0, 0, 1] = np.inf
+    v = _cell_vertices(f, k)
+    assert np.array_equal(v[0], [0.0, 0.0, 0.0])
+    f[0, 0, 1] = 1.0
+    f[0, 0, 0] = -np.inf
+    v = _cell_vertices(f, k)
+    for axis in range(3):
+        assert np.isnan(v[axis][axis])
+        assert np.all(np.delete(v[axis], axis) == 0.0)
