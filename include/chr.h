@@ -255,6 +255,24 @@ chr_status isosurface_extract(const float *d_field, chr_dims dims, const float *
                               size_t workspace_bytes, void *stream);
 
 /*
+ * chr_isosurface — the visualization side of Sec. 2 in one call: decode
+ * level `level` of the CHR and run marching cubes on it for n_iso
+ * (1..CHR_MAX_ISO) isovalues.  Equal, bit for bit, to chr_reconstruct
+ * followed by isosurface_extract on the decoded field: same triangle layout,
+ * order, counts (d_ntris, device, n_iso uint64, true counts even past
+ * cap_tris) and error word (d_err, device uint32, cleared by the call; may be
+ * NULL).  d_field_out (caller-owned, nx*ny*nz floats) receives the decoded
+ * field when not NULL; when NULL the field lives in scratch.  The scratch
+ * (the field when not kept, and the full marching-cubes workspace) comes from
+ * `alloc` (NULL: the library pool) and is released, stream-ordered, before
+ * the call returns; CHR_ERR_OOM when the allocator returns NULL, with no
+ * kernel enqueued.  Asynchronous.
+ */
+chr_status chr_isosurface(const chr_handle *h, uint32_t level, const float *isovalues, uint32_t n_iso,
+                          float *d_field_out, float *d_tris, uint64_t cap_tris, uint64_t *d_ntris, uint32_t *d_err,
+                          const chr_allocator *alloc, void *stream);
+
+/*
  * isosurface_backward — adjoint of isosurface_extract's vertex positions with
  * respect to the field (this library's reading of attributing isosurface
  * error to grid points; the paper's translation of Sec. 2.2 runs from

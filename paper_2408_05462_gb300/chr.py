@@ -8,7 +8,7 @@ CPU path: if libchr.so is missing or cannot load, every call raises.
 
 Names follow the C ABI: chr_compress, chr_reconstruct, chr_reconstruct_box, chr_brick_range,
 chr_serve_request, chr_serve_request_bytes, chr_box_tri_bound,
-chr_topo_translate,
+chr_topo_translate, chr_isosurface,
 isosurface_extract, isosurface_workspace_size, isosurface_workspace_min_size, isosurface_extract_noalloc,
 isosurface_backward, isosurface_distance_loss, chr_serialize, chr_deserialize,
 chr_stats, chr_free, chr_pool_trim, chr_checked_build, chr_debug_bounds_word, and the chr_batch_*
@@ -118,6 +118,9 @@ def lib():
         L.isosurface_extract.restype = st
         L.isosurface_extract.argtypes = [c_void_p, ChrDims, POINTER(c_float), c_uint32, c_void_p, c_uint64, c_void_p,
                                          c_void_p, c_void_p, c_size_t, c_void_p]
+        L.chr_isosurface.restype = st
+        L.chr_isosurface.argtypes = [c_void_p, c_uint32, POINTER(c_float), c_uint32, c_void_p, c_void_p, c_uint64,
+                                     c_void_p, c_void_p, POINTER(ChrAllocator), c_void_p]
         L.isosurface_extract_noalloc.restype = st
         L.isosurface_extract_noalloc.argtypes = [c_void_p, ChrDims, POINTER(c_float), c_uint32, c_void_p, c_uint64,
                                                  c_void_p, c_void_p, c_void_p]
@@ -238,6 +241,9 @@ class Chr:
 
     def brick_range(self, level: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         return chr_brick_range(self, level, out, stream)
+
+    def isosurface(self, level: int, isovalues, cap: int, field_out: torch.Tensor | None = None, stream=None):
+        return chr_isosurface(self, level, isovalues, cap, field_out=field_out, stream=stream)
 
     def free(self):
         if self._ptr is not None and self._ptr.value:
@@ -407,6 +413,32 @@ def isosurface_extract(field: torch.Tensor, isovalues, cap: int, tris: torch.Ten
     _check(lib().isosurface_extract(field.data_ptr(), _dims(field), iso, ni, tris.data_ptr() if cap > 0 else None,
                                     int(cap), counts.data_ptr(), err.data_ptr(), workspace.data_ptr(),
                                     workspace.numel(), _stream(stream)))
+    return tris, counts, err
+
+
+def chr_isosurface(h: Chr, level: int, isovalues, cap: int, field_out: torch.Tensor | None = None,
+                   tris: torch.Tensor | None = None, counts: torch.Tensor | None = None,
+                   err: torch.Tensor | None = None, stream=None):
+    """Decode level `level` of a CHR and run marching cubes on it in one call
+    (chr.h: chr_isosurface).  Returns (tris, counts, err) as isosurface_extract
+    does; field_out, when given, receives the decoded field.  Scratch comes
+    from torch's caching allocator."""
+    iso, ni = _floats(isovalues)
+    if field_out is not None:
+        _check_field(field_out)
+        if tuple(field_out.shape) != h.shape:
+            raise ValueError("field_out has the wrong shape")
+    if tris is None:
+        tris = torch.empty((ni, max(int(cap), 0), 3, 3), dtype=torch.float32, device="cuda")
+    if counts is None:
+        counts = torch.empty(ni, dtype=torch.int64, device="cuda")
+    if err is None:
+        err = torch.empty(1, dtype=torch.int32, device="cuda")
+    if tris.numel() < ni * int(cap) * 9:
+        raise ValueError("tris too small for n_iso * cap triangles")
+    _check(lib().chr_isosurface(h.ptr, int(level), iso, ni, field_out.data_ptr() if field_out is not None else None,
+                                tris.data_ptr() if cap > 0 else None, int(cap), counts.data_ptr(), err.data_ptr(),
+                                ctypes.byref(TORCH_ALLOCATOR), _stream(stream)))
     return tris, counts, err
 
 

@@ -666,6 +666,50 @@ chr_status isosurface_extract(const float *d_field, chr_dims dims, const float *
     return CHR_OK;
 }
 
+chr_status chr_isosurface(const chr_handle *h, uint32_t level, const float *isovalues, uint32_t n_iso,
+                          float *d_field_out, float *d_tris, uint64_t cap_tris, uint64_t *d_ntris, uint32_t *d_err,
+                          const chr_allocator *alloc, void *stream)
+{
+    if (!h || !d_ntris || !isovalues) return fail(CHR_ERR_INVALID, "chr_isosurface: NULL handle, counts or isovalues");
+    if (level >= h->nlevels) return fail(CHR_ERR_INVALID, "chr_isosurface: level out of range");
+    if (n_iso < 1 || n_iso > CHR_MAX_ISO) return fail(CHR_ERR_INVALID, "chr_isosurface: n_iso must be 1..16");
+    for (uint32_t j = 0; j < n_iso; j++)
+        if (!isfinite(isovalues[j])) return fail(CHR_ERR_INVALID, "chr_isosurface: isovalues must be finite");
+    if (cap_tris > 0 && !d_tris) return fail(CHR_ERR_INVALID, "chr_isosurface: NULL triangle buffer");
+    if (cap_tris > (1ull << 58)) return fail(CHR_ERR_INVALID, "chr_isosurface: cap_tris too large");
+    if ((reinterpret_cast<uintptr_t>(d_field_out) & 3u) || (reinterpret_cast<uintptr_t>(d_tris) & 3u) ||
+        (reinterpret_cast<uintptr_t>(d_ntris) & 7u) || (reinterpret_cast<uintptr_t>(d_err) & 3u))
+        return fail(CHR_ERR_INVALID, "chr_isosurface: misaligned pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    Alloc al(alloc, s);
+    const Grid &g = h->g;
+    const size_t field_bytes = d_field_out ? 0 : (size_t)g.N * sizeof(float);
+    const size_t ws_bytes = mc_workspace_bytes(g, (int)n_iso);
+    void *field_scratch = nullptr;
+    if (!d_field_out && !(field_scratch = al.get(field_bytes)))
+        return fail(CHR_ERR_OOM, "chr_isosurface: allocator returned NULL");
+    void *ws = al.get(ws_bytes);
+    if (!ws) {
+        al.put(field_scratch, field_bytes);
+        return fail(CHR_ERR_OOM, "chr_isosurface: allocator returned NULL");
+    }
+    float *field = d_field_out ? d_field_out : reinterpret_cast<float *>(field_scratch);
+    CodecParams p;
+    fill_codec_params(h, p);
+    p.out = field;
+    p.nlevels = (int32_t)level + 1;
+    set_box(p, g, 0, 0, 0, g.nx, g.ny, g.nz);
+    chr_status st = CHR_OK;
+    cudaError_t e;
+    if ((e = launch_decode(p, s)) != cudaSuccess || (e = cudaMemsetAsync(d_ntris, 0, sizeof(uint64_t) * n_iso, s)) != cudaSuccess ||
+        (d_err && (e = cudaMemsetAsync(d_err, 0, sizeof(uint32_t), s)) != cudaSuccess) ||
+        (e = launch_mc(field, g, isovalues, (int)n_iso, d_tris, cap_tris, d_ntris, d_err, ws, ws_bytes, s)) != cudaSuccess)
+        st = cuda_fail(e, "chr_isosurface");
+    al.put(ws, ws_bytes);
+    al.put(field_scratch, field_bytes);
+    return st;
+}
+
 size_t isosurface_backward_workspace_size(chr_dims dims, uint32_t n_iso)
 {
     std::string why;

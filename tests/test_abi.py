@@ -78,6 +78,7 @@ def test_other_calls_reject_bad_arguments(L):
     iso = (ctypes.c_float * 1)(0.5)
     assert L.chr_reconstruct(None, 0, ctypes.c_void_p(0x1000), None) == 1
     assert L.isosurface_extract(None, d, iso, 1, None, 0, None, None, None, 0, None) == 1
+    assert L.chr_isosurface(None, 0, iso, 1, None, None, 0, ctypes.c_void_p(0x1000), None, None, None) == 1
     ws = L.isosurface_workspace_size(d, 1)
     ws_min = L.isosurface_workspace_min_size(d, 1)
     # the full workspace adds the stored classification of up to 4 isovalue slots to the tile arrays
