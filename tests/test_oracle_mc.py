@@ -241,3 +241,25 @@ def test_nan_and_infinite_corners():
     for axis in range(3):
         assert np.isnan(v[axis][axis])
         assert np.all(np.delete(v[axis], axis) == 0.0)
+
+
+def test_body_diagonal_outside_pair_keeps_the_interior_inside():
+    # Corners 0 and 7 outside, the other six inside: every face has exactly
+    # one outside corner (three inside, no diagonal pair), so each face adds
+    # one segment cutting off its outside corner, and the six segments close
+    # into two triangles, one around each outside corner.  Edge numbers:
+    # axis * 4 + the other two offset bits (lower axis first), so corner 0's
+    # edges are 0, 4, 8 and corner 7's are 3, 7, 11.  The cell's interior
+    # stays inside and joins the six inside corners, which under 6-adjacency
+    # alone form a cycle: why the mesh's Euler characteristic is not twice
+    # that of the 6-adjacency cubical complex of the inside vertices.
+    caseb = 0xFF & ~(1 | (1 << 7))
+    tris = oracle.cell_triangles(caseb)
+    assert sorted(sorted(t) for t in tris.tolist()) == [[0, 4, 8], [3, 7, 11]]
+    f = np.ones((4, 4, 4), np.float32)
+    for j in range(8):
+        if (caseb >> j) & 1:
+            f[1 + ((j >> 2) & 1), 1 + ((j >> 1) & 1), 1 + (j & 1)] = -1.0
+    m = oracle.mc(f, 0.0)
+    _assert_closed_oriented(m)
+    assert _euler(m) == 2  # one contractible inside region
