@@ -2,8 +2,10 @@
 
 Each check comes from outside the oracle: the error bound re-checked in
 float64, the sign rule of Sec. 2.2, closed forms of the Lorenzo residual on
-plane and constant fields, exact integer round trips, and a hand-derived
-worked example (tests/golden/codec_worked_example.txt)."""
+plane and constant fields, exact integer round trips, a hand-derived
+worked example (tests/golden/codec_worked_example.txt), and every int8 value
+in every slot of a 2^3 brick against the Lorenzo residual written out by
+inclusion-exclusion (mode, width, anchor, packed bits, exact decode)."""
 import os
 
 import numpy as np
@@ -229,3 +231,72 @@ def test_sign_fix_off_can_flip_and_on_cannot():
     assert np.array_equal(enc_on.R[0] < k, f < k)
     _check_bound(f, enc_off)
     _check_bound(f, enc_on)
+
+
+def _lorenzo_2x2x2(q):
+    """3-D Lorenzo residual with zero outside the brick, written out by
+    inclusion-exclusion over the up-to-seven lower neighbours."""
+    d = np.zeros_like(q)
+    for z in range(2):
+        for y in range(2):
+            for x in range(2):
+                pred = 0
+                for dz in (0, 1):
+                    for dy in (0, 1):
+                        for dx in (0, 1):
+                            if dx == dy == dz == 0:
+                                continue
+                            if x - dx < 0 or y - dy < 0 or z - dz < 0:
+                                continue
+                            sign = 1 if (dx + dy + dz) % 2 == 1 else -1
+                            pred += sign * int(q[z - dz, y - dy, x - dx])
+                d[z, y, x] = int(q[z, y, x]) - pred
+    return d
+
+
+def test_brute_force_int8_bricks():
+    # a 2^3 grid is one partial brick; with 2e = 1 its integer values are its
+    # codes.  Every slot takes every int8 value, the others from a plane (the
+    # Lorenzo form wins near it: widths 3 to 7) or from a seeded draw (the
+    # plain codes win): the mode is the residual form of smaller width (a tie
+    # keeps the plain codes), the anchor is the code at the origin and its
+    # slot packs 0, slot s = x + 8*(y + 8*z) sits at bit s*w, and decoding is
+    # exact.
+    z, y, x = np.meshgrid(np.arange(2), np.arange(2), np.arange(2), indexing="ij")
+    g = np.random.Generator(np.random.PCG64(8))
+    seen = set()
+    for base in (20 + 3 * x - 2 * y + 5 * z, g.integers(-128, 128, size=(2, 2, 2))):
+        seen |= _brute_force_brick(base)
+    assert {m for m, _ in seen} == {0, 1} and len({w for _, w in seen}) >= 5
+
+
+def _brute_force_brick(base):
+    seen = set()
+    for slot in range(8):
+        z, y, x = (slot >> 2) & 1, (slot >> 1) & 1, slot & 1
+        for v in range(-128, 128):
+            q = base.copy()
+            q[z, y, x] = v
+            f = q.astype(np.float32)
+            enc = oracle.encode(f, [0.5], [], fix=False)
+            assert enc.exc_idx[0].size == 0
+            plain = q.copy()
+            lor = _lorenzo_2x2x2(q)
+            wp = _bitlen(_zz(plain.ravel()[1:]).max())
+            wl = _bitlen(_zz(lor.ravel()[1:]).max())
+            mode, w = (1, wl) if wl < wp else (0, wp)
+            seen.add((mode, w))
+            assert int(enc.mode(0)[0]) == mode and int(enc.width(0)[0]) == w, (slot, v)
+            assert int(enc.recs[0][0, 2].view(np.int32)) == int(q[0, 0, 0])
+            resid = (lor if mode else plain).copy()
+            resid[0, 0, 0] = 0
+            if w:
+                bits = np.unpackbits(enc.words[0].view(np.uint8), bitorder="little")
+                for zz in range(2):
+                    for yy in range(2):
+                        for xx in range(2):
+                            s = xx + 8 * (yy + 8 * zz)
+                            code = int(np.dot(bits[s * w:(s + 1) * w], 1 << np.arange(w)))
+                            assert code == int(_zz(resid[zz, yy, xx])), (slot, v, s)
+            assert np.array_equal(oracle.decode(enc, 0), f)
+    return seen
