@@ -3,8 +3,9 @@
 Checks from outside the oracle: hand-derived single cells, closed oriented
 2-manifolds for all 256 cases and random grids, Euler characteristics of a
 sphere (2), two spheres (4) and a torus (0), exact planes, the enclosed volume
-of a sphere, normals that point up the gradient, and hand-worked cells with
-NaN and infinite corners."""
+of a sphere, normals that point up the gradient, hand-worked cells with
+NaN and infinite corners, and for every case the patch's unshared sides on
+its faces, matched in reverse by every neighbouring case across each face."""
 import os
 from collections import Counter, deque
 
@@ -263,3 +264,67 @@ def test_body_diagonal_outside_pair_keeps_the_interior_inside():
     m = oracle.mc(f, 0.0)
     _assert_closed_oriented(m)
     assert _euler(m) == 2  # one contractible inside region
+
+
+def _edge_geom(e):
+    """Local edge number -> (axis, [x, y, z] offsets, None along the axis):
+    axis * 4 + the other two offset bits, lower axis first."""
+    a = e >> 2
+    others = [ax for ax in range(3) if ax != a]
+    c = [None] * 3
+    c[others[0]] = e & 1
+    c[others[1]] = (e >> 1) & 1
+    return a, c
+
+
+def _edge_num(a, c):
+    others = [ax for ax in range(3) if ax != a]
+    return 4 * a + c[others[0]] + 2 * c[others[1]]
+
+
+def _boundary_sides(caseb):
+    """Directed sides of a cell's triangles not cancelled by their reverse
+    inside the cell (fan diagonals are used twice, once each way)."""
+    sides = Counter()
+    for tri in oracle.cell_triangles(caseb).tolist():
+        for u, v in ((tri[0], tri[1]), (tri[1], tri[2]), (tri[2], tri[0])):
+            sides[(u, v)] += 1
+    assert all(n == 1 for n in sides.values())
+    return {s for s in sides if (s[1], s[0]) not in sides}
+
+
+def _on_face(e, f, s):
+    a, c = _edge_geom(e)
+    return a != f and c[f] == s
+
+
+def test_face_segments_and_shared_face_compatibility():
+    # Every side of a cell's surface patch that is not shared inside the cell
+    # lies on one of its faces.  Two cells meeting at a face (the +f face of
+    # case A and the -f face of case B, with equal corner bits there) put the
+    # same segments on it in opposite directions, so the surface continues
+    # across the face without a crack: 256 x 3 x 16 pairs.
+    bnd = {c: _boundary_sides(c) for c in range(256)}
+    for c, sides in bnd.items():
+        for u, v in sides:
+            assert any(_on_face(u, f, s) and _on_face(v, f, s) for f in range(3) for s in (0, 1)), (c, u, v)
+    pairs = 0
+    for f in range(3):
+        up = [j for j in range(8) if (j >> f) & 1]
+        for ca in range(256):
+            seg_a = set()
+            for u, v in bnd[ca]:
+                if _on_face(u, f, 1) and _on_face(v, f, 1):
+                    mapped = []
+                    for e in (u, v):
+                        a, cc = _edge_geom(e)
+                        cc[f] = 0
+                        mapped.append(_edge_num(a, cc))
+                    seg_a.add(tuple(mapped))
+            for cb in range(256):
+                if any(((ca >> j) & 1) != ((cb >> (j ^ (1 << f))) & 1) for j in up):
+                    continue
+                seg_b = {(v, u) for u, v in bnd[cb] if _on_face(u, f, 0) and _on_face(v, f, 0)}
+                assert seg_a == seg_b, (f, ca, cb)
+                pairs += 1
+    assert pairs == 3 * 256 * 16
