@@ -16,6 +16,13 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
                         surfaces, sphere volume.
   translate_D / _eb     pinned: closed-form ramps with known multiplicities,
                         downward rounding, the sign-preservation property.
+  cases                 pinned: hand-set corners of single cells, the
+                        triangle count of mc() as the sum of the cases'
+                        triangle counts, complement symmetry.
+  brick_index           pinned: brute force over tiny grids (no active cell
+                        of mc() lies in a brick whose range excludes k, and
+                        each bound is attained), hand-worked bricks at grid
+                        edges, NaN as +inf, cell-less bricks.
 """
 from __future__ import annotations
 
@@ -68,6 +75,10 @@ def _load():
         lib.orc_mc_backward.argtypes = [P, i64, i64, i64, ctypes.c_float, P, P]
         lib.orc_dist_loss.restype = ctypes.c_double
         lib.orc_dist_loss.argtypes = [P, i64, i64, i64, ctypes.c_float, P, i64, P]
+        lib.orc_cases.restype = None
+        lib.orc_cases.argtypes = [P, i64, i64, i64, ctypes.c_float, P]
+        lib.orc_brick_index.restype = None
+        lib.orc_brick_index.argtypes = [P, i64, i64, i64, P, P]
         lib.orc_translate_eb.restype = ctypes.c_float
         lib.orc_translate_eb.argtypes = [P, i64, i64, i64, P, ctypes.c_int, ctypes.c_float, P]
         _lib = lib
@@ -258,3 +269,27 @@ def dist_loss(f_orig: np.ndarray, k: float, pts: np.ndarray, with_grad: bool = T
     g = np.zeros_like(P) if with_grad else None
     L = lib.orc_dist_loss(_ptr(f), nx, ny, nz, ctypes.c_float(k), _ptr(P), P.shape[0], _ptr(g) if with_grad else None)
     return float(L), (g.reshape(np.shape(pts)) if with_grad else None)
+
+
+def cases(f: np.ndarray, k: float) -> np.ndarray:
+    """Case byte of every cell, [z, y, x] over (nz-1, ny-1, nx-1) cells; bit j
+    is corner (j&1, j>>1&1, j>>2&1) inside (v < k)."""
+    lib = _load()
+    f = _field(f)
+    nz, ny, nx = f.shape
+    out = np.zeros((nz - 1) * (ny - 1) * (nx - 1), np.uint8)
+    lib.orc_cases(_ptr(f), nx, ny, nz, ctypes.c_float(k), _ptr(out))
+    return out.reshape(nz - 1, ny - 1, nx - 1)
+
+
+def brick_index(f: np.ndarray):
+    """(lo, hi) per 8^3 brick, [nbz, nby, nbx] float32: the range over the
+    vertices of the brick's cells, NaN as +inf, (+inf, -inf) without cells."""
+    lib = _load()
+    f = _field(f)
+    nz, ny, nx = f.shape
+    nbx, nby, nbz = -(-nx // BRICK), -(-ny // BRICK), -(-nz // BRICK)
+    lo = np.zeros(nbx * nby * nbz, np.float32)
+    hi = np.zeros(nbx * nby * nbz, np.float32)
+    lib.orc_brick_index(_ptr(f), nx, ny, nz, _ptr(lo), _ptr(hi))
+    return lo.reshape(nbz, nby, nbx), hi.reshape(nbz, nby, nbx)

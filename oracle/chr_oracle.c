@@ -34,6 +34,12 @@
  *                     distances d0, d1 from the isovalue to both ends of every
  *                     edge with s0 < k < s1, and its smallest (or n-th
  *                     smallest) element.
+ *   orc_cases         the marching-cubes case byte of every cell (Sec. 2.2:
+ *                     topology preservation keeps these bytes).
+ *   orc_brick_index   Sec. 2.1, the CHR's index over its blocks for the
+ *                     candidate isovalues ("isovalue based data pruning"):
+ *                     per 8^3 brick the value range over the vertices of
+ *                     its cells.
  */
 #include <fenv.h>
 #include <math.h>
@@ -714,4 +720,67 @@ double orc_dist_loss(const float *f, int64_t nx, int64_t ny, int64_t nz, float k
         }
     }
     return npts ? sum / (double)npts : 0.0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Case bytes and the per-brick index (Sec. 2.1, Sec. 2.2)             */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Case byte of every cell for isovalue k: bit j set when corner j (offset
+ * (j&1, j>>1&1, j>>2&1)) is inside, v < k (NaN is outside).  cases[c] for
+ * cell c = x + (nx-1)*(y + (ny-1)*z).  A cell is active (carries triangles)
+ * when its byte is neither 0 nor 255.
+ */
+void orc_cases(const float *f, int64_t nx, int64_t ny, int64_t nz, float k, uint8_t *cases)
+{
+    if (nx < 2 || ny < 2 || nz < 2) return;
+    for (int64_t z = 0; z + 1 < nz; z++)
+        for (int64_t y = 0; y + 1 < ny; y++)
+            for (int64_t x = 0; x + 1 < nx; x++) {
+                int caseb = 0;
+                for (int j = 0; j < 8; j++) {
+                    int64_t v = (x + corner_off(j, 0)) + nx * ((y + corner_off(j, 1)) + ny * (z + corner_off(j, 2)));
+                    if (f[v] < k) caseb |= 1 << j;
+                }
+                cases[x + (nx - 1) * (y + (ny - 1) * z)] = (uint8_t)caseb;
+            }
+}
+
+/*
+ * Per-brick value index of a field.  Brick b = bx + nbx*(by + nby*bz)
+ * (nbx = ceil(nx/8), ...) owns the cells whose lower corner lies in it,
+ * x in [8bx, min(8bx+8, nx-1)) and likewise along y and z; those cells
+ * touch the vertices x in [8bx, min(8bx+8, nx-1)] (the brick and the first
+ * vertex plane of its +x, +y and +z neighbours).  lo[b], hi[b]: the
+ * smallest and largest value over those vertices, NaN counted as +inf.  A
+ * brick without cells gets lo = +inf, hi = -inf.  A cell of brick b is
+ * active for k only if one corner has v < k and another v >= k (or NaN),
+ * hence only if lo[b] < k <= hi[b].
+ */
+void orc_brick_index(const float *f, int64_t nx, int64_t ny, int64_t nz, float *lo, float *hi)
+{
+    const int64_t nbx = cdiv64(nx, ORC_BRICK), nby = cdiv64(ny, ORC_BRICK), nbz = cdiv64(nz, ORC_BRICK);
+    for (int64_t bz = 0; bz < nbz; bz++)
+        for (int64_t by = 0; by < nby; by++)
+            for (int64_t bx = 0; bx < nbx; bx++) {
+                const int64_t b = bx + nbx * (by + nby * bz);
+                float mn = INFINITY, mx = -INFINITY;
+                const int64_t x0 = 8 * bx, y0 = 8 * by, z0 = 8 * bz;
+                if (x0 < nx - 1 && y0 < ny - 1 && z0 < nz - 1) {
+                    const int64_t x1 = (x0 + 8 < nx - 1) ? x0 + 8 : nx - 1;
+                    const int64_t y1 = (y0 + 8 < ny - 1) ? y0 + 8 : ny - 1;
+                    const int64_t z1 = (z0 + 8 < nz - 1) ? z0 + 8 : nz - 1;
+                    for (int64_t z = z0; z <= z1; z++)
+                        for (int64_t y = y0; y <= y1; y++)
+                            for (int64_t x = x0; x <= x1; x++) {
+                                float v = f[x + nx * (y + ny * z)];
+                                if (isnan(v)) v = INFINITY;
+                                if (v < mn) mn = v;
+                                if (v > mx) mx = v;
+                            }
+                }
+                lo[b] = mn;
+                hi[b] = mx;
+            }
 }
