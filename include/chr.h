@@ -261,16 +261,55 @@ chr_status isosurface_extract(const float *d_field, chr_dims dims, const float *
  * followed by isosurface_extract on the decoded field: same triangle layout,
  * order, counts (d_ntris, device, n_iso uint64, true counts even past
  * cap_tris) and error word (d_err, device uint32, cleared by the call; may be
- * NULL).  d_field_out (caller-owned, nx*ny*nz floats) receives the decoded
- * field when not NULL; when NULL the field lives in scratch.  The scratch
- * (the field when not kept, and the full marching-cubes workspace) comes from
- * `alloc` (NULL: the library pool) and is released, stream-ordered, before
- * the call returns; CHR_ERR_OOM when the allocator returns NULL, with no
- * kernel enqueued.  Asynchronous.
+ * NULL).  Every flag combination gives that same output.
+ *
+ * Default: the decoder writes the level into a field (d_field_out, or
+ * scratch when NULL) and the marching cubes read it back, in the form
+ * isosurface_extract takes with its full workspace.
+ * CHR_ISO_INDEX: the CHR's value index (chr_brick_index) decides which 8^3
+ * bricks can hold a crossing of each isovalue (min < k <= max over the
+ * brick's cell vertices) and the others are not classified for it; their
+ * cells have no triangles.  (On GB300 the tile classification is bound by
+ * latency rather than by its instructions, and the index read costs
+ * registers: this measured no faster, so it is not the default.)
+ * CHR_ISO_FUSED: one launch per group of 4 isovalues, in which persistent
+ * blocks claim 32x8x8-cell tiles in order, decode each tile's vertex box
+ * (its 4 bricks and the first vertex planes of the bricks after them,
+ * levels 0..level with their exact vertices) straight into shared memory
+ * and mesh it there: the field never goes to memory; with CHR_ISO_INDEX a
+ * tile none of whose bricks crosses an isovalue is not even decoded.  On
+ * GB300 this form is the slower one (the per-tile decode is bound by memory
+ * latency inside each block), so it is not the default; d_field_out, when
+ * not NULL, is written by one more decoding launch.
+ * Scratch (the field, the marching-cubes workspace; with CHR_ISO_FUSED only
+ * the tile arrays, 48 bytes per tile) comes from `alloc` (NULL: the library
+ * pool) and is released, stream-ordered, before the call returns;
+ * CHR_ERR_OOM when the allocator returns NULL, with no kernel enqueued.
+ * Asynchronous.  (chr_params has no `block` field: the paper's 64^3/128^3
+ * domain blocks are the caller's boxes here, and the format's unit is the
+ * 8^3 brick; chr_params.flags stays reserved, see chr_compress.)
  */
+#define CHR_ISO_INDEX 1u
+#define CHR_ISO_FUSED 2u
 chr_status chr_isosurface(const chr_handle *h, uint32_t level, const float *isovalues, uint32_t n_iso,
                           float *d_field_out, float *d_tris, uint64_t cap_tris, uint64_t *d_ntris, uint32_t *d_err,
-                          const chr_allocator *alloc, void *stream);
+                          uint32_t flags, const chr_allocator *alloc, void *stream);
+
+/*
+ * chr_brick_index — the CHR's value index of level `level` (Sec. 2.1: an
+ * index over the blocks so that isovalue-based pruning can skip them):
+ * d_out (caller-owned, 8-byte aligned, 2 floats per 8^3 brick, brick (bx,
+ * by, bz) at bx + nbx*(by + nby*bz)) receives (min, max) of the level's
+ * reconstructed values over the vertices of the brick's cells, x in
+ * [8bx, min(8bx+8, nx-1)] and likewise along y and z (the brick and the
+ * first vertex plane of its +x, +y and +z neighbours), NaN counted as
+ * +inf; (+inf, -inf) for a brick without cells.  A cell of the brick can
+ * cross k only if min < k <= max.  chr_compress builds it (the encoder
+ * reduces each brick's reconstruction, a small pass assembles the
+ * neighbours' planes); it is stored in the byte string.  CHR_ERR_INVALID
+ * for a handle read from a version-1 string (no index).  Asynchronous.
+ */
+chr_status chr_brick_index(const chr_handle *h, uint32_t level, float *d_out, void *stream);
 
 /*
  * isosurface_backward — adjoint of isosurface_extract's vertex positions with
@@ -336,12 +375,14 @@ chr_status isosurface_extract_noalloc(const float *d_field, chr_dims dims, const
  * crosses the network in the paper's in-transit setting (Sec. 3 streams it
  * over a WAN).  Writes into host_buf when cap >= the size; *need always
  * receives the size.  Synchronises `stream`.
- * Layout: "CHR1", u32 version 1, i64 nx,ny,nz, u32 nlevels, n_iso, topo_mode,
+ * Layout: "CHR1", u32 version 2, i64 nx,ny,nz, u32 nlevels, n_iso, topo_mode,
  * flags, f32 topo_accuracy, eb_translated, u64 translate_D_count,
  * f32 eb[nlevels], f32 isovalues[n_iso], then per level u64 nwords, u64 nexc,
  * then per level: records (nbricks x {u32 wsum, u32 exc_off, i32 anchor,
  * u32 w | mode<<8 | nexc<<16}), u32 words[nwords], u16 exc_idx[nexc] padded
- * to 4 bytes, u32 exc_val[nexc] (value bits).
+ * to 4 bytes, u32 exc_val[nexc] (value bits); then per level the value
+ * index, nbricks x {f32 min, f32 max} (see chr_brick_index).  Version 1
+ * strings (no index) are still read; their handles classify every brick.
  */
 chr_status chr_serialize(const chr_handle *h, void *host_buf, size_t cap, size_t *need, void *stream);
 
@@ -454,7 +495,7 @@ chr_status chr_debug_bounds_word(uint32_t *h_word, int reset);
 /* chr_last_error — message for the last failing call on this thread. */
 const char *chr_last_error(void);
 
-/* chr_version — ABI version (1). */
+/* chr_version — ABI version (2: chr_isosurface takes flags; chr_brick_index). */
 int chr_version(void);
 
 #ifdef __cplusplus

@@ -8,7 +8,7 @@ CPU path: if libchr.so is missing or cannot load, every call raises.
 
 Names follow the C ABI: chr_compress, chr_reconstruct, chr_reconstruct_box, chr_brick_range,
 chr_serve_request, chr_serve_request_bytes, chr_box_tri_bound,
-chr_topo_translate, chr_isosurface,
+chr_topo_translate, chr_isosurface, chr_brick_index,
 isosurface_extract, isosurface_workspace_size, isosurface_workspace_min_size, isosurface_extract_noalloc,
 isosurface_backward, isosurface_distance_loss, chr_serialize, chr_deserialize,
 chr_stats, chr_free, chr_pool_trim, chr_checked_build, chr_debug_bounds_word, and the chr_batch_*
@@ -120,7 +120,9 @@ def lib():
                                          c_void_p, c_void_p, c_size_t, c_void_p]
         L.chr_isosurface.restype = st
         L.chr_isosurface.argtypes = [c_void_p, c_uint32, POINTER(c_float), c_uint32, c_void_p, c_void_p, c_uint64,
-                                     c_void_p, c_void_p, POINTER(ChrAllocator), c_void_p]
+                                     c_void_p, c_void_p, c_uint32, POINTER(ChrAllocator), c_void_p]
+        L.chr_brick_index.restype = st
+        L.chr_brick_index.argtypes = [c_void_p, c_uint32, c_void_p, c_void_p]
         L.isosurface_extract_noalloc.restype = st
         L.isosurface_extract_noalloc.argtypes = [c_void_p, ChrDims, POINTER(c_float), c_uint32, c_void_p, c_uint64,
                                                  c_void_p, c_void_p, c_void_p]
@@ -242,8 +244,9 @@ class Chr:
     def brick_range(self, level: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         return chr_brick_range(self, level, out, stream)
 
-    def isosurface(self, level: int, isovalues, cap: int, field_out: torch.Tensor | None = None, stream=None):
-        return chr_isosurface(self, level, isovalues, cap, field_out=field_out, stream=stream)
+    def isosurface(self, level: int, isovalues, cap: int, field_out: torch.Tensor | None = None, stream=None,
+                   flags: int = 0):
+        return chr_isosurface(self, level, isovalues, cap, field_out=field_out, stream=stream, flags=flags)
 
     def free(self):
         if self._ptr is not None and self._ptr.value:
@@ -416,13 +419,18 @@ def isosurface_extract(field: torch.Tensor, isovalues, cap: int, tris: torch.Ten
     return tris, counts, err
 
 
+ISO_INDEX = 1
+ISO_FUSED = 2
+
+
 def chr_isosurface(h: Chr, level: int, isovalues, cap: int, field_out: torch.Tensor | None = None,
                    tris: torch.Tensor | None = None, counts: torch.Tensor | None = None,
-                   err: torch.Tensor | None = None, stream=None):
+                   err: torch.Tensor | None = None, stream=None, flags: int = 0):
     """Decode level `level` of a CHR and run marching cubes on it in one call
     (chr.h: chr_isosurface).  Returns (tris, counts, err) as isosurface_extract
-    does; field_out, when given, receives the decoded field.  Scratch comes
-    from torch's caching allocator."""
+    does; field_out, when given, receives the decoded field.  flags:
+    ISO_INDEX (skip the bricks the value index rules out), ISO_FUSED (the
+    one-launch form that decodes each tile in shared memory); same output.  Scratch comes from torch's caching allocator."""
     iso, ni = _floats(isovalues)
     if field_out is not None:
         _check_field(field_out)
@@ -438,8 +446,21 @@ def chr_isosurface(h: Chr, level: int, isovalues, cap: int, field_out: torch.Ten
         raise ValueError("tris too small for n_iso * cap triangles")
     _check(lib().chr_isosurface(h.ptr, int(level), iso, ni, field_out.data_ptr() if field_out is not None else None,
                                 tris.data_ptr() if cap > 0 else None, int(cap), counts.data_ptr(), err.data_ptr(),
-                                ctypes.byref(TORCH_ALLOCATOR), _stream(stream)))
+                                int(flags), ctypes.byref(TORCH_ALLOCATOR), _stream(stream)))
     return tris, counts, err
+
+
+def chr_brick_index(h: Chr, level: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """The CHR's value index of level `level`: (min, max) over each brick's
+    cell vertices, shape [nbz, nby, nbx, 2] (chr.h: chr_brick_index)."""
+    nz, ny, nx = h.shape
+    shape = ((nz + 7) // 8, (ny + 7) // 8, (nx + 7) // 8, 2)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, device="cuda")
+    if tuple(out.shape) != shape or out.dtype != torch.float32 or not out.is_contiguous() or not out.is_cuda:
+        raise ValueError("out must be a contiguous float32 CUDA tensor of shape %s" % (shape,))
+    _check(lib().chr_brick_index(h.ptr, int(level), out.data_ptr(), _stream(stream)))
+    return out
 
 
 def isosurface_extract_noalloc(field: torch.Tensor, isovalues, cap: int, tris: torch.Tensor | None = None,
@@ -633,6 +654,9 @@ def parse_serialized(data: bytes) -> dict:
         off += ((2 * ne + 3) & ~3) - 2 * ne
         val = take(np.uint32, ne).copy()
         levels.append({"recs": recs, "words": words, "exc_idx": idx, "exc_val": val})
+    if version >= 2:
+        for l in range(nlevels):
+            levels[l]["index"] = take(np.float32, 2 * nb).reshape(nb, 2).copy()
     return {"version": version, "dims": (nx, ny, nz), "nlevels": nlevels, "n_iso": n_iso, "topo_mode": topo,
             "flags": flags, "topo_accuracy": acc, "eb_translated": ebt, "translate_D_count": dcount, "eb": eb,
             "isovalues": iso, "levels": levels}

@@ -59,6 +59,7 @@ void free_handle_buffers(chr_handle *h)
     h->d_rec_block = h->d_pay_block = nullptr;
     for (uint32_t l = 0; l < CHR_MAX_LEVELS; l++) {
         h->d_recs[l] = nullptr;
+        h->d_index[l] = nullptr;
         h->d_words[l] = nullptr;
         h->d_exc_idx[l] = nullptr;
         h->d_exc_val[l] = nullptr;
@@ -67,16 +68,21 @@ void free_handle_buffers(chr_handle *h)
 
 size_t up256(size_t n) { return (n + 255) & ~size_t(255); }
 
-// Every level's records in one allocation; false if the allocator failed.
-bool alloc_records(chr_handle *h, Alloc &al)
+// Every level's records (and, with_index, its value index) in one
+// allocation; false if the allocator failed.
+bool alloc_records(chr_handle *h, Alloc &al, bool with_index)
 {
     h->sz_recs = (size_t)h->g.nbricks * sizeof(uint4);
-    const size_t per = up256(h->sz_recs);
-    h->sz_rec_block = per * h->nlevels;
+    const size_t per = up256(h->sz_recs), per_idx = with_index ? up256((size_t)h->g.nbricks * sizeof(float2)) : 0;
+    h->sz_rec_block = (per + per_idx) * h->nlevels;
     char *b = (char *)al.get(h->sz_rec_block);
     h->d_rec_block = b;
     if (!b) return false;
-    for (uint32_t l = 0; l < h->nlevels; l++) h->d_recs[l] = reinterpret_cast<uint4 *>(b + per * l);
+    h->has_index = with_index;
+    for (uint32_t l = 0; l < h->nlevels; l++) {
+        h->d_recs[l] = reinterpret_cast<uint4 *>(b + per * l);
+        h->d_index[l] = with_index ? reinterpret_cast<float2 *>(b + per * h->nlevels + per_idx * l) : nullptr;
+    }
     return true;
 }
 
@@ -139,6 +145,7 @@ void fill_codec_params(const chr_handle *h, CodecParams &p)
         p.two_e[l] = h->two_e[l];
         p.inv2e[l] = h->inv2e[l];
         p.recs[l] = h->d_recs[l];
+        p.index[l] = h->d_index[l];
         p.words[l] = h->d_words[l];
         p.exc_idx[l] = h->d_exc_idx[l];
         p.exc_val[l] = h->d_exc_val[l];
@@ -309,7 +316,7 @@ using namespace chr;
 
 extern "C" {
 
-int chr_version(void) { return 1; }
+int chr_version(void) { return 2; }
 
 int chr_checked_build(void)
 {
@@ -398,13 +405,14 @@ chr_status chr_compress(const float *d_field, chr_dims dims, const chr_params *p
     // same block back to the next call; then the handle's records
     const size_t slot_bytes = encode_slot_bytes(g.nbricks);
     const size_t scan_bytes = scan_scratch_bytes(g.nbricks, (int)h->nlevels);
-    const size_t scr_bytes = slot_bytes * h->nlevels + scan_bytes + 16 * CHR_MAX_LEVELS;
+    const size_t idx_off = up256(slot_bytes * h->nlevels + scan_bytes + 16 * CHR_MAX_LEVELS);
+    const size_t scr_bytes = idx_off + index_part_bytes(g.nbricks, (int)h->nlevels);
     char *scr = (char *)al.get(scr_bytes);
     if (!scr) {
         delete h;
         return fail(CHR_ERR_OOM, "chr_compress: allocator returned NULL");
     }
-    if (!alloc_records(h, al)) {
+    if (!alloc_records(h, al, true)) {
         al.put(scr, scr_bytes);
         free_handle_buffers(h);
         delete h;
@@ -425,7 +433,9 @@ chr_status chr_compress(const float *d_field, chr_dims dims, const chr_params *p
         }
         char *scan_scr = scr + slot_bytes * h->nlevels;
         uint64_t *d_tot = reinterpret_cast<uint64_t *>(scan_scr + scan_bytes);
+        p.idx_part = reinterpret_cast<float2 *>(scr + idx_off);
         e = launch_encode(p, s);
+        if (e == cudaSuccess) e = launch_brick_index(p, s);
         if (e == cudaSuccess) e = launch_scan_records(h->d_recs, (int)h->nlevels, g.nbricks, scan_scr, d_tot, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(totals, d_tot, 16 * h->nlevels, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -668,13 +678,14 @@ chr_status isosurface_extract(const float *d_field, chr_dims dims, const float *
 
 chr_status chr_isosurface(const chr_handle *h, uint32_t level, const float *isovalues, uint32_t n_iso,
                           float *d_field_out, float *d_tris, uint64_t cap_tris, uint64_t *d_ntris, uint32_t *d_err,
-                          const chr_allocator *alloc, void *stream)
+                          uint32_t flags, const chr_allocator *alloc, void *stream)
 {
     if (!h || !d_ntris || !isovalues) return fail(CHR_ERR_INVALID, "chr_isosurface: NULL handle, counts or isovalues");
     if (level >= h->nlevels) return fail(CHR_ERR_INVALID, "chr_isosurface: level out of range");
     if (n_iso < 1 || n_iso > CHR_MAX_ISO) return fail(CHR_ERR_INVALID, "chr_isosurface: n_iso must be 1..16");
     for (uint32_t j = 0; j < n_iso; j++)
         if (!isfinite(isovalues[j])) return fail(CHR_ERR_INVALID, "chr_isosurface: isovalues must be finite");
+    if (flags & ~(uint32_t)(CHR_ISO_INDEX | CHR_ISO_FUSED)) return fail(CHR_ERR_INVALID, "chr_isosurface: unknown flags");
     if (cap_tris > 0 && !d_tris) return fail(CHR_ERR_INVALID, "chr_isosurface: NULL triangle buffer");
     if (cap_tris > (1ull << 58)) return fail(CHR_ERR_INVALID, "chr_isosurface: cap_tris too large");
     if ((reinterpret_cast<uintptr_t>(d_field_out) & 3u) || (reinterpret_cast<uintptr_t>(d_tris) & 3u) ||
@@ -683,31 +694,76 @@ chr_status chr_isosurface(const chr_handle *h, uint32_t level, const float *isov
     cudaStream_t s = (cudaStream_t)stream;
     Alloc al(alloc, s);
     const Grid &g = h->g;
-    const size_t field_bytes = d_field_out ? 0 : (size_t)g.N * sizeof(float);
-    const size_t ws_bytes = mc_workspace_bytes(g, (int)n_iso);
-    void *field_scratch = nullptr;
-    if (!d_field_out && !(field_scratch = al.get(field_bytes)))
-        return fail(CHR_ERR_OOM, "chr_isosurface: allocator returned NULL");
-    void *ws = al.get(ws_bytes);
-    if (!ws) {
-        al.put(field_scratch, field_bytes);
-        return fail(CHR_ERR_OOM, "chr_isosurface: allocator returned NULL");
-    }
-    float *field = d_field_out ? d_field_out : reinterpret_cast<float *>(field_scratch);
+    const float2 *index = (h->has_index && (flags & CHR_ISO_INDEX)) ? h->d_index[level] : nullptr;
     CodecParams p;
     fill_codec_params(h, p);
-    p.out = field;
     p.nlevels = (int32_t)level + 1;
     set_box(p, g, 0, 0, 0, g.nx, g.ny, g.nz);
     chr_status st = CHR_OK;
-    cudaError_t e;
-    if ((e = launch_decode(p, s)) != cudaSuccess || (e = cudaMemsetAsync(d_ntris, 0, sizeof(uint64_t) * n_iso, s)) != cudaSuccess ||
+    cudaError_t e = cudaSuccess;
+    if (!(flags & CHR_ISO_FUSED)) {
+        // decode into a field (scratch when d_field_out is NULL), then
+        // marching cubes on it with the index
+        const size_t field_bytes = d_field_out ? 0 : (size_t)g.N * sizeof(float);
+        const size_t ws_bytes = mc_workspace_bytes(g, (int)n_iso);
+        void *field_scratch = nullptr;
+        if (!d_field_out && !(field_scratch = al.get(field_bytes)))
+            return fail(CHR_ERR_OOM, "chr_isosurface: allocator returned NULL");
+        void *ws = al.get(ws_bytes);
+        if (!ws) {
+            al.put(field_scratch, field_bytes);
+            return fail(CHR_ERR_OOM, "chr_isosurface: allocator returned NULL");
+        }
+        float *field = d_field_out ? d_field_out : reinterpret_cast<float *>(field_scratch);
+        p.out = field;
+        if ((e = launch_decode(p, s)) != cudaSuccess ||
+            (e = cudaMemsetAsync(d_ntris, 0, sizeof(uint64_t) * n_iso, s)) != cudaSuccess ||
+            (d_err && (e = cudaMemsetAsync(d_err, 0, sizeof(uint32_t), s)) != cudaSuccess) ||
+            (e = launch_mc(field, g, isovalues, (int)n_iso, d_tris, cap_tris, d_ntris, d_err, ws, ws_bytes, s,
+                           index)) != cudaSuccess)
+            st = cuda_fail(e, "chr_isosurface");
+        al.put(ws, ws_bytes);
+        al.put(field_scratch, field_bytes);
+        return st;
+    }
+    // one launch per 4 isovalues: each tile's box is decoded in shared memory
+    const size_t ws_bytes = mc_workspace_min_bytes(g, (int)n_iso);
+    void *ws = al.get(ws_bytes);
+    if (!ws) return fail(CHR_ERR_OOM, "chr_isosurface: allocator returned NULL");
+    ChrMcLevels c;
+    memset(&c, 0, sizeof(c));
+    for (uint32_t l = 0; l <= level; l++) {
+        c.recs[l] = h->d_recs[l];
+        c.words[l] = h->d_words[l];
+        c.exc_idx[l] = h->d_exc_idx[l];
+        c.exc_val[l] = h->d_exc_val[l];
+        c.two_e[l] = h->two_e[l];
+    }
+    c.nlevels = (int32_t)level + 1;
+    c.index = index;
+    if (d_field_out) {
+        p.out = d_field_out;
+        e = launch_decode(p, s);
+    }
+    if (e != cudaSuccess || (e = cudaMemsetAsync(d_ntris, 0, sizeof(uint64_t) * n_iso, s)) != cudaSuccess ||
         (d_err && (e = cudaMemsetAsync(d_err, 0, sizeof(uint32_t), s)) != cudaSuccess) ||
-        (e = launch_mc(field, g, isovalues, (int)n_iso, d_tris, cap_tris, d_ntris, d_err, ws, ws_bytes, s)) != cudaSuccess)
+        (e = launch_mc_chr(c, g, isovalues, (int)n_iso, d_tris, cap_tris, d_ntris, d_err, ws, ws_bytes, s)) !=
+            cudaSuccess)
         st = cuda_fail(e, "chr_isosurface");
     al.put(ws, ws_bytes);
-    al.put(field_scratch, field_bytes);
     return st;
+}
+
+chr_status chr_brick_index(const chr_handle *h, uint32_t level, float *d_out, void *stream)
+{
+    if (!h || !d_out) return fail(CHR_ERR_INVALID, "chr_brick_index: NULL handle or output");
+    if (level >= h->nlevels) return fail(CHR_ERR_INVALID, "chr_brick_index: level out of range");
+    if (!h->has_index) return fail(CHR_ERR_INVALID, "chr_brick_index: the handle has no value index (a version-1 byte string)");
+    if (reinterpret_cast<uintptr_t>(d_out) & 7u) return fail(CHR_ERR_INVALID, "chr_brick_index: misaligned output");
+    CHR_CUDA(cudaMemcpyAsync(d_out, h->d_index[level], (size_t)h->g.nbricks * sizeof(float2), cudaMemcpyDeviceToDevice,
+                             (cudaStream_t)stream),
+             "chr_brick_index");
+    return CHR_OK;
 }
 
 size_t isosurface_backward_workspace_size(chr_dims dims, uint32_t n_iso)
@@ -790,12 +846,13 @@ chr_status chr_serialize(const chr_handle *h, void *host_buf, size_t cap, size_t
     if (!h || !need) return fail(CHR_ERR_INVALID, "chr_serialize: NULL handle or size");
     size_t total = header_bytes(h->nlevels, h->n_iso);
     for (uint32_t l = 0; l < h->nlevels; l++) total += level_bytes(h, l);
+    if (h->has_index) total += (size_t)h->nlevels * h->g.nbricks * 8;
     *need = total;
     if (!host_buf || cap < total) return CHR_OK;
     std::vector<char> hdr;
     Writer w{&hdr};
     hdr.insert(hdr.end(), {'C', 'H', 'R', '1'});
-    w.put<uint32_t>(1);
+    w.put<uint32_t>(h->has_index ? 2 : 1);
     w.put<int64_t>(h->dims.nx);
     w.put<int64_t>(h->dims.ny);
     w.put<int64_t>(h->dims.nz);
@@ -829,6 +886,12 @@ chr_status chr_serialize(const chr_handle *h, void *host_buf, size_t cap, size_t
         if (ne) CHR_CUDA(cudaMemcpyAsync(dst + off, h->d_exc_val[l], ne * 4, cudaMemcpyDeviceToHost, s), "chr_serialize");
         off += ne * 4;
     }
+    if (h->has_index)
+        for (uint32_t l = 0; l < h->nlevels; l++) {
+            CHR_CUDA(cudaMemcpyAsync(dst + off, h->d_index[l], (size_t)h->g.nbricks * 8, cudaMemcpyDeviceToHost, s),
+                     "chr_serialize");
+            off += (size_t)h->g.nbricks * 8;
+        }
     CHR_CUDA(cudaStreamSynchronize(s), "chr_serialize");
     return CHR_OK;
 }
@@ -852,7 +915,8 @@ chr_status chr_deserialize(const void *host_buf, size_t n, const chr_allocator *
     float acc = 1.0f, ebt = INFINITY;
     uint64_t dcount = 0;
     if (!take(magic, 4) || memcmp(magic, "CHR1", 4) != 0) return fail(CHR_ERR_CORRUPT, "chr_deserialize: bad magic");
-    if (!take(&version, 4) || version != 1) return fail(CHR_ERR_CORRUPT, "chr_deserialize: unsupported version");
+    if (!take(&version, 4) || (version != 1 && version != 2))
+        return fail(CHR_ERR_CORRUPT, "chr_deserialize: unsupported version");
     if (!take(&dims.nx, 8) || !take(&dims.ny, 8) || !take(&dims.nz, 8) || !take(&nlevels, 4) || !take(&n_iso, 4) ||
         !take(&topo, 4) || !take(&flags, 4) || !take(&acc, 4) || !take(&ebt, 4) || !take(&dcount, 8))
         return fail(CHR_ERR_CORRUPT, "chr_deserialize: truncated header");
@@ -923,9 +987,23 @@ chr_status chr_deserialize(const void *host_buf, size_t n, const chr_allocator *
         }
         off += level_bytes(h, l);
     }
+    // version 2: every level's value index follows the levels (any values
+    // are safe to upload: the index only decides which bricks are classified)
+    const bool with_index = (version == 2);
+    const size_t index_off = off, index_bytes = (size_t)g.nbricks * 8;
+    if (with_index && off + index_bytes * nlevels > n) {
+        delete h;
+        return fail(CHR_ERR_CORRUPT, "chr_deserialize: truncated value index");
+    }
     Alloc al(alloc, s);
     chr_status st = CHR_OK;
-    if (!alloc_records(h, al) || !alloc_payload(h, al)) st = fail(CHR_ERR_OOM, "chr_deserialize: allocator returned NULL");
+    if (!alloc_records(h, al, with_index) || !alloc_payload(h, al))
+        st = fail(CHR_ERR_OOM, "chr_deserialize: allocator returned NULL");
+    for (uint32_t l = 0; l < nlevels && st == CHR_OK && with_index; l++) {
+        cudaError_t e = cudaMemcpyAsync(h->d_index[l], src + index_off + index_bytes * l, index_bytes,
+                                        cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) st = cuda_fail(e, "chr_deserialize");
+    }
     for (uint32_t l = 0; l < nlevels && st == CHR_OK; l++) {
         size_t o = level_off[l];
         const size_t nr = (size_t)g.nbricks * 16, nw = (size_t)h->nwords[l] * 4, ne = (size_t)h->nexc[l];

@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ Codec
     __shared__ uint32_t s_red[kEncBricks][2][4];                // per warp: max L, max plain, exceptions, -
     __shared__ __align__(16) uint32_t s_pk[kEncBricks][512];    // packed words of each brick (zero between levels)
     __shared__ float s_kup[CHR_MAX_ISO + 1], s_kdn[CHR_MAX_ISO + 1];  // by count of candidates above f
+    __shared__ float2 s_rng[kEncBricks][2][4];                  // per warp: value ranges for the index
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int j = tid >> 6, r = tid & 63, wb = r >> 5;
@@ -161,6 +162,57 @@ __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ Codec
             }
         }
 
+        // The value index (Sec. 2.1: which bricks an isovalue can cross).
+        // Ranges of R over 8 vertex subsets of the brick, NaN as +inf: all of
+        // it, the planes x = 0, y = 0, z = 0, the lines x = y = 0, x = z = 0,
+        // y = z = 0 and the corner; k_brick_index assembles each brick's
+        // cell-vertex range from its own range and its neighbours' planes,
+        // lines and corner.  Along y by xor 1, 2, 4 (after which the z = 0
+        // rows hold the z = 0 plane and the x = z = 0 line), then along z by
+        // xor 8, 16 (the y = 0 lanes' own values give the y = 0 plane and the
+        // x = y = 0 line), then across the brick's two warps.
+        float2 rg_z0, rg_x0z0, rg_y0z0, rg_c;
+        if (p.idx_part) {
+            float mn = __int_as_float(0x7f800000), mx = -mn, a0 = mn, b0 = mx;
+#pragma unroll
+            for (int x = 0; x < 8; x++)
+                if ((valid >> x) & 1u) {
+                    const float v = isnan(R[x]) ? __int_as_float(0x7f800000) : R[x];
+                    mn = fminf(mn, v);
+                    mx = fmaxf(mx, v);
+                    if (x == 0) a0 = b0 = v;
+                }
+            rg_y0z0 = make_float2(mn, mx);
+            rg_c = make_float2(a0, b0);
+            float omn = mn, omx = mx, xmn = a0, xmx = b0;
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                omn = fminf(omn, __shfl_xor_sync(CHR_FULL_MASK, omn, o));
+                omx = fmaxf(omx, __shfl_xor_sync(CHR_FULL_MASK, omx, o));
+                xmn = fminf(xmn, __shfl_xor_sync(CHR_FULL_MASK, xmn, o));
+                xmx = fmaxf(xmx, __shfl_xor_sync(CHR_FULL_MASK, xmx, o));
+            }
+            rg_z0 = make_float2(omn, omx);
+            rg_x0z0 = make_float2(xmn, xmx);
+#pragma unroll
+            for (int o = 8; o < 32; o <<= 1) {
+                omn = fminf(omn, __shfl_xor_sync(CHR_FULL_MASK, omn, o));
+                omx = fmaxf(omx, __shfl_xor_sync(CHR_FULL_MASK, omx, o));
+                xmn = fminf(xmn, __shfl_xor_sync(CHR_FULL_MASK, xmn, o));
+                xmx = fmaxf(xmx, __shfl_xor_sync(CHR_FULL_MASK, xmx, o));
+                mn = fminf(mn, __shfl_xor_sync(CHR_FULL_MASK, mn, o));
+                mx = fmaxf(mx, __shfl_xor_sync(CHR_FULL_MASK, mx, o));
+                a0 = fminf(a0, __shfl_xor_sync(CHR_FULL_MASK, a0, o));
+                b0 = fmaxf(b0, __shfl_xor_sync(CHR_FULL_MASK, b0, o));
+            }
+            if (lane == 0) {  // (ly = 0): this warp's whole part, x = 0 plane, y = 0 plane, x = y = 0 line
+                s_rng[j][wb][0] = make_float2(omn, omx);
+                s_rng[j][wb][1] = make_float2(xmn, xmx);
+                s_rng[j][wb][2] = make_float2(mn, mx);
+                s_rng[j][wb][3] = make_float2(a0, b0);
+            }
+        }
+
         // Lorenzo residual: first differences along x, y (lanes 1 apart) and z
         // (lanes 8 apart; the z = 4 rows take the z = 3 rows from shared memory)
         int32_t d[8];
@@ -214,6 +266,16 @@ __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ Codec
         const int w = mode ? wl : wn;
         if (mine && r == 0)
             p.recs[l][c.b] = make_uint4(0u, 0u, (uint32_t)q[0], (uint32_t)w | ((uint32_t)mode << 8) | (nexc << 16));
+        if (p.idx_part && mine && r == 0) {  // (thread 0 holds the z = 0 rows' and its own parts)
+            auto un = [](float2 a, float2 b) { return make_float2(fminf(a.x, b.x), fmaxf(a.y, b.y)); };
+            float4 *dst = reinterpret_cast<float4 *>(p.idx_part + ((size_t)l * p.nbx * p.nby * p.nbz + c.b) * kIdxParts);
+            const float2 all = un(s_rng[j][0][0], s_rng[j][1][0]), x0 = un(s_rng[j][0][1], s_rng[j][1][1]);
+            const float2 y0 = un(s_rng[j][0][2], s_rng[j][1][2]), x0y0 = un(s_rng[j][0][3], s_rng[j][1][3]);
+            dst[0] = make_float4(all.x, all.y, x0.x, x0.y);
+            dst[1] = make_float4(y0.x, y0.y, rg_z0.x, rg_z0.y);
+            dst[2] = make_float4(x0y0.x, x0y0.y, rg_x0z0.x, rg_x0z0.y);
+            dst[3] = make_float4(rg_y0z0.x, rg_y0z0.y, rg_c.x, rg_c.y);
+        }
 
         // pack: row r's 8 codes are bits [8*r*w, 8*r*w + 8*w) of the brick's
         // stream; each thread ORs its bits into the zeroed shared words, then
@@ -726,6 +788,49 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const __grid_consta
 
 }  // namespace
 
+
+// One thread per brick and level: the range over the vertices of the
+// brick's cells (the brick, plus the first vertex plane of its +x, +y, +z
+// neighbours), from the parts k_encode wrote: the brick's own range, the
+// x = 0 plane of brick +x, the y = 0 plane of +y, the z = 0 plane of +z,
+// the x = y = 0 line of +x+y, the x = z = 0 line of +x+z, the y = z = 0
+// line of +y+z and the corner of +x+y+z.  A brick without cells (its first
+// vertex on the grid's last plane) gets (+inf, -inf).
+__global__ void __launch_bounds__(256) k_brick_index(const __grid_constant__ CodecParams p)
+{
+    const int64_t nb = (int64_t)p.nbx * p.nby * p.nbz;
+    const int64_t b = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const int l = blockIdx.y;
+    if (b >= nb) return;
+    const int32_t bx = (int32_t)(b % p.nbx), by = (int32_t)((b / p.nbx) % p.nby), bz = (int32_t)(b / ((int64_t)p.nbx * p.nby));
+    float2 r = make_float2(__int_as_float(0x7f800000), __int_as_float(0xff800000));
+    if ((int64_t)bx * 8 < p.nx - 1 && (int64_t)by * 8 < p.ny - 1 && (int64_t)bz * 8 < p.nz - 1) {
+        const float2 *P = p.idx_part + (size_t)l * nb * kIdxParts;
+        const bool ex = bx + 1 < p.nbx, ey = by + 1 < p.nby, ez = bz + 1 < p.nbz;
+        const int64_t sx = 1, sy = p.nbx, sz = (int64_t)p.nbx * p.nby;
+        auto add = [&](int64_t bb, int part) {
+            const float2 v = P[bb * kIdxParts + part];
+            r.x = fminf(r.x, v.x);
+            r.y = fmaxf(r.y, v.y);
+        };
+        add(b, 0);
+        if (ex) add(b + sx, 1);
+        if (ey) add(b + sy, 2);
+        if (ez) add(b + sz, 3);
+        if (ex && ey) add(b + sx + sy, 4);
+        if (ex && ez) add(b + sx + sz, 5);
+        if (ey && ez) add(b + sy + sz, 6);
+        if (ex && ey && ez) add(b + sx + sy + sz, 7);
+    }
+    p.index[l][b] = r;
+}
+
+cudaError_t launch_brick_index(const CodecParams &p, cudaStream_t s)
+{
+    const int64_t nb = (int64_t)p.nbx * p.nby * p.nbz;
+    k_brick_index<<<dim3((unsigned)((nb + 255) / 256), (unsigned)p.nlevels), 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_encode(const CodecParams &p, cudaStream_t s)
 {

@@ -59,6 +59,11 @@ struct CodecParams {
     int64_t out_sx, out_sy;  // output row and plane pitch in floats
     int32_t box_brick0[3], box_bricks[3];
     float2 *range;  // optional per-brick (min, max) of the decoded values
+    // encode: per brick and level the value ranges of 8 vertex subsets of the
+    // brick (kIdxParts float2 each, see k_encode), combined into the index by
+    // k_brick_index; NULL: no index
+    float2 *idx_part;
+    float2 *index[CHR_MAX_LEVELS];  // the index per level (nbricks float2)
     // encode scratch: fixed per-brick slots (512 words, 512 exception entries)
     uint32_t *slot_words[CHR_MAX_LEVELS];
     uint16_t *slot_idx[CHR_MAX_LEVELS];
@@ -69,6 +74,12 @@ struct CodecParams {
 inline size_t encode_slot_bytes(int64_t nbricks) { return (size_t)nbricks * 512 * (4 + 2 + 4); }
 
 cudaError_t launch_encode(const CodecParams &p, cudaStream_t s);
+// The per-brick value index (min, max over the vertices of each brick's
+// cells, NaN as +inf, (+inf, -inf) for a brick without cells) of every
+// level, from the encoder's per-brick parts (p.idx_part -> p.index[l]).
+constexpr int kIdxParts = 8;
+inline size_t index_part_bytes(int64_t nbricks, int nlevels) { return (size_t)nbricks * nlevels * kIdxParts * 8; }
+cudaError_t launch_brick_index(const CodecParams &p, cudaStream_t s);
 cudaError_t launch_compact(const CodecParams &p, cudaStream_t s);
 cudaError_t launch_decode(const CodecParams &p, cudaStream_t s);
 // Decode of many CHRs in one launch (descs, brick_start [nboxes+1] on the device).
@@ -92,12 +103,33 @@ uint32_t codec_bounds_word(bool reset);
 // plus that classification; mc_workspace_min_bytes: the tile arrays alone.
 size_t mc_workspace_bytes(const Grid &g, int n_iso);
 size_t mc_workspace_min_bytes(const Grid &g, int n_iso);
+// index: the field's value index (nbricks (min, max) over each 8^3 brick's
+// cell vertices, a CHR level's), or NULL; bricks whose range does not
+// straddle an isovalue are not classified for it (same output).
 cudaError_t launch_mc(const float *field, const Grid &g, const float *iso, int n_iso, float *tris, uint64_t cap,
-                      uint64_t *ntris, uint32_t *err, void *workspace, size_t workspace_bytes, cudaStream_t s);
+                      uint64_t *ntris, uint32_t *err, void *workspace, size_t workspace_bytes, cudaStream_t s,
+                      const float2 *index = nullptr);
 // The same over a pitched field: value (x, y, z) at field[x + sx*y + sy*z].
 cudaError_t launch_mc_pitched(const float *field, const Grid &g, int64_t sx, int64_t sy, const float *iso, int n_iso,
                               float *tris, uint64_t cap, uint64_t *ntris, uint32_t *err, void *workspace,
-                              size_t workspace_bytes, cudaStream_t s);
+                              size_t workspace_bytes, cudaStream_t s, const float2 *index = nullptr);
+
+// Decode + marching cubes of one CHR level in one launch per group of up to
+// 4 isovalues (k_mc_chr): levels 0..nlevels-1 of the stream below are
+// decoded tile by tile into shared memory and meshed there; same output as
+// launch_decode followed by launch_mc.  index: the level's value index, or
+// NULL to classify every brick.  workspace: mc_workspace_min_bytes.
+struct ChrMcLevels {
+    const uint4 *recs[CHR_MAX_LEVELS];
+    const uint32_t *words[CHR_MAX_LEVELS];
+    const uint16_t *exc_idx[CHR_MAX_LEVELS];
+    const uint32_t *exc_val[CHR_MAX_LEVELS];
+    float two_e[CHR_MAX_LEVELS];
+    int32_t nlevels;
+    const float2 *index;
+};
+cudaError_t launch_mc_chr(const ChrMcLevels &c, const Grid &g, const float *iso, int n_iso, float *tris, uint64_t cap,
+                          uint64_t *ntris, uint32_t *err, void *workspace, size_t workspace_bytes, cudaStream_t s);
 
 // Marching cubes of many fields (each with its own isovalue and pitch) in one
 // launch sequence: count over the concatenated tile list, one scan, emit.
@@ -235,10 +267,15 @@ struct chr_handle {
     uint32_t *d_words[CHR_MAX_LEVELS];
     uint16_t *d_exc_idx[CHR_MAX_LEVELS];
     uint32_t *d_exc_val[CHR_MAX_LEVELS];
+    // the value index per level (Sec. 2.1): nbricks (min, max) over each
+    // brick's cell vertices; NULL when the handle has none (a version-1
+    // byte string), and then nothing is skipped
+    float2 *d_index[CHR_MAX_LEVELS];
+    bool has_index;
     size_t sz_recs, sz_words[CHR_MAX_LEVELS], sz_exc_idx[CHR_MAX_LEVELS], sz_exc_val[CHR_MAX_LEVELS];
-    // the arrays above live in two allocations: every level's records in one
-    // block, every level's packed words and exception slots and values in
-    // the other (each array 256-byte aligned inside its block)
+    // the arrays above live in two allocations: every level's records and
+    // index in one block, every level's packed words and exception slots and
+    // values in the other (each array 256-byte aligned inside its block)
     void *d_rec_block, *d_pay_block;
     size_t sz_rec_block, sz_pay_block;
     chr_allocator alloc;

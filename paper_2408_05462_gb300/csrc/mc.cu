@@ -37,6 +37,7 @@
 #include <mutex>
 #include <type_traits>
 
+#include "chr_box.cuh"
 #include "common.cuh"
 #include "internal.h"
 #include "mc_table.h"
@@ -113,6 +114,11 @@ struct McParams {
     // test only: a tile that never publishes its counts or prefix (-1: none),
     // so that the tiles after it wait out their bounded look-back
     int64_t unpublished_tile;
+    // the field's value index (a CHR level's, chr_brick_index), NULL: none;
+    // ibx, iby: its bricks along x and y.  A cell brick whose range does not
+    // straddle an isovalue slot is not classified for it (tile_activity)
+    const float2 *index;
+    int32_t ibx, iby;
 };
 
 struct TileXYZ {
@@ -153,8 +159,10 @@ __device__ __forceinline__ void issue_box(float *buf, const CUtensorMap *map, ui
 
 // Inside masks (v < k) of the box rows: bit x of s_row[i*81 + row], x < 33.
 // Lane i (i < NISO) keeps isovalue i's ballot and writes its row mask.
+// Isovalue slots whose bit in isomask is clear are not needed (no cell of
+// the tile crosses them) and get no ballot.
 template <int NISO>
-__device__ __forceinline__ void row_masks(const float *buf, uint64_t *s_row, const McParams &p)
+__device__ __forceinline__ void row_masks(const float *buf, uint64_t *s_row, const McParams &p, uint32_t isomask = 0xfu)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float k[NISO];
@@ -167,11 +175,53 @@ __device__ __forceinline__ void row_masks(const float *buf, uint64_t *s_row, con
         uint32_t mine = 0;
 #pragma unroll
         for (int i = 0; i < NISO; i++) {
+            if (!((isomask >> i) & 1u)) continue;  // (uniform)
             const uint32_t b = __ballot_sync(CHR_FULL_MASK, v < k[i]);
             mine = (lane == i) ? b : mine;
         }
         if (lane < NISO) s_row[lane * kRows + row] = (uint64_t)mine | ((uint64_t)(vh < kl) << 32);
     }
+}
+
+// Which (cell brick j, isovalue slot i) of the tile at o can have cells
+// crossing k_i (bit 4j + i): min < k <= max in the value index, which
+// bounds the brick's cell vertices; every pair without an index.  Each
+// calling warp gets the same mask.
+template <int NISO>
+__device__ __forceinline__ uint32_t tile_activity(const McParams &p, const TileXYZ &o)
+{
+    if (!p.index) return 0xffffu;
+    const int lane = threadIdx.x & 31;
+    const int32_t bx0 = (int32_t)(o.x0 >> 3), by = (int32_t)(o.y0 >> 3), bz = (int32_t)(o.z0 >> 3);
+    uint32_t bits = 0;
+    if (lane < 4 && bx0 + lane < p.ibx) {
+        const float2 r = __ldg(p.index + (bx0 + lane) + (int64_t)p.ibx * (by + (int64_t)p.iby * bz));
+#pragma unroll
+        for (int i = 0; i < NISO; i++) bits |= (uint32_t)(r.x < p.k[i] && p.k[i] <= r.y) << i;
+    }
+    return __reduce_or_sync(CHR_FULL_MASK, bits << (4 * (lane & 3)));
+}
+
+__device__ __forceinline__ uint32_t iso_mask(uint32_t act) { return (act | (act >> 4) | (act >> 8) | (act >> 12)) & 0xfu; }
+
+// The index entry of cell brick `lane` (lanes 0..3) of the tile at o, or an
+// empty range; loaded a tile ahead so its latency hides behind a tile.
+__device__ __forceinline__ float2 tile_index_entry(const McParams &p, const TileXYZ &o, int lane)
+{
+    const int32_t bx0 = (int32_t)(o.x0 >> 3), by = (int32_t)(o.y0 >> 3), bz = (int32_t)(o.z0 >> 3);
+    if (lane < 4 && bx0 + lane < p.ibx) return __ldg(p.index + (bx0 + lane) + (int64_t)p.ibx * (by + (int64_t)p.iby * bz));
+    return make_float2(__int_as_float(0x7f800000), __int_as_float(0xff800000));
+}
+
+// tile_activity from entries loaded by tile_index_entry (by a whole warp).
+template <int NISO>
+__device__ __forceinline__ uint32_t activity_from(const McParams &p, float2 r)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t bits = 0;
+#pragma unroll
+    for (int i = 0; i < NISO; i++) bits |= (uint32_t)(r.x < p.k[i] && p.k[i] <= r.y) << i;
+    return __reduce_or_sync(CHR_FULL_MASK, (lane < 4) ? bits << (4 * lane) : 0u);
 }
 
 // Exchanges the bits of w at positions p and p + s for every p in m: with
@@ -292,6 +342,14 @@ struct SrcMany {
     }
 };
 
+// One CHR level: tile t's box is decoded from the compressed stream.
+// index: the level's value index (NULL: every brick is classified).
+struct SrcChr {
+    const McParams *p;
+    const ChrLevels *L;
+    const float2 *index;
+};
+
 // After a box copy gave up: one more bounded wait for each copy this block
 // still has in flight (phase `par` of mbar[b], and of mbar[b ^ 1] when
 // `other` is set), so that no copy lands in shared memory the block has
@@ -306,10 +364,15 @@ __device__ __noinline__ void drain_box_copies(uint64_t *mbar, int b, uint32_t pa
 // while `body` processes the current one.  A copy that never arrives
 // (bounded wait) raises CHR_ERR_TIMEOUT and the block stops.
 // body(tile, local tile, field params, box).
-template <class Src, class Body>
-__device__ __forceinline__ void tile_loop(const Src &src, uint32_t *err, float *bufs, uint64_t *mbar, Body body)
+// IDX: warp 0 also reads the next tile's index entries when its box is
+// issued and leaves the tile's activity mask (tile_activity) in act before
+// body runs on it.
+template <int NISO = 1, bool IDX = false, class Src, class Body>
+__device__ __forceinline__ void tile_loop(const Src &src, uint32_t *err, float *bufs, uint64_t *mbar, Body body,
+                                          uint32_t *act = nullptr)
 {
     const int tid = threadIdx.x;
+    __shared__ uint32_t s_act[2];
     const int64_t G = gridDim.x, ntiles = src.ntiles();
     const bool tma = src.use_tma();
     int64_t tile = blockIdx.x;
@@ -330,6 +393,14 @@ __device__ __forceinline__ void tile_loop(const Src &src, uint32_t *err, float *
     }
     uint32_t phase0 = 0, phase1 = 0;
     int cur = 0;
+    if (IDX && tid < 32 && tile < ntiles) {
+        const McParams *bp;
+        const CUtensorMap *m;
+        int64_t local;
+        src.at(tile, bp, m, local);
+        const uint32_t a = activity_from<NISO>(*bp, tile_index_entry(*bp, tile_origin(*bp, local), tid));
+        if (tid == 0) s_act[0] = a;
+    }
     for (; tile < ntiles; tile += G) {
         float *buf = bufs + cur * (kBufBytes / 4);
         const int64_t next = tile + G;
@@ -337,6 +408,14 @@ __device__ __forceinline__ void tile_loop(const Src &src, uint32_t *err, float *
         const CUtensorMap *m;
         int64_t local;
         src.at(tile, bp, m, local);
+        float2 rnext = make_float2(0.0f, 0.0f);
+        if (IDX && tid < 32 && next < ntiles) {
+            const McParams *nbp;
+            const CUtensorMap *nm;
+            int64_t nlocal;
+            src.at(next, nbp, nm, nlocal);
+            rnext = tile_index_entry(*nbp, tile_origin(*nbp, nlocal), tid);
+        }
         bool ok = true;
         if (tma) {
             if (tid == 0 && next < ntiles) {
@@ -362,13 +441,22 @@ __device__ __forceinline__ void tile_loop(const Src &src, uint32_t *err, float *
             }
             return;
         }
+        if (IDX) *act = s_act[cur];
         body(tile, local, *bp, buf);
+        if (IDX && tid < 32 && next < ntiles) {
+            const McParams *nbp;
+            const CUtensorMap *nm;
+            int64_t nlocal;
+            src.at(next, nbp, nm, nlocal);
+            const uint32_t a = activity_from<NISO>(*nbp, rnext);
+            if (tid == 0) s_act[cur ^ 1] = a;
+        }
         __syncthreads();  // every read of buf is done before it is refilled
         cur ^= 1;
     }
 }
 
-template <int NISO, class Src>
+template <int NISO, bool IDX, class Src>
 __device__ __forceinline__ void mc_count_run(const Src &src, uint32_t *err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -381,17 +469,19 @@ __device__ __forceinline__ void mc_count_run(const Src &src, uint32_t *err)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     s_cnt[tid] = (uint8_t)(g_mc_case[case_order(tid)] >> 60);
 
-    tile_loop(src, err, bufs, mbar, [&](int64_t, int64_t tile, const McParams &p, const float *buf) {
-        row_masks<NISO>(buf, s_row, p);
-        __syncthreads();
+    uint32_t act_idx = 0xffffu;
+    tile_loop<NISO, IDX>(src, err, bufs, mbar, [&](int64_t, int64_t tile, const McParams &p, const float *buf) {
         const TileXYZ o = tile_origin(p, tile);
+        const uint32_t act = IDX ? act_idx : 0xffffu;
+        row_masks<NISO>(buf, s_row, p, iso_mask(act));
+        __syncthreads();
         const int nvalid = valid_cells(p, o);
         const int j = tid >> 6, ly = tid & 7, lz = (tid >> 3) & 7;
         const int r00 = lz * 9 + ly;
 #pragma unroll
         for (int i = 0; i < NISO; i++) {
-            uint32_t lo, hi;
-            cases8(s_row + i * kRows, r00, j, nvalid, lo, hi);
+            uint32_t lo = 0u, hi = 0u;
+            if ((act >> (4 * j + i)) & 1u) cases8(s_row + i * kRows, r00, j, nvalid, lo, hi);
             uint32_t c = 0;
 #pragma unroll
             for (int x = 0; x < 4; x++) c += s_cnt[(lo >> (8 * x)) & 0xffu] + s_cnt[(hi >> (8 * x)) & 0xffu];
@@ -413,29 +503,42 @@ __device__ __forceinline__ void mc_count_run(const Src &src, uint32_t *err)
                 for (int i = 0; i < NISO; i++) t[i] += s_sum[w][i];
             p.tile_cnt[tile] = make_uint4(t[0], t[1], t[2], t[3]);
         }
-    });
+    }, &act_idx);
 }
 
+// IDX: the field has a value index (McParams.index), and cell bricks whose
+// range does not straddle an isovalue are not classified for it.
 template <int NISO>
 __global__ void __launch_bounds__(256) k_mc_count(const __grid_constant__ McParams p,
                                                  const __grid_constant__ CUtensorMap map)
 {
-    mc_count_run<NISO>(SrcOne{&p, &map}, p.err);
+    mc_count_run<NISO, false>(SrcOne{&p, &map}, p.err);
+}
+
+template <int NISO>
+__global__ void __launch_bounds__(256, 5) k_mc_count_idx(const __grid_constant__ McParams p,
+                                                        const __grid_constant__ CUtensorMap map)
+{
+    mc_count_run<NISO, true>(SrcOne{&p, &map}, p.err);
 }
 
 __global__ void __launch_bounds__(256) k_mc_count_batched(const __grid_constant__ McBatch b, uint32_t *err)
 {
-    mc_count_run<1>(SrcMany{&b}, err);
+    mc_count_run<1, false>(SrcMany{&b}, err);
 }
 
 // t = (k - f0) / (f1 - f0): the edge parameter of a crossing.  f0 and f1 lie
 // on opposite sides of k, so the quotient is in (0, 1]; the fast reciprocal
 // quotient is within 2 ulp of the rounded one, and the IEEE quotient is used
-// where the fast form does not apply (|f1 - f0| >= 2^126).
+// where the fast form does not apply (|f1 - f0| >= 2^126).  A tile whose
+// values all lie below kHugeValue = 2^124 in magnitude has |f1 - f0| <= 2^125
+// on every edge and takes the fast quotient throughout (FAST below): the
+// same bits as this function, so which tiles take FAST never changes the
+// output.
 __device__ __forceinline__ float edge_t(float k, float f0, float f1)
 {
     const float num = __fsub_rn(k, f0), den = __fsub_rn(f1, f0);
-    return (fabsf(den) < 8.5e37f) ? __fdividef(num, den) : __fdiv_rn(num, den);
+    return (fabsf(den) < 8.507059173023462e37f) ? __fdividef(num, den) : __fdiv_rn(num, den);
 }
 
 
@@ -579,6 +682,47 @@ __device__ __forceinline__ bool look_back(const McParams &p, int64_t t, uint64_t
     return true;
 }
 
+// By warp 0 of the block: publish tile t's triangle counts (cnt[i] for
+// isovalue slot i), find the triangles before it by the look-back, publish
+// its inclusive prefix, and leave the tile's first triangle per slot in
+// g0[i] (shared memory); the last tile also writes the totals and the
+// overflow bit.  A wait that gave up sets the abort word and the timeout bit.
+template <int NISO>
+__device__ __forceinline__ void publish_tile(const McParams &p, int64_t tile, const uint32_t (&cnt)[NISO], uint64_t *g0)
+{
+    const int lane = threadIdx.x & 31;
+    uint64_t own = 0;
+#pragma unroll
+    for (int i = 0; i < NISO; i++) own |= (uint64_t)(cnt[i] & 0xffffu) << (14 * i);
+    uint64_t ex[NISO];
+    bool ok = true;
+    const bool publish = tile != p.unpublished_tile;
+    if (tile == 0) {
+#pragma unroll
+        for (int i = 0; i < NISO; i++) ex[i] = 0;
+    } else {
+        if (lane == 0 && publish) st_relaxed_u64(p.tstat + tile, kTileOwn | own);
+        ok = look_back<NISO>(p, tile, ex);
+    }
+    if (lane == 0) {
+        if (!ok) {
+            atomicExch(p.tabort, 1u);
+            if (p.err) atomicOr(p.err, 1u << CHR_ERR_TIMEOUT);
+        }
+#pragma unroll
+        for (int i = 0; i < NISO; i++) {
+            const uint64_t incl = ex[i] + (cnt[i] & 0xffffu);
+            st_relaxed_u64(p.tile_off + tile * kMcIsoPerPass + i, incl);
+            g0[i] = ex[i];
+            if (tile == p.ntiles - 1) {  // the totals, and whether every triangle fitted below cap
+                p.ntris[i] = incl;
+                if (incl > p.cap && p.err) atomicOr(p.err, 1u << CHR_ERR_OVERFLOW);
+            }
+        }
+        if (publish) st_release_u64(p.tstat + tile, kTilePrefix | own);
+    }
+}
+
 // The single pass's tile loop: blocks claim tiles from p.tctr in increasing
 // order.  A block claims its next tile only near the end of the current one
 // (the first warp done with its share of the current tile's triangles calls
@@ -586,20 +730,40 @@ __device__ __forceinline__ bool look_back(const McParams &p, int64_t t, uint64_t
 // started would hold up the look-back of every later tile until its block
 // got to it.  The next box is fetched into the other buffer meanwhile.
 // body(tile, tile, params, box, claim).
-template <class Body>
+// IDX: the claiming thread also reads the claimed tile's index entries and
+// leaves its activity mask (tile_activity) in act before body runs on it.
+template <int NISO = 1, bool IDX = false, class Body>
 __device__ __forceinline__ void tile_loop_claimed(const McParams &p, const CUtensorMap *map, float *bufs,
-                                                  uint64_t *mbar, Body body)
+                                                  uint64_t *mbar, Body body, uint32_t *act = nullptr)
 {
     __shared__ int64_t s_tile;
-    __shared__ uint32_t s_claimed;
+    __shared__ uint32_t s_claimed, s_act;
     const int tid = threadIdx.x;
     const bool tma = p.use_tma != 0;
     int cur = 0;
+    // by one thread: the activity mask of tile t from its four index entries
+    auto activity1 = [&](int64_t t) -> uint32_t {
+        const TileXYZ o = tile_origin(p, t);
+        const int32_t bx0 = (int32_t)(o.x0 >> 3), by = (int32_t)(o.y0 >> 3), bz = (int32_t)(o.z0 >> 3);
+        float2 r[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            r[j] = make_float2(__int_as_float(0x7f800000), __int_as_float(0xff800000));
+            if (bx0 + j < p.ibx) r[j] = __ldg(p.index + (bx0 + j) + (int64_t)p.ibx * (by + (int64_t)p.iby * bz));
+        }
+        uint32_t a = 0;
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+#pragma unroll
+            for (int i = 0; i < NISO; i++) a |= (uint32_t)(r[j].x < p.k[i] && p.k[i] <= r[j].y) << (4 * j + i);
+        return a;
+    };
     auto claim = [&]() {  // one thread per tile: the next tile, and its box on its way
         if (atomicExch(&s_claimed, 1u) != 0u) return;
         const int64_t t = (int64_t)atomicAdd(p.tctr, 1u);
         s_tile = t;
         if (tma && t < p.ntiles) issue_box(bufs + (cur ^ 1) * (kBufBytes / 4), map, &mbar[cur ^ 1], p, t);
+        if (IDX && t < p.ntiles) s_act = activity1(t);
     };
     if (tid == 0) {
         if (tma) {
@@ -611,6 +775,7 @@ __device__ __forceinline__ void tile_loop_claimed(const McParams &p, const CUten
         s_tile = t;
         s_claimed = 0u;
         if (tma && t < p.ntiles) issue_box(bufs, map, &mbar[0], p, t);
+        if (IDX && t < p.ntiles) s_act = activity1(t);
     }
     __syncthreads();
     int64_t tile = s_tile;
@@ -636,12 +801,187 @@ __device__ __forceinline__ void tile_loop_claimed(const McParams &p, const CUten
             return;
         }
         // (the other buffer's last reads ended at the previous barrier, so claim() may refill it)
+        if (IDX) *act = s_act;
         body(tile, tile, p, buf, claim);
         if (tid == 0) claim();  // unless a warp already did
         __syncthreads();        // every read of buf is done, and s_tile holds the next tile
         tile = s_tile;          // (read before the next tile's first barrier, so before the next claim)
         if (tid == 0) s_claimed = 0u;
         cur ^= 1;
+    }
+}
+
+// The one-pass decode + marching-cubes tile loop: like tile_loop_claimed,
+// but each tile's box is decoded from the CHR by the block's own warps
+// (warps 0-3 the tile's four vertex bricks, staged through the second box
+// buffer; warps 4-7 the first planes, lines and corner of the bricks after
+// them).  The first warp done with its share of a tile's triangles claims
+// the next tile and reads the records of its 20 bricks (every level) and
+// the index of its four cell bricks: act bit 4j + i says that brick j can
+// have cells crossing isovalue slot i (min < k <= max over the brick's cell
+// vertices).  A tile with none is not decoded: warp 0 publishes zero
+// counts for it.  fast: no box value reaches 2^124.
+// body(tile, tile, params, box, claim).
+template <int NISO, class Body>
+__device__ __forceinline__ void tile_loop_chr(const McParams &p, const ChrLevels &L, const float2 *index, float *bufs,
+                                              uint32_t &act, bool &fast, uint64_t *g0, Body body)
+{
+    __shared__ int64_t s_tile[2];
+    __shared__ uint32_t s_act[2];
+    __shared__ uint32_t s_claimed;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float *box = bufs;
+    // the second box buffer: 4 staging areas of the own-brick warps, then the records
+    constexpr int kRecBytes = CHR_MAX_LEVELS * kTileBricks * 16;
+    constexpr int kStageWords = ((kBufBytes - kRecBytes) / 16) & ~3;  // per own-brick warp
+    static_assert(4 * kStageWords * 4 + kRecBytes <= kBufBytes, "staging and records fit the second buffer");
+    uint32_t *stage = reinterpret_cast<uint32_t *>(bufs + kBufBytes / 4);
+    uint4(*s_rec)[kTileBricks] = reinterpret_cast<uint4(*)[kTileBricks]>(bufs + kBufBytes / 4 + 4 * kStageWords);
+    int par = 0;
+    // by a whole warp, the first to call it for the current tile: claim the
+    // next tile, read its records and its bricks' index
+    auto claim = [&]() {
+        uint32_t first = 0u;
+        if (lane == 0) first = atomicExch(&s_claimed, 1u);
+        if (__shfl_sync(CHR_FULL_MASK, first, 0) != 0u) return;
+        int64_t t = 0;
+        if (lane == 0) t = (int64_t)atomicAdd(p.tctr, 1u);
+        t = __shfl_sync(CHR_FULL_MASK, t, 0);
+        uint32_t a = 0u;
+        if (t < p.ntiles) {
+            const TileXYZ o = tile_origin(p, t);
+            const int32_t bx0 = (int32_t)(o.x0 >> 3), by = (int32_t)(o.y0 >> 3), bz = (int32_t)(o.z0 >> 3);
+            load_tile_records(s_rec, L, bx0, by, bz, lane);
+            a = 0xffffu;
+            if (index) {
+                uint32_t bits = 0;
+                if (lane < 4 && bx0 + lane < L.nbx) {
+                    const float2 r = __ldg(index + (bx0 + lane) + (int64_t)L.nbx * (by + (int64_t)L.nby * bz));
+#pragma unroll
+                    for (int i = 0; i < NISO; i++) bits |= (uint32_t)(r.x < p.k[i] && p.k[i] <= r.y) << i;
+                }
+                a = __reduce_or_sync(CHR_FULL_MASK, bits << (4 * (lane & 3)));
+            }
+        }
+        if (lane == 0) {
+            s_tile[par] = t;
+            s_act[par] = a;
+        }
+    };
+    if (tid == 0) s_claimed = 0u;
+    __syncthreads();
+    if (warp == 0) claim();
+    __syncthreads();
+    int64_t tile = s_tile[par];
+    uint32_t a = s_act[par];
+    if (tid == 0) s_claimed = 0u;
+    par ^= 1;
+    while (tile < p.ntiles) {
+        act = a;
+        if (a == 0) {
+            if (warp == 0) {
+                uint32_t zero[NISO];
+#pragma unroll
+                for (int i = 0; i < NISO; i++) zero[i] = 0u;
+                publish_tile<NISO>(p, tile, zero, g0);
+            }
+        } else {
+            const TileXYZ o = tile_origin(p, tile);
+            const int32_t bx0 = (int32_t)(o.x0 >> 3), by = (int32_t)(o.y0 >> 3), bz = (int32_t)(o.z0 >> 3);
+            auto slot = [&](int dx, int dy, int dz) -> int {  // the brick's record slot, -1 outside the grid
+                return (bx0 + dx < L.nbx && by + dy < L.nby && bz + dz < L.nbz) ? dx + 5 * (dy + 2 * dz) : -1;
+            };
+            bool huge = false;
+            if (warp < 4) {
+                const int id = slot(warp, 0, 0);
+                if (id >= 0) {
+                    huge = box_own_brick<kVX, kPlane>(box, L, s_rec, id, 8 * warp, lane, stage + warp * kStageWords,
+                                                      kStageWords);
+                } else {
+                    float *row0 = box + 8 * warp + kVX * (lane & 7) + kPlane * (lane >> 3);
+                    const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    *reinterpret_cast<float4 *>(row0) = z4;
+                    *reinterpret_cast<float4 *>(row0 + 4) = z4;
+                    *reinterpret_cast<float4 *>(row0 + 4 * kPlane) = z4;
+                    *reinterpret_cast<float4 *>(row0 + 4 * kPlane + 4) = z4;
+                }
+            } else if (warp < 7) {
+                // warps 4-6: nine planes, three each: the y = 0 planes of the
+                // bricks after the tile's along y (q 0-3), the z = 0 planes of
+                // those after it along z (q 4-7), the x = 0 plane of the one
+                // after it along x (q 8)
+#pragma unroll 1
+                for (int q = 3 * (warp - 4); q < 3 * (warp - 3); q++) {
+                    HaloPiece hp;
+                    hp.len = 8;
+                    if (q < 4) {
+                        hp.id = slot(q, 1, 0);
+                        hp.axa = 0;
+                        hp.axb = 2;
+                        hp.base = 8 * kVX + 8 * q;
+                        hp.da = 1;
+                        hp.db = kPlane;
+                    } else if (q < 8) {
+                        hp.id = slot(q - 4, 0, 1);
+                        hp.axa = 0;
+                        hp.axb = 1;
+                        hp.base = 8 * kPlane + 8 * (q - 4);
+                        hp.da = 1;
+                        hp.db = kVX;
+                    } else {
+                        hp.id = slot(4, 0, 0);
+                        hp.axa = 1;
+                        hp.axb = 2;
+                        hp.base = kTX;
+                        hp.da = kVX;
+                        hp.db = kPlane;
+                    }
+                    huge |= box_halo<true, kVX, kPlane>(box, L, s_rec, hp, lane);
+                }
+            } else {
+                // warp 7: the y = z = 0 lines of the bricks after the tile's
+                // along y and z, then the lines x = y = 0 (+x+y brick), x = z = 0
+                // (+x+z) and the corner (+x+y+z); lanes 8g..8g+7 take line g
+                const int g = lane >> 3;
+                HaloPiece hp;
+                hp.axb = 0;
+                hp.db = 0;
+                hp.id = slot(g, 1, 1);
+                hp.axa = 0;
+                hp.base = 8 * kVX + 8 * kPlane + 8 * g;
+                hp.da = 1;
+                hp.len = 8;
+                huge |= box_halo<false, kVX, kPlane>(box, L, s_rec, hp, lane);
+                if (g == 0) {
+                    hp.id = slot(4, 1, 0);
+                    hp.axa = 2;
+                    hp.base = kTX + 8 * kVX;
+                    hp.da = kPlane;
+                    hp.len = 8;
+                } else if (g == 1) {
+                    hp.id = slot(4, 0, 1);
+                    hp.axa = 1;
+                    hp.base = kTX + 8 * kPlane;
+                    hp.da = kVX;
+                    hp.len = 8;
+                } else {
+                    hp.id = (g == 2) ? slot(4, 1, 1) : -1;
+                    hp.axa = 0;
+                    hp.base = kTX + 8 * kVX + 8 * kPlane;
+                    hp.da = 1;
+                    hp.len = (g == 2) ? 1 : 0;
+                }
+                huge |= box_halo<false, kVX, kPlane>(box, L, s_rec, hp, lane);
+            }
+            fast = !__syncthreads_or(huge);
+            body(tile, tile, p, box, claim);
+        }
+        if (warp == 0) claim();  // unless a warp already did
+        __syncthreads();         // the box is free, and s_tile[par] holds the next tile
+        tile = s_tile[par];
+        a = s_act[par];
+        if (tid == 0) s_claimed = 0u;
+        par ^= 1;
     }
 }
 
@@ -674,10 +1014,11 @@ __device__ __forceinline__ uint32_t lanemask_le()
 // claimed-tile loop and the case bytes from the box, and once the block scan
 // has the tile's totals, warp 0 publishes them and finds the tile's offsets
 // by the look-back while the other warps compact.
-template <int NISO, bool STORED, bool FUSED, class Src>
+template <int NISO, bool STORED, bool FUSED, class Src, bool CHR = false, bool IDX = false>
 __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
 {
     static_assert(!(FUSED && STORED), "the single pass classifies from the box");
+    static_assert(!CHR || FUSED, "the CHR box is decoded in the single pass");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     float *bufs = reinterpret_cast<float *>(smem + kOffBuf);
@@ -705,19 +1046,28 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
     }
     if (tid < 12) s_edgew[tid] = edge_word(tid);
 
+    // CHR: which (cell brick j, isovalue slot i) can have triangles (bit
+    // 4j + i; the others are not classified), and whether no box value
+    // reaches 2^124, both set by the tile loop
+    uint32_t chr_act = 0xffffu, idx_act = 0xffffu;
+    bool chr_fast = true;
     auto body = [&](int64_t, int64_t tile, const McParams &p, const float *box, auto &&claim) {
-        // fast quotients unless some value of the box is 2^125 or more in magnitude (or infinite)
-        bool huge = false;
-        for (int u = tid; u < kRows * kVX / 4; u += 256) {
-            const float4 v = reinterpret_cast<const float4 *>(box)[u];
-            huge |= fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))) >= 4.2535296e37f;
-        }
-        const bool fast = !__syncthreads_or(huge);
-        if (!STORED) {
-            row_masks<NISO>(box, s_row, p);
-            __syncthreads();
+        // fast quotients unless some value of the box is 2^124 or more in magnitude (or infinite)
+        bool fast = chr_fast;
+        if (!CHR) {
+            bool huge = false;
+            for (int u = tid; u < kRows * kVX / 4; u += 256) {
+                const float4 v = reinterpret_cast<const float4 *>(box)[u];
+                huge |= fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))) >= kHugeValue;
+            }
+            fast = !__syncthreads_or(huge);
         }
         const TileXYZ o = tile_origin(p, tile);
+        const uint32_t act = CHR ? chr_act : ((IDX && !STORED) ? idx_act : 0xffffu);
+        if (!STORED) {
+            row_masks<NISO>(box, s_row, p, iso_mask(act));
+            __syncthreads();
+        }
         const int j = tid >> 6, ly = tid & 7, lz = (tid >> 3) & 7;
         const int r00 = lz * 9 + ly;
         const int nvalid = STORED ? 8 : valid_cells(p, o);
@@ -732,6 +1082,10 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
                 lo = cw.x;
                 hi = cw.y;
                 return __ldg(p.tcnt + at0 + 256 * i);
+            }
+            if (!((act >> (4 * j + i)) & 1u)) {  // (uniform across the thread's two warps)
+                lo = hi = 0u;
+                return 0u;
             }
             cases8(s_row + i * kRows, r00, j, nvalid, lo, hi);
             uint32_t cnt = 0;
@@ -850,36 +1204,10 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
         __syncthreads();
         if (FUSED && warp == 0) {
             // publish this tile's counts, find the triangles before it, publish its inclusive prefix
-            uint64_t own = 0;
+            uint32_t cnt[NISO];
 #pragma unroll
-            for (int i = 0; i < NISO; i++) own |= (uint64_t)(s_w[i][8] & 0xffffu) << (14 * i);
-            uint64_t ex[NISO];
-            bool ok = true;
-            const bool publish = tile != p.unpublished_tile;
-            if (tile == 0) {
-#pragma unroll
-                for (int i = 0; i < NISO; i++) ex[i] = 0;
-            } else {
-                if (lane == 0 && publish) st_relaxed_u64(p.tstat + tile, kTileOwn | own);
-                ok = look_back<NISO>(p, tile, ex);
-            }
-            if (lane == 0) {
-                if (!ok) {
-                    atomicExch(p.tabort, 1u);
-                    if (p.err) atomicOr(p.err, 1u << CHR_ERR_TIMEOUT);
-                }
-#pragma unroll
-                for (int i = 0; i < NISO; i++) {
-                    const uint64_t incl = ex[i] + (s_w[i][8] & 0xffffu);
-                    st_relaxed_u64(p.tile_off + tile * kMcIsoPerPass + i, incl);
-                    s_g0[i] = ex[i];
-                    if (tile == p.ntiles - 1) {  // the totals, and whether every triangle fitted below cap
-                        p.ntris[i] = incl;
-                        if (incl > p.cap && p.err) atomicOr(p.err, 1u << CHR_ERR_OVERFLOW);
-                    }
-                }
-                if (publish) st_release_u64(p.tstat + tile, kTilePrefix | own);
-            }
+            for (int i = 0; i < NISO; i++) cnt[i] = s_w[i][8];
+            publish_tile<NISO>(p, tile, cnt, s_g0);
         }
         // pool entries and chunk-table entries of the slots, all lists together
         uint32_t used = 0;
@@ -896,7 +1224,12 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
                 if (n) {
                     const uint32_t ex = s_w[i][warp] + excl[i];
                     // without a stored classification the case bytes are made again rather than kept
-                    if (!STORED) cases8(s_row + i * kRows, r00, j, nvalid, lo[i], hi[i]);
+                    if (!STORED) {
+                        if (!((act >> (4 * j + i)) & 1u))
+                            lo[i] = hi[i] = 0u;
+                        else
+                            cases8(s_row + i * kRows, r00, j, nvalid, lo[i], hi[i]);
+                    }
                     compact(lo[i], hi[i], ab + (ex >> 16), ex & 0xffffu, cq);
                     if (tid < 32 && CHR_IN_BOUNDS(ab + na + tid < (uint32_t)kPool))
                         s_apre[ab + na + tid] = 0xffffu;  // window tail past the last active cell
@@ -914,7 +1247,8 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
                     cq += (n + 31u) >> 5;
                 }
             }
-            if (FUSED && lane == 0) claim();  // the first warp done claims the next tile
+            // the first warp done claims the next tile (the CHR loop claims at the tile's end)
+            if (FUSED && !CHR && lane == 0) claim();
             // (the tile loop's barrier keeps the pool until every chunk is written)
         } else {
 #pragma unroll 1
@@ -932,12 +1266,14 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
             }
         }
     };
-    if constexpr (FUSED)
-        tile_loop_claimed(*src.p, src.map, bufs, mbar, body);
+    if constexpr (CHR)
+        tile_loop_chr<NISO>(*src.p, *src.L, src.index, bufs, chr_act, chr_fast, s_g0, body);
+    else if constexpr (FUSED)
+        tile_loop_claimed<NISO, IDX>(*src.p, src.map, bufs, mbar, body, &idx_act);
     else
-        tile_loop(src, err, bufs, mbar, [&](int64_t g, int64_t t, const McParams &p, const float *box) {
-            body(g, t, p, box, [] {});
-        });
+        tile_loop<NISO, IDX && !STORED>(
+            src, err, bufs, mbar,
+            [&](int64_t g, int64_t t, const McParams &p, const float *box) { body(g, t, p, box, [] {}); }, &idx_act);
     if (lane == 0) bulk_wait_all();  // shared memory stays valid until every bulk store is done
 }
 
@@ -951,11 +1287,20 @@ __global__ void __launch_bounds__(256, 4) k_mc_emit_stored(const __grid_constant
 }
 
 // Classification, tile offsets and emission in one launch (no count pass).
-template <int NISO>
+template <int NISO, bool IDX>
 __global__ void __launch_bounds__(256, 4) k_mc_fused(const __grid_constant__ McParams p,
                                                     const __grid_constant__ CUtensorMap map)
 {
-    mc_emit_run<NISO, false, true>(SrcOne{&p, &map}, p.err);
+    mc_emit_run<NISO, false, true, SrcOne, false, IDX>(SrcOne{&p, &map}, p.err);
+}
+
+// Decode of a CHR level, classification, tile offsets and emission in one
+// launch: the field never goes to memory.
+template <int NISO>
+__global__ void __launch_bounds__(256, 4) k_mc_chr(const __grid_constant__ McParams p,
+                                                  const __grid_constant__ ChrLevels L, const float2 *index)
+{
+    mc_emit_run<NISO, false, true, SrcChr, true, true>(SrcChr{&p, &L, index}, p.err);
 }
 
 __global__ void __launch_bounds__(256, 4) k_mc_emit_batched(const __grid_constant__ McBatch b, uint32_t *err)
@@ -1354,6 +1699,7 @@ static int64_t two_pass_min_tiles(int n) { return (int64_t)2048 * n * n * n; }
 
 struct McGrids {
     int count, adjoint, fused, emit;  // resident blocks of each persistent kernel
+    int count_idx, fused_idx;         // (the variants that read a value index)
 };
 
 template <int NISO>
@@ -1372,18 +1718,26 @@ static cudaError_t mc_prepare(McGrids &out)
             if (e != cudaSuccess) return e;
             e = cudaFuncSetAttribute(k_mc_count<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCountSmem);
             if (e != cudaSuccess) return e;
-            e = cudaFuncSetAttribute(k_mc_fused<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
+            e = cudaFuncSetAttribute(k_mc_fused<NISO, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
+            if (e != cudaSuccess) return e;
+            e = cudaFuncSetAttribute(k_mc_count_idx<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCountSmem);
+            if (e != cudaSuccess) return e;
+            e = cudaFuncSetAttribute(k_mc_fused<NISO, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
             if (e != cudaSuccess) return e;
             e = cudaFuncSetAttribute(k_mc_emit_stored<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
             if (e != cudaSuccess) return e;
-            int sms = 0, bc = 0, ba = 0, bu = 0, be = 0;
+            int sms = 0, bc = 0, ba = 0, bu = 0, be = 0, bci = 0, bui = 0;
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bc, k_mc_count<NISO>, 256, kCountSmem);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ba, k_mc_adjoint<NISO>, 256, kEmitSmem);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu, k_mc_fused<NISO>, 256, kEmitSmem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu, k_mc_fused<NISO, false>, 256, kEmitSmem);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&be, k_mc_emit_stored<NISO>, 256, kEmitSmem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bci, k_mc_count_idx<NISO>, 256, kCountSmem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bui, k_mc_fused<NISO, true>, 256, kEmitSmem);
             if (sms < 1) sms = 1;
             McGrids &G = Gd[dev];
+            G.count_idx = sms * (bci > 0 ? bci : 1);
+            G.fused_idx = sms * (bui > 0 ? bui : 1);
             G.count = sms * (bc > 0 ? bc : 1);
             G.adjoint = sms * (ba > 0 ? ba : 1);
             G.fused = sms * (bu > 0 ? bu : 1);
@@ -1403,8 +1757,13 @@ static cudaError_t launch_count_scan(const McParams &p, const CUtensorMap &map, 
     McGrids G;
     cudaError_t e = mc_prepare<NISO>(G);
     if (e != cudaSuccess) return e;
-    const unsigned gc = (unsigned)(p.ntiles < G.count ? p.ntiles : G.count);
-    k_mc_count<NISO><<<gc, 256, kCountSmem, s>>>(p, map);
+    if (p.index) {
+        const unsigned gc = (unsigned)(p.ntiles < G.count_idx ? p.ntiles : G.count_idx);
+        k_mc_count_idx<NISO><<<gc, 256, kCountSmem, s>>>(p, map);
+    } else {
+        const unsigned gc = (unsigned)(p.ntiles < G.count ? p.ntiles : G.count);
+        k_mc_count<NISO><<<gc, 256, kCountSmem, s>>>(p, map);
+    }
     TScanArgs a;
     a.cnt = w.cnt;
     a.off = w.off;
@@ -1461,8 +1820,13 @@ static cudaError_t launch_mc_group(const McParams &p0, const CUtensorMap &map, c
     p.ntris = ntris;
     e = cudaMemsetAsync(p.tstat, 0, (size_t)p.ntiles * 8 + 8, s);
     if (e != cudaSuccess) return e;
-    const unsigned gf = (unsigned)(p.ntiles < G.fused ? p.ntiles : G.fused);
-    k_mc_fused<NISO><<<gf, 256, kEmitSmem, s>>>(p, map);
+    if (p.index) {
+        const unsigned gf = (unsigned)(p.ntiles < G.fused_idx ? p.ntiles : G.fused_idx);
+        k_mc_fused<NISO, true><<<gf, 256, kEmitSmem, s>>>(p, map);
+    } else {
+        const unsigned gf = (unsigned)(p.ntiles < G.fused ? p.ntiles : G.fused);
+        k_mc_fused<NISO, false><<<gf, 256, kEmitSmem, s>>>(p, map);
+    }
     return cudaGetLastError();
 }
 
@@ -1483,15 +1847,16 @@ static cudaError_t launch_adjoint_group(const McParams &p, const AdjParams &a, c
 }
 
 cudaError_t launch_mc(const float *field, const Grid &g, const float *iso, int n_iso, float *tris, uint64_t cap,
-                      uint64_t *ntris, uint32_t *err, void *workspace, size_t workspace_bytes, cudaStream_t s)
+                      uint64_t *ntris, uint32_t *err, void *workspace, size_t workspace_bytes, cudaStream_t s,
+                      const float2 *index)
 {
     return launch_mc_pitched(field, g, g.nx, g.nx * g.ny, iso, n_iso, tris, cap, ntris, err, workspace,
-                             workspace_bytes, s);
+                             workspace_bytes, s, index);
 }
 
 cudaError_t launch_mc_pitched(const float *field, const Grid &g, int64_t sx, int64_t sy, const float *iso, int n_iso,
                               float *tris, uint64_t cap, uint64_t *ntris, uint32_t *err, void *workspace,
-                              size_t workspace_bytes, cudaStream_t s)
+                              size_t workspace_bytes, cudaStream_t s, const float2 *index)
 {
     McParams p;
     memset(&p, 0, sizeof(p));
@@ -1504,6 +1869,9 @@ cudaError_t launch_mc_pitched(const float *field, const Grid &g, int64_t sx, int
     mc_tiles(g, p.ntx, p.ncby, p.ncbz, p.ntiles);
     p.cap = cap;
     p.err = err;
+    p.index = index;
+    p.ibx = (int32_t)g.nbx;
+    p.iby = (int32_t)g.nby;
     // the stored classification when the workspace holds it (large grids take two passes)
     const int cstride = (workspace_bytes >= mc_workspace_bytes(g, n_iso)) ? stored_slots(n_iso) : 0;
     McWorkspace w;
@@ -1528,6 +1896,97 @@ cudaError_t launch_mc_pitched(const float *field, const Grid &g, int64_t sx, int
             case 2: e = launch_mc_group<2>(p, map, w, ntris + i0, n, s); break;
             case 3: e = launch_mc_group<3>(p, map, w, ntris + i0, n, s); break;
             default: e = launch_mc_group<4>(p, map, w, ntris + i0, n, s); break;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Resident blocks of k_mc_chr<NISO>, once per device (as mc_prepare).
+template <int NISO>
+static cudaError_t mc_chr_prepare(int &grid)
+{
+    static int Gd[kMaxDevices] = {};
+    static std::atomic<bool> ready[kMaxDevices] = {};
+    static std::mutex mu;
+    const int dev = current_device();
+    if (!ready[dev].load(std::memory_order_acquire)) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!ready[dev].load(std::memory_order_relaxed)) {
+            cudaError_t e = cudaFuncSetAttribute(k_mc_chr<NISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEmitSmem);
+            if (e != cudaSuccess) return e;
+            int sms = 0, bu = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu, k_mc_chr<NISO>, 256, kEmitSmem);
+            Gd[dev] = (sms > 0 ? sms : 1) * (bu > 0 ? bu : 1);
+            ready[dev].store(true, std::memory_order_release);
+        }
+    }
+    grid = Gd[dev];
+    return cudaSuccess;
+}
+
+template <int NISO>
+static cudaError_t launch_chr_group(const McParams &p0, const ChrLevels &L, const float2 *index,
+                                    const McWorkspace &w, uint64_t *ntris, cudaStream_t s)
+{
+    int grid = 0;
+    cudaError_t e = mc_chr_prepare<NISO>(grid);
+    if (e != cudaSuccess) return e;
+    McParams p = p0;
+    p.unpublished_tile = test_unpublished_tile();
+    p.tstat = reinterpret_cast<uint64_t *>(w.cnt);
+    p.tctr = reinterpret_cast<uint32_t *>(p.tstat + p.ntiles);
+    p.tabort = p.tctr + 1;
+    p.ntris = ntris;
+    e = cudaMemsetAsync(p.tstat, 0, (size_t)p.ntiles * 8 + 8, s);
+    if (e != cudaSuccess) return e;
+    const unsigned gf = (unsigned)(p.ntiles < grid ? p.ntiles : grid);
+    k_mc_chr<NISO><<<gf, 256, kEmitSmem, s>>>(p, L, index);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mc_chr(const ChrMcLevels &c, const Grid &g, const float *iso, int n_iso, float *tris, uint64_t cap,
+                          uint64_t *ntris, uint32_t *err, void *workspace, size_t workspace_bytes, cudaStream_t s)
+{
+    if (workspace_bytes < mc_workspace_min_bytes(g, n_iso)) return cudaErrorInvalidValue;
+    McParams p;
+    memset(&p, 0, sizeof(p));
+    p.nx = g.nx;
+    p.ny = g.ny;
+    p.nz = g.nz;
+    mc_tiles(g, p.ntx, p.ncby, p.ncbz, p.ntiles);
+    p.cap = cap;
+    p.err = err;
+    McWorkspace w;
+    mc_layout(g, 0, workspace, &w);
+    p.tile_cnt = w.cnt;
+    p.tile_off = w.off;
+    ChrLevels L;
+    memset(&L, 0, sizeof(L));
+    for (int l = 0; l < c.nlevels; l++) {
+        L.recs[l] = c.recs[l];
+        L.words[l] = c.words[l];
+        L.exc_idx[l] = c.exc_idx[l];
+        L.exc_val[l] = c.exc_val[l];
+        L.two_e[l] = c.two_e[l];
+    }
+    L.nlevels = c.nlevels;
+    L.nbx = (int32_t)g.nbx;
+    L.nby = (int32_t)g.nby;
+    L.nbz = (int32_t)g.nbz;
+    for (int i0 = 0; i0 < n_iso; i0 += kMcIsoPerPass) {
+        const int n = (n_iso - i0) < kMcIsoPerPass ? (n_iso - i0) : kMcIsoPerPass;
+        for (int i = 0; i < kMcIsoPerPass; i++) {
+            p.k[i] = (i < n) ? iso[i0 + i] : 0.0f;
+            p.tris[i] = (i < n) ? tris + 9ull * cap * (uint64_t)(i0 + i) : nullptr;
+        }
+        cudaError_t e;
+        switch (n) {
+            case 1: e = launch_chr_group<1>(p, L, c.index, w, ntris + i0, s); break;
+            case 2: e = launch_chr_group<2>(p, L, c.index, w, ntris + i0, s); break;
+            case 3: e = launch_chr_group<3>(p, L, c.index, w, ntris + i0, s); break;
+            default: e = launch_chr_group<4>(p, L, c.index, w, ntris + i0, s); break;
         }
         if (e != cudaSuccess) return e;
     }

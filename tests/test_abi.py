@@ -37,7 +37,7 @@ def test_exports_every_declared_function(L):
     assert {"chr_compress", "chr_reconstruct", "isosurface_extract", "chr_topo_translate"} <= names
     for n in sorted(names):
         assert hasattr(L, n), f"libchr.so does not export {n}"
-    assert L.chr_version() == 1
+    assert L.chr_version() == 2
 
 
 def _params(eb=(0.1,), iso=(0.5,), topo=1, acc=1.0, flags=0):
@@ -78,7 +78,8 @@ def test_other_calls_reject_bad_arguments(L):
     iso = (ctypes.c_float * 1)(0.5)
     assert L.chr_reconstruct(None, 0, ctypes.c_void_p(0x1000), None) == 1
     assert L.isosurface_extract(None, d, iso, 1, None, 0, None, None, None, 0, None) == 1
-    assert L.chr_isosurface(None, 0, iso, 1, None, None, 0, ctypes.c_void_p(0x1000), None, None, None) == 1
+    assert L.chr_isosurface(None, 0, iso, 1, None, None, 0, ctypes.c_void_p(0x1000), None, 0, None, None) == 1
+    assert L.chr_brick_index(None, 0, ctypes.c_void_p(0x1000), None) == 1
     ws = L.isosurface_workspace_size(d, 1)
     ws_min = L.isosurface_workspace_min_size(d, 1)
     # the full workspace adds the stored classification of up to 4 isovalue slots to the tile arrays
@@ -115,7 +116,7 @@ def test_deserialize_rejects_corrupt_bytes(L):
         return L.chr_deserialize(b, len(b), None, None, ctypes.byref(out))
 
     assert des(b"XXXX" + b"\0" * 100) == 6
-    assert des(b"CHR1" + struct.pack("<I", 2) + b"\0" * 100) == 6
+    assert des(b"CHR1" + struct.pack("<I", 3) + b"\0" * 100) == 6   # unknown version
     assert des(_header()[:30]) == 6                      # truncated header
     assert des(_header(nlevels=9)) == 6
     assert des(_header()) == 6                           # header without the level data
