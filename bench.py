@@ -1,19 +1,24 @@
-"""Benchmark of the hot path: chr_compress (quantise, level chain, sign fix,
-Lorenzo, pack) -> chr_reconstruct (decode + exact vertices) -> marching cubes
-for every isovalue, on a seeded 512^3 float32 turbulence field (energy
-spectrum k^-5/3, unit variance), isovalues {-1,-0.5,0.5,1}, relative bounds
-1e-2/1e-3/1e-4, 3 CHR levels, topology fix on.
+"""Benchmark of the visualization side's hot path (paper Sec. 2): decode a
+CHR level, its exact vertices (the topology fix), and marching cubes for 4
+isovalues, in one chr_isosurface call, on a seeded 1024^3 float32 turbulence
+field (energy spectrum k^-5/3, unit variance, generated on the GPU),
+isovalues {-1,-0.5,0.5,1}, CHR levels at relative bounds 1e-2/1e-3/1e-4 with
+the topology fix, level 2 requested.
 
-One step = one pass of the whole path over the field.  `value` is field GB/s
-(4*N bytes of field per step / step time), timed with CUDA events over K
-steps after W warm-up steps, inputs resident in HBM (512 MiB field > L2).
-`e2e` is the same through the public API with the field in pinned host
-memory: host->device copy, the three calls, and the device->host read of the
-triangle counts inside the timed region.
+One step = one chr_isosurface call over the whole field.  `value` is field
+GB/s (4*N bytes of field per step / step time), timed with CUDA events over
+K steps after W warm-up steps, inputs resident in HBM (the 2 GB CHR, the
+4.3 GB decoded field and the 32 GB mesh are far larger than L2).  The
+compression (chr_compress, the data source's side) is timed separately
+(stages).  `e2e` is the same call through the public API with the CHR's
+bytes in pinned host memory: chr_deserialize (host validation and upload),
+chr_isosurface and the read-back of the triangle counts in the timed region,
+the mesh consumed on the device (e2e.mesh_d2h adds the mesh's copy back).
 
---impl reference times the CPU oracle (tests-only infrastructure) on a
-bounded sub-box of the same field; it is the baseline, not the target.
-Under torchrun every rank runs its own replica on its own field (weak scaling).
+--impl reference times the CPU oracle (test infrastructure) on every host
+core, each on its own sub-box of the same field; it is the baseline, not
+the target.  Under torchrun every rank runs its own replica on its own field
+(weak scaling).
 """
 from __future__ import annotations
 
@@ -34,18 +39,23 @@ ISOVALUES = [-1.0, -0.5, 0.5, 1.0]
 REL_BOUNDS = [1e-2, 1e-3, 1e-4]
 
 
+LEVEL = 2
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="chr", choices=["chr", "reference"])
-    ap.add_argument("--size", type=int, default=512)
-    ap.add_argument("--seed", type=int, default=512)
+    ap.add_argument("--size", type=int, default=1024)
+    ap.add_argument("--seed", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
-    ap.add_argument("--sample", type=int, default=352, help="edge of the oracle's sub-box")
+    ap.add_argument("--sample", type=int, default=160, help="edge of each oracle process's sub-box")
+    ap.add_argument("--no-forms", action="store_true", help="skip timing the other chr_isosurface forms")
+    ap.add_argument("--no-side", action="store_true", help="skip the 512^3 configuration")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-loop measurement")
     ap.add_argument("--serve-size", type=int, default=1024, help="grid side of the served timesteps")
     ap.add_argument("--serve-requests", type=int, default=200)
@@ -70,21 +80,20 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def profiled_traffic_ratio():
-    """DRAM traffic / algorithmic bytes of isosurface_extract from the committed
-    ncu summary, or None when mc.cu has changed since that capture."""
+def profiled_traffic(name="chr_isosurface_turb1024.md"):
+    """DRAM bytes per step of the headline call from the committed ncu
+    summary, or None when a source it depends on has changed since."""
     import hashlib
     import re
 
-    summary = os.path.join(ROOT, "profiles", "k_mc_turb384.md")
-    src = os.path.join(ROOT, "paper_2408_05462_gb300", "csrc", "mc.cu")
+    summary = os.path.join(ROOT, "profiles", name)
     try:
         text = open(summary).read()
-        ratio = float(re.search(r"traffic_over_algorithmic: ([0-9.]+)", text).group(1))
-        sha = re.search(r"mc\.cu sha256 ([0-9a-f]{64})", text).group(1)
-        if hashlib.sha256(open(src, "rb").read()).hexdigest() != sha:
-            return None
-        return ratio
+        traffic = float(re.search(r"traffic_per_step_bytes: ([0-9.e+]+)", text).group(1))
+        for src, sha in re.findall(r"source: (\S+) sha256 ([0-9a-f]{64})", text):
+            if hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest() != sha:
+                return None
+        return traffic
     except (OSError, AttributeError, ValueError):
         return None
 
@@ -98,14 +107,43 @@ def aggregate_ranks(total_ms, world, n_per_rank, reduce_max=None):
 
 
 def workload_config(n, args, extra=None):
-    cfg = {"workload": f"turbulence {n}^3 float32, k^-5/3, seed {args.seed}; 4 isovalues {ISOVALUES}; "
-                       f"3-level CHR, bounds {REL_BOUNDS} x range; topology fix",
-           "field_shape": [n, n, n], "isovalues": ISOVALUES, "levels": 3, "topo": "fix",
-           "step": "chr_compress + chr_reconstruct(level 2) + isosurface_extract(4 isovalues)",
-           "l2": "inputs larger than L2 (field 512 MiB, compressed stream > 129 MB); no flush"}
+    cfg = {"workload": f"turbulence {n}^3 float32, k^-5/3, unit variance, GPU generator seed {args.seed}; "
+                       f"3-level CHR at {REL_BOUNDS} x range with the topology fix for isovalues {ISOVALUES}; "
+                       f"chr_isosurface of level {LEVEL} at those 4 isovalues",
+           "field_shape": [n, n, n], "isovalues": ISOVALUES, "levels": 3, "level": LEVEL, "topo": "fix",
+           "step": f"chr_isosurface(level {LEVEL}, 4 isovalues): decode + exact vertices + marching cubes; "
+                   "chr_compress timed separately (stages.chr_compress)",
+           "l2": "inputs larger than L2 (CHR about 2 GB, decoded field 4.3 GB, mesh 32 GB); no flush",
+           "mesh": "consumed on the device; e2e.mesh_d2h adds its copy to the host"}
     if extra:
         cfg.update(extra)
     return cfg
+
+
+def host_info():
+    """(threads this process may use, CPU model)."""
+    try:
+        ncores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        ncores = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return ncores, (model or "unknown") + " (%s)" % os.uname().machine
 
 
 class Clocks:
@@ -167,67 +205,154 @@ class Clocks:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def make_field(n, seed):
+def _oracle_worker(conn, sub, eb):
+    """One oracle process (test infrastructure: the CPU baseline): encode its
+    sub-box once (untimed), then on every "run" decode level LEVEL and count
+    the marching-cubes triangles of the 4 isovalues, and send (seconds,
+    triangles) back."""
+    sys.path.insert(0, ROOT)
+    import oracle
+
+    enc = oracle.encode(sub, eb, ISOVALUES, fix=True)
+    conn.send("ready")
+    while True:
+        msg = conn.recv()
+        if msg != "run":
+            break
+        t0 = time.perf_counter()
+        R = oracle.decode(enc, LEVEL)
+        tris = sum(oracle.mc_count(R, k) for k in ISOVALUES)
+        conn.send((time.perf_counter() - t0, tris))
+    conn.close()
+
+
+class OraclePool:
+    """One spawned process per sub-box (each pinned to nothing: the OS
+    spreads them over the host cores); run() times one round of decode +
+    marching cubes in every process at once."""
+
+    def __init__(self, subs, eb):
+        import multiprocessing as mp
+
+        import oracle
+
+        oracle.build()
+        ctx = mp.get_context("spawn")
+        self.conns, self.procs = [], []
+        for sub in subs:
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_oracle_worker, args=(b, sub, eb), daemon=True)
+            p.start()
+            self.conns.append(a)
+            self.procs.append(p)
+        for c in self.conns:
+            assert c.recv() == "ready"
+        self.vertices = sum(int(sub.size) for sub in subs)
+
+    def run(self):
+        t0 = time.perf_counter()
+        for c in self.conns:
+            c.send("run")
+        res = [c.recv() for c in self.conns]
+        return time.perf_counter() - t0, sum(r[1] for r in res)
+
+    def close(self):
+        for c in self.conns:
+            c.send("stop")
+        for p in self.procs:
+            p.join(timeout=30)
+
+
+def sub_boxes(field, count, s):
+    """`count` sub-boxes of s^3 vertices of a [n, n, n] field (torch, CUDA or
+    CPU), at distinct positions, copied to host numpy."""
+    n = field.shape[0]
+    s = min(s, n)
+    per = max(n // s, 1)
+    out = []
+    for i in range(count):
+        z, y, x = (i % per) * s, ((i // per) % per) * s, ((i // (per * per)) % per) * s
+        out.append(np.ascontiguousarray(field[z:z + s, y:y + s, x:x + s].cpu().numpy()))
+    return out
+
+
+def reference_field(n, seed):
+    """The bench's field: on the GPU when there is one, else the same
+    recipe on the host at no more than 256^3 (a smaller sample)."""
+    import torch
+
     from paper_2408_05462_gb300 import synth
 
-    return synth.turbulence(n, seed=seed)
+    if torch.cuda.is_available():
+        torch.cuda.set_device(0)
+        return synth.turbulence_cuda(n, seed=seed), n
+    m = min(n, 256)
+    return torch.from_numpy(synth.turbulence(m, seed=seed)), m
 
 
 def run_reference(args):
-    """The CPU oracle on a bounded sub-box of the same workload."""
+    """The CPU oracle (as it stands) on every host core: each process
+    decodes level LEVEL of its own oracle-encoded s^3 sub-box of the field
+    and counts the marching-cubes triangles of the 4 isovalues; one step is
+    one such round in every process at once."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    import oracle
-    from paper_2408_05462_gb300 import synth
-
-    oracle.build()
-    f = make_field(args.size, args.seed)
-    r = synth.value_range(f)
+    ncores, model = host_info()
+    f, n = reference_field(args.size, args.seed)
+    r = float(f.max() - f.min())
     eb = np.array([b * r for b in REL_BOUNDS], np.float32)
-    s = min(args.sample, args.size)
-    sub = np.ascontiguousarray(f[:s // 2, :s, :s])  # s x s x s/2 vertices
-
-    def step():
-        enc = oracle.encode(sub, eb, ISOVALUES, fix=True)
-        R = oracle.decode(enc, 2)
-        return sum(oracle.mc_count(R, k) for k in ISOVALUES)
-
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    dt = (time.perf_counter() - t0) / args.steps
-    gbs = 4.0 * sub.size / dt / 1e9
-    sample = f"sub-box {s}x{s}x{s // 2} of the {args.size}^3 field per step (oracle encode 3 levels + decode + MC count x4)"
+    subs = sub_boxes(f, ncores, args.sample)
+    del f
+    pool = OraclePool(subs, eb)
+    try:
+        for _ in range(args.warmup):
+            pool.run()
+        t = 0.0
+        for _ in range(args.steps):
+            t += pool.run()[0]
+    finally:
+        pool.close()
+    dt = t / args.steps
+    gbs = 4.0 * pool.vertices / dt / 1e9
+    s = subs[0].shape[0]
+    sample = (f"{len(subs)} processes, each an {s}^3 sub-box of the {n}^3 field: oracle decode of level {LEVEL} "
+              f"(3-level CHR, fix) + marching-cubes count x4, encode untimed; host: {model}")
     print(json.dumps({
         "impl": "reference", "metric": "field GB/s (decode+fix+marching cubes), % HBM roofline; serve p50/p99 ms",
         "value": gbs, "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": workload_config(args.size, args, {"sample": sample}),
-        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "data": "synthetic", "config": workload_config(n, args, {"sample": sample}),
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": len(subs), "kind": "oracle", "sample": sample,
+                         "nproc": ncores, "cpu_model": model},
         "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
 
-def cpu_baseline(f, args):
-    import oracle
-    from paper_2408_05462_gb300 import synth
-
-    oracle.build()
-    r = synth.value_range(f)
-    eb = np.array([b * r for b in REL_BOUNDS], np.float32)
-    s = min(args.sample, f.shape[0])
-    sub = np.ascontiguousarray(f[:s, :s, :s])
-    t0 = time.perf_counter()
-    enc = oracle.encode(sub, eb, ISOVALUES, fix=True)
-    R = oracle.decode(enc, 2)
-    tris = sum(oracle.mc_count(R, k) for k in ISOVALUES)
-    dt = time.perf_counter() - t0
-    return {"value": 4.0 * sub.size / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"{s}^3 sub-box of the field: oracle encode (3 levels, fix) + decode + MC for 4 isovalues "
-                      f"({tris} triangles) in {dt:.1f} s, single thread"}
+def cpu_baseline(subs, eb):
+    """The oracle on 1 core (one process, one sub-box) and on every host core
+    (one process per sub-box), field GB/s of decode + marching cubes."""
+    ncores, model = host_info()
+    one = OraclePool(subs[:1], eb)
+    try:
+        one.run()
+        t1, _ = one.run()
+    finally:
+        one.close()
+    v1 = 4.0 * one.vertices / t1 / 1e9
+    pool = OraclePool(subs, eb)
+    try:
+        pool.run()
+        tn, tris = pool.run()
+    finally:
+        pool.close()
+    vn = 4.0 * pool.vertices / tn / 1e9
+    s = subs[0].shape[0]
+    return {"value": vn, "unit": "GB/s", "cores": len(subs), "kind": "oracle",
+            "sample": f"{len(subs)} processes at once, each an {s}^3 sub-box of the field: oracle decode of level "
+                      f"{LEVEL} + marching-cubes count x4 ({tris} triangles) in {tn:.2f} s; encode untimed",
+            "one_core": {"value": v1, "unit": "GB/s", "cores": 1, "seconds": t1},
+            "nproc": ncores, "cpu_model": model}
 
 
 def adjoint_timing(n=256, seed=256256, reps=10):
@@ -301,48 +426,6 @@ def adjoint_cpu_baseline(n=64, seed=256256):
                       "thread, %.2f s" % (n, m.ntri, dt)}
 
 
-def viz_full_grid(h, n, reps=5):
-    """Decode + marching cubes of a whole n^3 timestep: chr_reconstruct of
-    the 1e-4 x range level, then isosurface_extract at the 4 candidate
-    isovalues, each timed with CUDA events (field and mesh far above L2)."""
-    import torch
-
-    from paper_2408_05462_gb300 import chr
-
-    R = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
-    h.reconstruct(2, R)
-    _, counts, _ = chr.isosurface_extract(R, ISOVALUES, 0)
-    torch.cuda.synchronize()
-    cap = int(counts.max()) + 1024
-    tris = torch.empty((len(ISOVALUES), cap, 3, 3), dtype=torch.float32, device="cuda")
-    ws = torch.empty(chr.isosurface_workspace_size(R.shape, len(ISOVALUES)), dtype=torch.uint8, device="cuda")
-    err = torch.zeros(1, dtype=torch.int32, device="cuda")
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    t_dec = t_mc = 0.0
-    for it in range(reps + 2):
-        ev[0].record()
-        h.reconstruct(2, R)
-        ev[1].record()
-        chr.isosurface_extract(R, ISOVALUES, cap, tris=tris, counts=counts, err=err, workspace=ws)
-        ev[2].record()
-        torch.cuda.synchronize()
-        if it >= 2:
-            t_dec += ev[0].elapsed_time(ev[1]) / reps
-            t_mc += ev[1].elapsed_time(ev[2]) / reps
-    T = int(counts.sum())
-    N = n ** 3
-    peak, _ = measured_peaks()
-    mc_bytes = 4.0 * N + 36.0 * T
-    out = {"grid": n, "level_eb_rel": 1e-4, "isovalues": ISOVALUES, "triangles": T,
-           "chr_reconstruct_ms": t_dec, "isosurface_extract_ms": t_mc,
-           "field_GBps": 4.0 * N / ((t_dec + t_mc) * 1e-3) / 1e9,
-           "isosurface_extract_GBps": mc_bytes / (t_mc * 1e-3) / 1e9,
-           "isosurface_extract_frac_of_measured_hbm": mc_bytes / (t_mc * 1e-3) / 1e9 / peak,
-           "error_word": int(err.item())}
-    del R, tris, ws
-    return out
-
-
 def batched_cpu_baseline(n_boxes=12):
     """The oracle (single thread) on the smallest boxes of the 256-box
     workload: encode with the box's bound and k fixed, decode, marching cubes
@@ -383,10 +466,7 @@ def serve_measurement(args):
     srv.ingest(1, f)
     del f
     torch.cuda.empty_cache()
-    viz = viz_full_grid(srv.steps[1].handle, n)
-    torch.cuda.empty_cache()
     out = serve.measure(srv, (n, n, n), [0, 1], args.serve_requests)
-    out["viz_full_grid"] = viz
     out.update({"workload": "turbulence k^-5/3 %d^3 (GPU generator, seed 1024), 2 timesteps advected by (3,2,1), "
                             "levels 1e-2..1e-5 x range, requests: k~U[-1,1], level~U{0..3}, sides~U{64..512}, "
                             "seed 5" % n,
@@ -394,6 +474,60 @@ def serve_measurement(args):
                 "latency": "arrival to triangles and count ready (device event), results left on the device"})
     for ts in list(srv.steps.values()):
         ts.handle.free()
+    return out
+
+
+def fused_bytes(st, level, T):
+    """Algorithmic bytes of chr_isosurface at `level` (SURVEY's fused form):
+    every brick's record (16 B), the packed words and the exceptions (6 B
+    each) of levels 0..level, and 36 B per triangle written."""
+    nb = st["nbricks"]
+    return sum(16.0 * nb + 4.0 * st["payload_words"][l] + 6.0 * st["exceptions"][l] for l in range(level + 1)) + 36.0 * T
+
+
+def time_events(fn, reps, warm=2):
+    import torch
+
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def side_512(args):
+    """The 512^3 configuration (host-generated turbulence, seed 512): compress,
+    chr_isosurface of level 2, each timed with CUDA events."""
+    import torch
+
+    from paper_2408_05462_gb300 import chr, synth
+
+    f = torch.from_numpy(synth.turbulence(512, seed=512)).cuda()
+    r = synth.value_range(f.cpu().numpy())
+    eb = [b * r for b in REL_BOUNDS]
+    t_c = time_events(lambda: chr.chr_compress(f, eb, ISOVALUES).free(), 5)
+    h = chr.chr_compress(f, eb, ISOVALUES)
+    _, c, _ = chr.chr_isosurface(h, LEVEL, ISOVALUES, 0)
+    torch.cuda.synchronize()
+    cap = int(c.max()) + 1024
+    tris = torch.empty((len(ISOVALUES), cap, 3, 3), dtype=torch.float32, device="cuda")
+    t_i = time_events(lambda: chr.chr_isosurface(h, LEVEL, ISOVALUES, cap, tris=tris, counts=c), 10)
+    st = h.stats()
+    T = int(c.sum())
+    peak, _ = measured_peaks()
+    fb = fused_bytes(st, LEVEL, T)
+    N = 512 ** 3
+    out = {"workload": "turbulence 512^3 (host generator, seed 512), same levels and isovalues",
+           "chr_compress_ms": t_c, "chr_isosurface_ms": t_i, "field_GBps": 4.0 * N / (t_i * 1e-3) / 1e9,
+           "triangles": T, "fused_algorithmic_bytes": fb, "frac_of_measured_hbm": fb / (t_i * 1e-3) / 1e9 / peak,
+           "compressed_bytes": sum(st["level_bytes"])}
+    h.free()
+    del f, tris
     return out
 
 
@@ -418,39 +552,30 @@ def main():
     from paper_2408_05462_gb300 import chr, synth
 
     n = args.size
-    f_host = make_field(n, args.seed + rank)
-    N = f_host.size
-    r = synth.value_range(f_host)
-    eb = np.array([b * r for b in REL_BOUNDS], np.float32)
+    N = n ** 3
     stream = torch.cuda.current_stream()
-    field = torch.from_numpy(f_host).cuda()
-    recon = torch.empty_like(field)
+    f = synth.turbulence_cuda(n, seed=args.seed + rank)
+    r = float(f.max() - f.min())
+    eb = [b * r for b in REL_BOUNDS]
+    ncores, _ = host_info()
+    subs = sub_boxes(f, ncores, args.sample) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
 
-    # size the triangle buffers from one untimed pass
-    h = chr.chr_compress(field, eb, ISOVALUES)
-    h.reconstruct(2, recon)
-    _, counts, err = chr.isosurface_extract(recon, ISOVALUES, 0)
+    # the data source's side, timed on its own
+    t_comp = time_events(lambda: chr.chr_compress(f, eb, ISOVALUES).free(), 3, warm=1)
+    h = chr.chr_compress(f, eb, ISOVALUES)
+    del f
+    torch.cuda.empty_cache()
+    st = h.stats()
+    comp_bytes = sum(st["level_bytes"])
+
+    # size the triangle buffers from one untimed call
+    _, counts, err = chr.chr_isosurface(h, LEVEL, ISOVALUES, 0)
     torch.cuda.synchronize()
     cap = int(counts.max().item() * 1.02) + 1024
     tris = torch.empty((len(ISOVALUES), cap, 3, 3), dtype=torch.float32, device="cuda")
-    ws = torch.empty(chr.isosurface_workspace_size(field.shape, len(ISOVALUES)), dtype=torch.uint8, device="cuda")
-    st = h.stats()
-    comp_bytes = sum(st["level_bytes"])
-    del h
 
-    def step(ev=None, src=None):
-        if ev is not None:
-            ev[0].record(stream)
-        hh = chr.chr_compress(field if src is None else src, eb, ISOVALUES)
-        if ev is not None:
-            ev[1].record(stream)
-        hh.reconstruct(2, recon)
-        if ev is not None:
-            ev[2].record(stream)
-        chr.isosurface_extract(recon, ISOVALUES, cap, tris=tris, counts=counts, err=err, workspace=ws)
-        if ev is not None:
-            ev[3].record(stream)
-        hh.free()
+    def step():
+        chr.chr_isosurface(h, LEVEL, ISOVALUES, cap, tris=tris, counts=counts, err=err)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -459,7 +584,6 @@ def main():
     assert int(err.item()) == 0, "overflow or timeout during warm-up"
     T = sum(ntri)
 
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -467,16 +591,14 @@ def main():
     end = torch.cuda.Event(enable_timing=True)
     with Clocks(not args.no_clocks and rank == 0, local) as clk:
         start.record(stream)
-        for i in range(args.steps):
-            step(evs[i])
+        for _ in range(args.steps):
+            step()
         end.record(stream)
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     total_ms = start.elapsed_time(end)
-    t_comp = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
-    t_dec = sum(e[1].elapsed_time(e[2]) for e in evs) / args.steps
-    t_mc = sum(e[2].elapsed_time(e[3]) for e in evs) / args.steps
+
     def _max_over_ranks(v):
         t = torch.tensor([v], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -485,81 +607,95 @@ def main():
     total_ms, _ = aggregate_ranks(total_ms, world, N, _max_over_ranks if world > 1 else None)
     ms_step = total_ms / args.steps
     _, value = aggregate_ranks(ms_step, 1, world * N)
+    peak, peak_kind = measured_peaks()
+
+    # the two kernels the default form runs, each timed on its own, and the
+    # other forms of the call (same output)
+    stages = {"chr_compress": {"ms": t_comp, "algorithmic_bytes": 4.0 * N + comp_bytes}}
+    forms = {}
+    if not args.no_forms:
+        R = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+        ws = torch.empty(chr.isosurface_workspace_size(R.shape, len(ISOVALUES)), dtype=torch.uint8, device="cuda")
+        t_dec = time_events(lambda: chr.chr_reconstruct(h, LEVEL, R), 5)
+        t_mc = time_events(lambda: chr.isosurface_extract(R, ISOVALUES, cap, tris=tris, counts=counts, workspace=ws), 5)
+        dec_bytes = sum(16.0 * st["nbricks"] + 4.0 * st["payload_words"][l] + 6.0 * st["exceptions"][l]
+                        for l in range(LEVEL + 1)) + 4.0 * N
+        stages["chr_reconstruct"] = {"ms": t_dec, "algorithmic_bytes": dec_bytes}
+        stages["isosurface_extract"] = {"ms": t_mc, "algorithmic_bytes": 4.0 * N + 36.0 * T}
+        del R, ws
+        torch.cuda.empty_cache()
+        for name, flags in (("index", chr.ISO_INDEX), ("fused_kernel", chr.ISO_FUSED),
+                            ("fused_kernel_index", chr.ISO_FUSED | chr.ISO_INDEX)):
+            ms = time_events(lambda: chr.chr_isosurface(h, LEVEL, ISOVALUES, cap, tris=tris, counts=counts,
+                                                        err=err, flags=flags), 3, warm=1)
+            forms[name] = {"ms": ms, "field_GBps": 4.0 * N / (ms * 1e-3) / 1e9}
+        torch.cuda.synchronize()
+        assert int(err.item()) == 0
+    for v in stages.values():
+        v["GBps"] = v["algorithmic_bytes"] / (v["ms"] * 1e-3) / 1e9
+        v["frac_of_measured_hbm"] = v["GBps"] / peak
+
+    # the roofline of the step (one chr_isosurface call: k_decode, then
+    # k_mc_count, three scan kernels and k_mc_emit_stored) on the fused
+    # algorithmic bytes: what the method must move, levels 0..2 of the CHR
+    # read once and the mesh written once
+    fb = fused_bytes(st, LEVEL, T)
+    achieved = fb / (ms_step * 1e-3) / 1e9
+    traffic = profiled_traffic()
+    roofline = {"bound": "hbm", "kernel": "chr_isosurface (k_decode + k_mc_count + scans + k_mc_emit_stored)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": fb,
+                "traffic_note": "DRAM read+write bytes of one call from the committed ncu capture "
+                                "(profiles/chr_isosurface_turb1024.md); null when its sources changed since"}
 
     # end to end through the public API from pinned host memory: every step
-    # copies its field in and reads its triangle counts back inside the timed
-    # region.  The next step's copy runs on a copy stream into a second device
-    # buffer while the current step computes (an in-transit pipeline); the
-    # same steps with the copy in series are reported beside it.
+    # uploads the CHR's bytes (chr_deserialize: host validation, upload),
+    # runs chr_isosurface and reads the triangle counts back
     e2e = None
     if not args.no_e2e:
-        host = torch.from_numpy(f_host).pin_memory()
+        blob = torch.empty(chr.chr_serialized_size(h), dtype=torch.uint8).pin_memory()
+        blob = chr.chr_serialize(h, out=blob)
         counts_host = torch.empty(len(ISOVALUES), dtype=torch.int64).pin_memory()
-        copy_stream = torch.cuda.Stream()
-        bufs = [field, torch.empty_like(field)]
-        copied = [torch.cuda.Event() for _ in range(2)]
-        freed = [torch.cuda.Event() for _ in range(2)]
-        used = [False, False]
 
-        def e2e_steps(nsteps, after=None):
-            if after is not None:
-                copy_stream.wait_event(after)
-            for i in range(nsteps):
-                b = i & 1
-                with torch.cuda.stream(copy_stream):
-                    if used[b]:
-                        copy_stream.wait_event(freed[b])
-                    bufs[b].copy_(host, non_blocking=True)
-                    copied[b].record(copy_stream)
-                stream.wait_event(copied[b])
-                step(src=bufs[b])
-                counts_host.copy_(counts, non_blocking=True)
-                freed[b].record(stream)
-                used[b] = True
-
-        def serial_step():
-            field.copy_(host, non_blocking=True)
-            step()
+        def e2e_step(mesh_host=None):
+            h2 = chr.chr_deserialize(blob)
+            chr.chr_isosurface(h2, LEVEL, ISOVALUES, cap, tris=tris, counts=counts, err=err)
             counts_host.copy_(counts, non_blocking=True)
+            if mesh_host is not None:
+                for j, t in enumerate(ntri):
+                    mesh_host[j].copy_(tris[j, :t].reshape(-1), non_blocking=True)
+            torch.cuda.synchronize()
+            h2.free()
 
-        e2e_steps(3)
-        for _ in range(3):
-            serial_step()
-        torch.cuda.synchronize()
-        s0 = torch.cuda.Event(enable_timing=True)
-        s1 = torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        e2e_steps(args.steps, after=s0)
-        s1.record(stream)
-        torch.cuda.synchronize()
-        e2e_ms = s0.elapsed_time(s1) / args.steps
-        s0.record(stream)
-        for _ in range(args.steps):
-            serial_step()
-        s1.record(stream)
-        torch.cuda.synchronize()
-        serial_ms = s0.elapsed_time(s1) / args.steps
-        e2e = {"value": world * 4.0 * N / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": e2e_ms,
-               "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 8 * len(ISOVALUES),
-               "pipelined": "next step's host-to-device copy overlaps this step's compute (two device buffers)",
-               "serial_ms_per_step": serial_ms,
-               "serial_value": world * 4.0 * N / (serial_ms * 1e-3) / 1e9}
-
-    # error-bound translation (the alternative topology mode): min D is one
-    # pass over the field, an n-th smallest four radix passes; not in the step
-    translate = {}
-    for acc in (1.0, 0.95):
-        chr.chr_topo_translate(field, ISOVALUES, acc)
-        torch.cuda.synchronize()
+        e2e_step()
+        ke = min(args.steps, 5)
         t0 = time.perf_counter()
-        reps = 5
-        for _ in range(reps):
-            eb_t, nD = chr.chr_topo_translate(field, ISOVALUES, acc)
-        t_ms = (time.perf_counter() - t0) / reps * 1e3
-        passes = 1 if acc >= 1.0 else 4
-        translate[f"accuracy_{acc}"] = {"ms": t_ms, "eb": eb_t, "D": nD, "passes": passes,
-                                        "field_GBps": passes * 4.0 * N / (t_ms * 1e-3) / 1e9}
+        for _ in range(ke):
+            e2e_step()
+        e2e_ms = (time.perf_counter() - t0) / ke * 1e3
+        e2e = {"value": world * 4.0 * N / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": e2e_ms,
+               "h2d_bytes_per_step": int(blob.numel()), "d2h_bytes_per_step": 8 * len(ISOVALUES),
+               "steps": ke, "clock": "host wall clock (chr_deserialize synchronizes)",
+               "mesh": "consumed on the device"}
+        try:
+            mesh_host = [torch.empty(9 * t, dtype=torch.float32).pin_memory() for t in ntri]
+            e2e_step(mesh_host)
+            t0 = time.perf_counter()
+            for _ in range(2):
+                e2e_step(mesh_host)
+            m_ms = (time.perf_counter() - t0) / 2 * 1e3
+            e2e["mesh_d2h"] = {"value": world * 4.0 * N / (m_ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": m_ms,
+                               "d2h_bytes_per_step": 36 * T + 8 * len(ISOVALUES), "steps": 2}
+            del mesh_host
+        except RuntimeError as ex:
+            e2e["mesh_d2h"] = {"unavailable": str(ex).splitlines()[0][:200]}
+        del blob
 
+    del tris
+    h.free()
+    torch.cuda.empty_cache()
+
+    side = None if args.no_side or world > 1 else side_512(args)
     adjoint = None if args.no_adjoint or world > 1 else adjoint_timing()
     if adjoint is not None and not args.no_cpu_baseline:
         adjoint["cpu_baseline"] = adjoint_cpu_baseline()
@@ -568,37 +704,14 @@ def main():
         from paper_2408_05462_gb300 import batched
 
         batch = batched.measure(256, 256, reps=20)
-        peak, peak_kind = measured_peaks()
         batch["roofline"] = {"bound": "hbm", "achieved": batch["batched_algorithmic_GBps"], "peak": peak,
                              "unit": "GB/s", "frac": batch["batched_algorithmic_GBps"] / peak, "peak_kind": peak_kind}
         if not args.no_cpu_baseline:
             batch["cpu_baseline"] = batched_cpu_baseline()
     serving = None if args.no_serve or world > 1 else serve_measurement(args)
 
-    peak, peak_kind = measured_peaks()
-    mc_bytes = 4.0 * N + 36.0 * T
-    dec_bytes = comp_bytes + 4.0 * N
-    stages = {
-        "chr_compress": {"ms": t_comp, "algorithmic_bytes": 4.0 * N + comp_bytes},
-        "chr_reconstruct": {"ms": t_dec, "algorithmic_bytes": dec_bytes},
-        "isosurface_extract": {"ms": t_mc, "algorithmic_bytes": mc_bytes},
-    }
-    for v in stages.values():
-        v["GBps"] = v["algorithmic_bytes"] / (v["ms"] * 1e-3) / 1e9
-        v["frac_of_measured_hbm"] = v["GBps"] / peak
-    # the dominant stage: isosurface_extract (one k_mc_fused launch for the 4
-    # isovalues, after a clear of its tile status words; timed by the events
-    # around the call); algorithmic bytes =
-    # the field read once + 36 B per triangle written
-    dom = "isosurface_extract"
-    achieved = stages[dom]["GBps"]
-    ratio = profiled_traffic_ratio()
-    roofline = {"bound": "hbm", "kernel": "isosurface_extract (k_mc_fused)",
-                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": (ratio * mc_bytes) if ratio else None, "peak_kind": peak_kind,
-                "algorithmic_bytes_per_launch": mc_bytes,
-                "traffic_note": "DRAM bytes of the call from the committed 384^3 ncu capture, scaled by "
-                                "algorithmic bytes; null when mc.cu changed since"}
+    ntiles = ((n - 1 + 31) // 32) * ((n - 1 + 7) // 8) ** 2
+    per_step = 1 + (5 if ntiles >= 2048 * 64 else 1)  # decoder, then count + 3 scans + emit, or the single pass
     out = {
         "metric": "field GB/s (decode+fix+marching cubes), % HBM roofline; serve p50/p99 ms",
         "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -606,17 +719,15 @@ def main():
         "data": "synthetic",
         "config": workload_config(n, args, {"parallelism": "replicas" if world > 1 else "single"}),
         "roofline": roofline,
-        "viz_side": {"field_GBps": 4.0 * N / ((t_dec + t_mc) * 1e-3) / 1e9, "ms": t_dec + t_mc,
-                     "tris_per_s": T / ((t_dec + t_mc) * 1e-3)},
-        "stages": stages,
+        "tris_per_s": T / (ms_step * 1e-3),
+        "stages": stages, "forms": forms,
         "triangles": ntri, "compressed_bytes": comp_bytes, "compression_ratio": 4.0 * N / comp_bytes,
         "exceptions": st["exceptions"],
-        "translate": translate,
-        # per step: encode (a second launch for partial bricks when a side is not a multiple of 8),
-        # 3 record scans, compact, decode, one single-pass marching-cubes launch for the 4 isovalues
-        "gpu_launches": (7 + (1 if args.size % 8 else 0)) * args.steps,
+        "gpu_launches": per_step * args.steps,
         "e2e": e2e,
     }
+    if side is not None:
+        out["turb512"] = side
     if adjoint is not None:
         out["adjoint"] = adjoint
     if batch is not None:
@@ -627,8 +738,8 @@ def main():
         clk_s = clk.summary()
         if clk_s:
             out["clocks"] = clk_s
-        if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(f_host, args)
+        if subs is not None:
+            out["cpu_baseline"] = cpu_baseline(subs, np.array(eb, np.float32))
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()

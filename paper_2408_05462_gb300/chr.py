@@ -523,17 +523,39 @@ def isosurface_distance_loss(orig_field: torch.Tensor, isovalue: float, points: 
     return loss, grad
 
 
-def chr_serialize(h: Chr, stream=None) -> bytes:
+def chr_serialize(h: Chr, stream=None, out: torch.Tensor | None = None):
+    """The CHR as bytes (chr.h: chr_serialize); with `out` (a CPU uint8
+    tensor, e.g. pinned, of at least the size) the bytes go there and the
+    used view of it is returned."""
     need = c_size_t()
     _check(lib().chr_serialize(h.ptr, None, 0, ctypes.byref(need), _stream(stream)))
+    if out is not None:
+        if out.dtype != torch.uint8 or out.is_cuda or not out.is_contiguous() or out.numel() < need.value:
+            raise ValueError("out must be a contiguous CPU uint8 tensor of at least %d bytes" % need.value)
+        _check(lib().chr_serialize(h.ptr, out.data_ptr(), need.value, ctypes.byref(need), _stream(stream)))
+        return out[:need.value]
     buf = ctypes.create_string_buffer(need.value)
     _check(lib().chr_serialize(h.ptr, buf, need.value, ctypes.byref(need), _stream(stream)))
     return buf.raw
 
 
-def chr_deserialize(data: bytes, stream=None) -> Chr:
+def chr_serialized_size(h: Chr) -> int:
+    need = c_size_t()
+    _check(lib().chr_serialize(h.ptr, None, 0, ctypes.byref(need), None))
+    return int(need.value)
+
+
+def chr_deserialize(data, stream=None) -> Chr:
+    """A handle from chr_serialize's bytes (chr.h: chr_deserialize): `data`
+    is a bytes object or a CPU uint8 tensor (pinned memory uploads fastest)."""
     out = c_void_p()
-    _check(lib().chr_deserialize(data, len(data), ctypes.byref(TORCH_ALLOCATOR), _stream(stream), ctypes.byref(out)))
+    if isinstance(data, torch.Tensor):
+        if data.dtype != torch.uint8 or data.is_cuda or not data.is_contiguous():
+            raise ValueError("data must be a contiguous CPU uint8 tensor")
+        ptr, n = c_void_p(data.data_ptr()), data.numel()
+    else:
+        ptr, n = data, len(data)
+    _check(lib().chr_deserialize(ptr, n, ctypes.byref(TORCH_ALLOCATOR), _stream(stream), ctypes.byref(out)))
     h = Chr(out.value, (1, 1, 1))
     st = chr_stats(h)
     h.shape = (st["dims"][2], st["dims"][1], st["dims"][0])

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -275,6 +276,86 @@ struct Writer {
 size_t header_bytes(uint32_t nlevels, uint32_t n_iso)
 {
     return 4 + 4 + 24 + 16 + 8 + 8 + 4 * (size_t)nlevels + 4 * (size_t)n_iso + 16 * (size_t)nlevels;
+}
+
+// One level's records and exception slots of a byte string, checked on the
+// host: widths <= 32, modes 0/1, <= 512 exceptions per brick, every record's
+// prefix sums (wsum, exc_off) equal to the sums over the bricks before it,
+// exception slots ascending inside each brick and on the grid.  The bricks
+// are split into chunks checked by several threads: a first sweep sums each
+// chunk's widths and exception counts, the prefix over chunks gives every
+// chunk its starting sums, a second sweep checks the records against them.
+// wsum, esum: the level's totals.
+bool validate_level(const uint32_t *rec, const uint16_t *eidx, const Grid &g, uint64_t nexc, uint64_t &wsum,
+                    uint64_t &esum)
+{
+    const int64_t nb = g.nbricks;
+    unsigned hw = std::thread::hardware_concurrency();
+    const int64_t nchunks = std::max<int64_t>(1, std::min<int64_t>(hw ? hw : 1, std::min<int64_t>(64, nb / 4096)));
+    const int64_t per = (nb + nchunks - 1) / nchunks;
+    std::vector<uint64_t> cw(nchunks, 0), ce(nchunks, 0);
+    std::vector<char> good(nchunks, 1);
+    auto sweep = [&](int64_t c, bool check) {
+        const int64_t b0 = c * per, b1 = std::min(nb, b0 + per);
+        uint64_t w_run = check ? cw[c] : 0, e_run = check ? ce[c] : 0;
+        for (int64_t b = b0; b < b1; b++) {
+            uint32_t r[4];
+            memcpy(r, rec + 4 * b, 16);
+            const uint32_t w = r[3] & 0xffu, mode = (r[3] >> 8) & 0xffu, ne = r[3] >> 16;
+            if (w > 32 || mode > 1 || ne > 512) {
+                good[c] = 0;
+                return;
+            }
+            if (check) {
+                if (r[0] != w_run || r[1] != e_run || e_run + ne > nexc) {
+                    good[c] = 0;
+                    return;
+                }
+                const int64_t bx = b % g.nbx, by = (b / g.nbx) % g.nby, bz = b / (g.nbx * g.nby);
+                int prev = -1;
+                for (uint32_t j = 0; j < ne; j++) {
+                    uint16_t sl;
+                    memcpy(&sl, eidx + e_run + j, 2);
+                    const int64_t x = bx * 8 + (sl & 7), y = by * 8 + ((sl >> 3) & 7), z = bz * 8 + (sl >> 6);
+                    if (sl >= 512 || (int)sl <= prev || x >= g.nx || y >= g.ny || z >= g.nz) {
+                        good[c] = 0;
+                        return;
+                    }
+                    prev = sl;
+                }
+            }
+            w_run += w;
+            e_run += ne;
+        }
+        if (!check) {
+            cw[c] = w_run;
+            ce[c] = e_run;
+        }
+    };
+    auto run = [&](bool check) {
+        std::vector<std::thread> th;
+        for (int64_t c = 1; c < nchunks; c++) th.emplace_back(sweep, c, check);
+        sweep(0, check);
+        for (auto &t : th) t.join();
+    };
+    run(false);
+    for (int64_t c = 0; c < nchunks; c++)
+        if (!good[c]) return false;
+    uint64_t W = 0, E = 0;
+    for (int64_t c = 0; c < nchunks; c++) {  // exclusive prefix: each chunk's starting sums
+        const uint64_t w = cw[c], e = ce[c];
+        cw[c] = W;
+        ce[c] = E;
+        W += w;
+        E += e;
+    }
+    if (E > nexc) return false;
+    run(true);
+    for (int64_t c = 0; c < nchunks; c++)
+        if (!good[c]) return false;
+    wsum = W;
+    esum = E;
+    return true;
 }
 
 size_t level_bytes(const chr_handle *h, uint32_t l)
@@ -954,33 +1035,7 @@ chr_status chr_deserialize(const void *host_buf, size_t n, const chr_allocator *
         const uint32_t *rec = reinterpret_cast<const uint32_t *>(src + off);
         const uint16_t *eidx = reinterpret_cast<const uint16_t *>(src + off + nr + h->nwords[l] * 4);
         uint64_t wsum = 0, esum = 0;
-        for (int64_t b = 0; b < g.nbricks && ok; b++) {
-            uint32_t r[4];
-            memcpy(r, rec + 4 * b, 16);
-            const uint32_t w = r[3] & 0xffu, mode = (r[3] >> 8) & 0xffu, ne = r[3] >> 16;
-            if (w > 32 || mode > 1 || ne > 512 || r[0] != wsum || r[1] != esum) {
-                ok = false;
-                break;
-            }
-            const int64_t bx = b % g.nbx, by = (b / g.nbx) % g.nby, bz = b / (g.nbx * g.nby);
-            int prev = -1;
-            for (uint32_t j = 0; j < ne; j++) {
-                if (esum + j >= h->nexc[l]) {
-                    ok = false;
-                    break;
-                }
-                uint16_t sl;
-                memcpy(&sl, eidx + esum + j, 2);
-                const int64_t x = bx * 8 + (sl & 7), y = by * 8 + ((sl >> 3) & 7), z = bz * 8 + (sl >> 6);
-                if (sl >= 512 || (int)sl <= prev || x >= g.nx || y >= g.ny || z >= g.nz) {
-                    ok = false;
-                    break;
-                }
-                prev = sl;
-            }
-            wsum += w;
-            esum += ne;
-        }
+        ok = validate_level(rec, eidx, g, h->nexc[l], wsum, esum);
         if (!ok || 16 * wsum != h->nwords[l] || esum != h->nexc[l]) {
             delete h;
             return fail(CHR_ERR_CORRUPT, "chr_deserialize: records inconsistent (widths, prefix sums or exception slots)");

@@ -1,6 +1,7 @@
 """CPU checks of bench.py's host logic: the reference (oracle) arm's JSON
-line, and the whole-job aggregation across ranks (max of the ranks' times,
-sum of their work) run as two gloo processes."""
+line (one oracle process per host core), and the whole-job aggregation
+across ranks (max of the ranks' times, sum of their work) run as two gloo
+processes."""
 import json
 import os
 import socket
@@ -23,7 +24,9 @@ def test_reference_arm_prints_one_json_line():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["unit"] == "GB/s" and d["value"] > 0
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    cores = len(os.sched_getaffinity(0))
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == cores
+    assert d["cpu_baseline"]["nproc"] == cores and d["cpu_baseline"]["cpu_model"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
 
 
