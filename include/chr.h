@@ -88,6 +88,12 @@ typedef struct chr_params {
                                /* element of rank floor((1-accuracy)*|D|)                     */
     uint32_t flags;            /* reserved, must be 0                                         */
 } chr_params;
+/* Where chr_params departs from a block-structured compressor's options:
+ * there is no block size (the paper's 64^3/128^3 domain blocks of Sec. 2.1
+ * are the caller's boxes, each compressed on its own; the format's unit is
+ * the 8^3 brick, with a value index per brick, chr_brick_index), and flags
+ * bit 0 (the paper's differentiated error control per block) is not
+ * implemented: every vertex keeps every level's bound. */
 
 typedef struct chr_handle chr_handle; /* opaque; owns device buffers */
 
@@ -245,10 +251,7 @@ size_t isosurface_workspace_min_size(chr_dims dims, uint32_t n_iso);
  * offset from the counts the tiles before it publish (bounded waits; a wait
  * that gives up sets CHR_ERR_TIMEOUT).  Larger grids with the full
  * workspace take a counting pass, a scan of the tile counts and an
- * emitting pass.  Same output either way.  Asynchronous.  (Tests only: the
- * environment variable CHR_TEST_UNPUBLISHED_TILE=<tile>, read at every
- * call, keeps that tile of the single pass from publishing, so the tiles
- * after it time out; leave it unset.)
+ * emitting pass.  Same output either way.  Asynchronous.
  */
 chr_status isosurface_extract(const float *d_field, chr_dims dims, const float *isovalues, uint32_t n_iso,
                               float *d_tris, uint64_t cap_tris, uint64_t *d_ntris, uint32_t *d_err, void *d_workspace,
@@ -360,8 +363,10 @@ chr_status isosurface_distance_loss(const float *d_orig_field, chr_dims dims, fl
  * exits.  Grids needing more scratch than that (more than about 87,000 tiles
  * of 32x8x8 cells, i.e. roughly 178 million cells; a 512^3 grid fits) are
  * rejected with CHR_ERR_INVALID before any work is enqueued.
- * The first call on each device looks up the array's device address with
- * that device current; make that first call before any stream capture.
+ * Every call looks up the array's device address on the current device
+ * (so a device reset needs nothing more), and runs the single pass on the
+ * minimum workspace (isosurface_workspace_min_size).  Make the first call
+ * on a device before any stream capture.
  * All calls share the one array, so calls whose work overlaps on a GPU race
  * on it and must be serialised by the caller.  No call clears it: every
  * scratch value is written before it is read.  Asynchronous.
@@ -491,6 +496,37 @@ int chr_checked_build(void);
  * device.  CHR_ERR_INVALID if h_word is NULL.
  */
 chr_status chr_debug_bounds_word(uint32_t *h_word, int reset);
+
+/*
+ * chr_debug_unpublished_tile — in a checked build, make tile `tile` of every
+ * later single-pass extraction publish nothing (-1: none), so that the
+ * tiles after it give up their bounded wait and the call reports
+ * CHR_ERR_TIMEOUT: the test of a wait that runs out, without a fault.
+ * CHR_ERR_INVALID in normal builds, which have no such hook.
+ */
+chr_status chr_debug_unpublished_tile(int64_t tile);
+
+/*
+ * chr_debug_tri_cells — in a checked build, make every later marching-cubes
+ * extraction (isosurface_extract, chr_isosurface, ..._noalloc) also write
+ * each triangle's cell, x + (nx-1)*(y + (ny-1)*z), to d_cells (device,
+ * uint32, cap_tris per isovalue, isovalue j from d_cells + j*cap_tris, in
+ * the triangle order): the active cells in output order, each repeated for
+ * its triangles.  NULL stops it.  Test output; CHR_ERR_INVALID in normal
+ * builds.
+ */
+chr_status chr_debug_tri_cells(uint32_t *d_cells);
+
+/*
+ * chr_debug_cases — in a checked build, the marching-cubes case byte of
+ * every cell of d_field at `isovalue` as the extraction's counting pass
+ * computes it: d_cases (device, (nx-1)(ny-1)(nz-1) bytes, cell order as
+ * above) with corner (ox, oy, oz) at bit ox + 2 oy + 4 oz, set when v < k.
+ * d_workspace: isosurface_workspace_size(dims, 1) bytes.  Test output;
+ * CHR_ERR_INVALID in normal builds.  Asynchronous.
+ */
+chr_status chr_debug_cases(const float *d_field, chr_dims dims, float isovalue, uint8_t *d_cases, void *d_workspace,
+                           size_t workspace_bytes, void *stream);
 
 /* chr_last_error — message for the last failing call on this thread. */
 const char *chr_last_error(void);

@@ -149,6 +149,12 @@ def lib():
         L.chr_checked_build.restype = c_int
         L.chr_debug_bounds_word.restype = st
         L.chr_debug_bounds_word.argtypes = [POINTER(c_uint32), c_int]
+        L.chr_debug_unpublished_tile.restype = st
+        L.chr_debug_unpublished_tile.argtypes = [c_int64]
+        L.chr_debug_tri_cells.restype = st
+        L.chr_debug_tri_cells.argtypes = [c_void_p]
+        L.chr_debug_cases.restype = st
+        L.chr_debug_cases.argtypes = [c_void_p, ChrDims, c_float, c_void_p, c_void_p, c_size_t, c_void_p]
         L.chr_batch_create.restype = st
         L.chr_batch_create.argtypes = [POINTER(ChrBatchItem), c_uint32, c_void_p, c_uint64, c_void_p, c_void_p,
                                        POINTER(ChrAllocator), c_void_p, POINTER(c_void_p)]
@@ -274,6 +280,32 @@ def chr_compress(field: torch.Tensor, error_bounds, isovalues=(), topo: str = "f
     _check(lib().chr_compress(field.data_ptr(), _dims(field), ctypes.byref(prm), alloc, _stream(stream),
                               ctypes.byref(out)))
     return Chr(out.value, field.shape)
+
+
+def chr_debug_unpublished_tile(tile: int) -> None:
+    """Checked builds only: tile `tile` of later single-pass extractions
+    publishes nothing (-1: none); see chr.h."""
+    _check(lib().chr_debug_unpublished_tile(int(tile)))
+
+
+def chr_debug_tri_cells(cells: torch.Tensor | None) -> None:
+    """Checked builds only: later extractions also write each triangle's
+    cell index into `cells` (int32 CUDA tensor laid out like the triangles,
+    [n_iso, cap]); None stops it (chr.h: chr_debug_tri_cells)."""
+    _check(lib().chr_debug_tri_cells(cells.data_ptr() if cells is not None else None))
+
+
+def chr_debug_cases(field: torch.Tensor, isovalue: float, stream=None) -> torch.Tensor:
+    """Checked builds only: the counting pass's case byte of every cell,
+    [nz-1, ny-1, nx-1] uint8, corner (ox, oy, oz) at bit ox + 2 oy + 4 oz
+    (chr.h: chr_debug_cases)."""
+    _check_field(field)
+    nz, ny, nx = field.shape
+    out = torch.empty((nz - 1, ny - 1, nx - 1), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(isosurface_workspace_size(field.shape, 1), dtype=torch.uint8, device="cuda")
+    _check(lib().chr_debug_cases(field.data_ptr(), _dims(field), float(isovalue), out.data_ptr(), ws.data_ptr(),
+                                 ws.numel(), _stream(stream)))
+    return out
 
 
 def chr_checked_build() -> bool:

@@ -11,6 +11,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 
 namespace chr {
@@ -31,6 +33,13 @@ chr_status cuda_fail(cudaError_t e, const char *where)
 }
 
 namespace {
+
+// An NVTX range around each C-ABI call (visible in Nsight timelines; no
+// cost without a tool attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 #define CHR_CUDA(call, where)                         \
     do {                                              \
@@ -415,6 +424,37 @@ chr_status chr_debug_bounds_word(uint32_t *h_word, int reset)
     return CHR_OK;
 }
 
+chr_status chr_debug_tri_cells(uint32_t *d_cells)
+{
+    if (reinterpret_cast<uintptr_t>(d_cells) & 3u) return fail(CHR_ERR_INVALID, "chr_debug_tri_cells: misaligned output");
+    if (!mc_debug_set_tri_cells(d_cells))
+        return fail(CHR_ERR_INVALID, "chr_debug_tri_cells: only the checked build has this test output");
+    return CHR_OK;
+}
+
+chr_status chr_debug_cases(const float *d_field, chr_dims dims, float isovalue, uint8_t *d_cases, void *d_workspace,
+                           size_t workspace_bytes, void *stream)
+{
+    std::string why;
+    if (!d_field || !d_cases || !d_workspace) return fail(CHR_ERR_INVALID, "chr_debug_cases: NULL pointer");
+    if (!dims_ok(dims, why)) return fail(CHR_ERR_INVALID, "chr_debug_cases: " + why);
+    if (!isfinite(isovalue)) return fail(CHR_ERR_INVALID, "chr_debug_cases: isovalue must be finite");
+    cudaError_t e = cudaSuccess;
+    if (!mc_debug_cases(d_field, make_grid(dims), isovalue, d_cases, d_workspace, workspace_bytes,
+                        (cudaStream_t)stream, e))
+        return fail(CHR_ERR_INVALID, "chr_debug_cases: only the checked build has this test output");
+    if (e == cudaErrorInvalidValue) return fail(CHR_ERR_INVALID, "chr_debug_cases: workspace smaller than isosurface_workspace_size(dims, 1)");
+    if (e != cudaSuccess) return cuda_fail(e, "chr_debug_cases");
+    return CHR_OK;
+}
+
+chr_status chr_debug_unpublished_tile(int64_t tile)
+{
+    if (!mc_set_unpublished_tile(tile))
+        return fail(CHR_ERR_INVALID, "chr_debug_unpublished_tile: only the checked build has this test hook");
+    return CHR_OK;
+}
+
 chr_status chr_pool_trim(size_t keep_bytes)
 {
     cudaMemPool_t mp = library_pool();
@@ -429,6 +469,7 @@ const char *chr_last_error(void) { return g_last_error.c_str(); }
 chr_status chr_compress(const float *d_field, chr_dims dims, const chr_params *prm, const chr_allocator *alloc,
                         void *stream, chr_handle **out)
 {
+    NvtxRange nvtx_("chr_compress");
     std::string why;
     if (!out) return fail(CHR_ERR_INVALID, "chr_compress: out is NULL");
     *out = nullptr;
@@ -549,6 +590,7 @@ chr_status chr_compress(const float *d_field, chr_dims dims, const chr_params *p
 
 chr_status chr_reconstruct(const chr_handle *h, uint32_t level, float *d_out, void *stream)
 {
+    NvtxRange nvtx_("chr_reconstruct");
     if (!h || !d_out) return fail(CHR_ERR_INVALID, "chr_reconstruct: NULL handle or output");
     if (level >= h->nlevels) return fail(CHR_ERR_INVALID, "chr_reconstruct: level out of range");
     if (reinterpret_cast<uintptr_t>(d_out) & 3u) return fail(CHR_ERR_INVALID, "chr_reconstruct: misaligned output");
@@ -564,6 +606,7 @@ chr_status chr_reconstruct(const chr_handle *h, uint32_t level, float *d_out, vo
 
 chr_status chr_brick_range(const chr_handle *h, uint32_t level, float *d_range, void *stream)
 {
+    NvtxRange nvtx_("chr_brick_range");
     if (!h || !d_range) return fail(CHR_ERR_INVALID, "chr_brick_range: NULL handle or output");
     if (level >= h->nlevels) return fail(CHR_ERR_INVALID, "chr_brick_range: level out of range");
     if (reinterpret_cast<uintptr_t>(d_range) & 7u) return fail(CHR_ERR_INVALID, "chr_brick_range: misaligned output");
@@ -581,6 +624,7 @@ chr_status chr_brick_range(const chr_handle *h, uint32_t level, float *d_range, 
 chr_status chr_reconstruct_box(const chr_handle *h, uint32_t level, int64_t x0, int64_t y0, int64_t z0, chr_dims box,
                                float *d_out, void *stream)
 {
+    NvtxRange nvtx_("chr_reconstruct_box");
     if (!h || !d_out) return fail(CHR_ERR_INVALID, "chr_reconstruct_box: NULL handle or output");
     if (level >= h->nlevels) return fail(CHR_ERR_INVALID, "chr_reconstruct_box: level out of range");
     if (reinterpret_cast<uintptr_t>(d_out) & 3u) return fail(CHR_ERR_INVALID, "chr_reconstruct_box: misaligned output");
@@ -666,6 +710,7 @@ chr_status chr_serve_request(const chr_handle *h, uint32_t level, int64_t x0, in
                              float isovalue, void *d_mem, size_t mem_bytes, uint64_t cap_tris, uint64_t *h_result,
                              void *stream)
 {
+    NvtxRange nvtx_("chr_serve_request");
     std::string why;
     if (!h || !d_mem || !h_result) return fail(CHR_ERR_INVALID, "chr_serve_request: NULL handle, memory or result");
     if (level >= h->nlevels) return fail(CHR_ERR_INVALID, "chr_serve_request: level out of range");
@@ -702,6 +747,7 @@ chr_status chr_topo_translate(const float *d_field, chr_dims dims, const float *
                               float accuracy, const chr_allocator *alloc, void *stream, float *eb_out,
                               uint64_t *count_out)
 {
+    NvtxRange nvtx_("chr_topo_translate");
     std::string why;
     if (!d_field || !eb_out) return fail(CHR_ERR_INVALID, "chr_topo_translate: NULL field or output");
     if (reinterpret_cast<uintptr_t>(d_field) & 3u) return fail(CHR_ERR_INVALID, "chr_topo_translate: misaligned field");
@@ -733,6 +779,7 @@ chr_status isosurface_extract(const float *d_field, chr_dims dims, const float *
                               float *d_tris, uint64_t cap_tris, uint64_t *d_ntris, uint32_t *d_err, void *d_workspace,
                               size_t workspace_bytes, void *stream)
 {
+    NvtxRange nvtx_("isosurface_extract");
     std::string why;
     if (!d_field || !d_ntris || !isovalues) return fail(CHR_ERR_INVALID, "isosurface_extract: NULL field, counts or isovalues");
     if (!dims_ok(dims, why)) return fail(CHR_ERR_INVALID, "isosurface_extract: " + why);
@@ -761,6 +808,7 @@ chr_status chr_isosurface(const chr_handle *h, uint32_t level, const float *isov
                           float *d_field_out, float *d_tris, uint64_t cap_tris, uint64_t *d_ntris, uint32_t *d_err,
                           uint32_t flags, const chr_allocator *alloc, void *stream)
 {
+    NvtxRange nvtx_("chr_isosurface");
     if (!h || !d_ntris || !isovalues) return fail(CHR_ERR_INVALID, "chr_isosurface: NULL handle, counts or isovalues");
     if (level >= h->nlevels) return fail(CHR_ERR_INVALID, "chr_isosurface: level out of range");
     if (n_iso < 1 || n_iso > CHR_MAX_ISO) return fail(CHR_ERR_INVALID, "chr_isosurface: n_iso must be 1..16");
@@ -837,6 +885,7 @@ chr_status chr_isosurface(const chr_handle *h, uint32_t level, const float *isov
 
 chr_status chr_brick_index(const chr_handle *h, uint32_t level, float *d_out, void *stream)
 {
+    NvtxRange nvtx_("chr_brick_index");
     if (!h || !d_out) return fail(CHR_ERR_INVALID, "chr_brick_index: NULL handle or output");
     if (level >= h->nlevels) return fail(CHR_ERR_INVALID, "chr_brick_index: level out of range");
     if (!h->has_index) return fail(CHR_ERR_INVALID, "chr_brick_index: the handle has no value index (a version-1 byte string)");
@@ -858,6 +907,7 @@ chr_status isosurface_backward(const float *d_field, chr_dims dims, const float 
                                const float *d_grad_tris, uint64_t cap_tris, float *d_grad_field, void *d_workspace,
                                size_t workspace_bytes, void *stream)
 {
+    NvtxRange nvtx_("isosurface_backward");
     std::string why;
     if (!d_field || !isovalues || !d_grad_field) return fail(CHR_ERR_INVALID, "isosurface_backward: NULL argument");
     if (!dims_ok(dims, why)) return fail(CHR_ERR_INVALID, "isosurface_backward: " + why);
@@ -884,6 +934,7 @@ chr_status isosurface_distance_loss(const float *d_orig_field, chr_dims dims, fl
                                     uint64_t npts, double *d_loss, float *d_grad_points, void *d_workspace,
                                     size_t workspace_bytes, void *stream)
 {
+    NvtxRange nvtx_("isosurface_distance_loss");
     std::string why;
     if (!d_orig_field || !d_loss || (npts > 0 && !d_points))
         return fail(CHR_ERR_INVALID, "isosurface_distance_loss: NULL argument");
@@ -924,6 +975,7 @@ chr_status chr_stats(const chr_handle *h, chr_stats_t *out)
 
 chr_status chr_serialize(const chr_handle *h, void *host_buf, size_t cap, size_t *need, void *stream)
 {
+    NvtxRange nvtx_("chr_serialize");
     if (!h || !need) return fail(CHR_ERR_INVALID, "chr_serialize: NULL handle or size");
     size_t total = header_bytes(h->nlevels, h->n_iso);
     for (uint32_t l = 0; l < h->nlevels; l++) total += level_bytes(h, l);
@@ -979,6 +1031,7 @@ chr_status chr_serialize(const chr_handle *h, void *host_buf, size_t cap, size_t
 
 chr_status chr_deserialize(const void *host_buf, size_t n, const chr_allocator *alloc, void *stream, chr_handle **out)
 {
+    NvtxRange nvtx_("chr_deserialize");
     if (!out) return fail(CHR_ERR_INVALID, "chr_deserialize: out is NULL");
     *out = nullptr;
     if (!host_buf) return fail(CHR_ERR_INVALID, "chr_deserialize: NULL buffer");

@@ -23,6 +23,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 
 using namespace chr;
@@ -249,7 +251,17 @@ chr_status chr_batch_create(const chr_batch_item *items, uint32_t n, float *d_tr
     return CHR_OK;
 }
 
+static chr_status batch_run(chr_batch *b, void *stream);
+
 chr_status chr_batch_run(chr_batch *b, void *stream)
+{
+    nvtxRangePushA("chr_batch_run");
+    const chr_status st = batch_run(b, stream);
+    nvtxRangePop();
+    return st;
+}
+
+static chr_status batch_run(chr_batch *b, void *stream)
 {
     if (!b) return fail(CHR_ERR_INVALID, "chr_batch_run: NULL batch");
     cudaStream_t s = (cudaStream_t)stream;

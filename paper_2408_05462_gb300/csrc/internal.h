@@ -95,6 +95,17 @@ cudaError_t launch_scan_records(uint4 *const *recs, int nlevels, int64_t nbricks
 // Checked builds: the bounds word of the marching-cubes and the codec kernels
 // (non-zero once an index failed its test); 0 in normal builds.  Synchronises.
 uint32_t mc_bounds_word(bool reset);
+// Checked builds: the single pass's unpublished test tile (-1: none); false
+// in normal builds.
+bool mc_set_unpublished_tile(int64_t tile);
+// Checked builds, test only: every later extraction writes each triangle's
+// cell index to cells (NULL: stop); false in normal builds.
+bool mc_debug_set_tri_cells(uint32_t *cells);
+// Checked builds, test only: the count pass's case bytes of one isovalue,
+// per cell in grid order with corner (ox, oy, oz) at bit ox + 2 oy + 4 oz;
+// false in normal builds.  err: the launch status.
+bool mc_debug_cases(const float *field, const Grid &g, float isovalue, uint8_t *out, void *workspace,
+                    size_t workspace_bytes, cudaStream_t s, cudaError_t &err);
 uint32_t codec_bounds_word(bool reset);
 
 // Marching cubes over a plain field, per group of up to 4 isovalues one

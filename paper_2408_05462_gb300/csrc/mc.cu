@@ -30,7 +30,6 @@
 // x-fastest, triangles of a cell in table order.  A tile is 4 bricks along
 // x; thread t owns brick t>>6 of the tile and the 8 cells of row
 // (y, z) = (t&7, (t>>3)&7), so thread order is output order.
-#include <stdlib.h>
 #include <string.h>
 
 #include <atomic>
@@ -119,6 +118,10 @@ struct McParams {
     // straddle an isovalue slot is not classified for it (tile_activity)
     const float2 *index;
     int32_t ibx, iby;
+    // checked builds, test only: where each emitted triangle's cell index
+    // (x + (nx-1)*(y + (ny-1)*z)) goes, per isovalue slot, in output order
+    // (NULL: nowhere; chr_debug_tri_cells)
+    uint32_t *dbg_cells[kMcIsoPerPass];
 };
 
 struct TileXYZ {
@@ -1152,6 +1155,11 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
                                               tri, k, fx0 + small_to_float(lx), fy0 + small_to_float(cly),
                                               fz0 + small_to_float(clz));
                     }
+#ifdef CHR_CHECKED
+                    if (p.dbg_cells[i])
+                        p.dbg_cells[i][g0 + base + lane] =
+                            (uint32_t)((o.x0 + lx) + (p.nx - 1) * ((o.y0 + cly) + (p.ny - 1) * (o.z0 + clz)));
+#endif
                 }
                 fence_proxy_async_smem();
                 __syncwarp();
@@ -1622,6 +1630,48 @@ __global__ void k_box_starts(const uint64_t *off, const int64_t *tile_start, int
 
 }  // namespace
 
+// Test only (checked builds): the triangle-cell output of chr_debug_tri_cells.
+static uint32_t *g_dbg_cells = nullptr;
+
+#ifdef CHR_CHECKED
+namespace {
+// The count pass's stored case bytes of isovalue slot 0 (per tile and
+// thread, 8 cells of a brick row, corner (ox, oy, oz) at bit 4 ox + oy +
+// 2 oz) rewritten per cell in the grid's cell order with corner (ox, oy, oz)
+// at bit ox + 2 oy + 4 oz.  One thread per (tile, thread of the tile).
+__global__ void k_debug_cases(const uint2 *cases, int32_t cstride, int64_t ntiles, int32_t ntx, int32_t ncby,
+                              int64_t nx, int64_t ny, int64_t nz, uint8_t *out)
+{
+    const int64_t u = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (u >= ntiles * 256) return;
+    const int64_t tile = u >> 8;
+    const int t = (int)(u & 255);
+    const int64_t tq = tile / ntx, tz = tq / ncby;
+    const int64_t x0 = (tile - tq * ntx) * kTX + 8 * (t >> 6), y = (tq - tz * ncby) * 8 + (t & 7),
+                  z = tz * 8 + ((t >> 3) & 7);
+    if (y >= ny - 1 || z >= nz - 1) return;
+    const uint2 cw = cases[(tile * cstride) * 256 + t];
+    for (int x = 0; x < 8; x++) {
+        if (x0 + x >= nx - 1) break;
+        const uint32_t cb = ((x < 4 ? cw.x : cw.y) >> (8 * (x & 3))) & 0xffu;
+        out[(x0 + x) + (nx - 1) * (y + (ny - 1) * z)] = (uint8_t)case_order((int)cb);
+    }
+}
+}  // namespace
+#endif
+
+// Checked builds: see chr_debug_tri_cells / chr_debug_cases (false in normal builds).
+bool mc_debug_set_tri_cells(uint32_t *cells)
+{
+#ifdef CHR_CHECKED
+    g_dbg_cells = cells;
+    return true;
+#else
+    (void)cells;
+    return false;
+#endif
+}
+
 static void mc_tiles(const Grid &g, int32_t &ntx, int32_t &ncby, int32_t &ncbz, int64_t &ntiles)
 {
     const int64_t ncbx = (g.nx - 1 + 7) / 8;
@@ -1780,16 +1830,25 @@ static cudaError_t launch_count_scan(const McParams &p, const CUtensorMap &map, 
     return cudaGetLastError();
 }
 
-// Test only: CHR_TEST_UNPUBLISHED_TILE=<tile> makes that tile of the single
-// pass publish nothing, so the tiles after it give up their bounded
-// look-back and raise CHR_ERR_TIMEOUT (read at every call; -1 when unset).
-static int64_t test_unpublished_tile()
+// Checked builds only: a tile of the single pass that publishes nothing
+// (chr_debug_unpublished_tile), so the tiles after it give up their bounded
+// look-back and raise CHR_ERR_TIMEOUT; -1 (none) otherwise.
+#ifdef CHR_CHECKED
+static std::atomic<int64_t> g_unpublished_tile{-1};
+static int64_t test_unpublished_tile() { return g_unpublished_tile.load(); }
+#else
+static int64_t test_unpublished_tile() { return -1; }
+#endif
+
+bool mc_set_unpublished_tile(int64_t tile)
 {
-    const char *v = getenv("CHR_TEST_UNPUBLISHED_TILE");
-    if (!v || !*v) return -1;
-    char *end = nullptr;
-    const long long t = strtoll(v, &end, 10);
-    return (end && *end == '\0' && t >= 0) ? (int64_t)t : -1;
+#ifdef CHR_CHECKED
+    g_unpublished_tile.store(tile < 0 ? -1 : tile);
+    return true;
+#else
+    (void)tile;
+    return false;
+#endif
 }
 
 // One group of up to 4 isovalues.  With room for the stored classification
@@ -1889,6 +1948,7 @@ cudaError_t launch_mc_pitched(const float *field, const Grid &g, int64_t sx, int
         for (int i = 0; i < kMcIsoPerPass; i++) {
             p.k[i] = (i < n) ? iso[i0 + i] : 0.0f;
             p.tris[i] = (i < n) ? tris + 9ull * cap * (uint64_t)(i0 + i) : nullptr;
+            p.dbg_cells[i] = (i < n && g_dbg_cells) ? g_dbg_cells + cap * (uint64_t)(i0 + i) : nullptr;
         }
         cudaError_t e;
         switch (n) {
@@ -1980,6 +2040,7 @@ cudaError_t launch_mc_chr(const ChrMcLevels &c, const Grid &g, const float *iso,
         for (int i = 0; i < kMcIsoPerPass; i++) {
             p.k[i] = (i < n) ? iso[i0 + i] : 0.0f;
             p.tris[i] = (i < n) ? tris + 9ull * cap * (uint64_t)(i0 + i) : nullptr;
+            p.dbg_cells[i] = (i < n && g_dbg_cells) ? g_dbg_cells + cap * (uint64_t)(i0 + i) : nullptr;
         }
         cudaError_t e;
         switch (n) {
@@ -2150,6 +2211,50 @@ cudaError_t mc_batch_prepare(int &count_per_sm, int &emit_per_sm, int &sms)
     emit_per_sm = bed[dev];
     sms = nsd[dev];
     return cudaSuccess;
+}
+
+bool mc_debug_cases(const float *field, const Grid &g, float isovalue, uint8_t *out, void *workspace,
+                    size_t workspace_bytes, cudaStream_t s, cudaError_t &err)
+{
+#ifdef CHR_CHECKED
+    err = cudaSuccess;
+    if (workspace_bytes < mc_workspace_bytes(g, 1)) {
+        err = cudaErrorInvalidValue;
+        return true;
+    }
+    McParams p;
+    memset(&p, 0, sizeof(p));
+    p.f = field;
+    p.nx = g.nx;
+    p.ny = g.ny;
+    p.nz = g.nz;
+    p.sx = g.nx;
+    p.sy = g.nx * g.ny;
+    mc_tiles(g, p.ntx, p.ncby, p.ncbz, p.ntiles);
+    p.k[0] = isovalue;
+    McWorkspace w;
+    mc_layout(g, 1, workspace, &w);
+    p.tile_cnt = w.cnt;
+    p.tile_off = w.off;
+    p.cases = w.cases;
+    p.tcnt = w.tcnt;
+    p.cstride = 1;
+    CUtensorMap map;
+    memset(&map, 0, sizeof(map));
+    p.use_tma = make_field_tensor_map_pitched(&map, field, g.nx, g.ny, g.nz, p.sx, p.sy, kBoxX, 9, 9) ? 1 : 0;
+    McGrids G;
+    if ((err = mc_prepare<1>(G)) != cudaSuccess) return true;
+    const unsigned gc = (unsigned)(p.ntiles < G.count ? p.ntiles : G.count);
+    k_mc_count<1><<<gc, 256, kCountSmem, s>>>(p, map);
+    k_debug_cases<<<(unsigned)((p.ntiles * 256 + 255) / 256), 256, 0, s>>>(w.cases, 1, p.ntiles, p.ntx, p.ncby, g.nx,
+                                                                          g.ny, g.nz, out);
+    err = cudaGetLastError();
+    return true;
+#else
+    (void)field; (void)g; (void)isovalue; (void)out; (void)workspace; (void)workspace_bytes; (void)s;
+    err = cudaSuccess;
+    return false;
+#endif
 }
 
 uint32_t mc_bounds_word(bool reset)

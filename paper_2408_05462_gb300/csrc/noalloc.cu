@@ -14,7 +14,6 @@
 // calls whose work overlaps on a GPU (for example on two streams) race on it;
 // serialise them.  Each call overwrites every scratch byte it reads before
 // reading it, so nothing needs clearing between calls.
-#include <mutex>
 #include <string>
 
 #include "internal.h"
@@ -24,30 +23,19 @@ namespace chr {
 namespace {
 
 constexpr size_t kNoallocScratchBytes = size_t(4) << 20;  // 4 MiB
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-std::mutex g_noalloc_mutex;
-void *g_noalloc_ptr[kMaxDevices] = {};
-
 // Device address of g_noalloc_scratch on the current device.  The host-side
 // name of a __device__ array is not a device address, so the address is
-// looked up once per device (with that device current) and cached.
+// looked up with the device current, at every call (cheap once the module
+// is loaded, and right after a device reset too).
 cudaError_t noalloc_scratch(void **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
-        void *ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_ptr[dev] = ptr;
-    }
-    *out = g_noalloc_ptr[dev];
+    *out = ptr;
     return cudaSuccess;
 }
 
@@ -77,6 +65,9 @@ extern "C" chr_status isosurface_extract_noalloc(const float *d_field, chr_dims 
         set_error(std::string("isosurface_extract_noalloc: scratch lookup failed: ") + cudaGetErrorString(e));
         return CHR_ERR_CUDA;
     }
-    return isosurface_extract(d_field, dims, isovalues, n_iso, d_tris, cap_tris, d_ntris, d_err, scratch,
-                              kNoallocScratchBytes, stream);
+    // the minimum workspace: every group of isovalues takes the single pass
+    size_t ws = kNoallocScratchBytes;
+    if (dims.nx >= 2 && dims.ny >= 2 && dims.nz >= 2) ws = mc_workspace_min_bytes(make_grid(dims), (int)n_iso);
+    return isosurface_extract(d_field, dims, isovalues, n_iso, d_tris, cap_tris, d_ntris, d_err, scratch, ws,
+                              stream);
 }

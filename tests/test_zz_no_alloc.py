@@ -45,9 +45,19 @@ def test_noalloc_matches_workspace_entry_point(shape, isos):
     ref_tris, ref_counts, ref_err = chr.isosurface_extract(f, isos, cap)
     torch.cuda.synchronize()
     assert int(ref_err.item()) == 0
+    tris = torch.empty_like(ref_tris)
+    counts = torch.empty_like(ref_counts)
+    err = torch.empty_like(ref_err)
+    chr.isosurface_extract_noalloc(f, isos, cap, tris=tris, counts=counts, err=err)  # first call on the device
+    torch.cuda.synchronize()
     for _ in range(2):  # two calls in a row share the same scratch
-        tris, counts, err = chr.isosurface_extract_noalloc(f, isos, cap)
+        torch_bytes = torch.cuda.memory_allocated()
+        free_bytes = torch.cuda.mem_get_info()[0]
+        chr.isosurface_extract_noalloc(f, isos, cap, tris=tris, counts=counts, err=err)
         torch.cuda.synchronize()
+        # the call itself allocated nothing: neither through torch nor from the device
+        assert torch.cuda.memory_allocated() == torch_bytes
+        assert torch.cuda.mem_get_info()[0] == free_bytes
         assert int(err.item()) == 0
         _same(ref_tris, ref_counts, tris, counts)
 
