@@ -753,7 +753,8 @@ void orc_cases(const float *f, int64_t nx, int64_t ny, int64_t nz, float k, uint
  * x in [8bx, min(8bx+8, nx-1)) and likewise along y and z; those cells
  * touch the vertices x in [8bx, min(8bx+8, nx-1)] (the brick and the first
  * vertex plane of its +x, +y and +z neighbours).  lo[b], hi[b]: the
- * smallest and largest value over those vertices, NaN counted as +inf.  A
+ * smallest and largest value over those vertices, NaN counted as +inf, a
+ * zero stored as +0 (-0 and +0 are the same value).  A
  * brick without cells gets lo = +inf, hi = -inf.  A cell of brick b is
  * active for k only if one corner has v < k and another v >= k (or NaN),
  * hence only if lo[b] < k <= hi[b].
@@ -776,6 +777,7 @@ void orc_brick_index(const float *f, int64_t nx, int64_t ny, int64_t nz, float *
                             for (int64_t x = x0; x <= x1; x++) {
                                 float v = f[x + nx * (y + ny * z)];
                                 if (isnan(v)) v = INFINITY;
+                                v = v + 0.0f; /* -0 and +0 are one value: +0 stands for both */
                                 if (v < mn) mn = v;
                                 if (v > mx) mx = v;
                             }

@@ -21,6 +21,22 @@ struct BrickCoord {
     int64_t b;  // linear brick index
 };
 
+// Minimum / maximum of a float over the warp (one redux instruction; the
+// inputs here are never NaN).
+__device__ __forceinline__ float warp_min_f32(float v)
+{
+    float r;
+    asm("redux.sync.min.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+__device__ __forceinline__ float warp_max_f32(float v)
+{
+    float r;
+    asm("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
+}
+
 // Number of candidate isovalues strictly above v (K sorted ascending).  Two
 // values lie on the same side of every k exactly when these counts agree,
 // because {j : v < K[j]} is always a suffix of the sorted K.
@@ -81,7 +97,7 @@ __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ Codec
     __shared__ uint32_t s_red[kEncBricks][2][4];                // per warp: max L, max plain, exceptions, -
     __shared__ __align__(16) uint32_t s_pk[kEncBricks][512];    // packed words of each brick (zero between levels)
     __shared__ float s_kup[CHR_MAX_ISO + 1], s_kdn[CHR_MAX_ISO + 1];  // by count of candidates above f
-    __shared__ float2 s_rng[kEncBricks][2][4];                  // per warp: value ranges for the index
+    __shared__ float2 s_rng[kEncBricks][3][4];                  // per warp, then the z = 0 parts: ranges for the index
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int j = tid >> 6, r = tid & 63, wb = r >> 5;
@@ -162,57 +178,6 @@ __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ Codec
             }
         }
 
-        // The value index (Sec. 2.1: which bricks an isovalue can cross).
-        // Ranges of R over 8 vertex subsets of the brick, NaN as +inf: all of
-        // it, the planes x = 0, y = 0, z = 0, the lines x = y = 0, x = z = 0,
-        // y = z = 0 and the corner; k_brick_index assembles each brick's
-        // cell-vertex range from its own range and its neighbours' planes,
-        // lines and corner.  Along y by xor 1, 2, 4 (after which the z = 0
-        // rows hold the z = 0 plane and the x = z = 0 line), then along z by
-        // xor 8, 16 (the y = 0 lanes' own values give the y = 0 plane and the
-        // x = y = 0 line), then across the brick's two warps.
-        float2 rg_z0, rg_x0z0, rg_y0z0, rg_c;
-        if (p.idx_part) {
-            float mn = __int_as_float(0x7f800000), mx = -mn, a0 = mn, b0 = mx;
-#pragma unroll
-            for (int x = 0; x < 8; x++)
-                if ((valid >> x) & 1u) {
-                    const float v = isnan(R[x]) ? __int_as_float(0x7f800000) : R[x];
-                    mn = fminf(mn, v);
-                    mx = fmaxf(mx, v);
-                    if (x == 0) a0 = b0 = v;
-                }
-            rg_y0z0 = make_float2(mn, mx);
-            rg_c = make_float2(a0, b0);
-            float omn = mn, omx = mx, xmn = a0, xmx = b0;
-#pragma unroll
-            for (int o = 1; o < 8; o <<= 1) {
-                omn = fminf(omn, __shfl_xor_sync(CHR_FULL_MASK, omn, o));
-                omx = fmaxf(omx, __shfl_xor_sync(CHR_FULL_MASK, omx, o));
-                xmn = fminf(xmn, __shfl_xor_sync(CHR_FULL_MASK, xmn, o));
-                xmx = fmaxf(xmx, __shfl_xor_sync(CHR_FULL_MASK, xmx, o));
-            }
-            rg_z0 = make_float2(omn, omx);
-            rg_x0z0 = make_float2(xmn, xmx);
-#pragma unroll
-            for (int o = 8; o < 32; o <<= 1) {
-                omn = fminf(omn, __shfl_xor_sync(CHR_FULL_MASK, omn, o));
-                omx = fmaxf(omx, __shfl_xor_sync(CHR_FULL_MASK, omx, o));
-                xmn = fminf(xmn, __shfl_xor_sync(CHR_FULL_MASK, xmn, o));
-                xmx = fmaxf(xmx, __shfl_xor_sync(CHR_FULL_MASK, xmx, o));
-                mn = fminf(mn, __shfl_xor_sync(CHR_FULL_MASK, mn, o));
-                mx = fmaxf(mx, __shfl_xor_sync(CHR_FULL_MASK, mx, o));
-                a0 = fminf(a0, __shfl_xor_sync(CHR_FULL_MASK, a0, o));
-                b0 = fmaxf(b0, __shfl_xor_sync(CHR_FULL_MASK, b0, o));
-            }
-            if (lane == 0) {  // (ly = 0): this warp's whole part, x = 0 plane, y = 0 plane, x = y = 0 line
-                s_rng[j][wb][0] = make_float2(omn, omx);
-                s_rng[j][wb][1] = make_float2(xmn, xmx);
-                s_rng[j][wb][2] = make_float2(mn, mx);
-                s_rng[j][wb][3] = make_float2(a0, b0);
-            }
-        }
-
         // Lorenzo residual: first differences along x, y (lanes 1 apart) and z
         // (lanes 8 apart; the z = 4 rows take the z = 3 rows from shared memory)
         int32_t d[8];
@@ -266,17 +231,6 @@ __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ Codec
         const int w = mode ? wl : wn;
         if (mine && r == 0)
             p.recs[l][c.b] = make_uint4(0u, 0u, (uint32_t)q[0], (uint32_t)w | ((uint32_t)mode << 8) | (nexc << 16));
-        if (p.idx_part && mine && r == 0) {  // (thread 0 holds the z = 0 rows' and its own parts)
-            auto un = [](float2 a, float2 b) { return make_float2(fminf(a.x, b.x), fmaxf(a.y, b.y)); };
-            float4 *dst = reinterpret_cast<float4 *>(p.idx_part + ((size_t)l * p.nbx * p.nby * p.nbz + c.b) * kIdxParts);
-            const float2 all = un(s_rng[j][0][0], s_rng[j][1][0]), x0 = un(s_rng[j][0][1], s_rng[j][1][1]);
-            const float2 y0 = un(s_rng[j][0][2], s_rng[j][1][2]), x0y0 = un(s_rng[j][0][3], s_rng[j][1][3]);
-            dst[0] = make_float4(all.x, all.y, x0.x, x0.y);
-            dst[1] = make_float4(y0.x, y0.y, rg_z0.x, rg_z0.y);
-            dst[2] = make_float4(x0y0.x, x0y0.y, rg_x0z0.x, rg_x0z0.y);
-            dst[3] = make_float4(rg_y0z0.x, rg_y0z0.y, rg_c.x, rg_c.y);
-        }
-
         // pack: row r's 8 codes are bits [8*r*w, 8*r*w + 8*w) of the brick's
         // stream; each thread ORs its bits into the zeroed shared words, then
         // the brick's 16*w words are copied out (and zeroed for the next level)
@@ -322,7 +276,59 @@ __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ Codec
                 }
             }
         }
-        brick_sync(j);  // s_pk, s_zrow and s_red are reused by the next level
+        // The value index (Sec. 2.1: which bricks an isovalue can cross).
+        // Ranges of R over 8 vertex subsets of the brick, NaN as +inf and -0
+        // as +0: all of it, the planes x = 0, y = 0, z = 0, the lines
+        // x = y = 0, x = z = 0, y = z = 0 and the corner; k_brick_index
+        // assembles each brick's cell-vertex range from its own range and
+        // its neighbours' planes, lines and corner.  One warp-wide float
+        // reduction per range and end (non-members contribute the empty
+        // range): the whole warp, its y = 0 lanes, its z = 0 lanes (warp 0);
+        // thread 0 holds the y = z = 0 line and the corner itself.
+        if (p.idx_part) {
+            const float inf = __int_as_float(0x7f800000);
+            float mn = inf, mx = -inf, a0 = inf, b0 = -inf;
+#pragma unroll
+            for (int x = 0; x < 8; x++)
+                if ((valid >> x) & 1u) {
+                    const float v = isnan(R[x]) ? inf : __fadd_rn(R[x], 0.0f);
+                    mn = fminf(mn, v);
+                    mx = fmaxf(mx, v);
+                    if (x == 0) a0 = b0 = v;
+                }
+            if (r == 0) {  // the y = z = 0 line and the corner
+                s_rng[j][2][0] = make_float2(mn, mx);
+                s_rng[j][2][1] = make_float2(a0, b0);
+            }
+            const bool y0 = ly == 0, z0 = lz == 0;
+            float2 t;
+            t = make_float2(warp_min_f32(mn), warp_max_f32(mx));
+            if (lane == 0) s_rng[j][wb][0] = t;  // this warp's whole part
+            t = make_float2(warp_min_f32(a0), warp_max_f32(b0));
+            if (lane == 0) s_rng[j][wb][1] = t;  // x = 0 plane
+            t = make_float2(warp_min_f32(y0 ? mn : inf), warp_max_f32(y0 ? mx : -inf));
+            if (lane == 0) s_rng[j][wb][2] = t;  // y = 0 plane
+            t = make_float2(warp_min_f32(y0 ? a0 : inf), warp_max_f32(y0 ? b0 : -inf));
+            if (lane == 0) s_rng[j][wb][3] = t;  // x = y = 0 line
+            if (wb == 0) {                       // (the z = 0 rows are warp 0's lanes 0..7)
+                t = make_float2(warp_min_f32(z0 ? mn : inf), warp_max_f32(z0 ? mx : -inf));
+                if (lane == 0) s_rng[j][2][2] = t;  // z = 0 plane
+                t = make_float2(warp_min_f32(z0 ? a0 : inf), warp_max_f32(z0 ? b0 : -inf));
+                if (lane == 0) s_rng[j][2][3] = t;  // x = z = 0 line
+            }
+        }
+        brick_sync(j);  // s_pk, s_zrow, s_red and s_rng are reused by the next level
+        if (p.idx_part && mine && r == 0) {  // (thread 0 holds the z = 0 rows' and its own parts)
+            auto un = [](float2 a, float2 b) { return make_float2(fminf(a.x, b.x), fmaxf(a.y, b.y)); };
+            float4 *dst = reinterpret_cast<float4 *>(p.idx_part + ((size_t)l * p.nbx * p.nby * p.nbz + c.b) * kIdxParts);
+            const float2 all = un(s_rng[j][0][0], s_rng[j][1][0]), x0 = un(s_rng[j][0][1], s_rng[j][1][1]);
+            const float2 y0 = un(s_rng[j][0][2], s_rng[j][1][2]), x0y0 = un(s_rng[j][0][3], s_rng[j][1][3]);
+            const float2 z0 = s_rng[j][2][2], x0z0 = s_rng[j][2][3], y0z0 = s_rng[j][2][0], c0 = s_rng[j][2][1];
+            dst[0] = make_float4(all.x, all.y, x0.x, x0.y);
+            dst[1] = make_float4(y0.x, y0.y, z0.x, z0.y);
+            dst[2] = make_float4(x0y0.x, x0y0.y, x0z0.x, x0z0.y);
+            dst[3] = make_float4(y0z0.x, y0z0.y, c0.x, c0.y);
+        }
     }
 }
 

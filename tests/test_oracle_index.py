@@ -132,3 +132,13 @@ def test_index_brute_force(shape, seed):
         z, y, x = np.nonzero(active)
         straddle = (lo < k) & (k <= hi)
         assert straddle[z // 8, y // 8, x // 8].all()
+
+
+def test_index_zero_is_positive_zero():
+    # bricks whose extreme is a zero store +0 whichever zero the grid holds
+    f = np.ones((9, 9, 9), np.float32)
+    f[2, 2, 2] = -0.0
+    lo, hi = oracle.brick_index(-f * 0.0)  # every vertex -0
+    assert np.all(lo[0, 0, 0].view(np.uint32) == 0) and np.all(hi[0, 0, 0].view(np.uint32) == 0)
+    lo, hi = oracle.brick_index(f)
+    assert lo[0, 0, 0].view(np.uint32) == 0 and hi[0, 0, 0] == 1.0
