@@ -199,31 +199,53 @@ void set_constants(chr_handle *h)
     }
 }
 
-// The radix selection of chr_topo_translate; synchronises the stream.
+// The selection of chr_topo_translate; synchronises the stream.  Accuracy 1:
+// one walk for min D.  Otherwise a walk for the 4096-bin histogram of the
+// top 12 bits of D's elements, which names the bucket holding rank n; a walk
+// that collects that bucket's elements; and two small histogram passes over
+// them (bits 10..19, then 0..9 within the chosen bits 10..19).
 chr_status translate_impl(const float *d_field, const Grid &g, const float *K, uint32_t nK, float accuracy, Alloc &al,
                           float *eb_out, uint64_t *count_out)
 {
+    constexpr int kBins = 4096;
     const size_t sb = translate_scratch_bytes();
     char *scr = (char *)al.get(sb);
     if (!scr) return fail(CHR_ERR_OOM, "chr_topo_translate: allocator returned NULL");
     TranslateScratch sc;
+    memset(&sc, 0, sizeof(sc));
     sc.hist = reinterpret_cast<unsigned long long *>(scr);
-    sc.count = reinterpret_cast<unsigned long long *>(scr + 256 * 8);
-    sc.minbits = reinterpret_cast<unsigned int *>(scr + 256 * 8 + 8);
+    sc.count = reinterpret_cast<unsigned long long *>(scr + kBins * 8);
+    sc.minbits = reinterpret_cast<unsigned int *>(scr + kBins * 8 + 8);
+    sc.ncoll = reinterpret_cast<unsigned long long *>(scr + kBins * 8 + 16);
     chr_status st = CHR_OK;
-    std::vector<unsigned long long> hist(256);
+    std::vector<unsigned long long> hist(kBins);
     unsigned long long count = 0;
     unsigned int minbits = 0xffffffffu;
     float eb = INFINITY;
+    uint32_t *coll = nullptr;
+    size_t coll_bytes = 0;
+    auto pick = [](const std::vector<unsigned long long> &h, int nb, unsigned long long &rank) {
+        unsigned long long cum = 0;
+        for (int b = 0; b < nb; b++) {
+            if (rank < cum + h[b]) {
+                rank -= cum;
+                return b;
+            }
+            cum += h[b];
+        }
+        rank = 0;
+        return nb - 1;
+    };
     do {
         cudaError_t e;
         const bool min_only = (accuracy >= 1.0f);
-        if ((e = cudaMemsetAsync(scr, 0, 256 * 8 + 8, al.s)) != cudaSuccess ||
+        if ((e = cudaMemsetAsync(scr, 0, kBins * 8 + 24, al.s)) != cudaSuccess ||
             (e = cudaMemsetAsync(sc.minbits, 0xff, 4, al.s)) != cudaSuccess ||
-            (e = launch_translate_pass(d_field, g, K, (int)nK, 0, 0u, min_only, sc, al.s)) != cudaSuccess ||
+            (e = launch_translate_pass(d_field, g, K, (int)nK, min_only ? 0 : 1, 0u, sc, al.s)) != cudaSuccess ||
             (e = cudaMemcpyAsync(&count, sc.count, 8, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess ||
             (e = cudaMemcpyAsync(&minbits, sc.minbits, 4, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(hist.data(), sc.hist, 256 * 8, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess ||
+            (!min_only &&
+             (e = cudaMemcpyAsync(hist.data(), sc.hist, kBins * 8, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess) ||
             (e = cudaStreamSynchronize(al.s)) != cudaSuccess) {
             st = cuda_fail(e, "chr_topo_translate");
             break;
@@ -236,32 +258,42 @@ chr_status translate_impl(const float *d_field, const Grid &g, const float *K, u
         double r = floor((1.0 - (double)accuracy) * (double)count);
         unsigned long long rank = (r < 0) ? 0ull : (unsigned long long)r;
         if (rank > count - 1) rank = count - 1;
-        uint32_t prefix = 0;
-        for (int pass = 0; pass < 4; pass++) {
-            if (pass > 0) {
-                if ((e = cudaMemsetAsync(sc.hist, 0, 256 * 8, al.s)) != cudaSuccess ||
-                    (e = launch_translate_pass(d_field, g, K, (int)nK, pass, prefix, false, sc, al.s)) != cudaSuccess ||
-                    (e = cudaMemcpyAsync(hist.data(), sc.hist, 256 * 8, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess ||
-                    (e = cudaStreamSynchronize(al.s)) != cudaSuccess) {
-                    st = cuda_fail(e, "chr_topo_translate");
-                    break;
-                }
-            }
-            unsigned long long cum = 0;
-            int bucket = 255;
-            for (int b = 0; b < 256; b++) {
-                if (rank < cum + hist[b]) {
-                    bucket = b;
-                    break;
-                }
-                cum += hist[b];
-            }
-            rank -= cum;
-            prefix = (prefix << 8) | (uint32_t)bucket;
+        const uint32_t b1 = (uint32_t)pick(hist, kBins, rank);
+        const unsigned long long nb = hist[b1];
+        coll_bytes = nb * 4;
+        if (!(coll = (uint32_t *)al.get(coll_bytes))) {
+            st = fail(CHR_ERR_OOM, "chr_topo_translate: allocator returned NULL");
+            break;
         }
-        if (st != CHR_OK) break;
-        memcpy(&eb, &prefix, 4);
+        sc.coll = coll;
+        sc.cap = nb;
+        unsigned long long got = 0;
+        if ((e = launch_translate_pass(d_field, g, K, (int)nK, 2, b1, sc, al.s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(&got, sc.ncoll, 8, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess ||
+            (e = cudaMemsetAsync(sc.hist, 0, 1024 * 8, al.s)) != cudaSuccess ||
+            (e = launch_translate_select(coll, nb, 10, 0u, sc.hist, al.s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(hist.data(), sc.hist, 1024 * 8, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(al.s)) != cudaSuccess) {
+            st = cuda_fail(e, "chr_topo_translate");
+            break;
+        }
+        if (got != nb) {
+            st = fail(CHR_ERR_CUDA, "chr_topo_translate: the collecting walk found a different bucket size");
+            break;
+        }
+        const uint32_t b2 = (uint32_t)pick(hist, 1024, rank);
+        if ((e = cudaMemsetAsync(sc.hist, 0, 1024 * 8, al.s)) != cudaSuccess ||
+            (e = launch_translate_select(coll, nb, 0, b2, sc.hist, al.s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(hist.data(), sc.hist, 1024 * 8, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(al.s)) != cudaSuccess) {
+            st = cuda_fail(e, "chr_topo_translate");
+            break;
+        }
+        const uint32_t b3 = (uint32_t)pick(hist, 1024, rank);
+        const uint32_t bits = (b1 << 20) | (b2 << 10) | b3;
+        memcpy(&eb, &bits, 4);
     } while (0);
+    if (coll) al.put(coll, coll_bytes);
     al.put(scr, sb);
     if (st == CHR_OK) {
         *eb_out = eb;

@@ -179,15 +179,25 @@ size_t dist_loss_workspace_bytes(uint64_t npts);
 cudaError_t launch_dist_loss(const float *orig, const Grid &g, float k, const float *pts, uint64_t npts, double *loss,
                              float *grad_pts, void *workspace, cudaStream_t s);
 
-// Error-bound translation (radix selection over D).
+// Error-bound translation (selection over D).  mode 0: the minimum
+// (minbits) and |D| (count); mode 1: |D| and a 4096-bin histogram of the
+// elements' top 12 bits (hist); mode 2: every element whose top 12 bits equal
+// prefix, its low 20 bits appended to coll (at most cap; ncoll counts them).
 struct TranslateScratch {
-    unsigned long long *hist;  // 256 counters
+    unsigned long long *hist;  // 4096 counters
     unsigned long long *count; // |D|
     unsigned int *minbits;     // min D as float bits
+    unsigned long long *ncoll; // elements appended (mode 2)
+    uint32_t *coll;            // mode 2 output
+    unsigned long long cap;
 };
 size_t translate_scratch_bytes();
-cudaError_t launch_translate_pass(const float *field, const Grid &g, const float *K, int nK, int pass,
-                                  uint32_t prefix, bool min_only, TranslateScratch sc, cudaStream_t s);
+cudaError_t launch_translate_pass(const float *field, const Grid &g, const float *K, int nK, int mode,
+                                  uint32_t prefix, TranslateScratch sc, cudaStream_t s);
+// Histogram (1024 bins, hist) of bits [shift, shift+10) of the n collected
+// values whose bits [shift+10, 20) equal `above`.
+cudaError_t launch_translate_select(const uint32_t *coll, unsigned long long n, int shift, uint32_t above,
+                                    unsigned long long *hist, cudaStream_t s);
 
 void set_error(const std::string &msg);
 

@@ -1,9 +1,11 @@
 // Error-bound translation (paper Sec. 2.2): the multiset D of d0 = k - s0 and
 // d1 = s1 - k over every grid edge with s0 < k < s1, and its smallest or n-th
-// smallest element.  D is never materialised: each pass walks the edges again
-// and either takes the minimum (accuracy 1) or builds a 256-bin histogram of
-// the next 8 bits of the float patterns that match the prefix chosen so far
-// (radix selection; non-negative floats order like their bit patterns).
+// smallest element.  D is never materialised whole (non-negative floats order
+// like their bit patterns): one walk over the edges takes the minimum
+// (accuracy 1); for the n-th smallest, a first walk builds a 4096-bin
+// histogram of the elements' top 12 bits, a second appends every element of
+// the bucket that holds rank n to a compact array, and two small histogram
+// passes over that array (bits 10..19, then 0..9) select the element exactly.
 //
 // Each vertex v is summarised against the sorted isovalues by a = #{k < v}
 // and b = #{k > v}.  An edge (s, t) then holds c1 = a_t + b_s - nK isovalues
@@ -42,8 +44,7 @@ struct TrParams {
     int32_t nK;
     float Klt[CHR_MAX_ISO];  // sorted isovalues, +inf past nK (never below a vertex)
     float Kgt[CHR_MAX_ISO];  // sorted isovalues, -inf past nK (never above a vertex)
-    int32_t pass;            // 0..3: histogram of bits [24-8*pass, 32-8*pass)
-    uint32_t prefix;         // the top 8*pass bits already selected
+    uint32_t prefix;         // collect: the top 12 bits of the elements kept
     int64_t tiles_x, tiles_y, zc, items;
     TranslateScratch sc;
 };
@@ -61,20 +62,34 @@ __device__ __forceinline__ uint32_t below_above(float v, const TrParams &p)
     return a | (b << 8);
 }
 
-template <int NK, bool MIN>
+__device__ __forceinline__ uint32_t tr_lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+constexpr int kTrHistBins = 4096;  // the first walk's key: the top 12 bits
+
+// MODE: kTrMin (the minimum), kTrHist (the 12-bit histogram), kTrCollect
+// (the elements whose top 12 bits are p.prefix, appended to p.sc.coll).
+enum { kTrMin = 0, kTrHist = 1, kTrCollect = 2 };
+
+template <int NK, int MODE>
 __global__ void __launch_bounds__(kTrWarps * 32, kTrBlocksPerSm) k_translate(const __grid_constant__ TrParams p)
 {
+    constexpr bool MIN = MODE == kTrMin;
     constexpr int kSlots = MIN ? 3 : 2;  // exchanged words per vertex: ab, up, dn | ab, value
     __shared__ uint32_t s_x[kSlots][kTrG][kTrWarps][32];
-    __shared__ unsigned int s_hist[MIN ? 1 : kTrWarps * 256];  // one histogram per warp
+    __shared__ unsigned int s_hist[MODE == kTrHist ? kTrHistBins : 1];
     __shared__ float s_kup[CHR_MAX_ISO + 1];  // sorted isovalues, +inf at nK
     __shared__ float s_kdn[CHR_MAX_ISO + 1];  // -inf, then the sorted isovalues
     __shared__ unsigned long long s_cnt;
     __shared__ unsigned int s_min;
 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (!MIN)
-        for (int i = threadIdx.x; i < kTrWarps * 256; i += blockDim.x) s_hist[i] = 0u;
+    if (MODE == kTrHist)
+        for (int i = threadIdx.x; i < kTrHistBins; i += blockDim.x) s_hist[i] = 0u;
     if (threadIdx.x <= CHR_MAX_ISO) {
         const int i = threadIdx.x;
         s_kup[i] = (i < p.nK) ? p.Klt[i] : __int_as_float(0x7f800000);
@@ -88,14 +103,27 @@ __global__ void __launch_bounds__(kTrWarps * 32, kTrBlocksPerSm) k_translate(con
 
     unsigned long long cnt = 0;
     unsigned int mn = 0xffffffffu;
-    unsigned int *wh = s_hist + (MIN ? 0 : 256 * w);
-    const int shift = 24 - 8 * p.pass;
     const int nK = p.nK;
     const int64_t plane = p.nx * p.ny;
 
+    // one element of D: into the histogram, or (collect) appended when its
+    // top 12 bits match, by one atomic per group of lanes that append together
     auto put = [&](float d) {
         const uint32_t bits = __float_as_uint(d);
-        if (p.pass == 0 || (bits >> (shift + 8)) == p.prefix) atomicAdd(&wh[(bits >> shift) & 255u], 1u);
+        if (MODE == kTrHist) {
+            atomicAdd(&s_hist[bits >> 20], 1u);
+        } else if (MODE == kTrCollect) {
+            const bool want = (bits >> 20) == p.prefix;
+            const uint32_t m = __ballot_sync(__activemask(), want);
+            if (want) {
+                const int leader = __ffs(m) - 1;
+                unsigned long long base = 0;
+                if (lane == leader) base = atomicAdd(p.sc.ncoll, (unsigned long long)__popc(m));
+                base = __shfl_sync(m, base, leader);
+                const unsigned long long at = base + __popc(m & tr_lanemask_lt());
+                if (at < p.sc.cap) p.sc.coll[at] = bits & 0xfffffu;
+            }
+        }
     };
     // one edge: s the vertex, t its neighbour, each given by its exchanged words
     auto edge = [&](uint32_t ab_s, uint32_t e1_s, uint32_t e2_s, uint32_t ab_t, uint32_t e1_t, uint32_t e2_t,
@@ -107,7 +135,7 @@ __global__ void __launch_bounds__(kTrWarps * 32, kTrBlocksPerSm) k_translate(con
             if (c1 > 0) mn = min(mn, min(e1_s, e2_t));  // up(s), dn(t)
             if (c2 > 0) mn = min(mn, min(e1_t, e2_s));  // up(t), dn(s)
         } else {
-            if (p.pass == 0) c32 += (uint32_t)(max(c1, 0) + max(c2, 0));
+            if (MODE == kTrHist) c32 += (uint32_t)(max(c1, 0) + max(c2, 0));
             // one loop over the crossing isovalues (a single body keeps the
             // unrolled kernel small enough for the instruction cache)
             const bool s_low = c1 > 0;
@@ -200,31 +228,61 @@ __global__ void __launch_bounds__(kTrWarps * 32, kTrBlocksPerSm) k_translate(con
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (s_cnt && p.pass == 0) atomicAdd(p.sc.count, s_cnt);
+        if (s_cnt && MODE != kTrCollect) atomicAdd(p.sc.count, s_cnt);
         if (MIN) atomicMin(p.sc.minbits, s_min);
     }
-    if (!MIN && threadIdx.x < 256) {
-        unsigned long long h = 0;
-        for (int v = 0; v < kTrWarps; v++) h += s_hist[256 * v + threadIdx.x];
-        if (h) atomicAdd(p.sc.hist + threadIdx.x, h);
+    if (MODE == kTrHist)
+        for (int i = threadIdx.x; i < kTrHistBins; i += blockDim.x)
+            if (s_hist[i]) atomicAdd(p.sc.hist + i, (unsigned long long)s_hist[i]);
+}
+
+// Histogram of bits [shift, shift + 10) of the collected elements (the low
+// 20 bits of each), over those whose bits [shift + 10, 20) equal `above`.
+__global__ void __launch_bounds__(256) k_select_hist(const uint32_t *coll, unsigned long long n, int shift,
+                                                     uint32_t above, unsigned long long *hist)
+{
+    __shared__ unsigned int s_h[1024];
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) s_h[i] = 0u;
+    __syncthreads();
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t v = coll[i];
+        if ((v >> (shift + 10)) == above) atomicAdd(&s_h[(v >> shift) & 1023u], 1u);
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x)
+        if (s_h[i]) atomicAdd(hist + i, (unsigned long long)s_h[i]);
 }
 
 template <int NK>
-void launch_nk(const TrParams &p, bool min_only, unsigned blocks, cudaStream_t s)
+void launch_nk(const TrParams &p, int mode, unsigned blocks, cudaStream_t s)
 {
-    if (min_only)
-        k_translate<NK, true><<<blocks, kTrWarps * 32, 0, s>>>(p);
+    if (mode == kTrMin)
+        k_translate<NK, kTrMin><<<blocks, kTrWarps * 32, 0, s>>>(p);
+    else if (mode == kTrHist)
+        k_translate<NK, kTrHist><<<blocks, kTrWarps * 32, 0, s>>>(p);
     else
-        k_translate<NK, false><<<blocks, kTrWarps * 32, 0, s>>>(p);
+        k_translate<NK, kTrCollect><<<blocks, kTrWarps * 32, 0, s>>>(p);
 }
 
 }  // namespace
 
-size_t translate_scratch_bytes() { return 256 * sizeof(unsigned long long) + 64; }
+size_t translate_scratch_bytes() { return kTrHistBins * sizeof(unsigned long long) + 64; }
 
-cudaError_t launch_translate_pass(const float *field, const Grid &g, const float *K, int nK, int pass, uint32_t prefix,
-                                  bool min_only, TranslateScratch sc, cudaStream_t s)
+cudaError_t launch_translate_select(const uint32_t *coll, unsigned long long n, int shift, uint32_t above,
+                                    unsigned long long *hist, cudaStream_t s)
+{
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned long long want = (n + 255) / 256;
+    const unsigned blocks = (unsigned)std::max<unsigned long long>(1, std::min<unsigned long long>(want, 4ull * sms));
+    k_select_hist<<<blocks, 256, 0, s>>>(coll, n, shift, above, hist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_translate_pass(const float *field, const Grid &g, const float *K, int nK, int mode,
+                                  uint32_t prefix, TranslateScratch sc, cudaStream_t s)
 {
     if (nK < 1 || nK > CHR_MAX_ISO) return cudaErrorInvalidValue;
     TrParams p;
@@ -240,7 +298,6 @@ cudaError_t launch_translate_pass(const float *field, const Grid &g, const float
         p.Klt[j] = (j < nK) ? ks[j] : INFINITY;
         p.Kgt[j] = (j < nK) ? ks[j] : -INFINITY;
     }
-    p.pass = pass;
     p.prefix = prefix;
     p.sc = sc;
     int dev = 0, sms = 148;
@@ -258,15 +315,15 @@ cudaError_t launch_translate_pass(const float *field, const Grid &g, const float
     p.items = tiles * chunks;
     const unsigned blocks = (unsigned)std::min<int64_t>(p.items, grid);
     if (nK <= 1)
-        launch_nk<1>(p, min_only, blocks, s);
+        launch_nk<1>(p, mode, blocks, s);
     else if (nK <= 2)
-        launch_nk<2>(p, min_only, blocks, s);
+        launch_nk<2>(p, mode, blocks, s);
     else if (nK <= 4)
-        launch_nk<4>(p, min_only, blocks, s);
+        launch_nk<4>(p, mode, blocks, s);
     else if (nK <= 8)
-        launch_nk<8>(p, min_only, blocks, s);
+        launch_nk<8>(p, mode, blocks, s);
     else
-        launch_nk<16>(p, min_only, blocks, s);
+        launch_nk<16>(p, mode, blocks, s);
     return cudaGetLastError();
 }
 

@@ -10,10 +10,11 @@ finishes, its slot and memory are released and the next waiting requests are
 admitted in arrival order, so new work starts while older work is still on the
 device.  Admission is by a device-memory budget: a request holds its box
 field, its workspace and room for an upper bound on its triangles, taken from
-the per-brick value index (chr_brick_range): a brick's cells can only be
-active for k if the combined range of the brick and its +x/+y/+z neighbours
+the CHR's stored value index (chr_brick_index, Sec. 2.1): a brick's cells
+can only be active for k if the range over the vertices they touch
 straddles k, and a cell has at most 5 triangles.  With the bound as capacity
-no request can overflow.
+no request can overflow.  (dilate_range builds a looser index from
+chr_brick_range's per-brick extrema, for handles without a stored one.)
 
 Results are triangles in box-local grid coordinates, left on the device (for
 the renderer), plus the count copied to the host.  A request's result does
@@ -88,7 +89,7 @@ class Timestep:
     step: int
     handle: chr.Chr
     shape: tuple           # (nz, ny, nx)
-    index: list            # per level: (min, max) dilated, [nbz, nby, nbx]
+    index: list            # per level: (min, max) over each brick's cell vertices, [nbz, nby, nbx]
     resident_bytes: int
 
     def tri_bound(self, level: int, k: float, origin, size) -> int:
@@ -206,7 +207,12 @@ class Server:
         vrange = float(hi) - float(lo)
         ebs = [r * vrange for r in self.levels_rel]
         h = chr.chr_compress(field, ebs, self.fix_isovalues, "fix")
-        index = [dilate_range(h.brick_range(l).cpu().numpy()) for l in range(len(ebs))]
+        # the CHR's stored value index: each brick's range over its cell
+        # vertices, exactly the vertices its cells touch (no decoder pass)
+        index = []
+        for l in range(len(ebs)):
+            ix = chr.chr_brick_index(h, l).cpu().numpy()
+            index.append((np.ascontiguousarray(ix[..., 0]), np.ascontiguousarray(ix[..., 1])))
         st = h.stats()
         ts = Timestep(step, h, tuple(field.shape), index, int(sum(st["level_bytes"])))
         self.steps[step] = ts
