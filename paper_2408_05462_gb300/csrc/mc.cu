@@ -512,7 +512,7 @@ __device__ __forceinline__ void mc_count_run(const Src &src, uint32_t *err)
 // IDX: the field has a value index (McParams.index), and cell bricks whose
 // range does not straddle an isovalue are not classified for it.
 template <int NISO>
-__global__ void __launch_bounds__(256) k_mc_count(const __grid_constant__ McParams p,
+__global__ void __launch_bounds__(256, 8) k_mc_count(const __grid_constant__ McParams p,
                                                  const __grid_constant__ CUtensorMap map)
 {
     mc_count_run<NISO, false>(SrcOne{&p, &map}, p.err);
