@@ -13,9 +13,12 @@
 // lower end (at most one is positive; a NaN end has a = b = 0, so neither
 // is); they are the sorted isovalues of index nK - b_s .. a_t - 1 (resp.
 // nK - b_t .. a_s - 1).  The smallest d0 of such an edge belongs to the
-// smallest isovalue above s and the smallest d1 to the largest below t, so
-// the minimum pass needs only up(s) = K[nK - b_s] - s and dn(t) = t - K[a_t - 1]
-// per vertex (both rounded down, like every element of D).
+// smallest isovalue above s and the smallest d1 to the largest below t:
+// up(s) = K[nK - b_s] - s and dn(t) = t - K[a_t - 1] per vertex (both rounded
+// down, like every element of D).  The minimum pass needs nothing else; the
+// histogram and collecting walks take these two elements of every crossing
+// edge the same way and compute the others (edges across two isovalues or
+// more) from the two end values.
 //
 // Tiling: a block of 16 warps walks a tile of 32 x-columns by 16 rows along z.
 // Lane 31 and warp 15 are halo: they read the next tile's first column and
@@ -24,6 +27,7 @@
 // is the next plane, already in registers.  The field is read once per pass
 // (plus the one-column, one-row and one-plane halos).
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -79,8 +83,7 @@ template <int NK, int MODE>
 __global__ void __launch_bounds__(kTrWarps * 32, kTrBlocksPerSm) k_translate(const __grid_constant__ TrParams p)
 {
     constexpr bool MIN = MODE == kTrMin;
-    constexpr int kSlots = MIN ? 3 : 2;  // exchanged words per vertex: ab, up, dn | ab, value
-    __shared__ uint32_t s_x[kSlots][kTrG][kTrWarps][32];
+    __shared__ uint32_t s_x[3][kTrG][kTrWarps][32];  // exchanged words per vertex: ab, up, dn
     __shared__ unsigned int s_hist[MODE == kTrHist ? kTrHistBins : 1];
     __shared__ float s_kup[CHR_MAX_ISO + 1];  // sorted isovalues, +inf at nK
     __shared__ float s_kdn[CHR_MAX_ISO + 1];  // -inf, then the sorted isovalues
@@ -106,15 +109,16 @@ __global__ void __launch_bounds__(kTrWarps * 32, kTrBlocksPerSm) k_translate(con
     const int nK = p.nK;
     const int64_t plane = p.nx * p.ny;
 
-    // one element of D: into the histogram, or (collect) appended when its
-    // top 12 bits match, by one atomic per group of lanes that append together
-    auto put = [&](float d) {
-        const uint32_t bits = __float_as_uint(d);
+    // one element of D (where `valid`): into the histogram, or (collect)
+    // appended when its top 12 bits match, by one atomic per group of lanes
+    // that append together.  CONV: all 32 lanes call it together
+    auto put = [&](bool valid, uint32_t bits, auto conv) {
         if (MODE == kTrHist) {
-            atomicAdd(&s_hist[bits >> 20], 1u);
+            if (valid) atomicAdd(&s_hist[bits >> 20], 1u);
         } else if (MODE == kTrCollect) {
-            const bool want = (bits >> 20) == p.prefix;
-            const uint32_t m = __ballot_sync(__activemask(), want);
+            const bool want = valid && (bits >> 20) == p.prefix;
+            const uint32_t m = decltype(conv)::value ? __ballot_sync(CHR_FULL_MASK, want)
+                                                     : __ballot_sync(__activemask(), want);
             if (want) {
                 const int leader = __ffs(m) - 1;
                 unsigned long long base = 0;
@@ -125,28 +129,32 @@ __global__ void __launch_bounds__(kTrWarps * 32, kTrBlocksPerSm) k_translate(con
             }
         }
     };
-    // one edge: s the vertex, t its neighbour, each given by its exchanged words
-    auto edge = [&](uint32_t ab_s, uint32_t e1_s, uint32_t e2_s, uint32_t ab_t, uint32_t e1_t, uint32_t e2_t,
-                    uint32_t &c32) {
+    // one edge (where `on`): s the vertex, t its neighbour, each given by its
+    // exchanged words; `ends` gives their values (read only for an edge
+    // across two isovalues or more)
+    auto edge = [&](bool on, uint32_t ab_s, uint32_t up_s, uint32_t dn_s, uint32_t ab_t, uint32_t up_t,
+                    uint32_t dn_t, auto &&ends, uint32_t &c32) {
         const int as = (int)(ab_s & 0xffu), bs = (int)(ab_s >> 8), at = (int)(ab_t & 0xffu), bt = (int)(ab_t >> 8);
-        const int c1 = at + bs - nK, c2 = as + bt - nK;
+        const int c1 = on ? at + bs - nK : 0, c2 = on ? as + bt - nK : 0;
         if (MIN) {
             c32 += (uint32_t)(max(c1, 0) + max(c2, 0));
-            if (c1 > 0) mn = min(mn, min(e1_s, e2_t));  // up(s), dn(t)
-            if (c2 > 0) mn = min(mn, min(e1_t, e2_s));  // up(t), dn(s)
+            if (c1 > 0) mn = min(mn, min(up_s, dn_t));
+            if (c2 > 0) mn = min(mn, min(up_t, dn_s));
         } else {
             if (MODE == kTrHist) c32 += (uint32_t)(max(c1, 0) + max(c2, 0));
-            // one loop over the crossing isovalues (a single body keeps the
-            // unrolled kernel small enough for the instruction cache)
             const bool s_low = c1 > 0;
             const int c = s_low ? c1 : c2;
-            if (c > 0) {
-                const float lo = __uint_as_float(s_low ? e1_s : e1_t), hi = __uint_as_float(s_low ? e1_t : e1_s);
+            // d0 of the lowest crossing isovalue and d1 of the highest
+            put(c > 0, s_low ? up_s : up_t, std::true_type{});
+            put(c > 0, s_low ? dn_t : dn_s, std::true_type{});
+            if (c > 1) {  // the other crossing isovalues K[i0 + 1 ..] (d0) and K[.. i0 + c - 2] (d1)
+                float vs, vt;
+                ends(vs, vt);
+                const float lo = s_low ? vs : vt, hi = s_low ? vt : vs;
                 const int i0 = nK - (s_low ? bs : bt);
-                for (int i = i0; i < i0 + c; i++) {
-                    const float k = s_kup[i];
-                    put(__fsub_rd(k, lo));
-                    put(__fsub_rd(hi, k));
+                for (int i = 1; i < c; i++) {
+                    put(true, __float_as_uint(__fsub_rd(s_kup[i0 + i], lo)), std::false_type{});
+                    put(true, __float_as_uint(__fsub_rd(hi, s_kup[i0 + i - 1])), std::false_type{});
                 }
             }
         }
@@ -165,16 +173,11 @@ __global__ void __launch_bounds__(kTrWarps * 32, kTrBlocksPerSm) k_translate(con
         auto ld = [&](int64_t z) -> float {
             return (valid && z <= zl) ? __ldg(src + z * plane) : __int_as_float(0x7fffffff);
         };
-        // per-vertex words: ab, then up/dn bits (MIN) or the value bits
+        // per-vertex words: ab, up, dn
         auto attr = [&](float v, uint32_t &ab, uint32_t &e1, uint32_t &e2) {
             ab = below_above<NK>(v, p);
-            if (MIN) {
-                e1 = __float_as_uint(__fsub_rd(s_kup[nK - (int)(ab >> 8)], v));
-                e2 = __float_as_uint(__fsub_rd(v, s_kdn[ab & 0xffu]));
-            } else {
-                e1 = __float_as_uint(v);
-                e2 = 0u;
-            }
+            e1 = __float_as_uint(__fsub_rd(s_kup[nK - (int)(ab >> 8)], v));
+            e2 = __float_as_uint(__fsub_rd(v, s_kdn[ab & 0xffu]));
         };
 
         uint32_t ab[kTrG + 1], e1[kTrG + 1], e2[kTrG + 1];
@@ -192,21 +195,36 @@ __global__ void __launch_bounds__(kTrWarps * 32, kTrBlocksPerSm) k_translate(con
             for (int i = 0; i < kTrG; i++) {
                 s_x[0][i][w][lane] = ab[i];
                 s_x[1][i][w][lane] = e1[i];
-                if (MIN) s_x[kSlots - 1][i][w][lane] = e2[i];
+                s_x[2][i][w][lane] = e2[i];
             }
             __syncthreads();
 #pragma unroll
             for (int i = 0; i < kTrG; i++) {
                 const uint32_t xab = __shfl_down_sync(CHR_FULL_MASK, ab[i], 1);
                 const uint32_t xe1 = __shfl_down_sync(CHR_FULL_MASK, e1[i], 1);
-                const uint32_t xe2 = MIN ? __shfl_down_sync(CHR_FULL_MASK, e2[i], 1) : 0u;
+                const uint32_t xe2 = __shfl_down_sync(CHR_FULL_MASK, e2[i], 1);
+                const int wy = (w + 1 < kTrWarps) ? w + 1 : w;  // (the halo warp's reads go unused)
+                const uint32_t yab = s_x[0][i][wy][lane], ye1 = s_x[1][i][wy][lane], ye2 = s_x[2][i][wy][lane];
                 const int64_t z = zb + i;
-                if (own && z < z1) {
-                    if (hx) edge(ab[i], e1[i], e2[i], xab, xe1, xe2, c32);
-                    if (hy)
-                        edge(ab[i], e1[i], e2[i], s_x[0][i][w + 1][lane], s_x[1][i][w + 1][lane],
-                             MIN ? s_x[kSlots - 1][i][w + 1][lane] : 0u, c32);
-                    if (z + 1 < p.nz) edge(ab[i], e1[i], e2[i], ab[i + 1], e1[i + 1], e2[i + 1], c32);
+                const bool oz = own && z < z1;
+                // the end values of the +x, +y and +z edges from vertex (x, y, z)
+                auto ends_at = [&](int64_t step) {
+                    return [&, step](float &vs, float &vt) {
+                        vs = __ldg(src + z * plane);
+                        vt = __ldg(src + z * plane + step);
+                    };
+                };
+                if (MIN) {
+                    if (oz) {
+                        if (hx) edge(true, ab[i], e1[i], e2[i], xab, xe1, xe2, ends_at(1), c32);
+                        if (hy) edge(true, ab[i], e1[i], e2[i], yab, ye1, ye2, ends_at(p.nx), c32);
+                        if (z + 1 < p.nz) edge(true, ab[i], e1[i], e2[i], ab[i + 1], e1[i + 1], e2[i + 1], ends_at(plane), c32);
+                    }
+                } else {  // every lane takes every edge (the collecting walk's ballots take the whole warp)
+                    edge(oz && hx, ab[i], e1[i], e2[i], xab, xe1, xe2, ends_at(1), c32);
+                    edge(oz && hy, ab[i], e1[i], e2[i], yab, ye1, ye2, ends_at(p.nx), c32);
+                    edge(oz && z + 1 < p.nz, ab[i], e1[i], e2[i], ab[i + 1], e1[i + 1], e2[i + 1], ends_at(plane),
+                         c32);
                 }
             }
             __syncthreads();
