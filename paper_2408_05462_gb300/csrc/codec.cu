@@ -90,6 +90,31 @@ __device__ __forceinline__ void brick_sync(int j)
     asm volatile("bar.sync %0, 64;" ::"r"(1 + j) : "memory");
 }
 
+// Row r's 8 codes at width W <= 8 are bits [8Wr, 8Wr + 8W) of the brick's
+// stream: the W bytes from byte Wr of its slot (words are little-endian),
+// written straight from the row's bits.
+template <int W>
+__device__ __forceinline__ void store_row(uint32_t *slot, int r, const uint32_t (&zz)[8])
+{
+    uint64_t row = 0;
+#pragma unroll
+    for (int x = 0; x < 8; x++) row |= (uint64_t)zz[x] << (W * x);
+    unsigned char *dst = reinterpret_cast<unsigned char *>(slot) + W * r;
+    if (W == 1) {
+        *dst = (unsigned char)row;
+    } else if (W == 2 || W == 6) {
+#pragma unroll
+        for (int b = 0; b < W / 2; b++) reinterpret_cast<uint16_t *>(dst)[b] = (uint16_t)(row >> (16 * b));
+    } else if (W == 4) {
+        *reinterpret_cast<uint32_t *>(dst) = (uint32_t)row;
+    } else if (W == 8) {
+        *reinterpret_cast<uint64_t *>(dst) = row;
+    } else {
+#pragma unroll
+        for (int b = 0; b < W; b++) dst[b] = (unsigned char)(row >> (8 * b));
+    }
+}
+
 template <bool FULL>
 __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ CodecParams p)
 {
@@ -147,7 +172,9 @@ __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ Codec
                 }
         }
     }
-    if (FULL && mine) valid = 0xffu;
+    // a full brick's rows are whole (the threads of a brick that is not
+    // this kernel's compute on zeros and write nothing)
+    if (FULL) valid = 0xffu;
 
     const bool fix = p.fix != 0;
     uint32_t cfp[2] = {0u, 0u};  // count_above(f), one byte per vertex
@@ -232,36 +259,49 @@ __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ Codec
         if (mine && r == 0)
             p.recs[l][c.b] = make_uint4(0u, 0u, (uint32_t)q[0], (uint32_t)w | ((uint32_t)mode << 8) | (nexc << 16));
         // pack: row r's 8 codes are bits [8*r*w, 8*r*w + 8*w) of the brick's
-        // stream; each thread ORs its bits into the zeroed shared words, then
-        // the brick's 16*w words are copied out (and zeroed for the next level)
-        {
+        // stream.  Widths up to 8 go straight to the brick's slot, a row per
+        // thread; wider rows are ORed into the zeroed shared words, then the
+        // brick's 16*w words are copied out (and zeroed for the next level)
+        uint32_t zz[8];
+#pragma unroll
+        for (int x = 0; x < 8; x++) {
+            const bool live = ((valid >> x) & 1u) && !(r == 0 && x == 0);
+            zz[x] = mode ? zigzag(d[x]) : (live ? zigzag(q[x]) : 0u);
+        }
+        uint32_t *slot = p.slot_words[l] + 512ull * c.b;
+        if (w <= 8) {
+            if (mine) switch (w) {  // (uniform across the brick)
+                    case 1: store_row<1>(slot, r, zz); break;
+                    case 2: store_row<2>(slot, r, zz); break;
+                    case 3: store_row<3>(slot, r, zz); break;
+                    case 4: store_row<4>(slot, r, zz); break;
+                    case 5: store_row<5>(slot, r, zz); break;
+                    case 6: store_row<6>(slot, r, zz); break;
+                    case 7: store_row<7>(slot, r, zz); break;
+                    case 8: store_row<8>(slot, r, zz); break;
+                    default: break;  // w = 0: no words
+                }
+        } else {
             const uint32_t bit0 = 8u * (uint32_t)r * (uint32_t)w;
             uint32_t wi = bit0 >> 5;
             int pos = (int)(bit0 & 31u);
             uint64_t acc = 0;
-            if (w > 0) {
 #pragma unroll
-                for (int x = 0; x < 8; x++) {
-                    const bool live = ((valid >> x) & 1u) && !(r == 0 && x == 0);
-                    const uint32_t zz = mode ? zigzag(d[x]) : (live ? zigzag(q[x]) : 0u);
-                    acc |= (uint64_t)zz << pos;
-                    pos += w;
-                    if (pos >= 32) {
-                        if ((uint32_t)acc && CHR_IN_BOUNDS(wi < 512u)) atomicOr(&s_pk[j][wi], (uint32_t)acc);
-                        acc >>= 32;
-                        pos -= 32;
-                        wi++;
-                    }
+            for (int x = 0; x < 8; x++) {
+                acc |= (uint64_t)zz[x] << pos;
+                pos += w;
+                if (pos >= 32) {
+                    if ((uint32_t)acc && CHR_IN_BOUNDS(wi < 512u)) atomicOr(&s_pk[j][wi], (uint32_t)acc);
+                    acc >>= 32;
+                    pos -= 32;
+                    wi++;
                 }
-                if (pos > 0 && (uint32_t)acc && CHR_IN_BOUNDS(wi < 512u)) atomicOr(&s_pk[j][wi], (uint32_t)acc);
             }
-        }
-        brick_sync(j);
-        {
-            uint32_t *dst = p.slot_words[l] + 512ull * c.b;
+            if (pos > 0 && (uint32_t)acc && CHR_IN_BOUNDS(wi < 512u)) atomicOr(&s_pk[j][wi], (uint32_t)acc);
+            brick_sync(j);
             const int nw = 16 * w;
             for (int jw = r; jw < nw; jw += 64) {
-                if (mine) dst[jw] = s_pk[j][jw];
+                if (mine) slot[jw] = s_pk[j][jw];
                 s_pk[j][jw] = 0u;
             }
         }
