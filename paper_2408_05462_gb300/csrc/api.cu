@@ -161,7 +161,7 @@ void fill_codec_params(const chr_handle *h, CodecParams &p)
         p.exc_val[l] = h->d_exc_val[l];
     }
     p.nK = (int32_t)h->n_iso;
-    for (uint32_t j = 0; j < h->n_iso; j++) p.K[j] = h->iso[j];
+    for (uint32_t j = 0; j < CHR_MAX_ISO; j++) p.K[j] = (j < h->n_iso) ? h->iso[j] : -INFINITY;  // (-inf: never above a value)
     p.fix = (h->topo_mode == CHR_TOPO_FIX) ? 1 : 0;
     float ks[CHR_MAX_ISO];
     const int nK = (int)h->n_iso;

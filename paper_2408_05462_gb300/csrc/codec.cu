@@ -37,14 +37,34 @@ __device__ __forceinline__ float warp_max_f32(float v)
     return r;
 }
 
+// max(a, b), NaN when either is NaN
+__device__ __forceinline__ float fmax_nan(float a, float b)
+{
+    float r;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+
 // Number of candidate isovalues strictly above v (K sorted ascending).  Two
 // values lie on the same side of every k exactly when these counts agree,
 // because {j : v < K[j]} is always a suffix of the sorted K.
-__device__ __forceinline__ int count_above(float v, const float *K, int nK)
+// K[j] for j >= nK is -inf (never above anything), so NK may be any bound
+// >= nK.
+template <int NK>
+__device__ __forceinline__ int count_above(float v, const float *K)
 {
     int c = 0;
-    for (int j = 0; j < nK; j++) c += (v < K[j]) ? 1 : 0;
+#pragma unroll
+    for (int j = 0; j < NK; j++) c += (v < K[j]) ? 1 : 0;
     return c;
+}
+
+// count_above of the row's 8 values, one byte each
+template <int NK>
+__device__ __forceinline__ void count_above_row(const float (&f)[8], const float *K, uint32_t (&cfp)[2])
+{
+#pragma unroll
+    for (int x = 0; x < 8; x++) cfp[x >> 2] |= (uint32_t)count_above<NK>(f[x], K) << (8 * (x & 3));
 }
 
 // One level of the residual chain for one vertex (paper Sec. 2 accuracy
@@ -96,9 +116,22 @@ __device__ __forceinline__ void brick_sync(int j)
 template <int W>
 __device__ __forceinline__ void store_row(uint32_t *slot, int r, const uint32_t (&zz)[8])
 {
-    uint64_t row = 0;
+    // every code is below 2^W, so the row's two 32-bit halves are built
+    // directly (a code that straddles bit 32 goes to both)
+    uint32_t lo = 0u, hi = 0u;
 #pragma unroll
-    for (int x = 0; x < 8; x++) row |= (uint64_t)zz[x] << (W * x);
+    for (int x = 0; x < 8; x++) {
+        const int sh = W * x;
+        if (sh + W <= 32) {
+            lo |= zz[x] << sh;
+        } else if (sh >= 32) {
+            hi |= zz[x] << (sh - 32);
+        } else {
+            lo |= zz[x] << sh;
+            hi |= zz[x] >> (32 - sh);
+        }
+    }
+    const uint64_t row = ((uint64_t)hi << 32) | lo;
     unsigned char *dst = reinterpret_cast<unsigned char *>(slot) + W * r;
     if (W == 1) {
         *dst = (unsigned char)row;
@@ -179,8 +212,11 @@ __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ Codec
     const bool fix = p.fix != 0;
     uint32_t cfp[2] = {0u, 0u};  // count_above(f), one byte per vertex
     if (fix) {
-#pragma unroll
-        for (int x = 0; x < 8; x++) cfp[x >> 2] |= (uint32_t)count_above(f[x], p.K, p.nK) << (8 * (x & 3));
+        if (p.nK <= 1) count_above_row<1>(f, p.K, cfp);
+        else if (p.nK <= 2) count_above_row<2>(f, p.K, cfp);
+        else if (p.nK <= 4) count_above_row<4>(f, p.K, cfp);
+        else if (p.nK <= 8) count_above_row<8>(f, p.K, cfp);
+        else count_above_row<CHR_MAX_ISO>(f, p.K, cfp);
     }
     float R[8];
 #pragma unroll
@@ -230,26 +266,27 @@ __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ Codec
 #pragma unroll
             for (int x = 0; x < 8; x++) d[x] = (int32_t)((uint32_t)d[x] - (uint32_t)below[x]);
 
+        // the widths: bitlen of the largest zig-zag code = bitlen of their OR
         uint32_t maxl = 0, maxn = 0;
 #pragma unroll
         for (int x = 0; x < 8; x++) {
             const bool live = ((valid >> x) & 1u) && !(r == 0 && x == 0);
             if (!live) d[x] = 0;  // d is only read for packing from here on
-            maxl = max(maxl, zigzag(d[x]));
-            maxn = max(maxn, live ? zigzag(q[x]) : 0u);
+            maxl |= zigzag(d[x]);
+            maxn |= live ? zigzag(q[x]) : 0u;
         }
         const uint32_t cnt = __popc(excm);
         const uint32_t inc = warp_incl_scan_u32(cnt, lane);
-        maxl = __reduce_max_sync(CHR_FULL_MASK, maxl);
-        maxn = __reduce_max_sync(CHR_FULL_MASK, maxn);
+        maxl = __reduce_or_sync(CHR_FULL_MASK, maxl);
+        maxn = __reduce_or_sync(CHR_FULL_MASK, maxn);
         if (lane == 31) {
             s_red[j][wb][0] = maxl;
             s_red[j][wb][1] = maxn;
             s_red[j][wb][2] = inc;
         }
         brick_sync(j);
-        maxl = max(s_red[j][0][0], s_red[j][1][0]);
-        maxn = max(s_red[j][0][1], s_red[j][1][1]);
+        maxl = s_red[j][0][0] | s_red[j][1][0];
+        maxn = s_red[j][0][1] | s_red[j][1][1];
         const uint32_t tot0 = s_red[j][0][2];
         const uint32_t nexc = tot0 + s_red[j][1][2];
         const uint32_t exc_rank = inc - cnt + (wb ? tot0 : 0u);
@@ -331,11 +368,14 @@ __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ Codec
 #pragma unroll
             for (int x = 0; x < 8; x++)
                 if ((valid >> x) & 1u) {
-                    const float v = isnan(R[x]) ? inf : __fadd_rn(R[x], 0.0f);
-                    mn = fminf(mn, v);
-                    mx = fmaxf(mx, v);
-                    if (x == 0) a0 = b0 = v;
+                    mn = fminf(mn, R[x]);      // a NaN never lowers it (as +inf would not)
+                    mx = fmax_nan(mx, R[x]);   // NaN once any value is
                 }
+            // NaN as +inf; +0 added to the extremes, which are zeros exactly
+            // when some value is a zero (either sign) and none is beyond it
+            mn = __fadd_rn(mn, 0.0f);
+            mx = __fadd_rn(isnan(mx) ? inf : mx, 0.0f);
+            if (valid & 1u) a0 = b0 = isnan(R[0]) ? inf : __fadd_rn(R[0], 0.0f);
             if (r == 0) {  // the y = z = 0 line and the corner
                 s_rng[j][2][0] = make_float2(mn, mx);
                 s_rng[j][2][1] = make_float2(a0, b0);

@@ -42,7 +42,7 @@ struct CodecParams {
     int32_t nK;
     int32_t fix;
     float e[CHR_MAX_LEVELS], two_e[CHR_MAX_LEVELS], inv2e[CHR_MAX_LEVELS];
-    float K[CHR_MAX_ISO];
+    float K[CHR_MAX_ISO];  // the isovalues, -inf past nK
     // encoder sign check: a vertex with c candidates strictly above its value
     // keeps every sign exactly when its reconstruction lies in
     // [kdn[c], kup[c]): kup[c] the smallest of those c candidates (+inf if
