@@ -748,6 +748,30 @@ __device__ __forceinline__ void decode_brick(const CodecParams &p, const BrickCo
     if (bx0 + xhi > p.box_dim[0]) xhi = (int)(p.box_dim[0] - bx0);
     const bool vec = (xlo == 0) && (xhi == 8) && ((p.out_sx & 3) == 0) && ((p.out_sy & 3) == 0) &&
                      ((bx0 & 3) == 0) && ((reinterpret_cast<uintptr_t>(p.out) & 15u) == 0);
+    if (vec) {  // (uniform across the warp)
+        // through the warp's first level buffer, so that two neighbouring
+        // lanes write one row's 32 bytes (whole sectors) per store
+        float *fb = reinterpret_cast<float *>(s_dyn + warp * (kDecGroup * kLevelWords));
+#pragma unroll
+        for (int s = 0; s < 2; s++) {
+            const int slot = 8 * (lane + 32 * s);
+            *reinterpret_cast<float4 *>(fb + slot) = make_float4(R[s][0], R[s][1], R[s][2], R[s][3]);
+            *reinterpret_cast<float4 *>(fb + slot + 4) = make_float4(R[s][4], R[s][5], R[s][6], R[s][7]);
+        }
+        __syncwarp();
+        const int half = lane & 1;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int r = (lane >> 1) + 16 * k;  // row r: y = r & 7, z = r >> 3
+            const int64_t y = (int64_t)c.by * 8 + (r & 7) - p.box_org[1];
+            const int64_t z = (int64_t)c.bz * 8 + (r >> 3) - p.box_org[2];
+            if (y < 0 || z < 0 || y >= p.box_dim[1] || z >= p.box_dim[2]) continue;
+            if (y + p.box_org[1] >= p.ny || z + p.box_org[2] >= p.nz) continue;
+            __stcs(reinterpret_cast<float4 *>(p.out + bx0 + p.out_sx * y + p.out_sy * z) + half,
+                   *reinterpret_cast<const float4 *>(fb + 8 * r + 4 * half));
+        }
+        return;
+    }
 #pragma unroll
     for (int s = 0; s < 2; s++) {
         const int64_t y = (int64_t)c.by * 8 + ly - p.box_org[1];
