@@ -208,6 +208,7 @@ chr_status translate_impl(const float *d_field, const Grid &g, const float *K, u
                           float *eb_out, uint64_t *count_out)
 {
     constexpr int kBins = 4096;
+    constexpr int64_t kSampleStep = 16;  // the sample walks every 16th item
     const size_t sb = translate_scratch_bytes();
     char *scr = (char *)al.get(sb);
     if (!scr) return fail(CHR_ERR_OOM, "chr_topo_translate: allocator returned NULL");
@@ -217,6 +218,7 @@ chr_status translate_impl(const float *d_field, const Grid &g, const float *K, u
     sc.count = reinterpret_cast<unsigned long long *>(scr + kBins * 8);
     sc.minbits = reinterpret_cast<unsigned int *>(scr + kBins * 8 + 8);
     sc.ncoll = reinterpret_cast<unsigned long long *>(scr + kBins * 8 + 16);
+    sc.count_lo = reinterpret_cast<unsigned long long *>(scr + kBins * 8 + 24);
     chr_status st = CHR_OK;
     std::vector<unsigned long long> hist(kBins);
     unsigned long long count = 0;
@@ -236,28 +238,123 @@ chr_status translate_impl(const float *d_field, const Grid &g, const float *K, u
         rank = 0;
         return nb - 1;
     };
+    auto rank_of = [&](unsigned long long n) {  // the rank (from 0) of the element the accuracy names
+        const double r = floor((1.0 - (double)accuracy) * (double)n);
+        unsigned long long k = (r < 0) ? 0ull : (unsigned long long)r;
+        return (k > n - 1) ? n - 1 : k;
+    };
+    auto zero_scratch = [&]() -> cudaError_t {
+        cudaError_t e = cudaMemsetAsync(scr, 0, kBins * 8 + 32, al.s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(sc.minbits, 0xff, 4, al.s);
+        return e;
+    };
+    // the n collected values (each below 2^30) whose digits select rank `rank`:
+    // bits 20..29, then 10..19, then 0..9, one histogram pass each
+    auto select3 = [&](unsigned long long n, unsigned long long rank, uint32_t &out) -> cudaError_t {
+        uint32_t above = 0;
+        for (int shift = 20; shift >= 0; shift -= 10) {
+            cudaError_t e;
+            if ((e = cudaMemsetAsync(sc.hist, 0, 1024 * 8, al.s)) != cudaSuccess ||
+                (e = launch_translate_select(coll, n, shift, above, sc.hist, al.s)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(hist.data(), sc.hist, 1024 * 8, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess ||
+                (e = cudaStreamSynchronize(al.s)) != cudaSuccess)
+                return e;
+            above = (above << 10) | (uint32_t)pick(hist, 1024, rank);
+        }
+        out = above;
+        return cudaSuccess;
+    };
     do {
         cudaError_t e;
         const bool min_only = (accuracy >= 1.0f);
-        if ((e = cudaMemsetAsync(scr, 0, kBins * 8 + 24, al.s)) != cudaSuccess ||
-            (e = cudaMemsetAsync(sc.minbits, 0xff, 4, al.s)) != cudaSuccess ||
-            (e = launch_translate_pass(d_field, g, K, (int)nK, min_only ? 0 : 1, 0u, sc, al.s)) != cudaSuccess ||
+        if (min_only) {
+            if ((e = zero_scratch()) != cudaSuccess ||
+                (e = launch_translate_pass(d_field, g, K, (int)nK, 0, 0u, sc, al.s)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(&count, sc.count, 8, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(&minbits, sc.minbits, 4, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess ||
+                (e = cudaStreamSynchronize(al.s)) != cudaSuccess) {
+                st = cuda_fail(e, "chr_topo_translate");
+                break;
+            }
+            if (count) memcpy(&eb, &minbits, 4);
+            break;
+        }
+
+        // the sampled walk and the range that should hold rank n
+        int64_t items = 0;
+        unsigned long long count_s = 0;
+        if ((e = zero_scratch()) != cudaSuccess ||
+            (e = launch_translate_pass(d_field, g, K, (int)nK, 1, 0u, sc, al.s, 0u, 0u, kSampleStep, &items)) !=
+                cudaSuccess ||
+            (e = cudaMemcpyAsync(&count_s, sc.count, 8, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(hist.data(), sc.hist, kBins * 8, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(al.s)) != cudaSuccess) {
+            st = cuda_fail(e, "chr_topo_translate");
+            break;
+        }
+        bool done = false;
+        if (count_s >= 4096) {
+            const double scale = (double)items / (double)((items + kSampleStep - 1) / kSampleStep);
+            const double rs = floor((1.0 - (double)accuracy) * (double)count_s * scale) / scale;  // rank n in the sample
+            // 3% either side of it, plus four standard deviations of a
+            // binomial count (the sample misses that much only when it does
+            // not represent the field, and then the exact walks follow)
+            const double margin = 0.03 * rs + 4.0 * sqrt(rs + 1.0) + 32.0;
+            unsigned long long r_lo = (unsigned long long)std::max(0.0, rs - margin);
+            unsigned long long r_hi = (unsigned long long)std::min((double)(count_s - 1), rs + margin);
+            const uint32_t b_lo = (uint32_t)pick(hist, kBins, r_lo), b_hi = (uint32_t)pick(hist, kBins, r_hi);
+            // (elements are non-negative floats: bucket 2040 holds +inf, so b_hi + 1 never wraps)
+            if (b_hi - b_lo < 1024) {
+                unsigned long long in_s = 0;
+                for (uint32_t b = b_lo; b <= b_hi; b++) in_s += hist[b];
+                const unsigned long long cap = (unsigned long long)(1.5 * (double)in_s * scale) + 65536;
+                coll_bytes = cap * 4;
+                if (!(coll = (uint32_t *)al.get(coll_bytes))) {
+                    st = fail(CHR_ERR_OOM, "chr_topo_translate: allocator returned NULL");
+                    break;
+                }
+                sc.coll = coll;
+                sc.cap = cap;
+                const uint32_t lo_bits = b_lo << 20, hi_bits = (b_hi + 1) << 20;
+                unsigned long long got = 0, below = 0;
+                if ((e = zero_scratch()) != cudaSuccess ||
+                    (e = launch_translate_pass(d_field, g, K, (int)nK, 3, 0u, sc, al.s, lo_bits, hi_bits)) !=
+                        cudaSuccess ||
+                    (e = cudaMemcpyAsync(&count, sc.count, 8, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess ||
+                    (e = cudaMemcpyAsync(&below, sc.count_lo, 8, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess ||
+                    (e = cudaMemcpyAsync(&got, sc.ncoll, 8, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess ||
+                    (e = cudaStreamSynchronize(al.s)) != cudaSuccess) {
+                    st = cuda_fail(e, "chr_topo_translate");
+                    break;
+                }
+                const unsigned long long rank = count ? rank_of(count) : 0ull;
+                if (count && got <= cap && below <= rank && rank < below + got) {
+                    uint32_t off = 0;
+                    if ((e = select3(got, rank - below, off)) != cudaSuccess) {
+                        st = cuda_fail(e, "chr_topo_translate");
+                        break;
+                    }
+                    const uint32_t bits = lo_bits + off;
+                    memcpy(&eb, &bits, 4);
+                    done = true;
+                }
+                al.put(coll, coll_bytes);
+                coll = nullptr;
+            }
+        }
+        if (done) break;
+
+        // the exact two-walk selection
+        if ((e = zero_scratch()) != cudaSuccess ||
+            (e = launch_translate_pass(d_field, g, K, (int)nK, 1, 0u, sc, al.s)) != cudaSuccess ||
             (e = cudaMemcpyAsync(&count, sc.count, 8, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(&minbits, sc.minbits, 4, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess ||
-            (!min_only &&
-             (e = cudaMemcpyAsync(hist.data(), sc.hist, kBins * 8, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess) ||
+            (e = cudaMemcpyAsync(hist.data(), sc.hist, kBins * 8, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess ||
             (e = cudaStreamSynchronize(al.s)) != cudaSuccess) {
             st = cuda_fail(e, "chr_topo_translate");
             break;
         }
         if (count == 0) break;
-        if (min_only) {
-            memcpy(&eb, &minbits, 4);
-            break;
-        }
-        double r = floor((1.0 - (double)accuracy) * (double)count);
-        unsigned long long rank = (r < 0) ? 0ull : (unsigned long long)r;
-        if (rank > count - 1) rank = count - 1;
+        unsigned long long rank = rank_of(count);
         const uint32_t b1 = (uint32_t)pick(hist, kBins, rank);
         const unsigned long long nb = hist[b1];
         coll_bytes = nb * 4;
@@ -270,9 +367,6 @@ chr_status translate_impl(const float *d_field, const Grid &g, const float *K, u
         unsigned long long got = 0;
         if ((e = launch_translate_pass(d_field, g, K, (int)nK, 2, b1, sc, al.s)) != cudaSuccess ||
             (e = cudaMemcpyAsync(&got, sc.ncoll, 8, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess ||
-            (e = cudaMemsetAsync(sc.hist, 0, 1024 * 8, al.s)) != cudaSuccess ||
-            (e = launch_translate_select(coll, nb, 10, 0u, sc.hist, al.s)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(hist.data(), sc.hist, 1024 * 8, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess ||
             (e = cudaStreamSynchronize(al.s)) != cudaSuccess) {
             st = cuda_fail(e, "chr_topo_translate");
             break;
@@ -281,16 +375,21 @@ chr_status translate_impl(const float *d_field, const Grid &g, const float *K, u
             st = fail(CHR_ERR_CUDA, "chr_topo_translate: the collecting walk found a different bucket size");
             break;
         }
-        const uint32_t b2 = (uint32_t)pick(hist, 1024, rank);
-        if ((e = cudaMemsetAsync(sc.hist, 0, 1024 * 8, al.s)) != cudaSuccess ||
-            (e = launch_translate_select(coll, nb, 0, b2, sc.hist, al.s)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(hist.data(), sc.hist, 1024 * 8, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess ||
-            (e = cudaStreamSynchronize(al.s)) != cudaSuccess) {
+        // the bucket's values are its elements' low 20 bits: digits 10..19, then 0..9
+        uint32_t above = 0;
+        for (int shift = 10; shift >= 0; shift -= 10) {
+            if ((e = cudaMemsetAsync(sc.hist, 0, 1024 * 8, al.s)) != cudaSuccess ||
+                (e = launch_translate_select(coll, nb, shift, above, sc.hist, al.s)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(hist.data(), sc.hist, 1024 * 8, cudaMemcpyDeviceToHost, al.s)) != cudaSuccess ||
+                (e = cudaStreamSynchronize(al.s)) != cudaSuccess)
+                break;
+            above = (above << 10) | (uint32_t)pick(hist, 1024, rank);
+        }
+        if (e != cudaSuccess) {
             st = cuda_fail(e, "chr_topo_translate");
             break;
         }
-        const uint32_t b3 = (uint32_t)pick(hist, 1024, rank);
-        const uint32_t bits = (b1 << 20) | (b2 << 10) | b3;
+        const uint32_t bits = (b1 << 20) | above;
         memcpy(&eb, &bits, 4);
     } while (0);
     if (coll) al.put(coll, coll_bytes);

@@ -187,15 +187,21 @@ struct TranslateScratch {
     unsigned long long *hist;  // 4096 counters
     unsigned long long *count; // |D|
     unsigned int *minbits;     // min D as float bits
-    unsigned long long *ncoll; // elements appended (mode 2)
-    uint32_t *coll;            // mode 2 output
+    unsigned long long *ncoll; // elements appended (modes 2, 3)
+    unsigned long long *count_lo;  // elements below lo_bits (mode 3)
+    uint32_t *coll;            // modes 2, 3 output
     unsigned long long cap;
 };
 size_t translate_scratch_bytes();
+// One walk over the field's edges (mode 0 minimum, 1 histogram, 2 collect
+// the bucket `prefix`, 3 count below lo_bits and collect [lo_bits,
+// hi_bits)); item_step > 1 walks every item_step-th item only (a sample);
+// n_items (if set) receives the number of items of the whole walk.
 cudaError_t launch_translate_pass(const float *field, const Grid &g, const float *K, int nK, int mode,
-                                  uint32_t prefix, TranslateScratch sc, cudaStream_t s);
+                                  uint32_t prefix, TranslateScratch sc, cudaStream_t s, uint32_t lo_bits = 0,
+                                  uint32_t hi_bits = 0, int64_t item_step = 1, int64_t *n_items = nullptr);
 // Histogram (1024 bins, hist) of bits [shift, shift+10) of the n collected
-// values whose bits [shift+10, 20) equal `above`.
+// values whose bits from shift+10 up equal `above`.
 cudaError_t launch_translate_select(const uint32_t *coll, unsigned long long n, int shift, uint32_t above,
                                     unsigned long long *hist, cudaStream_t s);
 

@@ -2,10 +2,16 @@
 // d1 = s1 - k over every grid edge with s0 < k < s1, and its smallest or n-th
 // smallest element.  D is never materialised whole (non-negative floats order
 // like their bit patterns): one walk over the edges takes the minimum
-// (accuracy 1); for the n-th smallest, a first walk builds a 4096-bin
-// histogram of the elements' top 12 bits, a second appends every element of
-// the bucket that holds rank n to a compact array, and two small histogram
-// passes over that array (bits 10..19, then 0..9) select the element exactly.
+// (accuracy 1).  For the n-th smallest, a walk over a sample of the field
+// (every 16th item) builds a 4096-bin histogram of the elements' top 12
+// bits, from which a range of buckets that should hold rank n is chosen; one
+// walk over the whole field then counts the elements below the range and
+// appends those inside it to a compact array, and small histogram passes
+// over that array select the element exactly.  When the range misses rank n
+// (an unrepresentative sample), the exact two-walk selection runs instead: a
+// 4096-bin histogram of the whole field names the bucket that holds rank n,
+// a second walk appends that bucket's elements, and two histogram passes
+// over them (bits 10..19, then 0..9) select the element.
 //
 // Each vertex v is summarised against the sorted isovalues by a = #{k < v}
 // and b = #{k > v}.  An edge (s, t) then holds c1 = a_t + b_s - nK isovalues
@@ -49,7 +55,9 @@ struct TrParams {
     float Klt[CHR_MAX_ISO];  // sorted isovalues, +inf past nK (never below a vertex)
     float Kgt[CHR_MAX_ISO];  // sorted isovalues, -inf past nK (never above a vertex)
     uint32_t prefix;         // collect: the top 12 bits of the elements kept
+    uint32_t lo_bits, hi_bits;  // range: elements below lo_bits are counted, those in [lo_bits, hi_bits) kept
     int64_t tiles_x, tiles_y, zc, items;
+    int64_t item_step;       // every item_step-th item (1: all; more: a sample)
     TranslateScratch sc;
 };
 
@@ -76,8 +84,10 @@ __device__ __forceinline__ uint32_t tr_lanemask_lt()
 constexpr int kTrHistBins = 4096;  // the first walk's key: the top 12 bits
 
 // MODE: kTrMin (the minimum), kTrHist (the 12-bit histogram), kTrCollect
-// (the elements whose top 12 bits are p.prefix, appended to p.sc.coll).
-enum { kTrMin = 0, kTrHist = 1, kTrCollect = 2 };
+// (the elements whose top 12 bits are p.prefix, appended to p.sc.coll),
+// kTrRange (the elements below p.lo_bits counted, those in [p.lo_bits,
+// p.hi_bits) appended less p.lo_bits).
+enum { kTrMin = 0, kTrHist = 1, kTrCollect = 2, kTrRange = 3 };
 
 template <int NK, int MODE>
 __global__ void __launch_bounds__(kTrWarps * 32, kTrBlocksPerSm) k_translate(const __grid_constant__ TrParams p)
@@ -87,7 +97,7 @@ __global__ void __launch_bounds__(kTrWarps * 32, kTrBlocksPerSm) k_translate(con
     __shared__ unsigned int s_hist[MODE == kTrHist ? kTrHistBins : 1];
     __shared__ float s_kup[CHR_MAX_ISO + 1];  // sorted isovalues, +inf at nK
     __shared__ float s_kdn[CHR_MAX_ISO + 1];  // -inf, then the sorted isovalues
-    __shared__ unsigned long long s_cnt;
+    __shared__ unsigned long long s_cnt, s_lo;
     __shared__ unsigned int s_min;
 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -100,33 +110,41 @@ __global__ void __launch_bounds__(kTrWarps * 32, kTrBlocksPerSm) k_translate(con
     }
     if (threadIdx.x == 0) {
         s_cnt = 0ull;
+        s_lo = 0ull;
         s_min = 0xffffffffu;
     }
     __syncthreads();
 
-    unsigned long long cnt = 0;
+    unsigned long long cnt = 0, cnt_lo = 0;
+    uint32_t lo32 = 0;  // range: elements below lo_bits in the current item
     unsigned int mn = 0xffffffffu;
     const int nK = p.nK;
     const int64_t plane = p.nx * p.ny;
 
-    // one element of D (where `valid`): into the histogram, or (collect)
-    // appended when its top 12 bits match, by one atomic per group of lanes
-    // that append together.  CONV: all 32 lanes call it together
+    // v appended to p.sc.coll where `want`, by one atomic per group of
+    // lanes that append together.  CONV: all 32 lanes call it together
+    auto append = [&](bool want, uint32_t v, auto conv) {
+        const uint32_t m = decltype(conv)::value ? __ballot_sync(CHR_FULL_MASK, want) : __ballot_sync(__activemask(), want);
+        if (want) {
+            const int leader = __ffs(m) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(p.sc.ncoll, (unsigned long long)__popc(m));
+            base = __shfl_sync(m, base, leader);
+            const unsigned long long at = base + __popc(m & tr_lanemask_lt());
+            if (at < p.sc.cap) p.sc.coll[at] = v;
+        }
+    };
+    // one element of D (where `valid`): into the histogram, or appended when
+    // its top 12 bits match (collect) or when it lies in the range (range)
     auto put = [&](bool valid, uint32_t bits, auto conv) {
         if (MODE == kTrHist) {
             if (valid) atomicAdd(&s_hist[bits >> 20], 1u);
         } else if (MODE == kTrCollect) {
-            const bool want = valid && (bits >> 20) == p.prefix;
-            const uint32_t m = decltype(conv)::value ? __ballot_sync(CHR_FULL_MASK, want)
-                                                     : __ballot_sync(__activemask(), want);
-            if (want) {
-                const int leader = __ffs(m) - 1;
-                unsigned long long base = 0;
-                if (lane == leader) base = atomicAdd(p.sc.ncoll, (unsigned long long)__popc(m));
-                base = __shfl_sync(m, base, leader);
-                const unsigned long long at = base + __popc(m & tr_lanemask_lt());
-                if (at < p.sc.cap) p.sc.coll[at] = bits & 0xfffffu;
-            }
+            append(valid && (bits >> 20) == p.prefix, bits & 0xfffffu, conv);
+        } else if (MODE == kTrRange) {
+            const bool below = valid && bits < p.lo_bits;
+            lo32 += below ? 1u : 0u;
+            append(valid && !below && bits < p.hi_bits, bits - p.lo_bits, conv);
         }
     };
     // one edge (where `on`): s the vertex, t its neighbour, each given by its
@@ -141,7 +159,7 @@ __global__ void __launch_bounds__(kTrWarps * 32, kTrBlocksPerSm) k_translate(con
             if (c1 > 0) mn = min(mn, min(up_s, dn_t));
             if (c2 > 0) mn = min(mn, min(up_t, dn_s));
         } else {
-            if (MODE == kTrHist) c32 += (uint32_t)(max(c1, 0) + max(c2, 0));
+            if (MODE == kTrHist || MODE == kTrRange) c32 += (uint32_t)(max(c1, 0) + max(c2, 0));
             const bool s_low = c1 > 0;
             const int c = s_low ? c1 : c2;
             // d0 of the lowest crossing isovalue and d1 of the highest
@@ -160,7 +178,7 @@ __global__ void __launch_bounds__(kTrWarps * 32, kTrBlocksPerSm) k_translate(con
         }
     };
 
-    for (int64_t it = blockIdx.x; it < p.items; it += gridDim.x) {
+    for (int64_t it = (int64_t)blockIdx.x * p.item_step; it < p.items; it += (int64_t)gridDim.x * p.item_step) {
         const int64_t tx = it % p.tiles_x, r = it / p.tiles_x;
         const int64_t ty = r % p.tiles_y, tz = r / p.tiles_y;
         const int64_t x = tx * kTrOwnX + lane, y = ty * kTrOwnY + w;
@@ -233,20 +251,25 @@ __global__ void __launch_bounds__(kTrWarps * 32, kTrBlocksPerSm) k_translate(con
             e2[0] = e2[kTrG];
         }
         cnt += 2ull * c32;  // d0 and d1 per crossing; c32 <= 3 * 16 per plane, and an item spans <= 2^20 planes
+        cnt_lo += lo32;
+        lo32 = 0;
     }
 
     // block reduction, then one global update per block
     for (int o = 16; o > 0; o >>= 1) {
         cnt += __shfl_xor_sync(CHR_FULL_MASK, cnt, o);
+        if (MODE == kTrRange) cnt_lo += __shfl_xor_sync(CHR_FULL_MASK, cnt_lo, o);
         mn = min(mn, __shfl_xor_sync(CHR_FULL_MASK, mn, o));
     }
     if (lane == 0) {
         if (cnt) atomicAdd(&s_cnt, cnt);
+        if (MODE == kTrRange && cnt_lo) atomicAdd(&s_lo, cnt_lo);
         if (MIN) atomicMin(&s_min, mn);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         if (s_cnt && MODE != kTrCollect) atomicAdd(p.sc.count, s_cnt);
+        if (MODE == kTrRange && s_lo) atomicAdd(p.sc.count_lo, s_lo);
         if (MIN) atomicMin(p.sc.minbits, s_min);
     }
     if (MODE == kTrHist)
@@ -254,8 +277,8 @@ __global__ void __launch_bounds__(kTrWarps * 32, kTrBlocksPerSm) k_translate(con
             if (s_hist[i]) atomicAdd(p.sc.hist + i, (unsigned long long)s_hist[i]);
 }
 
-// Histogram of bits [shift, shift + 10) of the collected elements (the low
-// 20 bits of each), over those whose bits [shift + 10, 20) equal `above`.
+// Histogram of bits [shift, shift + 10) of the collected values, over those
+// whose bits from shift + 10 up equal `above`.
 __global__ void __launch_bounds__(256) k_select_hist(const uint32_t *coll, unsigned long long n, int shift,
                                                      uint32_t above, unsigned long long *hist)
 {
@@ -279,8 +302,10 @@ void launch_nk(const TrParams &p, int mode, unsigned blocks, cudaStream_t s)
         k_translate<NK, kTrMin><<<blocks, kTrWarps * 32, 0, s>>>(p);
     else if (mode == kTrHist)
         k_translate<NK, kTrHist><<<blocks, kTrWarps * 32, 0, s>>>(p);
-    else
+    else if (mode == kTrCollect)
         k_translate<NK, kTrCollect><<<blocks, kTrWarps * 32, 0, s>>>(p);
+    else
+        k_translate<NK, kTrRange><<<blocks, kTrWarps * 32, 0, s>>>(p);
 }
 
 }  // namespace
@@ -300,7 +325,8 @@ cudaError_t launch_translate_select(const uint32_t *coll, unsigned long long n, 
 }
 
 cudaError_t launch_translate_pass(const float *field, const Grid &g, const float *K, int nK, int mode,
-                                  uint32_t prefix, TranslateScratch sc, cudaStream_t s)
+                                  uint32_t prefix, TranslateScratch sc, cudaStream_t s, uint32_t lo_bits,
+                                  uint32_t hi_bits, int64_t item_step, int64_t *n_items)
 {
     if (nK < 1 || nK > CHR_MAX_ISO) return cudaErrorInvalidValue;
     TrParams p;
@@ -317,6 +343,9 @@ cudaError_t launch_translate_pass(const float *field, const Grid &g, const float
         p.Kgt[j] = (j < nK) ? ks[j] : -INFINITY;
     }
     p.prefix = prefix;
+    p.lo_bits = lo_bits;
+    p.hi_bits = hi_bits;
+    p.item_step = item_step < 1 ? 1 : item_step;
     p.sc = sc;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
@@ -331,7 +360,8 @@ cudaError_t launch_translate_pass(const float *field, const Grid &g, const float
     p.zc = std::min<int64_t>((g.nz + chunks - 1) / chunks, 1 << 20);
     chunks = (g.nz + p.zc - 1) / p.zc;
     p.items = tiles * chunks;
-    const unsigned blocks = (unsigned)std::min<int64_t>(p.items, grid);
+    if (n_items) *n_items = p.items;
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((p.items + p.item_step - 1) / p.item_step, grid));
     if (nK <= 1)
         launch_nk<1>(p, mode, blocks, s);
     else if (nK <= 2)

@@ -386,6 +386,37 @@ def test_translate_values_on_isovalues_and_non_finite(acc):
         assert np.float32(eb_g).view(np.uint32) == np.float32(eb_o).view(np.uint32)
 
 
+@pytest.mark.parametrize("acc", [0.99, 0.95, 0.5, 0.05])
+def test_translate_sampled_range_matches_oracle(acc):
+    # large enough that the sampled walk sees thousands of elements, so the
+    # n-th smallest comes from the range walk (the exact two walks are the
+    # fallback); 4 isovalues
+    f = synth.turbulence((96, 80, 112), seed=31)
+    K = [-1.0, -0.5, 0.5, 1.0]
+    eb_o, n_o = oracle.translate_eb(f, K, acc)
+    eb_g, n_g = chr.chr_topo_translate(_dev(f), K, acc)
+    assert n_g == n_o
+    assert np.float32(eb_g).view(np.uint32) == np.float32(eb_o).view(np.uint32)
+
+
+def test_translate_unrepresentative_sample_falls_back():
+    # 16 tiles of 31 columns along x and one-plane z chunks: the sampled walk
+    # (every 16th item) sees only the band x < 31, whose crossings are far
+    # from the isovalue, while the rest of the field crosses it closely; the
+    # range chosen from the sample misses rank n and the exact walks decide
+    rng = np.random.default_rng(5)
+    nz, ny, nx = 64, 15, 496
+    f = (0.5 + 1e-3 * rng.standard_normal((nz, ny, nx))).astype(np.float32)
+    band = np.where((np.indices((nz, ny, 31)).sum(axis=0) % 2) == 0, 5.0, -5.0).astype(np.float32)
+    f[:, :, :31] = band + rng.uniform(-0.5, 0.5, (nz, ny, 31)).astype(np.float32)
+    K = [0.5]
+    for acc in (0.95, 0.5):
+        eb_o, n_o = oracle.translate_eb(f, K, acc)
+        eb_g, n_g = chr.chr_topo_translate(_dev(f), K, acc)
+        assert n_g == n_o
+        assert np.float32(eb_g).view(np.uint32) == np.float32(eb_o).view(np.uint32)
+
+
 def test_compress_translate_mode_matches_oracle():
     f = synth.turbulence(36, seed=77)
     K = [-0.5, 0.5]
