@@ -82,6 +82,7 @@ __device__ __forceinline__ uint32_t tr_lanemask_lt()
 }
 
 constexpr int kTrHistBins = 4096;  // the first walk's key: the top 12 bits
+constexpr int kTrAppBuf = 4096;    // a block's appended elements staged in shared memory
 
 // MODE: kTrMin (the minimum), kTrHist (the 12-bit histogram), kTrCollect
 // (the elements whose top 12 bits are p.prefix, appended to p.sc.coll),
@@ -93,12 +94,20 @@ template <int NK, int MODE>
 __global__ void __launch_bounds__(kTrWarps * 32, kTrBlocksPerSm) k_translate(const __grid_constant__ TrParams p)
 {
     constexpr bool MIN = MODE == kTrMin;
+    constexpr bool APP = MODE == kTrCollect || MODE == kTrRange;
     __shared__ uint32_t s_x[3][kTrG][kTrWarps][32];  // exchanged words per vertex: ab, up, dn
     __shared__ unsigned int s_hist[MODE == kTrHist ? kTrHistBins : 1];
     __shared__ float s_kup[CHR_MAX_ISO + 1];  // sorted isovalues, +inf at nK
     __shared__ float s_kdn[CHR_MAX_ISO + 1];  // -inf, then the sorted isovalues
     __shared__ unsigned long long s_cnt, s_lo;
     __shared__ unsigned int s_min;
+    // appended elements: staged in s_app (s_napp reserved, the first s_valid
+    // of them written) and copied out when half full and at the end, so that
+    // the global counter takes one atomic per copy instead of one per group
+    // of lanes; a group that does not fit goes straight to global memory
+    __shared__ uint32_t s_app[APP ? kTrAppBuf : 1];
+    __shared__ unsigned int s_napp, s_valid;
+    __shared__ unsigned long long s_flush;
 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (MODE == kTrHist)
@@ -112,6 +121,8 @@ __global__ void __launch_bounds__(kTrWarps * 32, kTrBlocksPerSm) k_translate(con
         s_cnt = 0ull;
         s_lo = 0ull;
         s_min = 0xffffffffu;
+        s_napp = 0u;
+        s_valid = kTrAppBuf;
     }
     __syncthreads();
 
@@ -121,18 +132,43 @@ __global__ void __launch_bounds__(kTrWarps * 32, kTrBlocksPerSm) k_translate(con
     const int nK = p.nK;
     const int64_t plane = p.nx * p.ny;
 
-    // v appended to p.sc.coll where `want`, by one atomic per group of
-    // lanes that append together.  CONV: all 32 lanes call it together
+    // v appended where `want`, one shared atomic per group of lanes that
+    // append together.  CONV: all 32 lanes call it together
     auto append = [&](bool want, uint32_t v, auto conv) {
         const uint32_t m = decltype(conv)::value ? __ballot_sync(CHR_FULL_MASK, want) : __ballot_sync(__activemask(), want);
         if (want) {
             const int leader = __ffs(m) - 1;
-            unsigned long long base = 0;
-            if (lane == leader) base = atomicAdd(p.sc.ncoll, (unsigned long long)__popc(m));
-            base = __shfl_sync(m, base, leader);
-            const unsigned long long at = base + __popc(m & tr_lanemask_lt());
-            if (at < p.sc.cap) p.sc.coll[at] = v;
+            const uint32_t n = __popc(m), rank = __popc(m & tr_lanemask_lt());
+            uint32_t b = 0;
+            if (lane == leader) {
+                b = atomicAdd(&s_napp, n);
+                if (b < kTrAppBuf && b + n > kTrAppBuf) s_valid = b;  // (the one group that straddles the end)
+            }
+            b = __shfl_sync(m, b, leader);
+            if (b + n <= kTrAppBuf) {
+                s_app[b + rank] = v;
+            } else {
+                unsigned long long base = 0;
+                if (lane == leader) base = atomicAdd(p.sc.ncoll, (unsigned long long)n);
+                base = __shfl_sync(m, base, leader);
+                if (base + rank < p.sc.cap) p.sc.coll[base + rank] = v;
+            }
         }
+    };
+    // the staged elements out (every thread of the block, after a barrier)
+    auto flush = [&]() {
+        const uint32_t n = min(s_napp, s_valid);
+        if (threadIdx.x == 0) s_flush = n ? atomicAdd(p.sc.ncoll, (unsigned long long)n) : 0ull;
+        __syncthreads();
+        const unsigned long long base = s_flush;
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
+            if (base + i < p.sc.cap) p.sc.coll[base + i] = s_app[i];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_napp = 0u;
+            s_valid = kTrAppBuf;
+        }
+        __syncthreads();
     };
     // one element of D (where `valid`): into the histogram, or appended when
     // its top 12 bits match (collect) or when it lies in the range (range)
@@ -246,6 +282,7 @@ __global__ void __launch_bounds__(kTrWarps * 32, kTrBlocksPerSm) k_translate(con
                 }
             }
             __syncthreads();
+            if (APP && s_napp >= kTrAppBuf / 2) flush();  // (uniform: read after the barrier)
             ab[0] = ab[kTrG];
             e1[0] = e1[kTrG];
             e2[0] = e2[kTrG];
@@ -253,6 +290,11 @@ __global__ void __launch_bounds__(kTrWarps * 32, kTrBlocksPerSm) k_translate(con
         cnt += 2ull * c32;  // d0 and d1 per crossing; c32 <= 3 * 16 per plane, and an item spans <= 2^20 planes
         cnt_lo += lo32;
         lo32 = 0;
+    }
+
+    if (APP) {
+        __syncthreads();
+        if (s_napp) flush();
     }
 
     // block reduction, then one global update per block
