@@ -395,6 +395,11 @@ chr_status chr_serialize(const chr_handle *h, void *host_buf, size_t cap, size_t
  * chr_deserialize — validate a byte string from chr_serialize on the host
  * (CHR_ERR_CORRUPT on any inconsistency: sizes, widths > 32, prefix sums,
  * exception slots) and upload it into a new handle.  Synchronises `stream`.
+ * The copies to the device are issued before the records are checked, so
+ * that the checks run while the bytes move (from pinned memory the copies
+ * are asynchronous); nothing on the device reads them before the call
+ * returns, and a string that fails a check is freed after its copies end
+ * (CHR_ERR_CORRUPT is reported ahead of a failed allocation).
  */
 chr_status chr_deserialize(const void *host_buf, size_t n, const chr_allocator *alloc, void *stream,
                            chr_handle **out);

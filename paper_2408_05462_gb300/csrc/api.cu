@@ -1207,22 +1207,13 @@ chr_status chr_deserialize(const void *host_buf, size_t n, const chr_allocator *
     }
     set_constants(h);
     const Grid &g = h->g;
-    // validate every level on the host before anything is uploaded
+    // every level's place in the buffer (cheap size checks first)
     std::vector<size_t> level_off(nlevels);
     for (uint32_t l = 0; l < nlevels; l++) {
         level_off[l] = off;
-        const size_t nr = (size_t)g.nbricks * 16;
         if (h->nexc[l] > (uint64_t)g.N || h->nwords[l] > (uint64_t)g.nbricks * 512 || off + level_bytes(h, l) > n) {
             delete h;
             return fail(CHR_ERR_CORRUPT, "chr_deserialize: level sizes inconsistent with the buffer");
-        }
-        const uint32_t *rec = reinterpret_cast<const uint32_t *>(src + off);
-        const uint16_t *eidx = reinterpret_cast<const uint16_t *>(src + off + nr + h->nwords[l] * 4);
-        uint64_t wsum = 0, esum = 0;
-        ok = validate_level(rec, eidx, g, h->nexc[l], wsum, esum);
-        if (!ok || 16 * wsum != h->nwords[l] || esum != h->nexc[l]) {
-            delete h;
-            return fail(CHR_ERR_CORRUPT, "chr_deserialize: records inconsistent (widths, prefix sums or exception slots)");
         }
         off += level_bytes(h, l);
     }
@@ -1234,35 +1225,45 @@ chr_status chr_deserialize(const void *host_buf, size_t n, const chr_allocator *
         delete h;
         return fail(CHR_ERR_CORRUPT, "chr_deserialize: truncated value index");
     }
+    // The copies are issued first and the host checks every level while
+    // they are in flight: the device only holds the bytes, no kernel reads
+    // them before this call has returned the handle, and a failed check
+    // waits for the copies and frees the buffers.  A failed check is
+    // reported ahead of a failed allocation or copy.
     Alloc al(alloc, s);
-    chr_status st = CHR_OK;
-    if (!alloc_records(h, al, with_index) || !alloc_payload(h, al))
-        st = fail(CHR_ERR_OOM, "chr_deserialize: allocator returned NULL");
-    for (uint32_t l = 0; l < nlevels && st == CHR_OK && with_index; l++) {
-        cudaError_t e = cudaMemcpyAsync(h->d_index[l], src + index_off + index_bytes * l, index_bytes,
-                                        cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) st = cuda_fail(e, "chr_deserialize");
-    }
-    for (uint32_t l = 0; l < nlevels && st == CHR_OK; l++) {
+    bool oom = !alloc_records(h, al, with_index) || !alloc_payload(h, al);
+    cudaError_t ce = cudaSuccess;
+    for (uint32_t l = 0; l < nlevels && !oom && ce == cudaSuccess && with_index; l++)
+        ce = cudaMemcpyAsync(h->d_index[l], src + index_off + index_bytes * l, index_bytes, cudaMemcpyHostToDevice, s);
+    for (uint32_t l = 0; l < nlevels && !oom && ce == cudaSuccess; l++) {
         size_t o = level_off[l];
         const size_t nr = (size_t)g.nbricks * 16, nw = (size_t)h->nwords[l] * 4, ne = (size_t)h->nexc[l];
-        cudaError_t e = cudaMemcpyAsync(h->d_recs[l], src + o, nr, cudaMemcpyHostToDevice, s);
+        ce = cudaMemcpyAsync(h->d_recs[l], src + o, nr, cudaMemcpyHostToDevice, s);
         o += nr;
-        if (e == cudaSuccess && nw) e = cudaMemcpyAsync(h->d_words[l], src + o, nw, cudaMemcpyHostToDevice, s);
+        if (ce == cudaSuccess && nw) ce = cudaMemcpyAsync(h->d_words[l], src + o, nw, cudaMemcpyHostToDevice, s);
         o += nw;
-        if (e == cudaSuccess && ne) e = cudaMemcpyAsync(h->d_exc_idx[l], src + o, ne * 2, cudaMemcpyHostToDevice, s);
+        if (ce == cudaSuccess && ne) ce = cudaMemcpyAsync(h->d_exc_idx[l], src + o, ne * 2, cudaMemcpyHostToDevice, s);
         o += (ne * 2 + 3) & ~size_t(3);
-        if (e == cudaSuccess && ne) e = cudaMemcpyAsync(h->d_exc_val[l], src + o, ne * 4, cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) st = cuda_fail(e, "chr_deserialize");
+        if (ce == cudaSuccess && ne) ce = cudaMemcpyAsync(h->d_exc_val[l], src + o, ne * 4, cudaMemcpyHostToDevice, s);
     }
-    if (st == CHR_OK) {
-        cudaError_t e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) st = cuda_fail(e, "chr_deserialize");
+    bool corrupt = false;
+    for (uint32_t l = 0; l < nlevels && !corrupt; l++) {
+        const size_t nr = (size_t)g.nbricks * 16;
+        const uint32_t *rec = reinterpret_cast<const uint32_t *>(src + level_off[l]);
+        const uint16_t *eidx = reinterpret_cast<const uint16_t *>(src + level_off[l] + nr + h->nwords[l] * 4);
+        uint64_t wsum = 0, esum = 0;
+        corrupt = !validate_level(rec, eidx, g, h->nexc[l], wsum, esum) || 16 * wsum != h->nwords[l] ||
+                  esum != h->nexc[l];
     }
-    if (st != CHR_OK) {
+    // (always: the buffers are freed only after their copies are done)
+    const cudaError_t se = oom ? cudaSuccess : cudaStreamSynchronize(s);
+    if (corrupt || oom || ce != cudaSuccess || se != cudaSuccess) {
         free_handle_buffers(h);
         delete h;
-        return st;
+        if (corrupt)
+            return fail(CHR_ERR_CORRUPT, "chr_deserialize: records inconsistent (widths, prefix sums or exception slots)");
+        if (oom) return fail(CHR_ERR_OOM, "chr_deserialize: allocator returned NULL");
+        return cuda_fail(ce != cudaSuccess ? ce : se, "chr_deserialize");
     }
     *out = h;
     return CHR_OK;
