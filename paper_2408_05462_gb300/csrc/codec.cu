@@ -76,10 +76,12 @@ __device__ __forceinline__ void count_above_row(const float (&f)[8], const float
 // Both counts agree exactly when kdn <= R < kup, kup the smallest candidate
 // above f (+inf if none) and kdn the largest at or below it (-inf if none):
 // the same test without a second count.
-__device__ __forceinline__ bool encode_step(float f, float Rprev, bool first, float e, float two_e, float inv2e,
-                                            bool fix, float kdn, float kup, int32_t &q, float &R)
+__device__ __forceinline__ bool encode_step(float f, float Rprev, float e, float two_e, float inv2e, bool fix,
+                                            float kdn, float kup, int32_t &q, float &R)
 {
-    const float r = first ? f : __fsub_rn(f, Rprev);
+    // (level 0 starts from Rprev = +0: f - (+0) is f and (+0) + P is P
+    // exactly, P never being -0, so it takes the same operations)
+    const float r = __fsub_rn(f, Rprev);
     const float x = __fmul_rn(r, inv2e);
     q = 0;
     R = f;
@@ -87,7 +89,7 @@ __device__ __forceinline__ bool encode_step(float f, float Rprev, bool first, fl
     const int32_t qi = __float2int_rn(x);  // round half to even
     q = qi;  // kept by an exception too, so the neighbours' prediction stays smooth
     const float P = __fmul_rn(__int2float_rn(qi), two_e);
-    const float Rn = first ? P : __fadd_rn(Rprev, P);
+    const float Rn = __fadd_rn(Rprev, P);
     if (!(fabsf(__fsub_rn(f, Rn)) < e)) return true;
     if (fix && !(Rn >= kdn && Rn < kup)) return true;
     R = Rn;
@@ -233,7 +235,7 @@ __global__ void __launch_bounds__(256, 4) k_encode(const __grid_constant__ Codec
                 float Rn;
                 int32_t qq;
                 const int cf = (int)((cfp[x >> 2] >> (8 * (x & 3))) & 0xffu);
-                const bool ex = encode_step(f[x], R[x], l == 0, e, two_e, inv2e, fix, fix ? s_kdn[cf] : 0.0f,
+                const bool ex = encode_step(f[x], R[x], e, two_e, inv2e, fix, fix ? s_kdn[cf] : 0.0f,
                                             fix ? s_kup[cf] : 0.0f, qq, Rn);
                 q[x] = qq;
                 R[x] = Rn;
