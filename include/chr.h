@@ -350,6 +350,30 @@ chr_status isosurface_distance_loss(const float *d_orig_field, chr_dims dims, fl
                                     size_t workspace_bytes, void *stream);
 
 /*
+ * chr_brick_abs_sum — for every 8^3 brick (brick (bx, by, bz) at bx + nbx*(by
+ * + nby*bz)) the sum of |g| over its vertices, into d_out (caller-owned,
+ * nbricks floats).  Applied to isosurface_backward's gradient field it ranks
+ * the bricks whose refinement moves a loss on the mesh most (this library's
+ * reading of attributing isosurface error to blocks; the paper refines whole
+ * blocks, Sec. 2.1).  Each brick is summed in a fixed order (a lane's rows
+ * in x order, then a butterfly over the warp), so the result does not depend
+ * on scheduling.  Asynchronous.
+ */
+chr_status chr_brick_abs_sum(const float *d_g, chr_dims dims, float *d_out, void *stream);
+
+/*
+ * chr_case_agreement — the number of cells whose marching-cubes case byte
+ * at each of the n_iso (1..16, host array, no NaN) isovalues is the same in
+ * the fields d_a and d_b (same dims), summed over the isovalues, into
+ * *d_count (device, 8-byte aligned; set, not added to).  Divided by
+ * n_iso * (nx-1)(ny-1)(nz-1) it is the topology accuracy of Sec. 2.2, the
+ * share of cells whose isosurface topology survives compression.
+ * Asynchronous.
+ */
+chr_status chr_case_agreement(const float *d_a, const float *d_b, chr_dims dims, const float *isovalues,
+                              uint32_t n_iso, unsigned long long *d_count, void *stream);
+
+/*
  * isosurface_extract_noalloc — isosurface_extract for callers that may not
  * allocate device memory: code inside an application or framework that owns
  * all GPU memory through its own pool, plugins and callbacks that must not

@@ -50,12 +50,8 @@ class DistanceLoss(torch.autograd.Function):
         return (grad * grad_loss.to(grad.dtype)).view(-1, 3, 3), None, None
 
 
-def brick_attribution(grad_field: torch.Tensor, brick: int = 8) -> torch.Tensor:
+def brick_attribution(grad_field: torch.Tensor) -> torch.Tensor:
     """Sum of |dL/dfield| over every 8^3 brick (x-fastest brick order, the
-    CHR's brick order): the bricks with the largest values are the ones whose
-    refinement moves the loss most."""
-    nz, ny, nx = grad_field.shape
-    pz, py, px = (-nz) % brick, (-ny) % brick, (-nx) % brick
-    g = torch.nn.functional.pad(grad_field.abs(), (0, px, 0, py, 0, pz))
-    Z, Y, X = g.shape[0] // brick, g.shape[1] // brick, g.shape[2] // brick
-    return g.view(Z, brick, Y, brick, X, brick).sum(dim=(1, 3, 5)).flatten()
+    CHR's brick order), by the library (chr_brick_abs_sum): the bricks with
+    the largest values are the ones whose refinement moves the loss most."""
+    return chr.chr_brick_abs_sum(grad_field.contiguous())

@@ -10,7 +10,8 @@ Names follow the C ABI: chr_compress, chr_reconstruct, chr_reconstruct_box, chr_
 chr_serve_request, chr_serve_request_bytes, chr_box_tri_bound,
 chr_topo_translate, chr_isosurface, chr_brick_index,
 isosurface_extract, isosurface_workspace_size, isosurface_workspace_min_size, isosurface_extract_noalloc,
-isosurface_backward, isosurface_distance_loss, chr_serialize, chr_deserialize,
+isosurface_backward, isosurface_distance_loss, chr_brick_abs_sum, chr_case_agreement,
+chr_serialize, chr_deserialize,
 chr_stats, chr_free, chr_pool_trim, chr_checked_build, chr_debug_bounds_word, and the chr_batch_*
 calls (class Batch).
 """
@@ -136,6 +137,10 @@ def lib():
         L.isosurface_distance_loss.restype = st
         L.isosurface_distance_loss.argtypes = [c_void_p, ChrDims, c_float, c_void_p, c_uint64, c_void_p, c_void_p,
                                                c_void_p, c_size_t, c_void_p]
+        L.chr_brick_abs_sum.restype = st
+        L.chr_brick_abs_sum.argtypes = [c_void_p, ChrDims, c_void_p, c_void_p]
+        L.chr_case_agreement.restype = st
+        L.chr_case_agreement.argtypes = [c_void_p, c_void_p, ChrDims, POINTER(c_float), c_uint32, c_void_p, c_void_p]
         L.chr_serialize.restype = st
         L.chr_serialize.argtypes = [c_void_p, c_void_p, c_size_t, POINTER(c_size_t), c_void_p]
         L.chr_deserialize.restype = st
@@ -480,6 +485,36 @@ def chr_isosurface(h: Chr, level: int, isovalues, cap: int, field_out: torch.Ten
                                 tris.data_ptr() if cap > 0 else None, int(cap), counts.data_ptr(), err.data_ptr(),
                                 int(flags), ctypes.byref(TORCH_ALLOCATOR), _stream(stream)))
     return tris, counts, err
+
+
+def chr_brick_abs_sum(g: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Sum of |g| over every 8^3 brick, shape [nbz * nby * nbx] in x-fastest
+    brick order (chr.h: chr_brick_abs_sum)."""
+    _check_field(g)
+    nz, ny, nx = g.shape
+    nb = ((nz + 7) // 8) * ((ny + 7) // 8) * ((nx + 7) // 8)
+    if out is None:
+        out = torch.empty(nb, dtype=torch.float32, device=g.device)
+    if out.numel() != nb or out.dtype != torch.float32 or not out.is_contiguous() or not out.is_cuda:
+        raise ValueError("out must be a contiguous float32 CUDA tensor of %d elements" % nb)
+    _check(lib().chr_brick_abs_sum(g.data_ptr(), _dims(g), out.data_ptr(), _stream(stream)))
+    return out
+
+
+def chr_case_agreement(a: torch.Tensor, b: torch.Tensor, isovalues, count: torch.Tensor | None = None,
+                       stream=None) -> torch.Tensor:
+    """Number of cells whose case byte at each isovalue is the same in a and
+    b, summed over the isovalues, as a one-element int64 CUDA tensor
+    (chr.h: chr_case_agreement)."""
+    _check_field(a)
+    _check_field(b)
+    if a.shape != b.shape:
+        raise ValueError("a and b must have the same shape")
+    iso, ni = _floats(isovalues)
+    if count is None:
+        count = torch.empty(1, dtype=torch.int64, device=a.device)
+    _check(lib().chr_case_agreement(a.data_ptr(), b.data_ptr(), _dims(a), iso, ni, count.data_ptr(), _stream(stream)))
+    return count
 
 
 def chr_brick_index(h: Chr, level: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:

@@ -179,6 +179,14 @@ size_t dist_loss_workspace_bytes(uint64_t npts);
 cudaError_t launch_dist_loss(const float *orig, const Grid &g, float k, const float *pts, uint64_t npts, double *loss,
                              float *grad_pts, void *workspace, cudaStream_t s);
 
+// Reports (report.cu): the sum of |g| over every 8^3 brick into out
+// (nbricks floats, bricks x fastest); the number of cells whose case byte
+// at each of the nK host isovalues K is the same in fields a and b, summed
+// over the isovalues, into *count (device).
+cudaError_t launch_brick_abs_sum(const float *g, const Grid &G, float *out, cudaStream_t s);
+cudaError_t launch_case_agreement(const float *a, const float *b, const Grid &G, const float *K, int nK,
+                                  unsigned long long *count, cudaStream_t s);
+
 // Error-bound translation (selection over D).  mode 0: the minimum
 // (minbits) and |D| (count); mode 1: |D| and a 4096-bin histogram of the
 // elements' top 12 bits (hist); mode 2: every element whose top 12 bits equal

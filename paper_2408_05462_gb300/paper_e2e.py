@@ -42,15 +42,6 @@ def _time(fn, reps):
     return a.elapsed_time(b) / reps
 
 
-def _cases(F, k):
-    b = (F < k).to(torch.uint8)
-    c = torch.zeros((F.shape[0] - 1, F.shape[1] - 1, F.shape[2] - 1), dtype=torch.uint8, device=F.device)
-    for j in range(8):
-        ox, oy, oz = j & 1, (j >> 1) & 1, (j >> 2) & 1
-        c |= b[oz:oz + c.shape[0], oy:oy + c.shape[1], ox:ox + c.shape[2]] << j
-    return c
-
-
 def run(size: int = 512, reps: int = 5, seed: int = 512) -> dict:
     f = torch.from_numpy(synth.turbulence(size, seed=seed)).cuda()
     N = f.numel()
@@ -69,8 +60,7 @@ def run(size: int = 512, reps: int = 5, seed: int = 512) -> dict:
     t_mc_raw = _time(lambda: extract(f), reps)
     raw_s = 4.0 * N * 8 / WAN_BITS_PER_S
     base_ms = raw_s * 1e3 + t_mc_raw
-    orig_cases = [_cases(f, k) for k in ISOVALUES]
-    n_cells = sum(c.numel() for c in orig_cases)
+    n_cells = len(ISOVALUES) * (f.shape[0] - 1) * (f.shape[1] - 1) * (f.shape[2] - 1)
     out = {"size": size, "isovalues": ISOVALUES, "wan_gbps": WAN_BITS_PER_S / 1e9,
            "baseline": {"stream_ms": raw_s * 1e3, "extract_ms": t_mc_raw, "total_ms": base_ms, "bytes": 4 * N},
            "modes": {}}
@@ -87,7 +77,7 @@ def run(size: int = 512, reps: int = 5, seed: int = 512) -> dict:
         nbytes = sum(st["level_bytes"])
         t_dec = _time(lambda: h.reconstruct(0, R), reps)
         t_mc = _time(lambda: extract(R), reps)
-        same = sum(int((_cases(R, k) == c).sum().item()) for k, c in zip(ISOVALUES, orig_cases))
+        same = int(chr.chr_case_agreement(f, R, ISOVALUES).item())  # cells whose case survives, every isovalue
         stream_ms = nbytes * 8 / WAN_BITS_PER_S * 1e3
         total = t_comp + stream_ms + t_dec + t_mc
         out["modes"][name] = {
