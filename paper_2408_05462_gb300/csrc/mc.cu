@@ -485,11 +485,16 @@ __device__ __forceinline__ void mc_count_run(const Src &src, uint32_t *err)
         for (int i = 0; i < NISO; i++) {
             uint32_t lo = 0u, hi = 0u;
             if ((act >> (4 * j + i)) & 1u) cases8(s_row + i * kRows, r00, j, nvalid, lo, hi);
+            // (cells that are all inside or all outside have no triangles: a
+            // warp whose cells all are skips the table)
+            const uint32_t al = active_bytes(lo), ah = active_bytes(hi);
             uint32_t c = 0;
+            if (__any_sync(CHR_FULL_MASK, (al | ah) != 0u)) {
 #pragma unroll
-            for (int x = 0; x < 4; x++) c += s_cnt[(lo >> (8 * x)) & 0xffu] + s_cnt[(hi >> (8 * x)) & 0xffu];
+                for (int x = 0; x < 4; x++) c += s_cnt[(lo >> (8 * x)) & 0xffu] + s_cnt[(hi >> (8 * x)) & 0xffu];
+            }
             if (p.cases) {
-                const uint32_t na = __popc(active_bytes(lo)) + __popc(active_bytes(hi));
+                const uint32_t na = __popc(al) + __popc(ah);
                 const size_t at = ((size_t)tile * p.cstride + i) * 256 + tid;
                 p.cases[at] = make_uint2(lo, hi);
                 p.tcnt[at] = c | (na << 16);
