@@ -1236,14 +1236,17 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
                 const uint32_t tot = s_w[i][8], n = tot & 0xffffu, na = tot >> 16;
                 if (n) {
                     const uint32_t ex = s_w[i][warp] + excl[i];
-                    // without a stored classification the case bytes are made again rather than kept
-                    if (!STORED) {
-                        if (!((act >> (4 * j + i)) & 1u))
-                            lo[i] = hi[i] = 0u;
-                        else
-                            cases8(s_row + i * kRows, r00, j, nvalid, lo[i], hi[i]);
+                    // (a warp without active cells at slot i has nothing to compact)
+                    if (((warp < 7) ? s_w[i][warp + 1] : tot) != s_w[i][warp]) {
+                        // without a stored classification the case bytes are made again rather than kept
+                        if (!STORED) {
+                            if (!((act >> (4 * j + i)) & 1u))
+                                lo[i] = hi[i] = 0u;
+                            else
+                                cases8(s_row + i * kRows, r00, j, nvalid, lo[i], hi[i]);
+                        }
+                        compact(lo[i], hi[i], ab + (ex >> 16), ex & 0xffffu, cq);
                     }
-                    compact(lo[i], hi[i], ab + (ex >> 16), ex & 0xffffu, cq);
                     if (tid < 32 && CHR_IN_BOUNDS(ab + na + tid < (uint32_t)kPool))
                         s_apre[ab + na + tid] = 0xffffu;  // window tail past the last active cell
                     ab += na + 32u;
