@@ -1096,10 +1096,13 @@ __device__ __forceinline__ void mc_emit_run(const Src &src, uint32_t *err)
                 return 0u;
             }
             cases8(s_row + i * kRows, r00, j, nvalid, lo, hi);
+            const uint32_t al = active_bytes(lo), ah = active_bytes(hi);
             uint32_t cnt = 0;
+            if (__any_sync(CHR_FULL_MASK, (al | ah) != 0u)) {  // (a warp without active cells skips the table)
 #pragma unroll
-            for (int x = 0; x < 4; x++) cnt += s_cnt[(lo >> (8 * x)) & 0xffu] + s_cnt[(hi >> (8 * x)) & 0xffu];
-            return cnt | ((__popc(active_bytes(lo)) + __popc(active_bytes(hi))) << 16);
+                for (int x = 0; x < 4; x++) cnt += s_cnt[(lo >> (8 * x)) & 0xffu] + s_cnt[(hi >> (8 * x)) & 0xffu];
+            }
+            return cnt | ((__popc(al) + __popc(ah)) << 16);
         };
         // this thread's active cells of slot i into the pool from entry `a` on,
         // triangle prefix `pre`; chunk q of the slot is entry cq + q of the table
