@@ -643,6 +643,15 @@ def main():
             forms[name] = {"ms": ms, "field_GBps": 4.0 * N / (ms * 1e-3) / 1e9}
         torch.cuda.synchronize()
         assert int(err.item()) == 0
+        # what the value index lets the index forms skip: (cell brick,
+        # isovalue) pairs whose range does not straddle the isovalue, and
+        # whole tiles (4 bricks along x) with no straddling pair
+        idx = chr.chr_brick_index(h, LEVEL).cpu().numpy()
+        act = np.stack([(idx[..., 0] < k) & (k <= idx[..., 1]) for k in ISOVALUES])
+        pad = (-act.shape[-1]) % 4
+        tiles = np.pad(act, [(0, 0)] * 3 + [(0, pad)]).reshape(act.shape[:3] + (-1, 4)).any(axis=(0, 4))
+        forms["index"]["skipped_brick_isovalue_frac"] = float(1.0 - act.mean())
+        forms["index"]["skipped_tile_frac"] = float(1.0 - tiles.mean())
     for v in stages.values():
         v["GBps"] = v["algorithmic_bytes"] / (v["ms"] * 1e-3) / 1e9
         v["frac_of_measured_hbm"] = v["GBps"] / peak
