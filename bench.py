@@ -478,7 +478,7 @@ def serve_measurement(args):
 
 
 def fused_bytes(st, level, T):
-    """Algorithmic bytes of chr_isosurface at `level` (SURVEY's fused form):
+    """Algorithmic bytes of chr_isosurface at `level` (the bytes a fused decode and marching cubes moves):
     every brick's record (16 B), the packed words and the exceptions (6 B
     each) of levels 0..level, and 36 B per triangle written."""
     nb = st["nbricks"]
