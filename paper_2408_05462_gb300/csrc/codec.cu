@@ -474,7 +474,13 @@ __global__ void __launch_bounds__(256) k_compact(const __grid_constant__ CodecPa
 constexpr int kDecGroup = 3;       // levels whose loads are in flight together
 constexpr int kLevelWords = 516;   // shared words per level and warp: 512 payload + read-ahead slack
 constexpr int kExcPrefetch = 2;    // exception entries per lane and level loaded ahead (64 per brick)
-constexpr int kDecodeSmem = kWarpsPerBlock * kDecGroup * kLevelWords * 4;
+// k_decode stages only codes of width up to 8 (128 words a level, plus
+// read-ahead, a 16-byte multiple) and reads wider levels from global memory;
+// a separate 512-float buffer per warp takes the exception patch and the
+// rows on their way out.  The smaller footprint leaves more of the SM's
+// memory to the L1 cache.
+constexpr int kNarrowLevelWords = 132;
+constexpr int kDecodeSmem = kWarpsPerBlock * (kDecGroup * kNarrowLevelWords + 512) * 4;
 
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
 {
@@ -514,6 +520,9 @@ __device__ __forceinline__ void unpack_rows(const uint32_t *buf, int lane, uint3
 // the packed words (cp.async straight into shared memory) and the first 64
 // exception entries of each level (registers), so a brick costs about two
 // memory round trips instead of three per level.
+// LW: shared words a level for its packed codes; kLevelWords holds any
+// width, a smaller LW widths up to 8 (see kNarrowLevelWords).
+template <int LW>
 __device__ __forceinline__ void decode_brick(const CodecParams &p, const BrickCoord &c, uint32_t *s_dyn);
 
 __global__ void __launch_bounds__(256, 4) k_decode(const __grid_constant__ CodecParams p)
@@ -532,7 +541,7 @@ __global__ void __launch_bounds__(256, 4) k_decode(const __grid_constant__ Codec
     c.by = p.box_brick0[1] + (int32_t)(rest % p.box_bricks[1]);
     c.bz = p.box_brick0[2] + (int32_t)(rest / p.box_bricks[1]);
     c.b = c.bx + (int64_t)p.nbx * (c.by + (int64_t)p.nby * c.bz);
-    decode_brick(p, c, s_dyn);
+    decode_brick<kNarrowLevelWords>(p, c, s_dyn);
 }
 
 // Many CHRs in one launch: warp w of the grid decodes brick w of the
@@ -558,12 +567,16 @@ __global__ void __launch_bounds__(WPB * 32, 32 / WPB) k_decode_batched(const Cod
     c.by = (int32_t)((lb / p.nbx) % p.nby);
     c.bz = (int32_t)(lb / ((int64_t)p.nbx * p.nby));
     c.b = lb;
-    decode_brick(p, c, s_dyn);
+    decode_brick<kLevelWords>(p, c, s_dyn);
 }
 
 // Decode brick c of p into p.out (and its value range into p.range), by one warp.
+template <int LW>
 __device__ __forceinline__ void decode_brick(const CodecParams &p, const BrickCoord &c, uint32_t *s_dyn)
 {
+    constexpr bool WIDE = LW >= kLevelWords;  // every width staged; the level buffers double as the float buffer
+    constexpr int kWarpW = WIDE ? kDecGroup * LW : kDecGroup * LW + 512;
+    float *fbw = reinterpret_cast<float *>(s_dyn + (threadIdx.x >> 5) * kWarpW + (WIDE ? 0 : kDecGroup * LW));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ly = lane & 7;
 
@@ -596,8 +609,9 @@ __device__ __forceinline__ void decode_brick(const CodecParams &p, const BrickCo
             const int w = min((int)(rec[u].w & 0xffu), 32);
             const int nexc = (int)(rec[u].w >> 16);
             const uint4 *src = reinterpret_cast<const uint4 *>(p.words[l] + 16ull * rec[u].x);
-            uint32_t *dst = (s_dyn + warp * (kDecGroup * kLevelWords)) + u * kLevelWords;
-            for (int j = lane; j < 4 * w; j += 32) cp_async16(dst + 4 * j, src + j);
+            uint32_t *dst = (s_dyn + warp * kWarpW) + u * LW;
+            if (WIDE || w <= 8)
+                for (int j = lane; j < 4 * w; j += 32) cp_async16(dst + 4 * j, src + j);
 #pragma unroll
             for (int e = 0; e < kExcPrefetch; e++) {
                 const int jj = lane + 32 * e;
@@ -618,7 +632,7 @@ __device__ __forceinline__ void decode_brick(const CodecParams &p, const BrickCo
             const int l = g0 + u;
             const int w = min((int)(rec[u].w & 0xffu), 32), mode = (int)((rec[u].w >> 8) & 0xffu);
             const int nexc = (int)(rec[u].w >> 16);
-            const uint32_t *buf = (s_dyn + warp * (kDecGroup * kLevelWords)) + u * kLevelWords;
+            const uint32_t *buf = (WIDE || w <= 8) ? (s_dyn + warp * kWarpW) + u * LW : p.words[l] + 16ull * rec[u].x;
             uint32_t q[2][8];  // unsigned: prefix sums wrap like the encoder's int32
             switch (w) {  // (uniform across the warp) the common narrow widths with fixed offsets
                 case 1: unpack_rows<1>(buf, lane, q); break;
@@ -644,7 +658,10 @@ __device__ __forceinline__ void decode_brick(const CodecParams &p, const BrickCo
                             const int slot = 8 * (lane + 32 * s) + x;
                             const int pos = slot * w;
                             const int wd = pos >> 5;
-                            const uint32_t z = __funnelshift_r(buf[wd], buf[wd + 1], pos & 31) & mask;
+                            // (from global memory, the word after a code's first is read only when
+                            // the code reaches into it: the payload ends with its last code)
+                            const uint32_t hi1 = (WIDE || (pos & 31) + w > 32) ? buf[wd + 1] : 0u;
+                            const uint32_t z = __funnelshift_r(buf[wd], hi1, pos & 31) & mask;
                             q[s][x] = (uint32_t)unzigzag(z);
                         }
                 }
@@ -689,7 +706,7 @@ __device__ __forceinline__ void decode_brick(const CodecParams &p, const BrickCo
 
             if (nexc > 0) {  // vertices stored exactly at this level
                 __syncwarp();
-                float *fb = reinterpret_cast<float *>((s_dyn + warp * (kDecGroup * kLevelWords)) + u * kLevelWords);  // payload no longer needed
+                float *fb = WIDE ? reinterpret_cast<float *>((s_dyn + warp * kWarpW) + u * LW) : fbw;  // (payload no longer needed)
 #pragma unroll
                 for (int s = 0; s < 2; s++) {
                     const int slot = 8 * (lane + 32 * s);
@@ -751,9 +768,9 @@ __device__ __forceinline__ void decode_brick(const CodecParams &p, const BrickCo
     const bool vec = (xlo == 0) && (xhi == 8) && ((p.out_sx & 3) == 0) && ((p.out_sy & 3) == 0) &&
                      ((bx0 & 3) == 0) && ((reinterpret_cast<uintptr_t>(p.out) & 15u) == 0);
     if (vec) {  // (uniform across the warp)
-        // through the warp's first level buffer, so that two neighbouring
+        // through the warp's float buffer, so that two neighbouring
         // lanes write one row's 32 bytes (whole sectors) per store
-        float *fb = reinterpret_cast<float *>(s_dyn + warp * (kDecGroup * kLevelWords));
+        float *fb = WIDE ? reinterpret_cast<float *>(s_dyn + warp * kWarpW) : fbw;
 #pragma unroll
         for (int s = 0; s < 2; s++) {
             const int slot = 8 * (lane + 32 * s);
