@@ -567,7 +567,7 @@ __global__ void __launch_bounds__(WPB * 32, 32 / WPB) k_decode_batched(const Cod
     c.by = (int32_t)((lb / p.nbx) % p.nby);
     c.bz = (int32_t)(lb / ((int64_t)p.nbx * p.nby));
     c.b = lb;
-    decode_brick<kLevelWords>(p, c, s_dyn);
+    decode_brick<kNarrowLevelWords>(p, c, s_dyn);
 }
 
 // Decode brick c of p into p.out (and its value range into p.range), by one warp.
@@ -1012,20 +1012,20 @@ cudaError_t launch_decode_batched(const CodecParams *d_descs, const int64_t *d_b
     const int dev = current_device();
     if (!attr[dev]) {
         cudaError_t e = cudaFuncSetAttribute(k_decode_batched<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             8 * kDecGroup * kLevelWords * 4);
+                                             8 * (kDecGroup * kNarrowLevelWords + 512) * 4);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(k_decode_batched<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 4 * kDecGroup * kLevelWords * 4);
+                                 4 * (kDecGroup * kNarrowLevelWords + 512) * 4);
         if (e != cudaSuccess) return e;
         attr[dev] = true;
     }
     if (total_bricks == 0) return cudaSuccess;
     if (warps_per_block == 4) {
         const unsigned grid = (unsigned)((total_bricks + 3) / 4);
-        k_decode_batched<4><<<grid, 128, 4 * kDecGroup * kLevelWords * 4, s>>>(d_descs, d_brick_start, nboxes);
+        k_decode_batched<4><<<grid, 128, 4 * (kDecGroup * kNarrowLevelWords + 512) * 4, s>>>(d_descs, d_brick_start, nboxes);
     } else {
         const unsigned grid = (unsigned)((total_bricks + 7) / 8);
-        k_decode_batched<8><<<grid, 256, 8 * kDecGroup * kLevelWords * 4, s>>>(d_descs, d_brick_start, nboxes);
+        k_decode_batched<8><<<grid, 256, 8 * (kDecGroup * kNarrowLevelWords + 512) * 4, s>>>(d_descs, d_brick_start, nboxes);
     }
     return cudaGetLastError();
 }
