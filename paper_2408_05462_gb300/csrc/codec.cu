@@ -473,7 +473,7 @@ __global__ void __launch_bounds__(256) k_compact(const __grid_constant__ CodecPa
 
 constexpr int kDecGroup = 3;       // levels whose loads are in flight together
 constexpr int kLevelWords = 516;   // shared words per level and warp: 512 payload + read-ahead slack
-constexpr int kExcPrefetch = 2;    // exception entries per lane and level loaded ahead (64 per brick)
+constexpr int kExcPrefetch = 1;    // exception entries per lane and level loaded ahead (32 per brick)
 // k_decode stages only codes of width up to 8 (128 words a level, plus
 // read-ahead, a 16-byte multiple) and reads wider levels from global memory;
 // a separate 512-float buffer per warp takes the exception patch and the
@@ -517,7 +517,7 @@ __device__ __forceinline__ void unpack_rows(const uint32_t *buf, int lane, uint3
 
 // Decode one brick per warp.  For each group of up to three levels every
 // load is issued before any is consumed: the records (one lane per level),
-// the packed words (cp.async straight into shared memory) and the first 64
+// the packed words (cp.async straight into shared memory) and the first 32
 // exception entries of each level (registers), so a brick costs about two
 // memory round trips instead of three per level.
 // LW: shared words a level for its packed codes; kLevelWords holds any
