@@ -151,6 +151,22 @@ def test_deserialize_reports_a_failing_allocator(L):
     assert out.value is None and len(calls) == 1
 
 
+def test_deserialize_reports_corruption_ahead_of_a_failing_allocator(L):
+    # the copies are issued before the records are checked, so an allocation
+    # can fail first; a string that is also corrupt is still reported as
+    # corrupt, and no handle is left
+    rec = struct.pack("<IIiI", 5, 0, 0, 1)  # wsum of brick 0 must be 0
+    blob = _header(nwords=16) + rec + b"\0" * 64
+
+    def alloc(n, s, c):
+        return None
+
+    fail = chr.ChrAllocator(chr.ALLOC_FN(alloc), chr.FREE_FN(lambda p, n, s, c: None), None)
+    out = ctypes.c_void_p()
+    assert L.chr_deserialize(blob, len(blob), ctypes.byref(fail), None, ctypes.byref(out)) == 6
+    assert out.value is None
+
+
 def test_checked_build_is_a_separate_library():
     # build(checked=True) makes libchr_checked.so with the kernels' bounds
     # tests compiled in; the normal library reports none (no GPU needed)
